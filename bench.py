@@ -1,0 +1,301 @@
+"""Benchmark: pseudo-time iterations of the component-splitting LU-SGS scheme on one GB300.
+
+Workload (one "step" = one full pseudo-time iteration: residual, split LU-SGS operator,
+CS-1 correction and update): 2D Mach 15 flow over a cylinder, 384 x 256 cell O-grid,
+11-species two-temperature ionised air with 21 reactions, FP64.  Synthetic, seeded: the run
+starts from the uniform freestream.
+
+Metric: Mcell-iter/s (cells x iterations / second), higher is better.  ``value`` is the
+device time of the timed iterations (CUDA events on the library's stream, L2 flushed before
+every iteration); ``e2e`` is the same metric through the C ABI with host buffers (state
+uploaded, iterated, downloaded every step).  ``--impl reference`` times the FP64 oracle on
+the host cores instead.
+
+Multi-GPU (torchrun): every rank runs an independent replica (the LU-SGS sweep of one case
+does not shard exactly); value = total cells x iterations / max rank time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+NI, NJ = 384, 256
+MECH = inputs.MECH_AIR11
+MACH, T_INF, P_INF, T_WALL = 15.0, 300.0, 500.0, 500.0
+CFL, CFL_START, RAMP = 2.0, 0.5, 100
+WORKLOAD = "cylinder-384x256-air11-2T-mach15-CS1-fp64"
+# HBM bytes a phase must move per cell and iteration (FP64 words x 8), from the arrays each
+# kernel reads and writes once (section "Roofline"): used for the roofline of
+# memory-bound phases.
+ALGO_BYTES_PER_CELL = {
+    # primitive: Q (17) + warm-start T, Tv (2) in; aux record (23 + 6*11 = 89) out
+    "primitive": 8 * (17 + 2 + 89),
+    # gradient: 15 gradient variables of the cell in, 15*2 gradients out (neighbours cached)
+    "gradient": 8 * (15 + 30),
+    # flux: per face ~ 2 x (reconstruction 17 + gradient 30 + transport/enthalpy 26) in, 17 out;
+    # two faces per cell
+    "flux": 8 * 2 * (17 + 30 + 26 + 17),
+    "assemble": 8 * (2 * 2 * 17 + 12 + 17),
+    "spectral": 8 * (16 + 11 + 3 * 3 + 2 + 11),
+    "sweep_fwd": 8 * (17 + 16 + 10 + 3 + 16),
+    "sweep_bwd": 8 * (16 + 10 + 3 + 2 * 16),
+    "correct": 8 * (17 + 16 + 17),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_case(P):
+    nodes = inputs.cylinder_ogrid(NI, NJ, dr1=5e-5 / 8)
+    fs = inputs.freestream(MECH, T=T_INF, p=P_INF, mach=MACH)
+    return nodes, fs
+
+
+def step_kwargs(iters):
+    return dict(scheme=0, correction=1, clip=1, cfl=CFL, cfl_start=CFL_START, ramp_iters=RAMP,
+                iters=iters)
+
+
+def oracle_rate(iters, seconds_cap=30.0):
+    """Time the FP64 oracle (host, one core) on the same workload: iterations from the
+    freestream, bounded by iteration count and seconds."""
+    import oracle
+    oracle.build()
+    nodes, fs = make_case(None)
+    g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), MECH)
+    g.set_boundary(fs, Tw=T_WALL)
+    g.set_state(g.freestream_state())
+    done, t0 = 0, time.perf_counter()
+    while done < iters:
+        g.step(**step_kwargs(1))
+        done += 1
+        if time.perf_counter() - t0 > seconds_cap:
+            break
+    dt = time.perf_counter() - t0
+    return NI * NJ * done / dt / 1e6, done, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    # warm-up (untimed), then timed iterations; each iteration is a bounded sample of the
+    # same workload (one full pseudo-time iteration of the 384 x 256 grid)
+    import oracle
+    oracle.build()
+    nodes, fs = make_case(None)
+    g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), MECH)
+    g.set_boundary(fs, Tw=T_WALL)
+    g.set_state(g.freestream_state())
+    for _ in range(args.warmup):
+        g.step(**step_kwargs(1))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g.step(**step_kwargs(1))
+    dt = time.perf_counter() - t0
+    v = NI * NJ * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": "Mcell-iter/s", "value": v, "unit": "Mcell-iter/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": NI * NJ, "cfl": CFL},
+        "cpu_baseline": {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} iterations of the full grid from the freestream"},
+        "e2e": {"value": v, "unit": "Mcell-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if args.warmup < 3:
+        raise SystemExit("warmup must be >= 3")
+
+    import torch
+    import paper_2403_03440_gb300 as P
+    P.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    nodes, fs = make_case(P)
+    g = P.Grid(nodes, inputs.cylinder_bc(), MECH)
+    g.set_boundary(fs, Tw=T_WALL)
+    g.init_freestream()
+    N = g.ncell
+    for _ in range(args.warmup):
+        g.step(**step_kwargs(1))
+    # L2 flush buffer (larger than the 126 MiB L2)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    g.profile(True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev0[k].record(stream)
+            st = g.step(**step_kwargs(1))
+            ev1[k].record(stream)
+        torch.cuda.synchronize()
+    prof = g.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = world * N * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ----
+    Qh = torch.empty((g.nq, N), dtype=torch.float64, pin_memory=True).numpy()
+    g.get_state(Qh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g.set_state(Qh)
+        s = g.step(**step_kwargs(1))
+        g.get_state(Qh)
+    e2e_s = time.perf_counter() - t0
+    e2e = world * N * args.e2e_steps / e2e_s / 1e6
+    nbytes = Qh.nbytes
+
+    # ---- roofline of the dominant phase (live CUDA-event timing inside the timed region) ----
+    pk, pk_kind = peaks()
+    dom = max(prof, key=lambda p: prof[p][0])
+    dom_ms = prof[dom][0] / args.steps
+    launches = sum(v[1] for v in prof.values())
+    algo_bytes = ALGO_BYTES_PER_CELL[dom] * N
+    achieved = algo_bytes / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel_phase": dom,
+            "peak_kind": pk_kind,
+            "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof}}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, it, dt = oracle_rate(3, 30.0)
+        cpu = {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
+               "sample": f"{it} oracle iterations of the full 384x256 grid from the freestream ({dt:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": N, "species": 11, "temperatures": 2,
+                       "scheme": "CS-1 split LU-SGS", "cfl": CFL,
+                       "l2": "flushed before every timed iteration (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e, "unit": "Mcell-iter/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes + 24},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "last_stats": {k: (float(v) if isinstance(v, float) else v) for k, v in st.items()},
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * cs.h — C ABI of the GB300 (sm_103a) implementation of the component-splitting implicit
+ * LU-SGS scheme for multicomponent reacting flows (Zhang, Cai & Pan, arXiv:2403.03440).
+ *
+ * One pseudo-time iteration (Sec. 2.2-2.3 of the paper): explicit residual R(Q) (Eq.
+ * (iterate): MUSCL + Roe inviscid flux, central viscous and diffusive fluxes, finite-rate
+ * chemistry), then either the split (CS) operator — flow block with the flow spectral radius
+ * plus ns scalar species equations with their own radius and the chemical source diagonal
+ * (Sec. 2.3.1-2.3.2) — or the coupled (CI) (4+N)-block operator, both solved by LU-SGS
+ * forward/backward sweeps (Sec. 2.2), then the consistency corrections and the update
+ * (Sec. 2.3.3).
+ *
+ * Conventions
+ *  - Every function returns a cs_status; none aborts, exits or traps.  On error the grid keeps
+ *    a message (cs_last_error) and, for device-detected errors, the offending cell index.
+ *  - Units SI; 2D grids have unit depth.  FP64 throughout.
+ *  - Cells are numbered c = i + ni*(j + nj*k) (i fastest); arrays are struct-of-arrays
+ *    [var][cell].  Conserved state Q: var = rho_1..rho_ns, rho*u_1..rho*u_d, rho*E,
+ *    [rho*e_v] (two-temperature models), nq = ns + d + 1 (+1).
+ *  - Split increments dQ: (rho, rho*u_1..d, rho*E, [rho*e_v], rho_1..rho_ns), nsplit = nF + ns
+ *    with nF = d + 2 (+1).  Coupled increments: (rho, rho*u, rho*E, [rho*e_v],
+ *    rho_1..rho_{ns-1}), nci = nF + ns - 1 (rho_ns = rho - sum of the others).
+ *  - Pointers marked "host or device" may be either (the library copies with
+ *    cudaMemcpyDefault); they are borrowed for the duration of the call and owned by the
+ *    caller.  The grid owns all of its device work arrays.
+ *  - All device work is enqueued on the CUDA stream given at creation; functions that return
+ *    host values synchronise that stream.
+ */
+#ifndef CS_H
+#define CS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CS_OK = 0,
+  CS_ERR_ARG = 1,          /* invalid argument (size, pointer, option) */
+  CS_ERR_OOM = 2,          /* device allocation failed */
+  CS_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  CS_ERR_NONPHYSICAL = 4,  /* negative density / non-positive mixture sum / singular block */
+  CS_ERR_NEWTON = 5,       /* temperature solve did not converge */
+  CS_ERR_TIMEOUT = 6,      /* a bounded device wait gave up */
+  CS_ERR_STATE = 7         /* call order: e.g. operator before residual */
+} cs_status;
+
+enum { CS_BC_PERIODIC = 0, CS_BC_WALL = 1, CS_BC_FARFIELD = 2, CS_BC_OUTFLOW = 3, CS_BC_AXIS = 4 };
+/* Gas models: single-species perfect diatomic gas (tests), 5-species air with one
+ * temperature and 5 reactions, 11-species ionised air with two temperatures and 21
+ * reactions (Sec. 3.2 / 3.3 of the paper: Park's model). */
+enum { CS_MECH_PERFECT = 0, CS_MECH_AIR5 = 1, CS_MECH_AIR11 = 2 };
+enum { CS_SCHEME_SPLIT = 0, CS_SCHEME_COUPLED = 1 };
+enum { CS_FP64 = 0 };
+
+typedef struct cs_grid_s *cs_grid;
+
+typedef struct {
+  int ndim;          /* 2 or 3 */
+  int ni, nj, nk;    /* cells per direction (nk ignored for 2D) */
+  int bc[6];         /* imin, imax, jmin, jmax, kmin, kmax: CS_BC_*; a periodic pair must
+                        be periodic on both sides */
+  int mech;          /* CS_MECH_* */
+  int limiter;       /* 0 first order, 1 minmod (paper), 2 van Albada */
+  double entropy_fix;/* Harten coefficient eps (delta = eps (|u_n| + c)); 0.1 typical */
+  int reacting;      /* 1: chemical and vibrational sources on, 0: off */
+} cs_grid_desc;
+
+typedef struct {
+  double T, Tv, p, mach;   /* K, K, Pa, - ; Tv ignored by one-temperature models */
+  double Y[16];            /* mass fractions in the model's species order */
+  double dir[3];           /* flow direction (normalised by the library) */
+} cs_freestream;
+
+typedef struct {
+  double Tw;               /* isothermal wall temperature, K */
+  int catalytic;           /* must be 0 (non-catalytic) */
+} cs_wall;
+
+typedef struct {
+  int scheme;              /* CS_SCHEME_SPLIT | CS_SCHEME_COUPLED */
+  int correction;          /* 1 (CS-1) or 2 (CS-2); ignored by the coupled scheme */
+  int clip;                /* 1: negative densities set to 0 and counted */
+  double cfl;              /* target CFL */
+  double cfl_start;        /* first CFL of the geometric ramp */
+  int ramp_iters;          /* ramp length in iterations (0: no ramp) */
+  int precision;           /* CS_FP64 */
+  int iters;               /* iterations to run */
+} cs_step_opts;
+
+typedef struct {
+  int iters_done;
+  double r_species, r_energy;   /* L2 over cells of R/V, species and energy (last residual) */
+  double q_stag;                /* stagnation wall heat flux, W/m^2 */
+  int nclip;                    /* clipped values in the last correction */
+  int status_cell;              /* cell of the last device-detected error, or -1 */
+} cs_step_stats;
+
+/* Create a grid on the current CUDA device.  nodes_host: node coordinates, host memory,
+ * SoA [d][(nk+1)][(nj+1)][(ni+1)] (2D: [d][(nj+1)][(ni+1)]).  cuda_stream: cudaStream_t or
+ * NULL for the legacy default stream.  Geometry (a1: face area vectors S = xi_x/J, volumes
+ * V = 1/J, centroids; Sec. 2.2) is computed on the device.  Errors: CS_ERR_ARG (sizes, bc,
+ * mech), CS_ERR_OOM, CS_ERR_CUDA. */
+cs_status cs_grid_create(const cs_grid_desc *desc, const double *nodes_host, void *cuda_stream,
+                         cs_grid *out);
+cs_status cs_grid_destroy(cs_grid g);
+
+/* Sizes: out[0] = ncell, [1] = nq, [2] = nsplit, [3] = nci, [4] = ns, [5] = ntemp,
+ * [6] = nF, [7] = stagnation cell (-1 before cs_set_boundary). */
+cs_status cs_grid_dims(cs_grid g, int out[8]);
+
+/* Freestream and wall data (far-field ghost states, wall temperature, stagnation cell). */
+cs_status cs_set_boundary(cs_grid g, const cs_freestream *fs, const cs_wall *wall);
+
+/* Q (host or device, [nq][ncell]): set the conserved state.  Resets the iteration counter
+ * and the temperature warm starts. */
+cs_status cs_set_state(cs_grid g, const double *Q);
+/* Fill Q with the uniform freestream (after cs_set_boundary). */
+cs_status cs_init_freestream(cs_grid g);
+/* Q_out (host or device, [nq][ncell]). */
+cs_status cs_get_state(cs_grid g, double *Q_out);
+
+/* Residual R(Q) (Sec. 2.2 Eq. (iterate)): R = sum_faces (F_inv + F_vis).S_out - V S(Q).
+ * R_out (host or device, [nq][ncell], nullable).  norms_host[3] (nullable): r_species,
+ * r_energy, q_stag.  Errors: CS_ERR_NONPHYSICAL / CS_ERR_NEWTON from the primitive recovery. */
+cs_status cs_residual(cs_grid g, double *R_out, double norms_host[3]);
+
+/* Split operator (Sec. 2.3.1-2.3.2) solved by LU-SGS (Sec. 2.2) with the local time step of
+ * the given CFL; uses R of the last cs_residual.  dQ_out (host or device,
+ * [nsplit][ncell], nullable).  precision: CS_FP64.  Errors: CS_ERR_STATE (no residual). */
+cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double *dQ_out);
+
+/* Coupled (CI) operator: unified spectral radius, dense diagonal blocks with the source
+ * Jacobian, LU-SGS.  dQ_out (host or device, [nci][ncell], nullable). */
+cs_status cs_lusgs_coupled(cs_grid g, double cfl, double *dQ_out);
+
+/* Consistency correction and update (Sec. 2.3.3): mode 1 = CS-1 (increment normalisation),
+ * 2 = CS-2 (mass-fraction normalisation), 0 = coupled update.  dQ (host or device, nullable:
+ * NULL uses the increments of the last cs_lusgs_split / cs_lusgs_coupled); layout split for
+ * modes 1-2, coupled for mode 0.  nclip_out (nullable): clipped values. */
+cs_status cs_correct(cs_grid g, int mode, int clip, const double *dQ, int *nclip_out);
+
+/* opts->iters pseudo-time iterations: residual, operator, correction + update. */
+cs_status cs_step(cs_grid g, const cs_step_opts *opts, cs_step_stats *stats);
+
+/* Per-cell auxiliary fields for tests and monitors: name in {"T", "Tv", "p", "c", "rho",
+ * "mu", "lamF", "lamC", "lamCI", "DF", "DFev", "Ds", "omega", "dom", "V", "xc"}; out (host or
+ * device) must hold the returned count of doubles; *count_out = number written. */
+cs_status cs_get_field(cs_grid g, const char *name, double *out, int *count_out);
+
+/* Library's gas-model constants (host, no device work): M[ns] kg/kmol, hf[ns] J/kg,
+ * dims[3] = ns, nreactions, ntemp. */
+cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
+
+/* Per-phase device timing of cs_step with CUDA events on the grid's stream (not part of the
+ * method; a measurement aid).  Phases: 0 primitives + chemistry, 1 gradients, 2 face fluxes,
+ * 3 residual assembly + norms, 4 spectral radii / diagonals (+ coupled blocks), 5 forward
+ * sweep, 6 backward sweep, 7 correction + update.  ms_out[8] and launches_out[8] (host,
+ * nullable) receive the totals accumulated since the last call; the call then resets them
+ * and enables (enable = 1) or disables timing. */
+cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
+
+const char *cs_last_error(cs_grid g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CS_H */

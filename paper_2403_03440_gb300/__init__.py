@@ -1,0 +1,288 @@
+"""Python binding of the GB300 component-splitting LU-SGS library (``include/cs.h``).
+
+Argument marshalling only: every step of the iteration runs in the library's CUDA kernels.
+Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory); both are
+passed to the C ABI as plain pointers.  The library must have been built (``build()``); if it
+is missing, loading raises — there is no CPU fallback.
+"""
+import ctypes as C
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libcs_gb300.so")
+SOURCES = ["launch_air11_2d.cu", "launch_air11_3d.cu", "launch_air5_2d.cu", "launch_air5_3d.cu",
+           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC"]
+
+CS_OK, CS_ERR_ARG, CS_ERR_OOM, CS_ERR_CUDA, CS_ERR_NONPHYSICAL, CS_ERR_NEWTON, \
+    CS_ERR_TIMEOUT, CS_ERR_STATE = range(8)
+SCHEME_SPLIT, SCHEME_COUPLED = 0, 1
+STATUS_NAMES = {0: "CS_OK", 1: "CS_ERR_ARG", 2: "CS_ERR_OOM", 3: "CS_ERR_CUDA",
+                4: "CS_ERR_NONPHYSICAL", 5: "CS_ERR_NEWTON", 6: "CS_ERR_TIMEOUT",
+                7: "CS_ERR_STATE"}
+
+
+def _nvcc():
+    for cand in ("nvcc", "/usr/local/cuda/bin/nvcc"):
+        try:
+            subprocess.run([cand, "--version"], check=True, capture_output=True)
+            return cand
+        except (OSError, subprocess.CalledProcessError):
+            continue
+    raise RuntimeError("nvcc not found")
+
+
+def build(force=False, jobs=8):
+    """Compile the CUDA sources for sm_103a (in parallel) and link the shared library."""
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)]
+    deps.append(os.path.join(_HERE, "..", "include", "cs.h"))
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        cmd = [nvcc, *NVCC_FLAGS, "-c", os.path.join(_CSRC, src), "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
+        return obj
+
+    with ThreadPoolExecutor(max_workers=jobs) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    r = subprocess.run([nvcc, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp,
+                        *objs, "-lcudart"], capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class cs_grid_desc(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("ni", C.c_int), ("nj", C.c_int), ("nk", C.c_int),
+                ("bc", C.c_int * 6), ("mech", C.c_int), ("limiter", C.c_int),
+                ("entropy_fix", C.c_double), ("reacting", C.c_int)]
+
+
+class cs_freestream(C.Structure):
+    _fields_ = [("T", C.c_double), ("Tv", C.c_double), ("p", C.c_double), ("mach", C.c_double),
+                ("Y", C.c_double * 16), ("dir", C.c_double * 3)]
+
+
+class cs_wall(C.Structure):
+    _fields_ = [("Tw", C.c_double), ("catalytic", C.c_int)]
+
+
+class cs_step_opts(C.Structure):
+    _fields_ = [("scheme", C.c_int), ("correction", C.c_int), ("clip", C.c_int),
+                ("cfl", C.c_double), ("cfl_start", C.c_double), ("ramp_iters", C.c_int),
+                ("precision", C.c_int), ("iters", C.c_int)]
+
+
+class cs_step_stats(C.Structure):
+    _fields_ = [("iters_done", C.c_int), ("r_species", C.c_double), ("r_energy", C.c_double),
+                ("q_stag", C.c_double), ("nclip", C.c_int), ("status_cell", C.c_int)]
+
+
+EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary",
+           "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
+           "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
+           "cs_gas_info", "cs_profile", "cs_last_error"]
+
+_lib = None
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} (call build())")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+    L.cs_grid_create.argtypes = [C.POINTER(cs_grid_desc), vp, vp, C.POINTER(vp)]
+    L.cs_grid_destroy.argtypes = [vp]
+    L.cs_grid_dims.argtypes = [vp, ip]
+    L.cs_set_boundary.argtypes = [vp, C.POINTER(cs_freestream), C.POINTER(cs_wall)]
+    L.cs_set_state.argtypes = [vp, vp]
+    L.cs_init_freestream.argtypes = [vp]
+    L.cs_get_state.argtypes = [vp, vp]
+    L.cs_residual.argtypes = [vp, vp, dp]
+    L.cs_lusgs_split.argtypes = [vp, C.c_double, C.c_int, vp]
+    L.cs_lusgs_coupled.argtypes = [vp, C.c_double, vp]
+    L.cs_correct.argtypes = [vp, C.c_int, C.c_int, vp, ip]
+    L.cs_step.argtypes = [vp, C.POINTER(cs_step_opts), C.POINTER(cs_step_stats)]
+    L.cs_get_field.argtypes = [vp, C.c_char_p, vp, ip]
+    L.cs_gas_info.argtypes = [C.c_int, dp, dp, ip]
+    L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
+    L.cs_last_error.argtypes = [vp]
+    L.cs_last_error.restype = C.c_char_p
+    for name in EXPORTS:
+        getattr(L, name).restype = C.c_int if name != "cs_last_error" else C.c_char_p
+    _lib = L
+    return L
+
+
+class CSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(a):
+    """Pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or a.dtype.itemsize != 8:
+            raise ValueError("tensor must be contiguous float64")
+        return C.c_void_p(a.data_ptr())
+    if not (a.flags["C_CONTIGUOUS"] and a.dtype == np.float64):
+        raise ValueError("array must be C-contiguous float64")
+    return C.c_void_p(a.ctypes.data)
+
+
+def gas_info(mech):
+    M = np.zeros(16)
+    hf = np.zeros(16)
+    dims = np.zeros(3, dtype=np.int32)
+    st = lib().cs_gas_info(mech, M.ctypes.data_as(C.POINTER(C.c_double)),
+                           hf.ctypes.data_as(C.POINTER(C.c_double)),
+                           dims.ctypes.data_as(C.POINTER(C.c_int)))
+    if st:
+        raise CSError(st, "cs_gas_info")
+    ns = int(dims[0])
+    return dict(ns=ns, nr=int(dims[1]), ntemp=int(dims[2]), M=M[:ns].copy(), hf=hf[:ns].copy())
+
+
+class Grid:
+    """A structured grid with its state on the current CUDA device (one C-ABI grid object)."""
+
+    def __init__(self, nodes, bc, mech, limiter=1, efix=0.1, reacting=True, stream=None):
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        nd = nodes.shape[0]
+        d = cs_grid_desc()
+        d.ndim = nd
+        if nd == 2:
+            d.nj, d.ni, d.nk = nodes.shape[1] - 1, nodes.shape[2] - 1, 1
+        else:
+            d.nk, d.nj, d.ni = nodes.shape[1] - 1, nodes.shape[2] - 1, nodes.shape[3] - 1
+        for k in range(6):
+            d.bc[k] = int(bc[k])
+        d.mech, d.limiter, d.entropy_fix, d.reacting = mech, limiter, efix, int(bool(reacting))
+        h = C.c_void_p()
+        st = lib().cs_grid_create(C.byref(d), C.c_void_p(nodes.ctypes.data),
+                                  C.c_void_p(stream) if stream else None, C.byref(h))
+        if st:
+            raise CSError(st, "cs_grid_create")
+        self._h = h
+        self.nd, self.ni, self.nj, self.nk, self.mech = nd, d.ni, d.nj, d.nk, mech
+        self._dims()
+
+    def _dims(self):
+        dims = (C.c_int * 8)()
+        lib().cs_grid_dims(self._h, dims)
+        (self.ncell, self.nq, self.nsplit, self.nci, self.ns, self.ntemp, self.nF,
+         self.stag_cell) = list(dims)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().cs_grid_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st:
+            raise CSError(st, f"{what}: {lib().cs_last_error(self._h).decode()}")
+
+    def set_boundary(self, fs, Tw=500.0):
+        f = cs_freestream()
+        f.T, f.Tv, f.p, f.mach = fs["T"], fs["Tv"], fs["p"], fs["mach"]
+        for s, y in enumerate(fs["Y"]):
+            f.Y[s] = float(y)
+        for q in range(3):
+            f.dir[q] = float(fs["dir"][q]) if q < len(fs["dir"]) else 0.0
+        w = cs_wall()
+        w.Tw, w.catalytic = Tw, 0
+        self._check(lib().cs_set_boundary(self._h, C.byref(f), C.byref(w)), "cs_set_boundary")
+        self._dims()
+
+    def set_state(self, Q):
+        self._check(lib().cs_set_state(self._h, _ptr(Q)), "cs_set_state")
+
+    def init_freestream(self):
+        self._check(lib().cs_init_freestream(self._h), "cs_init_freestream")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((self.nq, self.ncell))
+        self._check(lib().cs_get_state(self._h, _ptr(out)), "cs_get_state")
+        return out
+
+    def residual(self, R_out=None, want_R=True):
+        if R_out is None and want_R:
+            R_out = np.zeros((self.nq, self.ncell))
+        norms = (C.c_double * 3)()
+        self._check(lib().cs_residual(self._h, _ptr(R_out), norms), "cs_residual")
+        return R_out, np.array(list(norms))
+
+    def lusgs_split(self, cfl, out=None, want=True, precision=0):
+        if out is None and want:
+            out = np.zeros((self.nsplit, self.ncell))
+        self._check(lib().cs_lusgs_split(self._h, cfl, precision, _ptr(out)), "cs_lusgs_split")
+        return out
+
+    def lusgs_coupled(self, cfl, out=None, want=True):
+        if out is None and want:
+            out = np.zeros((self.nci, self.ncell))
+        self._check(lib().cs_lusgs_coupled(self._h, cfl, _ptr(out)), "cs_lusgs_coupled")
+        return out
+
+    def correct(self, mode, clip, dQ=None):
+        n = C.c_int(0)
+        self._check(lib().cs_correct(self._h, mode, clip, _ptr(dQ), C.byref(n)), "cs_correct")
+        return n.value
+
+    def step(self, scheme=0, correction=1, clip=1, cfl=10.0, cfl_start=1.0, ramp_iters=0,
+             iters=1, precision=0):
+        o = cs_step_opts()
+        o.scheme, o.correction, o.clip, o.cfl, o.cfl_start = scheme, correction, clip, cfl, cfl_start
+        o.ramp_iters, o.precision, o.iters = ramp_iters, precision, iters
+        s = cs_step_stats()
+        self._check(lib().cs_step(self._h, C.byref(o), C.byref(s)), "cs_step")
+        return dict(iters_done=s.iters_done, r_species=s.r_species, r_energy=s.r_energy,
+                    q_stag=s.q_stag, nclip=s.nclip)
+
+    PHASES = ["primitive", "gradient", "flux", "assemble", "spectral", "sweep_fwd",
+              "sweep_bwd", "correct"]
+
+    def profile(self, enable):
+        """Return {phase: (ms, launches)} accumulated since the last call; (re)arm timing."""
+        ms = (C.c_double * 8)()
+        nl = (C.c_long * 8)()
+        self._check(lib().cs_profile(self._h, int(enable), ms, nl), "cs_profile")
+        return {p: (ms[k], nl[k]) for k, p in enumerate(self.PHASES)}
+
+    def field(self, name, size=None):
+        if size is None:
+            size = max(64 * 3 * self.ncell, 3 * (self.ni + 1) * (self.nj + 1) * (self.nk + 1) * self.nq)
+        out = np.zeros(size)
+        n = C.c_int(0)
+        self._check(lib().cs_get_field(self._h, name.encode(), _ptr(out), C.byref(n)), "cs_get_field")
+        return out[:n.value].copy()

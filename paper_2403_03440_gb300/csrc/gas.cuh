@@ -1,0 +1,149 @@
+// Device-side gas model for the GB300 path: species thermodynamics (rigid rotor / harmonic
+// oscillator, two-temperature pools), Park air kinetics and transport.
+//
+// Paper: arXiv:2403.03440 Sec. 2.1 (e_t, e_v, ideal-gas law; thermodynamic, transport and
+// kinetic data deferred to the paper's references) and Sec. 3.2 (Park's 11-species /
+// 21-reaction air, rates as tabulated by Gnoffo et al.).
+//
+// Everything is templated on the gas model so that per-species arrays have compile-time
+// size and live in registers.  All arithmetic is FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace cs {
+
+constexpr double kRu = 8314.462618;        // J/(kmol K)
+constexpr double kKb = 1.380649e-23;       // J/K
+constexpr double kH = 6.62607015e-34;      // J s
+constexpr double kNa = 6.02214076e26;      // 1/kmol
+constexpr double kPref = 101325.0;         // Pa, standard state
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTmin = 20.0, kTmax = 1.0e5;
+constexpr double kSuthMu = 1.458e-6, kSuthT = 110.4, kPr = 0.72, kSc = 0.5;
+
+enum Kind { ATOM = 0, DIATOMIC = 1, ELECTRON = 2 };
+enum TempKind { TK_T = 0, TK_A = 1, TK_V = 2 };
+
+struct SpeciesData {
+  int kind;
+  double M;       // kg/kmol
+  double thv;     // vibrational temperature, K (0: none)
+  double thr;     // rotational temperature, K
+  double sigma;   // symmetry number
+  double g0;      // ground-state degeneracy
+  double h0;      // formation energy at 0 K, J/kmol
+};
+
+struct ReactionData {
+  int nr, r[3], np, p[3];
+  int third;
+  double lnA;     // ln of A in m^3/(kmol s)
+  double n, theta;
+  int tf, tb;
+  double eff[11];
+};
+
+// Molar masses from the element masses so that every reaction conserves mass exactly.
+#define CS_MN 14.0067
+#define CS_MO 15.9994
+#define CS_ME 5.48579909e-4
+
+__constant__ SpeciesData c_species_air[11] = {
+    {DIATOMIC, 2 * CS_MN, 3395.0, 2.88, 2, 1, 0.0},
+    {DIATOMIC, 2 * CS_MO, 2239.0, 2.08, 2, 3, 0.0},
+    {DIATOMIC, CS_MN + CS_MO, 2817.0, 2.45, 1, 4, 89.77e6},
+    {ATOM, CS_MN, 0.0, 0.0, 1, 4, 470.82e6},
+    {ATOM, CS_MO, 0.0, 0.0, 1, 9, 246.79e6},
+    {DIATOMIC, CS_MN + CS_MO - CS_ME, 3419.0, 2.87, 1, 1, 983.6e6},
+    {DIATOMIC, 2 * CS_MN - CS_ME, 3175.0, 2.78, 2, 2, 1503.3e6},
+    {DIATOMIC, 2 * CS_MO - CS_ME, 2741.0, 2.43, 2, 4, 1164.5e6},
+    {ATOM, CS_MN - CS_ME, 0.0, 0.0, 1, 9, 1873.1e6},
+    {ATOM, CS_MO - CS_ME, 0.0, 0.0, 1, 4, 1560.7e6},
+    {ELECTRON, CS_ME, 0.0, 0.0, 1, 2, 0.0},
+};
+__constant__ SpeciesData c_species_perfect[1] = {
+    {DIATOMIC, 28.9647, 0.0, 2.88, 2, 1, 0.0},
+};
+
+// Park's air reactions, forward rate A T^n exp(-theta/T).  Species order:
+// N2 O2 NO N O NO+ N2+ O2+ N+ O+ e-.  ln A is filled on the host from A in cm^3/(mol s).
+#define CS_EFF_N2 {1, 1, 1, 30.0 / 7.0, 30.0 / 7.0, 1, 1, 1, 30.0 / 7.0, 30.0 / 7.0, 3.0e24 / 7.0e21}
+#define CS_EFF_O2 {1, 1, 1, 5, 5, 1, 1, 1, 5, 5, 0}
+#define CS_EFF_NO {1, 1, 22, 22, 22, 1, 1, 1, 22, 22, 0}
+__constant__ ReactionData c_reactions[21];
+
+struct ReactionInit {
+  int nr, r0, r1, np, p0, p1, p2, third;
+  double A_cgs, n, theta;
+  int tf, tb, effset;
+};
+// host-side initialiser table (copied to c_reactions by the library at load time)
+static const ReactionInit kReactionInit[21] = {
+    {1, 0, -1, 2, 3, 3, -1, 1, 7.0e21, -1.6, 113200.0, TK_A, TK_T, 1},
+    {1, 1, -1, 2, 4, 4, -1, 1, 2.0e21, -1.5, 59500.0, TK_A, TK_T, 2},
+    {1, 2, -1, 2, 3, 4, -1, 1, 5.0e15, 0.0, 75500.0, TK_A, TK_T, 3},
+    {2, 0, 4, 2, 2, 3, -1, 0, 6.4e17, -1.0, 38400.0, TK_T, TK_T, 0},
+    {2, 2, 4, 2, 1, 3, -1, 0, 8.4e12, 0.0, 19450.0, TK_T, TK_T, 0},
+    {2, 3, 4, 2, 5, 10, -1, 0, 8.8e8, 1.0, 31900.0, TK_T, TK_T, 0},
+    {2, 4, 4, 2, 7, 10, -1, 0, 7.1e2, 2.7, 80600.0, TK_T, TK_T, 0},
+    {2, 3, 3, 2, 6, 10, -1, 0, 4.4e7, 1.5, 67500.0, TK_T, TK_T, 0},
+    {2, 5, 4, 2, 8, 1, -1, 0, 1.0e12, 0.5, 77200.0, TK_T, TK_T, 0},
+    {2, 8, 0, 2, 6, 3, -1, 0, 1.0e12, 0.5, 12200.0, TK_T, TK_T, 0},
+    {2, 7, 3, 2, 8, 1, -1, 0, 8.7e13, 0.14, 28600.0, TK_T, TK_T, 0},
+    {2, 9, 2, 2, 8, 1, -1, 0, 1.4e5, 1.9, 26600.0, TK_T, TK_T, 0},
+    {2, 7, 0, 2, 6, 1, -1, 0, 9.9e12, 0.0, 40700.0, TK_T, TK_T, 0},
+    {2, 7, 4, 2, 9, 1, -1, 0, 4.0e12, -0.09, 18000.0, TK_T, TK_T, 0},
+    {2, 5, 3, 2, 9, 0, -1, 0, 3.4e13, -1.08, 12800.0, TK_T, TK_T, 0},
+    {2, 5, 1, 2, 7, 2, -1, 0, 2.4e13, 0.41, 32600.0, TK_T, TK_T, 0},
+    {2, 5, 4, 2, 7, 3, -1, 0, 7.2e12, 0.29, 48600.0, TK_T, TK_T, 0},
+    {2, 9, 0, 2, 6, 4, -1, 0, 9.1e11, 0.36, 22800.0, TK_T, TK_T, 0},
+    {2, 5, 3, 2, 6, 4, -1, 0, 7.2e13, 0.0, 35500.0, TK_T, TK_T, 0},
+    {2, 4, 10, 3, 9, 10, 10, 0, 3.9e33, -3.78, 158500.0, TK_V, TK_V, 0},
+    {2, 3, 10, 3, 8, 10, 10, 0, 2.5e34, -3.82, 168600.0, TK_V, TK_V, 0},
+};
+
+// Compile-time description of one gas model.
+template <int NS_, int NTEMP_, int NR_, bool PERFECT_ = false>
+struct Gas {
+  static constexpr int NS = NS_, NTEMP = NTEMP_, NR = NR_;
+  static constexpr bool PERFECT = PERFECT_;
+  __device__ static const SpeciesData& sp(int s) {
+    return PERFECT ? c_species_perfect[0] : c_species_air[s];
+  }
+};
+using GasPerfect = Gas<1, 1, 0, true>;
+using GasAir5 = Gas<5, 1, 5>;
+using GasAir11 = Gas<11, 2, 21>;
+
+// ---- species thermodynamics -------------------------------------------------------------
+
+template <class G>
+__device__ __forceinline__ double Rs(int s) { return kRu / G::sp(s).M; }
+
+// trans(-rot) heat capacity per unit mass
+template <class G>
+__device__ __forceinline__ double cvtr(int s) {
+  const int k = G::sp(s).kind;
+  if (k == DIATOMIC) return 2.5 * Rs<G>(s);
+  if (k == ATOM) return 1.5 * Rs<G>(s);
+  return G::NTEMP == 1 ? 1.5 * Rs<G>(s) : 0.0;
+}
+
+// Harmonic-oscillator energy and heat capacity per unit mass at temperature T; one exp.
+template <class G>
+__device__ __forceinline__ void vib(int s, double T, double& e, double& cv) {
+  const SpeciesData& d = G::sp(s);
+  if (d.kind != DIATOMIC || d.thv <= 0.0) { e = 0.0; cv = 0.0; return; }
+  const double x = d.thv / T;
+  const double em = exp(-x);
+  const double den = 1.0 - em;
+  const double R = kRu / d.M;
+  e = R * d.thv * em / den;
+  cv = R * x * x * em / (den * den);
+}
+
+template <class G>
+__device__ __forceinline__ double hf(int s) { return G::sp(s).h0 / G::sp(s).M; }
+
+}  // namespace cs

@@ -1,0 +1,1608 @@
+// CUDA kernels of one pseudo-time iteration of the component-splitting (CS) and coupled (CI)
+// implicit LU-SGS scheme (arXiv:2403.03440, Sec. 2.2-2.3), FP64, for sm_103a.
+//
+// Data layout (HBM): cell c = i + ni*(j + nj*k); every per-cell array is struct-of-arrays
+// [var][cell] so that a warp reads consecutive cells of one variable (coalesced).  Face arrays
+// are [var][face] per direction.  The per-cell auxiliary array W holds everything the
+// transcendental work produces (temperatures, transport, chemistry) so that the face kernels
+// and the sweeps are purely algebraic: on GB300 the FP64 pipe, not HBM, bounds this path.
+#pragma once
+#include <cstdint>
+
+#include "gas.cuh"
+
+namespace cs {
+
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_FARFIELD = 2, BC_OUTFLOW = 3, BC_AXIS = 4 };
+enum { ST_OK = 0, ST_NONPHYSICAL = 4, ST_NEWTON = 5, ST_TIMEOUT = 6 };
+
+// Per-cell auxiliary layout (offsets in units of N).
+template <class G, int ND>
+struct Aux {
+  static constexpr int NS = G::NS;
+  static constexpr int RHO = 0, U = 1, T = U + ND, TV = T + 1, P = TV + 1, C = P + 1,
+                       BETA = C + 1, GAM = BETA + 1, EV = GAM + 1, H = EV + 1, CVTR = H + 1,
+                       CVVE = CVTR + 1, CV = CVVE + 1, MU = CV + 1, KT = MU + 1, KV = KT + 1,
+                       RHOD = KV + 1, PREV = RHOD + 1, RELAX = PREV + 1, OMV = RELAX + 1,
+                       Y = OMV + 1, PRS = Y + NS, HS = PRS + NS, EVE = HS + NS, OM = EVE + NS,
+                       DOM = OM + NS, COUNT = DOM + NS;
+  static constexpr int NQ = NS + ND + 1 + (G::NTEMP == 2);
+  static constexpr int NF = 1 + ND + 1 + (G::NTEMP == 2);
+  static constexpr int NCI = NF + NS - 1;
+  static constexpr int NG = ND + 1 + (G::NTEMP == 2) + NS;      // gradient variables
+  static constexpr int NRC = NS + ND + 3 + (G::NTEMP == 2);      // reconstructed variables
+};
+
+struct DevGrid {
+  int nd, ni, nj, nk, N;
+  int bc[6];
+  int limiter, react;
+  double efix, Tw;
+  int nf[3];
+  const double* S[3];
+  const double* fc[3];
+  const double* V;
+  const double* xc;       // [3][N]
+  double* Q;              // [nq][N]
+  double* W;              // [aux][N]
+  double* fsW;            // freestream aux record [aux]
+  double* grad;           // [ng*3][N]
+  double* F[3];           // [nq][nf]
+  double* R;              // [nq][N]
+  double* lamF;           // [3][N]
+  double* lamC;
+  double* lamCI;
+  double* DF;
+  double* DFev;
+  double* Ds;             // [ns][N]
+  double* DLU;            // [N][nci*nci]
+  int* piv;               // [N][nci]
+  double* dQs;            // [nsplit][N]
+  double* dQ;
+  double* dQcs;           // [nci][N]
+  double* dQc;
+  double* red;            // reduction scratch
+  double* Vdt;            // [N] V / dtau
+  int* status;            // [0] code, [1] cell, [2] clip count
+  const double* params;   // [0] cfl
+};
+
+__device__ __forceinline__ void set_status(const DevGrid& g, int code, int cell) {
+  if (atomicCAS(&g.status[0], 0, code) == 0) g.status[1] = cell;
+}
+
+__device__ __forceinline__ void cell_ijk(const DevGrid& g, int c, int& i, int& j, int& k) {
+  i = c % g.ni;
+  j = (c / g.ni) % g.nj;
+  k = c / (g.ni * g.nj);
+}
+__device__ __forceinline__ int cell_of(const DevGrid& g, int i, int j, int k) {
+  return i + g.ni * (j + g.nj * k);
+}
+// face index along direction d of the face at the low side of (i,j,k) (+1 on d for high side)
+__device__ __forceinline__ int face_of(const DevGrid& g, int d, int i, int j, int k) {
+  const int fi = g.ni + (d == 0), fj = g.nj + (d == 1);
+  return i + fi * (j + fj * k);
+}
+__device__ __forceinline__ int coord(int d, int i, int j, int k) {
+  return d == 0 ? i : (d == 1 ? j : k);
+}
+__device__ __forceinline__ int extent(const DevGrid& g, int d) {
+  return d == 0 ? g.ni : (d == 1 ? g.nj : g.nk);
+}
+
+// Neighbour across side s (-1/+1) of direction d; -1 at a non-periodic boundary.
+// lower = neighbour precedes the cell in h = i+j+k order.
+__device__ __forceinline__ int neighbour(const DevGrid& g, int i, int j, int k, int d, int s,
+                                         bool& lower) {
+  int p[3] = {i, j, k};
+  const int n = extent(g, d);
+  int q = p[d] + s;
+  if (q < 0 || q >= n) {
+    if (g.bc[2 * d + (s > 0)] != BC_PERIODIC) return -1;
+    q = (q + n) % n;
+  }
+  lower = q < p[d];
+  p[d] = q;
+  return cell_of(g, p[0], p[1], p[2]);
+}
+
+__device__ __forceinline__ const double* face_vec(const DevGrid& g, int d, int i, int j, int k,
+                                                  int s) {
+  int p[3] = {i, j, k};
+  if (s > 0) p[d]++;
+  return g.S[d] + 3 * (size_t)face_of(g, d, p[0], p[1], p[2]);
+}
+
+// ---------------------------------------------------------------------------------------
+// Thermodynamic state of one cell (Sec. 2.1)
+// ---------------------------------------------------------------------------------------
+
+// Mixture energy in the one-temperature model: e(T) and c_v(T) per unit mass.
+template <class G>
+__device__ __forceinline__ void mix_e1(const double* Y, double T, double& e, double& cv) {
+  e = 0.0;
+  cv = 0.0;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    double ev, cvv;
+    vib<G>(s, T, ev, cvv);
+    e += Y[s] * (cvtr<G>(s) * T + ev + hf<G>(s));
+    cv += Y[s] * (cvtr<G>(s) + cvv);
+  }
+}
+// Vibrational-electronic pool energy (2T) and its heat capacity.
+template <class G>
+__device__ __forceinline__ void mix_pool(const double* Y, double Tv, double& e, double& cv) {
+  e = 0.0;
+  cv = 0.0;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    if (G::sp(s).kind == ELECTRON) {
+      e += Y[s] * 1.5 * Rs<G>(s) * Tv;
+      cv += Y[s] * 1.5 * Rs<G>(s);
+    } else {
+      double ev, cvv;
+      vib<G>(s, Tv, ev, cvv);
+      e += Y[s] * ev;
+      cv += Y[s] * cvv;
+    }
+  }
+}
+
+// Safeguarded Newton for a monotone energy: returns 0 on convergence, 1 otherwise.
+template <class G, bool POOL>
+__device__ int solve_temperature(const double* Y, double target, double guess, double& Tout) {
+  double lo = kTmin, hi = kTmax, e, cv;
+  if (POOL) mix_pool<G>(Y, lo, e, cv); else mix_e1<G>(Y, lo, e, cv);
+  if (e >= target) { Tout = lo; return 0; }
+  if (POOL) mix_pool<G>(Y, hi, e, cv); else mix_e1<G>(Y, hi, e, cv);
+  if (e <= target) { Tout = hi; return 1; }
+  double T = (guess > lo && guess < hi) ? guess : 1000.0;
+  for (int it = 0; it < 200; ++it) {
+    if (POOL) mix_pool<G>(Y, T, e, cv); else mix_e1<G>(Y, T, e, cv);
+    const double f = e - target;
+    if (f > 0) hi = T; else lo = T;
+    double Tn = (cv > 0) ? T - f / cv : 0.5 * (lo + hi);
+    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    if (fabs(Tn - T) <= 1e-12 * T) { Tout = Tn; return 0; }
+    T = Tn;
+  }
+  Tout = T;
+  return 1;
+}
+
+// Register-resident primitive record.
+template <class G, int ND>
+struct Prim {
+  double rhos[G::NS], Y[G::NS], rho, u[ND], T, Tv, p, c, beta, rhoE, rhoev, ev, H, Gam;
+  double prs[G::NS], prev, cvtr, cvve, cv, mu, kt, kv, rhoD, hs[G::NS], eve[G::NS];
+};
+
+// Conserved -> primitive.  Returns ST_OK, ST_NONPHYSICAL or ST_NEWTON.
+template <class G, int ND>
+__device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G, ND>& w) {
+  constexpr int NS = G::NS;
+  double rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    w.rhos[s] = q[s];
+    if (q[s] < 0.0) return ST_NONPHYSICAL;
+    rho += q[s];
+  }
+  if (!(rho > 0.0)) return ST_NONPHYSICAL;
+  w.rho = rho;
+  const double irho = 1.0 / rho;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) w.Y[s] = w.rhos[s] * irho;
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    w.u[d] = q[NS + d] * irho;
+    ke += 0.5 * w.u[d] * w.u[d];
+  }
+  w.rhoE = q[NS + ND];
+  const double rhoe = w.rhoE - rho * ke;
+  int st;
+  if (G::NTEMP == 1) {
+    double T;
+    st = solve_temperature<G, false>(w.Y, rhoe * irho, Tguess, T);
+    w.T = w.Tv = T;
+    w.rhoev = 0.0;
+    w.ev = 0.0;
+  } else {
+    w.rhoev = q[NS + ND + 1];
+    w.ev = w.rhoev * irho;
+    double Tv;
+    st = solve_temperature<G, true>(w.Y, w.ev, Tvguess > 0 ? Tvguess : Tguess, Tv);
+    w.Tv = Tv;
+    double etr = rhoe - w.rhoev, ct = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      etr -= w.rhos[s] * hf<G>(s);
+      ct += w.rhos[s] * cvtr<G>(s);
+    }
+    w.T = etr / ct;
+    if (!(w.T > kTmin)) w.T = kTmin;   // floor, as the temperature solves
+  }
+  if (st) return ST_NEWTON;
+  const double T = w.T, Tv = w.Tv;
+  double p = 0.0, Rh = 0.0, cvt = 0.0, cvve = 0.0, cv = 0.0, pe = 0.0;
+  double evs[NS], cvvs[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const bool elec = G::sp(s).kind == ELECTRON;
+    const double R = Rs<G>(s);
+    if (G::NTEMP == 2 && elec) {
+      p += w.rhos[s] * R * Tv;
+      pe += w.rhos[s] * R;
+      evs[s] = 1.5 * R * Tv;
+      cvvs[s] = 1.5 * R;
+    } else {
+      p += w.rhos[s] * R * T;
+      Rh += w.Y[s] * R;
+      vib<G>(s, G::NTEMP == 2 ? Tv : T, evs[s], cvvs[s]);
+    }
+    cvt += w.Y[s] * cvtr<G>(s);
+    if (G::NTEMP == 2) cvve += w.Y[s] * cvvs[s];
+    else cv += w.Y[s] * (cvtr<G>(s) + cvvs[s]);
+  }
+  w.p = p;
+  w.cvtr = cvt;
+  w.cvve = cvve;
+  w.cv = cv;
+  const double beta = (G::NTEMP == 2) ? Rh / cvt : Rh / cv;
+  w.beta = beta;
+  double pefac = 0.0;
+  if (G::NTEMP == 2) {
+    pefac = (cvve > 0.0) ? pe / (rho * cvve) : 0.0;
+    w.prev = -beta + pefac;
+  } else {
+    w.prev = 0.0;
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const bool elec = G::sp(s).kind == ELECTRON;
+    const double R = Rs<G>(s);
+    if (G::NTEMP == 1) {
+      const double es = cvtr<G>(s) * T + evs[s] + hf<G>(s);
+      w.prs[s] = R * T + beta * (ke - es);
+      w.hs[s] = es + R * T;
+      w.eve[s] = 0.0;
+    } else {
+      w.prs[s] = beta * (ke - hf<G>(s) - cvtr<G>(s) * T) - pefac * evs[s] +
+                 (elec ? R * Tv : R * T);
+      const double es = cvtr<G>(s) * T + evs[s] + hf<G>(s);
+      w.hs[s] = es + R * (elec ? Tv : T);
+      w.eve[s] = elec ? 2.5 * R * Tv : evs[s];
+    }
+  }
+  w.c = sqrt((1.0 + beta) * p * irho);
+  w.H = (w.rhoE + p) * irho;
+  w.Gam = rhoe / p;
+  w.mu = kSuthMu * T * sqrt(T) / (T + kSuthT);
+  if (G::NTEMP == 2) {
+    w.kt = w.mu * (cvt + Rh) / kPr;
+    w.kv = w.mu * cvve / kPr;
+  } else {
+    w.kt = w.mu * (cv + Rh) / kPr;
+    w.kv = 0.0;
+  }
+  w.rhoD = w.mu / kSc;
+  return ST_OK;
+}
+
+template <class G, int ND>
+__device__ __forceinline__ void store_prim(const DevGrid& g, int c, const Prim<G, ND>& w) {
+  using A = Aux<G, ND>;
+  double* W = g.W;
+  const size_t N = g.N;
+  W[A::RHO * N + c] = w.rho;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) W[(A::U + d) * N + c] = w.u[d];
+  W[A::T * N + c] = w.T;
+  W[A::TV * N + c] = w.Tv;
+  W[A::P * N + c] = w.p;
+  W[A::C * N + c] = w.c;
+  W[A::BETA * N + c] = w.beta;
+  W[A::GAM * N + c] = w.Gam;
+  W[A::EV * N + c] = w.ev;
+  W[A::H * N + c] = w.H;
+  W[A::CVTR * N + c] = w.cvtr;
+  W[A::CVVE * N + c] = w.cvve;
+  W[A::CV * N + c] = w.cv;
+  W[A::MU * N + c] = w.mu;
+  W[A::KT * N + c] = w.kt;
+  W[A::KV * N + c] = w.kv;
+  W[A::RHOD * N + c] = w.rhoD;
+  W[A::PREV * N + c] = w.prev;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    W[(A::Y + s) * N + c] = w.Y[s];
+    W[(A::PRS + s) * N + c] = w.prs[s];
+    W[(A::HS + s) * N + c] = w.hs[s];
+    W[(A::EVE + s) * N + c] = w.eve[s];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Chemistry (Sec. 2.1 source; Park air).  k_b = k_f(T_b)/K_c(T_b) in log space, K_c from the
+// species' RRHO Gibbs energies.  Derivatives: d omega/d rho at fixed T, Tv and d omega/dT,
+// d omega/dTv, giving the conserved-variable source Jacobian A_S of Sec. 2.2.
+// ---------------------------------------------------------------------------------------
+
+// g_s/(R_u T) and H_s/(R_u T) at the standard pressure, simplified form (translational,
+// rotational and vibrational enthalpy terms cancel between H/RT and S/R).
+template <class G>
+__device__ __forceinline__ void gibbs(int s, double T, double lnT, double& gRT, double& hRT) {
+  const SpeciesData& d = G::sp(s);
+  const double m = d.M / kNa;
+  // ln[(2 pi m k T / h^2)^{3/2} k T / p0] = 1.5 ln(2 pi m k / h^2) + 2.5 ln T + ln(k/p0)
+  const double lntr = 1.5 * log(2.0 * kPi * m * kKb / (kH * kH)) + 2.5 * lnT + log(kKb / kPref);
+  double g = d.h0 / (kRu * T) - lntr - log(d.g0);
+  double h = 2.5 + d.h0 / (kRu * T);
+  if (d.kind == DIATOMIC) {
+    g -= lnT - log(d.sigma * d.thr);
+    h += 1.0;
+    if (d.thv > 0.0) {
+      const double x = d.thv / T, em = exp(-x);
+      g += log(1.0 - em);
+      h += x * em / (1.0 - em);
+    }
+  }
+  gRT = g;
+  hRT = h;
+}
+
+__device__ __forceinline__ double rate_temp(int kind, double T, double Tv) {
+  return kind == TK_A ? sqrt(T * Tv) : (kind == TK_V ? Tv : T);
+}
+
+// omega[s]; optionally the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s, the full
+// fixed-T Jacobian J[s*NS+r] and the temperature derivatives wT[s], wTv[s].
+template <class G, bool FULL>
+__device__ void chemistry(const double* rhos, double T, double Tv, double* omega, double* jd,
+                          double* J, double* wT, double* wTv) {
+  constexpr int NS = G::NS;
+  double X[NS], gT[NS], hT[NS], gV[NS], hV[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    X[s] = rhos[s] / G::sp(s).M;
+    omega[s] = 0.0;
+    jd[s] = 0.0;
+    wT[s] = 0.0;
+    wTv[s] = 0.0;
+  }
+  if (FULL) for (int k = 0; k < NS * NS; ++k) J[k] = 0.0;
+  const double lnT = log(T), lnTv = log(Tv);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    gibbs<G>(s, T, lnT, gT[s], hT[s]);
+    if (G::NTEMP == 2) gibbs<G>(s, Tv, lnTv, gV[s], hV[s]);
+    else { gV[s] = gT[s]; hV[s] = hT[s]; }
+  }
+  for (int r = 0; r < G::NR; ++r) {
+    const ReactionData& x = c_reactions[r];
+    const double Tf = rate_temp(x.tf, T, Tv), Tb = rate_temp(x.tb, T, Tv);
+    const bool bv = (x.tb == TK_V);
+    // sum over species of nu * g/RT and nu * h/RT at the backward temperature
+    double sg = 0.0, sh = 0.0;
+    int dn = 0;
+    for (int a = 0; a < x.np; ++a) { sg += bv ? gV[x.p[a]] : gT[x.p[a]]; sh += bv ? hV[x.p[a]] : hT[x.p[a]]; ++dn; }
+    for (int a = 0; a < x.nr; ++a) { sg -= bv ? gV[x.r[a]] : gT[x.r[a]]; sh -= bv ? hV[x.r[a]] : hT[x.r[a]]; --dn; }
+    const double lnKc = -sg + dn * log(kPref / (kRu * Tb));
+    const double lnTf = log(Tf), lnTb = log(Tb);
+    const double kf = exp(x.lnA + x.n * lnTf - x.theta / Tf);
+    const double kb = exp(x.lnA + x.n * lnTb - x.theta / Tb - lnKc);
+    double M = 1.0;
+    if (x.third) {
+      M = 0.0;
+#pragma unroll
+      for (int s = 0; s < NS; ++s) M += x.eff[s] * X[s];
+    }
+    double Pf = 1.0, Pb = 1.0;
+    for (int a = 0; a < x.nr; ++a) Pf *= X[x.r[a]];
+    for (int a = 0; a < x.np; ++a) Pb *= X[x.p[a]];
+    const double Rf = kf * Pf * M, Rb = kb * Pb * M;
+    // temperature derivatives of ln k
+    const double dlf = x.n / Tf + x.theta / (Tf * Tf);
+    const double dlb = x.n / Tb + x.theta / (Tb * Tb) - (sh / Tb - dn / Tb);
+    const double fT = x.tf == TK_T ? 1.0 : (x.tf == TK_A ? 0.5 * Tf / T : 0.0);
+    const double fV = x.tf == TK_V ? 1.0 : (x.tf == TK_A ? 0.5 * Tf / Tv : 0.0);
+    const double bT = x.tb == TK_T ? 1.0 : (x.tb == TK_A ? 0.5 * Tb / T : 0.0);
+    const double bVv = x.tb == TK_V ? 1.0 : (x.tb == TK_A ? 0.5 * Tb / Tv : 0.0);
+    const double dRT = Rf * dlf * fT - Rb * dlb * bT;
+    const double dRV = Rf * dlf * fV - Rb * dlb * bVv;
+    const double net = Rf - Rb;
+    // stoichiometry: loop over the (<= 3 + 3) participating species
+    auto nu_of = [&](int s) {
+      int v = 0;
+      for (int a = 0; a < x.np; ++a) v += (x.p[a] == s);
+      for (int a = 0; a < x.nr; ++a) v -= (x.r[a] == s);
+      return v;
+    };
+    // d(Pf)/dX_q and d(Pb)/dX_q
+    auto dprod = [&](const int* lst, int n, int q) {
+      double v = 0.0;
+      for (int a = 0; a < n; ++a) {
+        if (lst[a] != q) continue;
+        double pr = 1.0;
+        for (int b = 0; b < n; ++b) if (b != a) pr *= X[lst[b]];
+        v += pr;
+      }
+      return v;
+    };
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int nu = nu_of(s);
+      const double Ms = G::sp(s).M;
+      if (nu != 0) {
+        omega[s] += Ms * nu * net;
+        wT[s] += Ms * nu * dRT;
+        wTv[s] += Ms * nu * dRV;
+      }
+      if (FULL) {
+        if (nu == 0) continue;
+        for (int q = 0; q < NS; ++q) {
+          const double dRf = kf * (dprod(x.r, x.nr, q) * M + Pf * (x.third ? x.eff[q] : 0.0));
+          const double dRb = kb * (dprod(x.p, x.np, q) * M + Pb * (x.third ? x.eff[q] : 0.0));
+          J[s * NS + q] += Ms * nu * (dRf - dRb) / G::sp(q).M;
+        }
+      } else {
+        // diagonal only: d omega_s / d rho_s
+        const double dRf = kf * (dprod(x.r, x.nr, s) * M + Pf * (x.third ? x.eff[s] : 0.0));
+        const double dRb = kb * (dprod(x.p, x.np, s) * M + Pb * (x.third ? x.eff[s] : 0.0));
+        if (nu != 0) jd[s] += Ms * nu * (dRf - dRb) / Ms;
+      }
+    }
+  }
+  if (FULL) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) jd[s] = J[s * NS + s];
+  }
+}
+
+// Derivatives of T and Tv with respect to rho_s at fixed other conserved variables.
+template <class G, int ND>
+__device__ __forceinline__ void dT_drho(const Prim<G, ND>& w, int s, double evs, double& dT,
+                                        double& dTv) {
+  double ke = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) ke += 0.5 * w.u[d] * w.u[d];
+  if (G::NTEMP == 1) {
+    const double es = cvtr<G>(s) * w.T + evs + hf<G>(s);
+    dT = (ke - es) / (w.rho * w.cv);
+    dTv = dT;
+  } else {
+    dT = (ke - hf<G>(s) - cvtr<G>(s) * w.T) / (w.rho * w.cvtr);
+    dTv = (w.cvve > 0.0) ? -evs / (w.rho * w.cvve) : 0.0;
+  }
+}
+
+// Millikan-White + Park vibrational relaxation and the vibrational source (2T).
+template <class G, int ND>
+__device__ void vib_source(const Prim<G, ND>& w, const double* omega, double& omv, double& relax) {
+  constexpr int NS = G::NS;
+  double X[NS], xs = 0.0, ph = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    X[s] = 0.0;
+    if (G::sp(s).kind == ELECTRON) continue;
+    X[s] = w.rhos[s] / G::sp(s).M;
+    xs += X[s];
+    ph += w.rhos[s] * Rs<G>(s) * w.T;
+  }
+  const double patm = ph / kPref, nden = xs * kNa, T13 = pow(w.T, -1.0 / 3.0);
+  double lt = 0.0, rc = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const SpeciesData& d = G::sp(s);
+    if (d.kind == DIATOMIC && d.thv > 0.0) {
+      double num = 0.0, den = 0.0;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        if (G::sp(q).kind == ELECTRON) continue;
+        const double Mq = G::sp(q).M;
+        const double mu = d.M * Mq / (d.M + Mq);
+        const double A = 1.16e-3 * sqrt(mu) * pow(d.thv, 4.0 / 3.0);
+        const double B = 0.015 * pow(mu, 0.25);
+        const double tsq = exp(A * (T13 - B) - 18.42) / patm;
+        num += X[q];
+        den += X[q] / tsq;
+      }
+      const double cbar = sqrt(8.0 * kRu * w.T / (kPi * d.M));
+      const double sv = 1e-21 * (50000.0 / w.T) * (50000.0 / w.T);
+      const double tau = num / den + 1.0 / (nden * sv * cbar);
+      double eT, cT, eV, cV;
+      vib<G>(s, w.T, eT, cT);
+      vib<G>(s, w.Tv, eV, cV);
+      lt += w.rhos[s] * (eT - eV) / tau;
+      rc += w.rhos[s] * cV / tau;
+    }
+    const double ep = (d.kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+    lt += omega[s] * ep;
+  }
+  omv = lt;
+  relax = (w.cvve > 0.0) ? rc / (w.rho * w.cvve) : 0.0;
+}
+
+// ---------------------------------------------------------------------------------------
+// K1: primitives, transport, chemistry, vibrational source (per cell)
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_primitive(DevGrid g) {
+  using A = Aux<G, ND>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double q[A::NQ];
+#pragma unroll
+  for (int v = 0; v < A::NQ; ++v) q[v] = g.Q[v * N + c];
+  Prim<G, ND> w;
+  const int st = primitive<G, ND>(q, g.W[A::T * N + c], g.W[A::TV * N + c], w);
+  if (st != ST_OK) {
+    set_status(g, st, c);
+    return;
+  }
+  store_prim<G, ND>(g, c, w);
+  double om[G::NS], jd[G::NS], wT[G::NS], wTv[G::NS];
+  double omv = 0.0, relax = 0.0;
+  if (g.react && G::NR > 0) {
+    chemistry<G, false>(w.rhos, w.T, w.Tv, om, jd, nullptr, wT, wTv);
+#pragma unroll
+    for (int s = 0; s < G::NS; ++s) {
+      double ev = 0.0, cvv;
+      if (G::NTEMP == 1) vib<G>(s, w.T, ev, cvv);
+      else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+      double dT, dTv;
+      dT_drho<G, ND>(w, s, ev, dT, dTv);
+      jd[s] += wT[s] * dT + wTv[s] * dTv;
+    }
+    if (G::NTEMP == 2) vib_source<G, ND>(w, om, omv, relax);
+  } else {
+#pragma unroll
+    for (int s = 0; s < G::NS; ++s) { om[s] = 0.0; jd[s] = 0.0; }
+  }
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    g.W[(A::OM + s) * N + c] = om[s];
+    g.W[(A::DOM + s) * N + c] = jd[s];
+  }
+  g.W[A::OMV * N + c] = omv;
+  g.W[A::RELAX * N + c] = relax;
+}
+
+// ---------------------------------------------------------------------------------------
+// Boundary ghost values (reading: far-field in/out by the freestream's normal velocity; wall
+// no-slip mirror for limiter slopes; outflow/axis copy).
+// ---------------------------------------------------------------------------------------
+
+// reconstructed variables of a cell: (rho_s, u, p, Gam, beta, [ev])
+template <class G, int ND>
+__device__ __forceinline__ void recon_load(const double* W, size_t N, int c, double* v) {
+  using A = Aux<G, ND>;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) v[s] = W[(A::Y + s) * N + c] * W[A::RHO * N + c];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) v[G::NS + d] = W[(A::U + d) * N + c];
+  v[G::NS + ND] = W[A::P * N + c];
+  v[G::NS + ND + 1] = W[A::GAM * N + c];
+  v[G::NS + ND + 2] = W[A::BETA * N + c];
+  if (G::NTEMP == 2) v[G::NS + ND + 3] = W[A::EV * N + c];
+}
+
+// Is the far-field boundary on side (d, s) an inflow face for the freestream?
+template <int ND>
+__device__ __forceinline__ bool farfield_inflow(const DevGrid& g, const double* fsu, const double* Sf,
+                                                int s) {
+  double un = 0.0;
+#pragma unroll
+  for (int q = 0; q < ND; ++q) un += fsu[q] * Sf[q] * (double)s;
+  return un < 0.0;
+}
+
+// Ghost reconstructed state beyond side (d, s) of interior cell c.
+template <class G, int ND>
+__device__ __forceinline__ void recon_ghost(const DevGrid& g, int c, int i, int j, int k, int d,
+                                            int s, double* v) {
+  using A = Aux<G, ND>;
+  const int b = g.bc[2 * d + (s > 0)];
+  if (b == BC_FARFIELD) {
+    const double* Sf = face_vec(g, d, i, j, k, s);
+    if (farfield_inflow<ND>(g, g.fsW + A::U, Sf, s)) {
+      recon_load<G, ND>(g.fsW, 1, 0, v);
+      return;
+    }
+  }
+  recon_load<G, ND>(g.W, g.N, c, v);
+  if (b == BC_WALL) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[G::NS + q] = -v[G::NS + q];
+  }
+}
+
+__device__ __forceinline__ double limiter(int type, double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  if (type == 1) return fabs(a) < fabs(b) ? a : b;
+  return (a * b * (a + b)) / (a * a + b * b);
+}
+
+// Roe flux (reading 17) from two reconstructed states; F = flux * |S|.
+template <class G, int ND>
+__device__ void roe(const double* L, const double* R, const double* S, double efix, double* F) {
+  constexpr int NS = G::NS, NQ = Aux<G, ND>::NQ;
+  constexpr bool TWO = G::NTEMP == 2;
+  double rl = 0.0, rr = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) { rl += L[s]; rr += R[s]; }
+  const double irl = 1.0 / rl, irr = 1.0 / rr;
+  double a2 = 0.0, UL = 0.0, UR = 0.0, kl = 0.0, kr = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    a2 += S[d] * S[d];
+    UL += L[NS + d] * S[d];
+    UR += R[NS + d] * S[d];
+    kl += 0.5 * L[NS + d] * L[NS + d];
+    kr += 0.5 * R[NS + d] * R[NS + d];
+  }
+  const double pl = L[NS + ND], pr = R[NS + ND];
+  const double EL = L[NS + ND + 1] * pl + rl * kl, ER = R[NS + ND + 1] * pr + rr * kr;
+  const double evl = TWO ? L[NS + ND + 3] : 0.0, evr = TWO ? R[NS + ND + 3] : 0.0;
+  const double area = sqrt(a2), ia = 1.0 / area;
+  const double sl = sqrt(rl), sr = sqrt(rr), wl = sl / (sl + sr), wr = 1.0 - wl;
+  const double rt = sl * sr;
+  double ut[ND], un = 0.0, du2 = 0.0, dun = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    ut[d] = wl * L[NS + d] + wr * R[NS + d];
+    const double nh = S[d] * ia;
+    un += ut[d] * nh;
+    const double du = R[NS + d] - L[NS + d];
+    du2 += du * du;
+    dun += du * nh;
+  }
+  const double HL = (EL + pl) * irl, HR = (ER + pr) * irr;
+  const double Ht = wl * HL + wr * HR;
+  const double bt = wl * L[NS + ND + 2] + wr * R[NS + ND + 2];
+  const double prt = wl * pl * irl + wr * pr * irr;
+  const double evt = wl * evl + wr * evr;
+  const double c2 = (1.0 + bt) * prt + 0.5 * bt * wl * wr * du2;
+  const double ct = sqrt(c2);
+  const double delta = efix * (fabs(un) + ct);
+  auto hfix = [delta](double l) {
+    const double a = fabs(l);
+    return a < delta ? (l * l + delta * delta) / (2.0 * delta) : a;
+  };
+  const double l1 = hfix(un - ct), l2 = hfix(un), l3 = hfix(un + ct);
+  const double dp = pr - pl;
+  const double i2c2 = 0.5 / c2;
+  const double ap = (dp + rt * ct * dun) * i2c2, am = (dp - rt * ct * dun) * i2c2;
+  const double cp = (l3 - l2) * ap, cm = (l1 - l2) * am;
+  const double ha = 0.5 * area;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const double Yt = wl * L[s] * irl + wr * R[s] * irr;
+    const double D = l2 * (R[s] - L[s]) + (cp + cm) * Yt;
+    F[s] = 0.5 * (L[s] * UL + R[s] * UR) - ha * D;
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const double nh = S[d] * ia;
+    const double D = l2 * (rr * R[NS + d] - rl * L[NS + d]) + cp * (ut[d] + ct * nh) + cm * (ut[d] - ct * nh);
+    F[NS + d] = 0.5 * (rl * L[NS + d] * UL + pl * S[d] + rr * R[NS + d] * UR + pr * S[d]) - ha * D;
+  }
+  {
+    const double D = l2 * (ER - EL) + cp * (Ht + un * ct) + cm * (Ht - un * ct);
+    F[NS + ND] = 0.5 * ((EL + pl) * UL + (ER + pr) * UR) - ha * D;
+  }
+  if (TWO) {
+    const double D = l2 * (rr * evr - rl * evl) + (cp + cm) * evt;
+    F[NQ - 1] = 0.5 * (rl * evl * UL + rr * evr * UR) - ha * D;
+  }
+}
+
+template <class G, int ND>
+__device__ __forceinline__ bool recon_ok(const double* v) {
+  constexpr int NS = G::NS;
+  double rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    if (v[s] < 0.0) return false;
+    rho += v[s];
+  }
+  if (!(v[NS + ND] > 0.0) || !(v[NS + ND + 1] > 0.0) || !(v[NS + ND + 2] > 0.0)) return false;
+  if (G::NTEMP == 2 && v[NS + ND + 3] < 0.0) return false;
+  return rho > 0.0;
+}
+
+// gradient variables of a cell: u, T, [Tv], Y
+template <class G, int ND>
+__device__ __forceinline__ void grad_vars(const double* W, size_t N, int c, double* v) {
+  using A = Aux<G, ND>;
+  int k = 0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) v[k++] = W[(A::U + d) * N + c];
+  v[k++] = W[A::T * N + c];
+  if (G::NTEMP == 2) v[k++] = W[A::TV * N + c];
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) v[k++] = W[(A::Y + s) * N + c];
+}
+
+// face value of the gradient variables on boundary side (d, s) of cell c
+template <class G, int ND>
+__device__ __forceinline__ void grad_boundary(const DevGrid& g, int c, int i, int j, int k, int d,
+                                              int s, double* v) {
+  using A = Aux<G, ND>;
+  constexpr int NG = A::NG;
+  const int b = g.bc[2 * d + (s > 0)];
+  grad_vars<G, ND>(g.W, g.N, c, v);
+  if (b == BC_WALL) {
+#pragma unroll
+    for (int q = 0; q < ND; ++q) v[q] = 0.0;
+    v[ND] = g.Tw;
+    if (G::NTEMP == 2) v[ND + 1] = g.Tw;
+  } else if (b == BC_FARFIELD) {
+    const double* Sf = face_vec(g, d, i, j, k, s);
+    if (farfield_inflow<ND>(g, g.fsW + A::U, Sf, s)) {
+      double vg[NG];
+      grad_vars<G, ND>(g.fsW, 1, 0, vg);
+#pragma unroll
+      for (int q = 0; q < NG; ++q) v[q] = 0.5 * (v[q] + vg[q]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K2: Green-Gauss cell gradients (per cell)
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_gradient(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NG = A::NG;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  const size_t N = g.N;
+  double vc[NG], gr[NG][ND];
+  grad_vars<G, ND>(g.W, N, c, vc);
+#pragma unroll
+  for (int v = 0; v < NG; ++v)
+#pragma unroll
+    for (int q = 0; q < ND; ++q) gr[v][q] = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int s = -1; s <= 1; s += 2) {
+      const double* Sf = face_vec(g, d, i, j, k, s);
+      double vf[NG];
+      bool lower;
+      const int nb = neighbour(g, i, j, k, d, s, lower);
+      if (nb >= 0) {
+        grad_vars<G, ND>(g.W, N, nb, vf);
+#pragma unroll
+        for (int v = 0; v < NG; ++v) vf[v] = 0.5 * (vc[v] + vf[v]);
+      } else {
+        grad_boundary<G, ND>(g, c, i, j, k, d, s, vf);
+      }
+#pragma unroll
+      for (int v = 0; v < NG; ++v)
+#pragma unroll
+        for (int q = 0; q < ND; ++q) gr[v][q] += (double)s * vf[v] * Sf[q];
+    }
+  const double iV = 1.0 / g.V[c];
+#pragma unroll
+  for (int v = 0; v < NG; ++v)
+#pragma unroll
+    for (int q = 0; q < ND; ++q) g.grad[(v * 3 + q) * N + c] = gr[v][q] * iV;
+}
+
+// Viscous / diffusive flux through S from face gradients (reading 13, 18).
+template <class G, int ND>
+__device__ void viscous(const double (*gf)[ND], const double* uf, double mu, double kt, double kv,
+                        double rhoD, const double* hs, const double* eve, const double* S,
+                        bool wall, double* F) {
+  constexpr int NS = G::NS, NQ = Aux<G, ND>::NQ;
+  constexpr bool TWO = G::NTEMP == 2;
+  constexpr int iT = ND, iTv = ND + 1, iY = ND + 1 + (TWO ? 1 : 0);
+  double div = 0.0;
+#pragma unroll
+  for (int a = 0; a < ND; ++a) div += gf[a][a];
+  double qd = 0.0, qvd = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double J = 0.0;
+    if (!wall) {
+#pragma unroll
+      for (int q = 0; q < ND; ++q) J -= rhoD * gf[iY + s][q] * S[q];
+    }
+    F[s] = J;
+    qd += J * hs[s];
+    if (TWO) qvd += J * eve[s];
+  }
+  double work = 0.0;
+#pragma unroll
+  for (int a = 0; a < ND; ++a) {
+    double ts = 0.0;
+#pragma unroll
+    for (int l = 0; l < ND; ++l) {
+      const double tau = mu * (gf[a][l] + gf[l][a]) - (a == l ? (2.0 / 3.0) * mu * div : 0.0);
+      ts += tau * S[l];
+    }
+    F[NS + a] = -ts;
+    work += uf[a] * ts;
+  }
+  double gT = 0.0, gTv = 0.0;
+#pragma unroll
+  for (int q = 0; q < ND; ++q) {
+    gT += gf[iT][q] * S[q];
+    if (TWO) gTv += gf[iTv][q] * S[q];
+  }
+  F[NS + ND] = -work - kt * gT - kv * gTv + qd;
+  if (TWO) F[NQ - 1] = -kv * gTv + qvd;
+}
+
+// ---------------------------------------------------------------------------------------
+// K3: face fluxes along direction D (per face): MUSCL + Roe + central viscous.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND, int D>
+__global__ void __launch_bounds__(128) k_flux(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NQ = A::NQ, NR = A::NRC, NG = A::NG;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= g.nf[D]) return;
+  const int fi = g.ni + (D == 0), fj = g.nj + (D == 1);
+  const int i = f % fi, j = (f / fi) % fj, k = f / (fi * fj);
+  const int n = extent(g, D);
+  const int pos = coord(D, i, j, k);
+  const double* S = g.S[D] + 3 * (size_t)f;
+  const size_t N = g.N;
+  double Fi[NQ], Fv[NQ];
+  const bool per = g.bc[2 * D] == BC_PERIODIC;
+  int a = -1, b = -1;     // minus / plus side cells
+  int p[3] = {i, j, k};
+  if (pos > 0 && pos < n) {
+    p[D] = pos - 1; a = cell_of(g, p[0], p[1], p[2]);
+    p[D] = pos;     b = cell_of(g, p[0], p[1], p[2]);
+  } else if (per) {
+    p[D] = n - 1; a = cell_of(g, p[0], p[1], p[2]);
+    p[D] = 0;     b = cell_of(g, p[0], p[1], p[2]);
+  }
+  if (a >= 0) {
+    // ---- interior face: MUSCL (reading 17) ----
+    int ai, aj, ak, bi, bj, bk;
+    cell_ijk(g, a, ai, aj, ak);
+    cell_ijk(g, b, bi, bj, bk);
+    double wa[NR], wb[NR], wam[NR], wbp[NR];
+    recon_load<G, ND>(g.W, N, a, wa);
+    recon_load<G, ND>(g.W, N, b, wb);
+    bool lw;
+    const int am = neighbour(g, ai, aj, ak, D, -1, lw);
+    if (am >= 0) recon_load<G, ND>(g.W, N, am, wam);
+    else recon_ghost<G, ND>(g, a, ai, aj, ak, D, -1, wam);
+    const int bp = neighbour(g, bi, bj, bk, D, +1, lw);
+    if (bp >= 0) recon_load<G, ND>(g.W, N, bp, wbp);
+    else recon_ghost<G, ND>(g, b, bi, bj, bk, D, +1, wbp);
+    double vl[NR], vr[NR];
+#pragma unroll
+    for (int v = 0; v < NR; ++v) {
+      vl[v] = wa[v];
+      vr[v] = wb[v];
+      if (g.limiter) {
+        const double dm = wa[v] - wam[v], dc = wb[v] - wa[v], dp = wbp[v] - wb[v];
+        vl[v] += 0.5 * limiter(g.limiter, dm, dc);
+        vr[v] -= 0.5 * limiter(g.limiter, dc, dp);
+      }
+    }
+    if (!recon_ok<G, ND>(vl) || !recon_ok<G, ND>(vr)) {
+      roe<G, ND>(wa, wb, S, g.efix, Fi);
+    } else {
+      roe<G, ND>(vl, vr, S, g.efix, Fi);
+    }
+    // ---- viscous (reading 18) ----
+    double t[3], tl = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      t[q] = g.xc[q * N + b] - g.xc[q * N + a];
+      tl += t[q] * t[q];
+    }
+    tl = sqrt(tl);
+    const double itl = 1.0 / tl;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) t[q] *= itl;
+    double va[NG], vb[NG], gf[NG][ND];
+    grad_vars<G, ND>(g.W, N, a, va);
+    grad_vars<G, ND>(g.W, N, b, vb);
+#pragma unroll
+    for (int v = 0; v < NG; ++v) {
+      double gt = 0.0;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) {
+        gf[v][q] = 0.5 * (g.grad[(v * 3 + q) * N + a] + g.grad[(v * 3 + q) * N + b]);
+        gt += gf[v][q] * t[q];
+      }
+      const double corr = (vb[v] - va[v]) * itl - gt;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) gf[v][q] += corr * t[q];
+    }
+    double uf[ND], hs[NS], eve[NS];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) uf[q] = 0.5 * (g.W[(A::U + q) * N + a] + g.W[(A::U + q) * N + b]);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      hs[s] = 0.5 * (g.W[(A::HS + s) * N + a] + g.W[(A::HS + s) * N + b]);
+      eve[s] = 0.5 * (g.W[(A::EVE + s) * N + a] + g.W[(A::EVE + s) * N + b]);
+    }
+    const double mu = 0.5 * (g.W[A::MU * N + a] + g.W[A::MU * N + b]);
+    const double kt = 0.5 * (g.W[A::KT * N + a] + g.W[A::KT * N + b]);
+    const double kv = 0.5 * (g.W[A::KV * N + a] + g.W[A::KV * N + b]);
+    const double rd = 0.5 * (g.W[A::RHOD * N + a] + g.W[A::RHOD * N + b]);
+    viscous<G, ND>(gf, uf, mu, kt, kv, rd, hs, eve, S, false, Fv);
+  } else {
+    // ---- boundary face ----
+    const int s = (pos == 0) ? -1 : +1;
+    p[D] = (pos == 0) ? 0 : n - 1;
+    const int c = cell_of(g, p[0], p[1], p[2]);
+    const int bcode = g.bc[2 * D + (s > 0)];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) { Fi[v] = 0.0; Fv[v] = 0.0; }
+    if (bcode == BC_WALL) {
+      const double pc = g.W[A::P * N + c];
+#pragma unroll
+      for (int q = 0; q < ND; ++q) Fi[NS + q] = pc * S[q];
+      // wall viscous flux: no slip, T = Tw at the face, no species flux
+      const double* xf = g.fc[D] + 3 * (size_t)f;
+      double t[3], tl = 0.0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        t[q] = (s < 0) ? g.xc[q * N + c] - xf[q] : xf[q] - g.xc[q * N + c];
+        tl += t[q] * t[q];
+      }
+      tl = sqrt(tl);
+      const double itl = 1.0 / tl;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) t[q] *= itl;
+      double vc[NG], vw[NG], gf[NG][ND];
+      grad_vars<G, ND>(g.W, N, c, vc);
+      grad_boundary<G, ND>(g, c, p[0], p[1], p[2], D, s, vw);
+#pragma unroll
+      for (int v = 0; v < NG; ++v) {
+        double gt = 0.0;
+#pragma unroll
+        for (int q = 0; q < ND; ++q) {
+          gf[v][q] = g.grad[(v * 3 + q) * N + c];
+          gt += gf[v][q] * t[q];
+        }
+        const double corr = ((s < 0) ? (vc[v] - vw[v]) : (vw[v] - vc[v])) * itl - gt;
+#pragma unroll
+        for (int q = 0; q < ND; ++q) gf[v][q] += corr * t[q];
+      }
+      double uf[ND], hs[NS], eve[NS];
+#pragma unroll
+      for (int q = 0; q < ND; ++q) uf[q] = 0.0;
+#pragma unroll
+      for (int sp = 0; sp < NS; ++sp) {
+        hs[sp] = g.W[(A::HS + sp) * N + c];
+        eve[sp] = g.W[(A::EVE + sp) * N + c];
+      }
+      viscous<G, ND>(gf, uf, g.W[A::MU * N + c], g.W[A::KT * N + c], g.W[A::KV * N + c],
+                     g.W[A::RHOD * N + c], hs, eve, S, true, Fv);
+    } else if (bcode == BC_FARFIELD || bcode == BC_OUTFLOW) {
+      double wi[NR], wg[NR];
+      recon_load<G, ND>(g.W, N, c, wi);
+      recon_ghost<G, ND>(g, c, p[0], p[1], p[2], D, s, wg);
+      if (s > 0) roe<G, ND>(wi, wg, S, g.efix, Fi);
+      else roe<G, ND>(wg, wi, S, g.efix, Fi);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) g.F[D][(size_t)v * g.nf[D] + f] = Fi[v] + Fv[v];
+}
+
+// ---------------------------------------------------------------------------------------
+// K4: residual assembly R = sum_d (F_+ - F_-) - V S, plus per-block norm partial sums.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(256) k_assemble(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NQ = A::NQ;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  double rs = 0.0, re = 0.0;
+  if (c < g.N) {
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    const size_t N = g.N;
+    double r[NQ];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) r[v] = 0.0;
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      const int fm = face_of(g, d, i, j, k);
+      int p[3] = {i, j, k};
+      p[d]++;
+      const int fp = face_of(g, d, p[0], p[1], p[2]);
+      const size_t nf = g.nf[d];
+#pragma unroll
+      for (int v = 0; v < NQ; ++v) r[v] += g.F[d][v * nf + fp] - g.F[d][v * nf + fm];
+    }
+    const double V = g.V[c];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) r[s] -= V * g.W[(A::OM + s) * N + c];
+    if (G::NTEMP == 2) r[NQ - 1] -= V * g.W[A::OMV * N + c];
+#pragma unroll
+    for (int v = 0; v < NQ; ++v) g.R[v * N + c] = r[v];
+    const double iV = 1.0 / V;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) rs += (r[s] * iV) * (r[s] * iV);
+    re = (r[NS + ND] * iV) * (r[NS + ND] * iV);
+  }
+  // deterministic block reduction
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = rs;
+  sh[1][threadIdx.x] = re;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    g.red[2 * blockIdx.x] = sh[0][0];
+    g.red[2 * blockIdx.x + 1] = sh[1][0];
+  }
+}
+
+// final reduction of the norm partials (one block); out[0..1] = sqrt of sums; also computes
+// the stagnation heat flux of cell `stag` (reading 22).
+template <class G, int ND>
+__global__ void __launch_bounds__(256) k_norms(DevGrid g, int nblocks, int stag, double* out) {
+  using A = Aux<G, ND>;
+  __shared__ double sh[2][256];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+    a += g.red[2 * k];
+    b += g.red[2 * k + 1];
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+      sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(sh[0][0]);
+    out[1] = sqrt(sh[1][0]);
+    out[2] = 0.0;
+    if (stag >= 0 && g.bc[2] == BC_WALL) {
+      const size_t N = g.N;
+      int i, j, k;
+      cell_ijk(g, stag, i, j, k);
+      const int f = face_of(g, 1, i, j, k);
+      const double* Sf = g.S[1] + 3 * (size_t)f;
+      const double* xf = g.fc[1] + 3 * (size_t)f;
+      double area = 0.0, dist = 0.0;
+      for (int q = 0; q < 3; ++q) area += Sf[q] * Sf[q];
+      area = sqrt(area);
+      for (int q = 0; q < 3; ++q) dist += (g.xc[q * N + stag] - xf[q]) * Sf[q] / area;
+      dist = fabs(dist);
+      double qw = g.W[A::KT * N + stag] * (g.W[A::T * N + stag] - g.Tw) / dist;
+      if (G::NTEMP == 2) qw += g.W[A::KV * N + stag] * (g.W[A::TV * N + stag] - g.Tw) / dist;
+      out[2] = qw;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K5: spectral radii, local time step, split diagonals (per cell).  Readings 7, 8, 9.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
+  using A = Aux<G, ND>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  int i, j, k;
+  cell_ijk(g, c, i, j, k);
+  const size_t N = g.N;
+  const double* W = g.W;
+  const double rho = W[A::RHO * N + c], mu = W[A::MU * N + c], kt = W[A::KT * N + c];
+  double nuF;
+  if (G::NTEMP == 2) {
+    nuF = fmax(4.0 * mu / 3.0, kt / W[A::CVTR * N + c]);
+    const double cvve = W[A::CVVE * N + c];
+    if (cvve > 0.0) nuF = fmax(nuF, W[A::KV * N + c] / cvve);
+  } else {
+    nuF = fmax(4.0 * mu / 3.0, kt / W[A::CV * N + c]);
+  }
+  const double irho = 1.0 / rho;
+  nuF *= irho;
+  const double nuC = W[A::RHOD * N + c] * irho;
+  const double nuCI = fmax(nuF, nuC);
+  const double V = g.V[c], iV = 1.0 / V, cs = W[A::C * N + c];
+  double sumdt = 0.0, sF = 0.0, sC = 0.0, sCI = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const double* Sm = face_vec(g, d, i, j, k, -1);
+    const double* Sp = face_vec(g, d, i, j, k, +1);
+    double a2 = 0.0, U = 0.0;
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+      const double sb = 0.5 * (Sm[q] + Sp[q]);
+      a2 += sb * sb;
+      U += W[(A::U + q) * N + c] * sb;
+    }
+    const double a = sqrt(a2);
+    const double liF = fabs(U) + cs * a, liC = fabs(U);
+    const double lvF = nuF * a2 * iV, lvC = nuC * a2 * iV, lvCI = nuCI * a2 * iV;
+    const double lF = liF + 2.0 * lvF, lC = liC + 2.0 * lvC, lCI = liF + 2.0 * lvCI;
+    g.lamF[d * N + c] = lF;
+    g.lamC[d * N + c] = lC;
+    g.lamCI[d * N + c] = lCI;
+    sumdt += liF + lvF;
+    sF += lF;
+    sC += lC;
+    sCI += lCI;
+  }
+  const double Vdt = sumdt / g.params[0];
+  g.Vdt[c] = Vdt;
+  g.DF[c] = Vdt + sF;
+  g.DFev[c] = Vdt + sF + V * W[A::RELAX * N + c];
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s)
+    g.Ds[s * N + c] = Vdt + sC + V * fmax(0.0, -W[(A::DOM + s) * N + c]);
+  if (g.DLU) g.DLU[(size_t)c * A::NCI * A::NCI] = sCI;   // sum of coupled radii, read by k_ci_block
+}
+
+// ---------------------------------------------------------------------------------------
+// Flux Jacobian times a vector at a cell state (Sec. 2.3 Eq. (convectiveJacobian)),
+// matrix-free.  Flow block with frozen mass fractions (Sec. 2.3.1) and coupled variables.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+struct CellState {       // what the Jacobian needs from the neighbour cell
+  double rho, u[ND], p, rhoE, rhoev, beta, prev, pY;   // pY = sum_s Y_s dp/drho_s
+};
+
+template <class G, int ND>
+__device__ __forceinline__ void load_state(const DevGrid& g, int c, CellState<G, ND>& s) {
+  using A = Aux<G, ND>;
+  const size_t N = g.N;
+  const double* W = g.W;
+  s.rho = W[A::RHO * N + c];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) s.u[d] = W[(A::U + d) * N + c];
+  s.p = W[A::P * N + c];
+  s.rhoE = g.Q[(G::NS + ND) * N + c];
+  s.rhoev = (G::NTEMP == 2) ? g.Q[(A::NQ - 1) * N + c] : 0.0;
+  s.beta = W[A::BETA * N + c];
+  s.prev = W[A::PREV * N + c];
+  double py = 0.0;
+#pragma unroll
+  for (int sp = 0; sp < G::NS; ++sp) py += W[(A::Y + sp) * N + c] * W[(A::PRS + sp) * N + c];
+  s.pY = py;
+}
+
+// flow block: x = (drho, dm, drhoE, [drho e_v]) -> A(S) x
+template <class G, int ND>
+__device__ __forceinline__ void jvp_flow(const CellState<G, ND>& w, const double* S, const double* x,
+                                         double* y) {
+  constexpr int NF = Aux<G, ND>::NF;
+  double U = 0.0, Sdm = 0.0, dp = w.pY * x[0] + w.beta * x[ND + 1];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    U += w.u[d] * S[d];
+    Sdm += S[d] * x[1 + d];
+    dp -= w.beta * w.u[d] * x[1 + d];
+  }
+  if (G::NTEMP == 2) dp += w.prev * x[NF - 1];
+  const double dU = (Sdm - U * x[0]) / w.rho;
+  y[0] = Sdm;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) y[1 + d] = x[1 + d] * U + w.rho * w.u[d] * dU + dp * S[d];
+  y[ND + 1] = (x[ND + 1] + dp) * U + (w.rhoE + w.p) * dU;
+  if (G::NTEMP == 2) y[NF - 1] = x[NF - 1] * U + w.rhoev * dU;
+}
+
+// ---------------------------------------------------------------------------------------
+// K6: split LU-SGS sweeps on hyperplanes h = i+j(+k) (Sec. 2.2 + 2.3.1-2.3.2).
+// One launch per hyperplane; each thread owns one cell of the hyperplane.
+// FWD: x = dQ* = D^-1(-R - sum_L coef x_nb); BWD: y = x + D^-1 sum_U (-coef) y_nb.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__device__ __forceinline__ bool hyperplane_cell(const DevGrid& g, int h, int t, int& i, int& j, int& k) {
+  if (ND == 2) {
+    j = t;
+    k = 0;
+    if (j >= g.nj) return false;
+    i = h - j;
+  } else {
+    j = t % g.nj;
+    k = t / g.nj;
+    if (k >= g.nk) return false;
+    i = h - j - k;
+  }
+  return i >= 0 && i < g.ni;
+}
+
+template <class G, int ND, bool FWD>
+__global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, int cnt) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (t >= cnt || !hyperplane_cell<G, ND>(g, h, t + off, i, j, k)) return;
+  const int c = cell_of(g, i, j, k);
+  const size_t N = g.N;
+  double acc[NF], accs[NS];
+  if (FWD) {
+    double rr = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const double r = g.R[s * N + c];
+      rr += r;
+      accs[s] = -r;
+    }
+    acc[0] = -rr;
+#pragma unroll
+    for (int q = 1; q < NF; ++q) acc[q] = -g.R[(NS + q - 1) * N + c];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) accs[s] = 0.0;
+  }
+  const double* X = FWD ? g.dQs : g.dQ;     // solution being built by this sweep
+#pragma unroll
+  for (int d = 0; d < ND; ++d)
+#pragma unroll
+    for (int s = -1; s <= 1; s += 2) {
+      bool lower;
+      const int nb = neighbour(g, i, j, k, d, s, lower);
+      if (nb < 0 || lower != FWD) continue;
+      const double* Sf = face_vec(g, d, i, j, k, s);
+      CellState<G, ND> w;
+      load_state<G, ND>(g, nb, w);
+      double xn[NF], ax[NF];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) xn[q] = X[q * N + nb];
+      jvp_flow<G, ND>(w, Sf, xn, ax);
+      const double l = g.lamF[d * N + nb];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) {
+        if (s < 0) acc[q] += 0.5 * (ax[q] + l * xn[q]);
+        else acc[q] -= 0.5 * (ax[q] - l * xn[q]);
+      }
+      double U = 0.0;
+#pragma unroll
+      for (int q = 0; q < ND; ++q) U += w.u[q] * Sf[q];
+      const double lc = g.lamC[d * N + nb];
+#pragma unroll
+      for (int sp = 0; sp < NS; ++sp) {
+        const double xs = X[(NF + sp) * N + nb];
+        if (s < 0) accs[sp] += 0.5 * (U * xs + lc * xs);
+        else accs[sp] -= 0.5 * (U * xs - lc * xs);
+      }
+    }
+  double* Y = FWD ? g.dQs : g.dQ;
+#pragma unroll
+  for (int q = 0; q < NF; ++q) {
+    const double D = (G::NTEMP == 2 && q == NF - 1) ? g.DFev[c] : g.DF[c];
+    const double v = acc[q] / D;
+    Y[q * N + c] = FWD ? v : g.dQs[q * N + c] + v;
+  }
+#pragma unroll
+  for (int sp = 0; sp < NS; ++sp) {
+    const double v = accs[sp] / g.Ds[sp * N + c];
+    Y[(NF + sp) * N + c] = FWD ? v : g.dQs[(NF + sp) * N + c] + v;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// K7: consistency corrections and update (Sec. 2.3.3; readings 10, 11).
+// mode 1: CS-1, 2: CS-2 (dQ in split layout), 0: coupled update (CI layout).
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, const double* dq) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double rs[NS], rho = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    rs[s] = g.Q[s * N + c];
+    rho += rs[s];
+  }
+  const double drho = dq[c];
+  const double rnew = rho + drho;
+  if (!(rnew > 0.0)) {
+    set_status(g, ST_NONPHYSICAL, c);
+    return;
+  }
+  int nclip = 0;
+  double out[NS];
+  if (mode == 1) {
+    double sd = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sd += dq[(NF + s) * N + c];
+    const double irho = 1.0 / rho, rem = drho - sd;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) out[s] = rs[s] + dq[(NF + s) * N + c] + rs[s] * irho * rem;
+  } else if (mode == 2) {
+    double t[NS], sum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      t[s] = rs[s] + dq[(NF + s) * N + c];
+      if (clip && t[s] < 0.0) { t[s] = 0.0; ++nclip; }
+      sum += t[s];
+    }
+    if (!(sum > 0.0)) {
+      set_status(g, ST_NONPHYSICAL, c);
+      return;
+    }
+    const double f = rnew / sum;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) out[s] = t[s] * f;
+  } else {
+    double sum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS - 1; ++s) {
+      out[s] = rs[s] + dq[(NF + s) * N + c];
+      sum += out[s];
+    }
+    out[NS - 1] = rnew - sum;
+  }
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double v = out[s];
+    if (clip && v < 0.0 && mode != 2) { v = 0.0; ++nclip; }
+    g.Q[s * N + c] = v;
+  }
+#pragma unroll
+  for (int q = 1; q < NF; ++q) {
+    double v = g.Q[(NS + q - 1) * N + c] + dq[q * N + c];
+    if (clip && G::NTEMP == 2 && q == NF - 1 && v < 0.0) { v = 0.0; ++nclip; }
+    g.Q[(NS + q - 1) * N + c] = v;
+  }
+  if (nclip) atomicAdd(&g.status[2], nclip);
+}
+
+// ---------------------------------------------------------------------------------------
+// Coupled (CI) operator: dense diagonal blocks (V/dtau + sum lambda) I - V dS/dQ_CI with
+// rho_ns = rho - sum_{s<ns} rho_s (Sec. 2.2, Sec. 2.3.3), LU with partial pivoting per cell.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF, NC = A::NCI, NQ = A::NQ;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double* M = g.DLU + (size_t)c * NC * NC;
+  const double diag = g.Vdt[c] + M[0];
+  for (int e = 0; e < NC * NC; ++e) M[e] = 0.0;
+  for (int e = 0; e < NC; ++e) M[e * NC + e] = diag;
+  const double V = g.V[c];
+  if (G::NTEMP == 2) M[(NF - 1) * NC + NF - 1] += V * g.W[A::RELAX * N + c];
+  if (g.react && G::NR > 0) {
+    double q[NQ];
+    for (int v = 0; v < NQ; ++v) q[v] = g.Q[v * N + c];
+    Prim<G, ND> w;
+    if (primitive<G, ND>(q, g.W[A::T * N + c], g.W[A::TV * N + c], w) != ST_OK) {
+      set_status(g, ST_NONPHYSICAL, c);
+      return;
+    }
+    double om[NS], jd[NS], J[NS * NS], wT[NS], wTv[NS];
+    chemistry<G, true>(w.rhos, w.T, w.Tv, om, jd, J, wT, wTv);
+    // temperature derivatives with respect to the full conserved variables
+    double dT[NQ], dTv[NQ];
+    double ke = 0.0;
+    for (int d = 0; d < ND; ++d) ke += 0.5 * w.u[d] * w.u[d];
+    for (int s = 0; s < NS; ++s) {
+      double ev = 0.0, cvv;
+      if (G::NTEMP == 1) vib<G>(s, w.T, ev, cvv);
+      else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+      dT_drho<G, ND>(w, s, ev, dT[s], dTv[s]);
+    }
+    const double rc = w.rho * (G::NTEMP == 1 ? w.cv : w.cvtr);
+    for (int d = 0; d < ND; ++d) dT[NS + d] = -w.u[d] / rc;
+    dT[NS + ND] = 1.0 / rc;
+    if (G::NTEMP == 1) {
+      for (int v = NS; v < NQ; ++v) dTv[v] = dT[v];
+    } else {
+      for (int d = 0; d < ND; ++d) dTv[NS + d] = 0.0;
+      dTv[NS + ND] = 0.0;
+      dT[NQ - 1] = -1.0 / rc;
+      dTv[NQ - 1] = (w.cvve > 0.0) ? 1.0 / (w.rho * w.cvve) : 0.0;
+    }
+    for (int s = 0; s < NS - 1; ++s) {
+      // full-layout row of d omega_s / dQ
+      auto jq = [&](int kcol) {
+        double v = wT[s] * dT[kcol] + wTv[s] * dTv[kcol];
+        if (kcol < NS) v += J[s * NS + kcol];
+        return v;
+      };
+      const double last = jq(NS - 1);
+      M[(NF + s) * NC + 0] -= V * last;
+      for (int kk = 1; kk < NF; ++kk) M[(NF + s) * NC + kk] -= V * jq(NS + kk - 1);
+      for (int r = 0; r < NS - 1; ++r) M[(NF + s) * NC + NF + r] -= V * (jq(r) - last);
+    }
+  }
+  // LU with partial pivoting (ties: lowest row), in place
+  int* piv = g.piv + (size_t)c * NC;
+  for (int kk = 0; kk < NC; ++kk) {
+    int p = kk;
+    double best = fabs(M[kk * NC + kk]);
+    for (int r = kk + 1; r < NC; ++r) {
+      const double v = fabs(M[r * NC + kk]);
+      if (v > best) { best = v; p = r; }
+    }
+    piv[kk] = p;
+    if (best == 0.0) {
+      set_status(g, ST_NONPHYSICAL, c);
+      return;
+    }
+    if (p != kk)
+      for (int col = 0; col < NC; ++col) {
+        const double t = M[kk * NC + col];
+        M[kk * NC + col] = M[p * NC + col];
+        M[p * NC + col] = t;
+      }
+    const double inv = 1.0 / M[kk * NC + kk];
+    for (int r = kk + 1; r < NC; ++r) {
+      const double l = M[r * NC + kk] * inv;
+      M[r * NC + kk] = l;
+      for (int col = kk + 1; col < NC; ++col) M[r * NC + col] -= l * M[kk * NC + col];
+    }
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void lu_solve(const double* M, const int* piv, double* b) {
+  for (int kk = 0; kk < NC; ++kk) {
+    const int p = piv[kk];
+    if (p != kk) { const double t = b[kk]; b[kk] = b[p]; b[p] = t; }
+  }
+  for (int r = 1; r < NC; ++r)
+    for (int col = 0; col < r; ++col) b[r] -= M[r * NC + col] * b[col];
+  for (int r = NC - 1; r >= 0; --r) {
+    for (int col = r + 1; col < NC; ++col) b[r] -= M[r * NC + col] * b[col];
+    b[r] /= M[r * NC + r];
+  }
+}
+
+// coupled Jacobian-vector product in CI variables (rho, m, rhoE, [rho e_v], rho_1..rho_{ns-1})
+template <class G, int ND>
+__device__ __forceinline__ void jvp_ci(const DevGrid& g, int nb, const double* S, const double* x,
+                                       double* y) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF;
+  const size_t N = g.N;
+  const double* W = g.W;
+  const double rho = W[A::RHO * N + nb], beta = W[A::BETA * N + nb];
+  double u[ND], U = 0.0, Sdm = 0.0, dp = 0.0;
+  double last = x[0];
+  for (int s = 0; s < NS - 1; ++s) {
+    dp += W[(A::PRS + s) * N + nb] * x[NF + s];
+    last -= x[NF + s];
+  }
+  dp += W[(A::PRS + NS - 1) * N + nb] * last;
+  for (int d = 0; d < ND; ++d) {
+    u[d] = W[(A::U + d) * N + nb];
+    U += u[d] * S[d];
+    Sdm += S[d] * x[1 + d];
+    dp -= beta * u[d] * x[1 + d];
+  }
+  dp += beta * x[ND + 1];
+  if (G::NTEMP == 2) dp += W[A::PREV * N + nb] * x[NF - 1];
+  const double dU = (Sdm - U * x[0]) / rho;
+  y[0] = Sdm;
+  for (int d = 0; d < ND; ++d) y[1 + d] = x[1 + d] * U + rho * u[d] * dU + dp * S[d];
+  const double rhoE = g.Q[(NS + ND) * N + nb], p = W[A::P * N + nb];
+  y[ND + 1] = (x[ND + 1] + dp) * U + (rhoE + p) * dU;
+  if (G::NTEMP == 2) y[NF - 1] = x[NF - 1] * U + g.Q[(A::NQ - 1) * N + nb] * dU;
+  for (int s = 0; s < NS - 1; ++s) y[NF + s] = x[NF + s] * U + rho * W[(A::Y + s) * N + nb] * dU;
+}
+
+template <class G, int ND, bool FWD>
+__global__ void __launch_bounds__(64) k_sweep_coupled(DevGrid g, int h, int off, int cnt) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF, NC = A::NCI;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (t >= cnt || !hyperplane_cell<G, ND>(g, h, t + off, i, j, k)) return;
+  const int c = cell_of(g, i, j, k);
+  const size_t N = g.N;
+  double acc[NC];
+  if (FWD) {
+    double rr = 0.0;
+    for (int s = 0; s < NS; ++s) rr += g.R[s * N + c];
+    acc[0] = -rr;
+    for (int q = 1; q < NF; ++q) acc[q] = -g.R[(NS + q - 1) * N + c];
+    for (int s = 0; s < NS - 1; ++s) acc[NF + s] = -g.R[s * N + c];
+  } else {
+    for (int q = 0; q < NC; ++q) acc[q] = 0.0;
+  }
+  const double* X = FWD ? g.dQcs : g.dQc;
+  for (int d = 0; d < ND; ++d)
+    for (int s = -1; s <= 1; s += 2) {
+      bool lower;
+      const int nb = neighbour(g, i, j, k, d, s, lower);
+      if (nb < 0 || lower != FWD) continue;
+      const double* Sf = face_vec(g, d, i, j, k, s);
+      double xn[NC], ax[NC];
+      for (int q = 0; q < NC; ++q) xn[q] = X[q * N + nb];
+      jvp_ci<G, ND>(g, nb, Sf, xn, ax);
+      const double l = g.lamCI[d * N + nb];
+      for (int q = 0; q < NC; ++q) {
+        if (s < 0) acc[q] += 0.5 * (ax[q] + l * xn[q]);
+        else acc[q] -= 0.5 * (ax[q] - l * xn[q]);
+      }
+    }
+  lu_solve<NC>(g.DLU + (size_t)c * NC * NC, g.piv + (size_t)c * NC, acc);
+  double* Y = FWD ? g.dQcs : g.dQc;
+  for (int q = 0; q < NC; ++q) Y[q * N + c] = FWD ? acc[q] : g.dQcs[q * N + c] + acc[q];
+}
+
+// ---------------------------------------------------------------------------------------
+// Freestream: density from p, T, Y; velocity = Mach * frozen sound speed; conserved state and
+// auxiliary record (one thread).
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void k_freestream(DevGrid g, const double* in, double* fsQ) {
+  // in: [T, Tv, p, mach, dir[3], Y[NS]]
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NQ = A::NQ;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double T = in[0], Tv = (G::NTEMP == 2) ? in[1] : in[0], p = in[2], mach = in[3];
+  const double* Y = in + 7;
+  double Rm = 0.0;
+  for (int s = 0; s < NS; ++s)
+    Rm += Y[s] * Rs<G>(s) * ((G::NTEMP == 2 && G::sp(s).kind == ELECTRON) ? Tv / T : 1.0);
+  const double rho = p / (Rm * T);
+  double q[NQ];
+  double e = 0.0, ev = 0.0;
+  for (int s = 0; s < NS; ++s) {
+    q[s] = rho * Y[s];
+    double evs, cvv;
+    if (G::sp(s).kind == ELECTRON && G::NTEMP == 2) evs = 1.5 * Rs<G>(s) * Tv;
+    else vib<G>(s, G::NTEMP == 2 ? Tv : T, evs, cvv);
+    e += q[s] * (cvtr<G>(s) * T + evs + hf<G>(s));
+    ev += q[s] * evs;
+  }
+  for (int d = 0; d < ND; ++d) q[NS + d] = 0.0;
+  q[NS + ND] = e;
+  if (G::NTEMP == 2) q[NQ - 1] = ev;
+  Prim<G, ND> w;
+  if (primitive<G, ND>(q, T, Tv, w) != ST_OK) { set_status(g, ST_NONPHYSICAL, -1); return; }
+  double dn = 0.0;
+  for (int d = 0; d < ND; ++d) dn += in[4 + d] * in[4 + d];
+  dn = sqrt(dn);
+  double ke = 0.0;
+  for (int d = 0; d < ND; ++d) {
+    const double u = mach * w.c * in[4 + d] / dn;
+    q[NS + d] = rho * u;
+    ke += 0.5 * u * u;
+  }
+  q[NS + ND] = e + rho * ke;
+  if (primitive<G, ND>(q, T, Tv, w) != ST_OK) { set_status(g, ST_NONPHYSICAL, -1); return; }
+  for (int v = 0; v < NQ; ++v) fsQ[v] = q[v];
+  DevGrid one = g;
+  one.W = g.fsW;
+  one.N = 1;
+  store_prim<G, ND>(one, 0, w);
+}
+
+template <class G, int ND>
+__global__ void __launch_bounds__(256) k_fill(DevGrid g, const double* fsQ) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  for (int v = 0; v < Aux<G, ND>::NQ; ++v) g.Q[(size_t)v * g.N + c] = fsQ[v];
+}
+
+}  // namespace cs

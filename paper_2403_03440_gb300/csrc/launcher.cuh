@@ -1,0 +1,176 @@
+// Host-side launch sequences for one gas model and dimension.  Each instantiation lives in
+// its own translation unit (launch_<model>.cu) so the three models compile in parallel.
+#pragma once
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace cs {
+
+struct Launcher {
+  virtual ~Launcher() {}
+  int ns, ntemp, nq, nF, nci, ng, naux, nd;
+  virtual cudaError_t init_constants() = 0;
+  virtual void freestream(const DevGrid& g, cudaStream_t st, const double* in, double* fsQ) = 0;
+  virtual void fill(const DevGrid& g, cudaStream_t st, const double* fsQ) = 0;
+  // residual: primitives + gradients + face fluxes + assembly + norms (out[3] on device)
+  void residual(const DevGrid& g, cudaStream_t st, int stag, double* out) {
+    primitive(g, st);
+    gradient(g, st);
+    flux(g, st);
+    assemble(g, st, stag, out);
+  }
+  virtual void primitive(const DevGrid& g, cudaStream_t st) = 0;
+  virtual void gradient(const DevGrid& g, cudaStream_t st) = 0;
+  virtual void flux(const DevGrid& g, cudaStream_t st) = 0;
+  virtual void assemble(const DevGrid& g, cudaStream_t st, int stag, double* out) = 0;
+  virtual void spectral(const DevGrid& g, cudaStream_t st) = 0;
+  void sweep_split(const DevGrid& g, cudaStream_t st) { sweep_split_dir(g, st, true); sweep_split_dir(g, st, false); }
+  virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;   // returns launches
+  virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
+  void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
+  virtual int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;
+  virtual void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) = 0;
+  // offset (in units of N) and count of a named auxiliary field, or -1
+  virtual int aux_field(const char* name, int* count) const = 0;
+  static int blocks(long n, int t) { return (int)((n + t - 1) / t); }
+};
+
+template <class G, int ND>
+struct LauncherT : Launcher {
+  using A = Aux<G, ND>;
+  LauncherT() {
+    ns = G::NS;
+    ntemp = G::NTEMP;
+    nq = A::NQ;
+    nF = A::NF;
+    nci = A::NCI;
+    ng = A::NG;
+    naux = A::COUNT;
+    nd = ND;
+  }
+
+  cudaError_t init_constants() override {
+    ReactionData h[21];
+    std::memset(h, 0, sizeof h);
+    static const double effs[4][11] = {{0}, CS_EFF_N2, CS_EFF_O2, CS_EFF_NO};
+    for (int r = 0; r < 21; ++r) {
+      const ReactionInit& x = kReactionInit[r];
+      h[r].nr = x.nr;
+      h[r].r[0] = x.r0;
+      h[r].r[1] = x.r1;
+      h[r].np = x.np;
+      h[r].p[0] = x.p0;
+      h[r].p[1] = x.p1;
+      h[r].p[2] = x.p2;
+      h[r].third = x.third;
+      h[r].lnA = log(x.A_cgs * 1e-3);   // cm^3/(mol s) -> m^3/(kmol s)
+      h[r].n = x.n;
+      h[r].theta = x.theta;
+      h[r].tf = x.tf;
+      h[r].tb = x.tb;
+      for (int s = 0; s < 11; ++s) h[r].eff[s] = effs[x.effset][s];
+    }
+    return cudaMemcpyToSymbol(c_reactions, h, sizeof h);
+  }
+
+  void freestream(const DevGrid& g, cudaStream_t st, const double* in, double* fsQ) override {
+    k_freestream<G, ND><<<1, 1, 0, st>>>(g, in, fsQ);
+  }
+  void fill(const DevGrid& g, cudaStream_t st, const double* fsQ) override {
+    k_fill<G, ND><<<blocks(g.N, 256), 256, 0, st>>>(g, fsQ);
+  }
+
+  void primitive(const DevGrid& g, cudaStream_t st) override {
+    k_primitive<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+  }
+  void gradient(const DevGrid& g, cudaStream_t st) override {
+    k_gradient<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+  }
+  void flux(const DevGrid& g, cudaStream_t st) override {
+    k_flux<G, ND, 0><<<blocks(g.nf[0], 128), 128, 0, st>>>(g);
+    k_flux<G, ND, 1><<<blocks(g.nf[1], 128), 128, 0, st>>>(g);
+    if (ND == 3) k_flux<G, ND, (ND == 3 ? 2 : 1)><<<blocks(g.nf[2], 128), 128, 0, st>>>(g);
+  }
+  void assemble(const DevGrid& g, cudaStream_t st, int stag, double* out) override {
+    const int nb = blocks(g.N, 256);
+    k_assemble<G, ND><<<nb, 256, 0, st>>>(g);
+    k_norms<G, ND><<<1, 256, 0, st>>>(g, nb, stag, out);
+  }
+
+  void spectral(const DevGrid& g, cudaStream_t st) override {
+    k_spectral<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+  }
+
+  // cells of hyperplane h: 2D j in [max(0, h-ni+1), min(h, nj-1)]; 3D all (j, k) pairs
+  void plane_range(const DevGrid& g, int h, int& off, int& count) const {
+    if (ND == 2) {
+      const int jlo = h - g.ni + 1 > 0 ? h - g.ni + 1 : 0;
+      const int jhi = h < g.nj - 1 ? h : g.nj - 1;
+      off = jlo;
+      count = jhi - jlo + 1;
+    } else {
+      off = 0;
+      count = g.nj * g.nk;
+    }
+  }
+
+  int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) override {
+    const int H = g.ni + g.nj + (ND == 3 ? g.nk : 1) - 2;
+    int launches = 0;
+    for (int t = 0; t <= H; ++t) {
+      const int h = fwd ? t : H - t;
+      int off, cnt;
+      plane_range(g, h, off, cnt);
+      if (cnt <= 0) continue;
+      if (fwd) k_sweep_split<G, ND, true><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
+      else k_sweep_split<G, ND, false><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
+      ++launches;
+    }
+    return launches;
+  }
+
+  void ci_block(const DevGrid& g, cudaStream_t st) override {
+    k_ci_block<G, ND><<<blocks(g.N, 64), 64, 0, st>>>(g);
+  }
+
+  int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) override {
+    const int H = g.ni + g.nj + (ND == 3 ? g.nk : 1) - 2;
+    int launches = 0;
+    for (int t = 0; t <= H; ++t) {
+      const int h = fwd ? t : H - t;
+      int off, cnt;
+      plane_range(g, h, off, cnt);
+      if (cnt <= 0) continue;
+      if (fwd) k_sweep_coupled<G, ND, true><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
+      else k_sweep_coupled<G, ND, false><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
+      ++launches;
+    }
+    return launches;
+  }
+
+  void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) override {
+    k_correct<G, ND><<<blocks(g.N, 256), 256, 0, st>>>(g, mode, clip, dq);
+  }
+
+  int aux_field(const char* name, int* count) const override {
+    struct E { const char* n; int off, cnt; };
+    const E tab[] = {{"rho", A::RHO, 1}, {"u", A::U, ND}, {"T", A::T, 1}, {"Tv", A::TV, 1},
+                     {"p", A::P, 1}, {"c", A::C, 1}, {"beta", A::BETA, 1}, {"Gam", A::GAM, 1},
+                     {"H", A::H, 1}, {"mu", A::MU, 1}, {"kt", A::KT, 1}, {"kv", A::KV, 1},
+                     {"rhoD", A::RHOD, 1}, {"relax", A::RELAX, 1}, {"omega_v", A::OMV, 1},
+                     {"omega", A::OM, G::NS}, {"dom", A::DOM, G::NS}, {"prs", A::PRS, G::NS}};
+    for (const E& e : tab)
+      if (!std::strcmp(e.n, name)) { *count = e.cnt; return e.off; }
+    return -1;
+  }
+};
+
+Launcher* make_launcher_perfect_2d();
+Launcher* make_launcher_perfect_3d();
+Launcher* make_launcher_air5_2d();
+Launcher* make_launcher_air5_3d();
+Launcher* make_launcher_air11_2d();
+Launcher* make_launcher_air11_3d();
+
+}  // namespace cs
