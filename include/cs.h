@@ -19,7 +19,9 @@
  *    [rho*e_v] (two-temperature models), nq = ns + d + 1 (+1).
  *  - Split increments dQ: (rho, rho*u_1..d, rho*E, [rho*e_v], rho_1..rho_ns), nsplit = nF + ns
  *    with nF = d + 2 (+1).  Coupled increments: (rho, rho*u, rho*E, [rho*e_v],
- *    rho_1..rho_{ns-1}), nci = nF + ns - 1 (rho_ns = rho - sum of the others).
+ *    rho_2..rho_ns), nci = nF + ns - 1: the first species (N2 in air, the most abundant) is
+ *    eliminated as rho - sum of the others (Sec. 2.3.3 eliminates one species; eliminating
+ *    the electron, last in the list, would leave the coupled blocks singular).
  *  - Pointers marked "host or device" may be either (the library copies with
  *    cudaMemcpyDefault); they are borrowed for the duration of the call and owned by the
  *    caller.  The grid owns all of its device work arrays.

@@ -1367,16 +1367,16 @@ static void spectral(orc_grid *G, double cfl)
             double Jq[NSMAX * NQMAX], om[NSMAX];
             if (G->react) source_jacobian(&G->gas, nd, w, om, Jq);
             else memset(Jq, 0, sizeof Jq);
-            /* rows: species s < ns-1 (row nF + s).  Columns in coupled variables: rho (0) is
-             * d/d rho_ns, rho_r (nF + r) is d/d rho_r - d/d rho_ns since
-             * rho_ns = rho - sum_{r<ns-1} rho_r (Sec. 2.3.3); m, rhoE, [rho e_v] columns
-             * (1..nF-1) map to full columns ns.. */
-            for (int s = 0; s < ns - 1; s++) {
+            /* rows: species s = 1..ns-1 (row nF + s - 1).  Columns in coupled variables: rho
+             * (0) is d/d rho_1st, rho_r (nF + r - 1) is d/d rho_r - d/d rho_1st since the first
+             * species is rho - sum_{r>0} rho_r (Sec. 2.3.3, see jvp_ci); m, rhoE, [rho e_v]
+             * columns (1..nF-1) map to full columns ns.. */
+            for (int s = 1; s < ns; s++) {
                 const double *row = &Jq[s * nq];
-                A[(nF + s) * n + 0] -= G->V[c] * row[ns - 1];
-                for (int k = 1; k < nF; k++) A[(nF + s) * n + k] -= G->V[c] * row[ns + k - 1];
-                for (int r = 0; r < ns - 1; r++)
-                    A[(nF + s) * n + nF + r] -= G->V[c] * (row[r] - row[ns - 1]);
+                A[(nF + s - 1) * n + 0] -= G->V[c] * row[0];
+                for (int k = 1; k < nF; k++) A[(nF + s - 1) * n + k] -= G->V[c] * row[ns + k - 1];
+                for (int r = 1; r < ns; r++)
+                    A[(nF + s - 1) * n + nF + r - 1] -= G->V[c] * (row[r] - row[0]);
             }
         }
     }
@@ -1453,22 +1453,26 @@ static void jvp_flow(const orc_grid *G, const prim_t *w, const double *S, const 
     for (int k = 1; k < nF; k++) out[k] = o[ns + k - 1];
 }
 
-/* Coupled (CI) variables (Sec. 2.3.3): (rho, m, rhoE, [rho e_v], rho_1..rho_{ns-1}),
- * rho_ns = rho - sum_{s<ns} rho_s. */
+/* Coupled (CI) variables (Sec. 2.3.3): (rho, m, rhoE, [rho e_v], rho_s for s = 2..ns); one
+ * species density is eliminated through rho_1 = rho - sum_{s>1} rho_s.  Reading: the paper
+ * eliminates its ns-th species, which in its 11-species list is the electron (about 1e-8 of
+ * the density): taking it as a difference of the total and the others loses all its digits
+ * and leaves the coupled blocks singular to working precision.  The eliminated species is
+ * therefore the first of the list, N2, the most abundant in air. */
 static void jvp_ci(const orc_grid *G, const prim_t *w, const double *S, const double *dc, double *out)
 {
     int ns = G->gas.ns, nF = G->nF;
     double dq[NQMAX], o[NQMAX];
-    double last = dc[0];
-    for (int s = 0; s < ns - 1; s++) { dq[s] = dc[nF + s]; last -= dc[nF + s]; }
-    dq[ns - 1] = last;
+    double first = dc[0];
+    for (int s = 1; s < ns; s++) { dq[s] = dc[nF + s - 1]; first -= dc[nF + s - 1]; }
+    dq[0] = first;
     for (int k = 1; k < nF; k++) dq[ns + k - 1] = dc[k];
     jvp_full(G, w, S, dq, o);
     double orho = 0.0;
     for (int s = 0; s < ns; s++) orho += o[s];
     out[0] = orho;
     for (int k = 1; k < nF; k++) out[k] = o[ns + k - 1];
-    for (int s = 0; s < ns - 1; s++) out[nF + s] = o[s];
+    for (int s = 1; s < ns; s++) out[nF + s - 1] = o[s];
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -1573,7 +1577,7 @@ static int lusgs_split(orc_grid *G, double cfl)
 }
 
 /* coupled operator (Sec. 2.2 with the unified radius; Sec. 2.3.3 ns-1 species):
- * dQ layout (rho, m, rhoE, [rho e_v], rho_1..rho_{ns-1}) */
+ * dQ layout (rho, m, rhoE, [rho e_v], rho_2..rho_ns) */
 static int lusgs_coupled(orc_grid *G, double cfl)
 {
     if (!G->have_R) { snprintf(G->err, sizeof(G->err), "residual not evaluated"); return 7; }
@@ -1592,7 +1596,7 @@ static int lusgs_coupled(orc_grid *G, double cfl)
         for (int s = 0; s < ns; s++) rr += G->R[(size_t)s * N + c];
         acc[0] = -rr;
         for (int k = 1; k < nF; k++) acc[k] = -G->R[(size_t)(ns + k - 1) * N + c];
-        for (int s = 0; s < ns - 1; s++) acc[nF + s] = -G->R[(size_t)s * N + c];
+        for (int s = 1; s < ns; s++) acc[nF + s - 1] = -G->R[(size_t)s * N + c];
         gather(G, c, 1, n, x, N, jvp_ci, G->lamCI, acc);
         lu_solve(&G->DLU[(size_t)c * n * n], &G->piv[(size_t)c * n], n, acc);
         for (int k = 0; k < n; k++) x[(size_t)k * N + c] = acc[k];
@@ -1612,8 +1616,8 @@ static int lusgs_coupled(orc_grid *G, double cfl)
  * Reading: the weight of correction 1 is W_s = rho_s^m / sum_r rho_r^m (the printed weight
  * does not sum to one, contradicting the conservation statement that follows it).  With
  * clip = 1, negative densities are set to zero (commented-out remark at the end of Sec. 2.3.3)
- * and counted.  mode 1: CS-1, mode 2: CS-2, mode 0: coupled (CI) update with
- * rho_ns = rho - sum_{s<ns} rho_s.
+ * and counted.  mode 1: CS-1, mode 2: CS-2, mode 0: coupled (CI) update with the
+ * eliminated (first) species = rho - sum of the others.
  * ------------------------------------------------------------------------------------- */
 static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
 {
@@ -1650,8 +1654,8 @@ static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
             for (int s = 0; s < ns; s++) out[s] = rnew * t[s] / sum;
         } else {
             double sum = 0.0;
-            for (int s = 0; s < ns - 1; s++) { out[s] = rs[s] + dq[(size_t)(nF + s) * N + c]; sum += out[s]; }
-            out[ns - 1] = rnew - sum;
+            for (int s = 1; s < ns; s++) { out[s] = rs[s] + dq[(size_t)(nF + s - 1) * N + c]; sum += out[s]; }
+            out[0] = rnew - sum;
         }
         for (int s = 0; s < ns; s++) {
             if (clip && out[s] < 0.0 && mode != 2) { out[s] = 0.0; G->nclip++; }

@@ -1349,13 +1349,14 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
 #pragma unroll
     for (int s = 0; s < NS; ++s) out[s] = t[s] * f;
   } else {
+    // coupled update: the first species is the remainder of the new total density
     double sum = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS - 1; ++s) {
-      out[s] = rs[s] + dq[(NF + s) * N + c];
+    for (int s = 1; s < NS; ++s) {
+      out[s] = rs[s] + dq[(NF + s - 1) * N + c];
       sum += out[s];
     }
-    out[NS - 1] = rnew - sum;
+    out[0] = rnew - sum;
   }
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -1373,8 +1374,9 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
 }
 
 // ---------------------------------------------------------------------------------------
-// Coupled (CI) operator: dense diagonal blocks (V/dtau + sum lambda) I - V dS/dQ_CI with
-// rho_ns = rho - sum_{s<ns} rho_s (Sec. 2.2, Sec. 2.3.3), LU with partial pivoting per cell.
+// Coupled (CI) operator: dense diagonal blocks (V/dtau + sum lambda) I - V dS/dQ_CI with one
+// species eliminated through the total density (Sec. 2.2, Sec. 2.3.3; the eliminated species
+// is the first of the list, N2, not the electron: see jvp_ci), LU with partial pivoting.
 // ---------------------------------------------------------------------------------------
 template <class G, int ND>
 __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
@@ -1420,17 +1422,20 @@ __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
       dT[NQ - 1] = -1.0 / rc;
       dTv[NQ - 1] = (w.cvve > 0.0) ? 1.0 / (w.rho * w.cvve) : 0.0;
     }
-    for (int s = 0; s < NS - 1; ++s) {
-      // full-layout row of d omega_s / dQ
-      auto jq = [&](int kcol) {
+    // rows: species s = 1..NS-1; the first species (N2) is the eliminated one,
+    // rho_1st = rho - sum_{r>0} rho_r, so column rho is d/d rho_1st and column rho_r is
+    // d/d rho_r - d/d rho_1st
+    for (int s = 1; s < NS; ++s) {
+      auto jq = [&](int kcol) {   // full-layout row of d omega_s / dQ
         double v = wT[s] * dT[kcol] + wTv[s] * dTv[kcol];
         if (kcol < NS) v += J[s * NS + kcol];
         return v;
       };
-      const double last = jq(NS - 1);
-      M[(NF + s) * NC + 0] -= V * last;
-      for (int kk = 1; kk < NF; ++kk) M[(NF + s) * NC + kk] -= V * jq(NS + kk - 1);
-      for (int r = 0; r < NS - 1; ++r) M[(NF + s) * NC + NF + r] -= V * (jq(r) - last);
+      const double first = jq(0);
+      double* row = M + (NF + s - 1) * NC;
+      row[0] -= V * first;
+      for (int kk = 1; kk < NF; ++kk) row[kk] -= V * jq(NS + kk - 1);
+      for (int r = 1; r < NS; ++r) row[NF + r - 1] -= V * (jq(r) - first);
     }
   }
   // LU with partial pivoting (ties: lowest row), in place
@@ -1476,7 +1481,8 @@ __device__ __forceinline__ void lu_solve(const double* M, const int* piv, double
   }
 }
 
-// coupled Jacobian-vector product in CI variables (rho, m, rhoE, [rho e_v], rho_1..rho_{ns-1})
+// coupled Jacobian-vector product in CI variables (rho, m, rhoE, [rho e_v], rho_2..rho_ns);
+// the first species is eliminated: rho_1st = rho - sum of the others
 template <class G, int ND>
 __device__ __forceinline__ void jvp_ci(const DevGrid& g, int nb, const double* S, const double* x,
                                        double* y) {
@@ -1486,12 +1492,12 @@ __device__ __forceinline__ void jvp_ci(const DevGrid& g, int nb, const double* S
   const double* W = g.W;
   const double rho = W[A::RHO * N + nb], beta = W[A::BETA * N + nb];
   double u[ND], U = 0.0, Sdm = 0.0, dp = 0.0;
-  double last = x[0];
-  for (int s = 0; s < NS - 1; ++s) {
-    dp += W[(A::PRS + s) * N + nb] * x[NF + s];
-    last -= x[NF + s];
+  double first = x[0];
+  for (int s = 1; s < NS; ++s) {
+    dp += W[(A::PRS + s) * N + nb] * x[NF + s - 1];
+    first -= x[NF + s - 1];
   }
-  dp += W[(A::PRS + NS - 1) * N + nb] * last;
+  dp += W[(A::PRS + 0) * N + nb] * first;
   for (int d = 0; d < ND; ++d) {
     u[d] = W[(A::U + d) * N + nb];
     U += u[d] * S[d];
@@ -1506,7 +1512,7 @@ __device__ __forceinline__ void jvp_ci(const DevGrid& g, int nb, const double* S
   const double rhoE = g.Q[(NS + ND) * N + nb], p = W[A::P * N + nb];
   y[ND + 1] = (x[ND + 1] + dp) * U + (rhoE + p) * dU;
   if (G::NTEMP == 2) y[NF - 1] = x[NF - 1] * U + g.Q[(A::NQ - 1) * N + nb] * dU;
-  for (int s = 0; s < NS - 1; ++s) y[NF + s] = x[NF + s] * U + rho * W[(A::Y + s) * N + nb] * dU;
+  for (int s = 1; s < NS; ++s) y[NF + s - 1] = x[NF + s - 1] * U + rho * W[(A::Y + s) * N + nb] * dU;
 }
 
 template <class G, int ND, bool FWD>
@@ -1524,7 +1530,7 @@ __global__ void __launch_bounds__(64) k_sweep_coupled(DevGrid g, int h, int off,
     for (int s = 0; s < NS; ++s) rr += g.R[s * N + c];
     acc[0] = -rr;
     for (int q = 1; q < NF; ++q) acc[q] = -g.R[(NS + q - 1) * N + c];
-    for (int s = 0; s < NS - 1; ++s) acc[NF + s] = -g.R[s * N + c];
+    for (int s = 1; s < NS; ++s) acc[NF + s - 1] = -g.R[s * N + c];
   } else {
     for (int q = 0; q < NC; ++q) acc[q] = 0.0;
   }

@@ -97,7 +97,7 @@ def rhs(g, R, scheme):
         return (-R[:ns]).T.reshape(-1)
     flow = np.concatenate([[R[:ns].sum(axis=0)], R[ns:]])
     if scheme == 2:
-        flow = np.concatenate([flow, R[:ns - 1]])
+        flow = np.concatenate([flow, R[1:ns]])
     return (-flow).T.reshape(-1)
 
 
@@ -129,10 +129,6 @@ def test_split_sweeps_equal_dense_factored_solve(name):
 @pytest.mark.parametrize("name", list(CASES))
 def test_coupled_sweeps_equal_dense_factored_solve(name):
     g, Q = make_case(name, seed=3)
-    if g.ns == 11:
-        # the ionised mixture's source Jacobian makes the coupled blocks so ill-conditioned
-        # (electron rows, cond ~1e15) that a global dense solve cannot serve as reference
-        g.set_reacting(False)
     R, _ = g.residual()
     cfl = 4.0
     g.build_diagonals(cfl)
@@ -140,8 +136,10 @@ def test_coupled_sweeps_equal_dense_factored_solve(name):
     x = scaled_factored_solve(g, Q, 2, D, L, U, rhs(g, R, 2))
     dQ = g.lusgs_coupled(cfl)
     x = x.reshape(g.ncell, g.nci).T
-    # the coupled blocks mix species and flow columns; the reference dense solve keeps ~1e-8
-    assert np.max(np.abs(dQ - x).max(axis=1) / np.abs(x).max(axis=1)) < 1e-7
+    # the coupled blocks carry the source Jacobian; for the ionised mixture their
+    # equilibrated condition number is ~4e7, so the dense reference keeps ~1e-7
+    tol = 1e-7 if g.ns < 11 else 1e-6
+    assert np.max(np.abs(dQ - x).max(axis=1) / np.abs(x).max(axis=1)) < tol
 
 
 @pytest.mark.parametrize("scheme", [0, 2])
@@ -204,11 +202,11 @@ def test_corrections_identities():
     # coupled update: rho_ns is the remainder of the total density
     dci = np.zeros((g.nci, N))
     dci[:nF] = dQ[:nF]
-    dci[nF:] = dQ[nF:nF + ns - 1]
+    dci[nF:] = dQ[nF + 1:nF + ns]
     g.set_state(Q)
     g.correct(0, 0, dci)
     Qc = g.get_state()
-    assert np.max(np.abs(Qc[:ns - 1] - (Q[:ns - 1] + dci[nF:])) / rho) < 1e-15
+    assert np.max(np.abs(Qc[1:ns] - (Q[1:ns] + dci[nF:])) / rho) < 1e-15
     assert np.max(np.abs(Qc[:ns].sum(axis=0) / (rho + dQ[0]) - 1)) < 1e-15
 
 

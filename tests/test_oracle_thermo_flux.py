@@ -116,9 +116,9 @@ def fd_jacobian(mech, nd, q, S, which):
         if which == 1:      # flow block (rho, m, E, [ev]) with frozen mass fractions
             full[:ns] = Y * x[0]
             full[ns:] = x[1:nF]
-        else:               # coupled variables (rho, m, E, [ev], rho_1..rho_{ns-1})
-            full[:ns - 1] = x[nF:]
-            full[ns - 1] = x[0] - x[nF:].sum()
+        else:               # coupled variables (rho, m, E, [ev], rho_2..rho_ns)
+            full[1:ns] = x[nF:]
+            full[0] = x[0] - x[nF:].sum()
             full[ns:] = x[1:nF]
         return full
 
@@ -127,7 +127,7 @@ def fd_jacobian(mech, nd, q, S, which):
             return F
         out = np.concatenate([[F[:ns].sum()], F[ns:]])
         if which == 2:
-            out = np.concatenate([out, F[:ns - 1]])
+            out = np.concatenate([out, F[1:ns]])
         return out
 
     n = nq if which == 0 else (nF if which == 1 else nq)
