@@ -161,6 +161,11 @@ cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
  * and enables (enable = 1) or disables timing. */
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
 
+/* Implementation options (not part of the method): "cluster_sweep" = 1 (default) runs the 2D
+ * split sweeps as one cluster launch where the device supports it, 0 forces one launch per
+ * hyperplane.  Both give the same arithmetic.  Errors: CS_ERR_ARG for an unknown name. */
+cs_status cs_set_option(cs_grid g, const char *name, double value);
+
 const char *cs_last_error(cs_grid g);
 
 #ifdef __cplusplus

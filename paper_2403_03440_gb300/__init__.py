@@ -97,7 +97,7 @@ class cs_step_stats(C.Structure):
 EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary",
            "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
-           "cs_gas_info", "cs_profile", "cs_last_error"]
+           "cs_gas_info", "cs_profile", "cs_set_option", "cs_last_error"]
 
 _lib = None
 
@@ -126,6 +126,7 @@ def lib():
     L.cs_get_field.argtypes = [vp, C.c_char_p, vp, ip]
     L.cs_gas_info.argtypes = [C.c_int, dp, dp, ip]
     L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
+    L.cs_set_option.argtypes = [vp, C.c_char_p, C.c_double]
     L.cs_last_error.argtypes = [vp]
     L.cs_last_error.restype = C.c_char_p
     for name in EXPORTS:
@@ -271,6 +272,9 @@ class Grid:
 
     PHASES = ["primitive", "gradient", "flux", "assemble", "spectral", "sweep_fwd",
               "sweep_bwd", "correct"]
+
+    def set_option(self, name, value):
+        self._check(lib().cs_set_option(self._h, name.encode(), float(value)), "cs_set_option")
 
     def profile(self, enable):
         """Return {phase: (ms, launches)} accumulated since the last call; (re)arm timing."""

@@ -345,6 +345,8 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   ALLOC(d.DFev, N);
   ALLOC(d.Ds, (size_t)L->ns * N);
   ALLOC(d.Vdt, N);
+  ALLOC(d.invD, (size_t)(2 + L->ns) * N);
+  ALLOC(d.rhsF, (size_t)L->nF * N);
   ALLOC(d.dQs, (size_t)(L->nF + L->ns) * N);
   ALLOC(d.dQ, (size_t)(L->nF + L->ns) * N);
   ALLOC(d.dQcs, (size_t)L->nci * N);
@@ -617,9 +619,12 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
     int nf, nb;
     if (o->scheme == CS_SCHEME_SPLIT) {
       prof_record(g, slot, 5);
-      nf = g->L->sweep_split_dir(d, g->stream, true);
+      // the cluster path runs both sweeps in one launch (timed as phase 5)
+      nf = g->L->use_cluster ? g->L->sweep_split_cluster(d, g->stream) : 0;
+      nb = 0;
+      if (!nf) nf = g->L->sweep_split_dir(d, g->stream, true);
       prof_record(g, slot, 6);
-      nb = g->L->sweep_split_dir(d, g->stream, false);
+      if (!g->L->use_cluster || !g->L->sweep_split_cluster_ok) nb = g->L->sweep_split_dir(d, g->stream, false);
       prof_record(g, slot, 7);
       g->L->correct(d, g->stream, o->correction, o->clip, d.dQ);
     } else {
@@ -694,6 +699,15 @@ extern "C" cs_status cs_get_field(cs_grid g, const char* name, double* out, int*
   CUDA_TRY(g, cudaStreamSynchronize(g->stream));
   if (count_out) *count_out = (int)n;
   return CS_OK;
+}
+
+extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
+  if (!g || !name) return CS_ERR_ARG;
+  if (!strcmp(name, "cluster_sweep")) {
+    g->L->use_cluster = value != 0.0;
+    return CS_OK;
+  }
+  return fail(g, CS_ERR_ARG, "unknown option %s", name);
 }
 
 extern "C" const char* cs_last_error(cs_grid g) { return g ? g->err : "null grid"; }

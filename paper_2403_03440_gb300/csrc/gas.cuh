@@ -49,19 +49,22 @@ struct ReactionData {
 #define CS_MO 15.9994
 #define CS_ME 5.48579909e-4
 
-__constant__ SpeciesData c_species_air[11] = {
-    {DIATOMIC, 2 * CS_MN, 3395.0, 2.88, 2, 1, 0.0},
-    {DIATOMIC, 2 * CS_MO, 2239.0, 2.08, 2, 3, 0.0},
-    {DIATOMIC, CS_MN + CS_MO, 2817.0, 2.45, 1, 4, 89.77e6},
-    {ATOM, CS_MN, 0.0, 0.0, 1, 4, 470.82e6},
-    {ATOM, CS_MO, 0.0, 0.0, 1, 9, 246.79e6},
-    {DIATOMIC, CS_MN + CS_MO - CS_ME, 3419.0, 2.87, 1, 1, 983.6e6},
-    {DIATOMIC, 2 * CS_MN - CS_ME, 3175.0, 2.78, 2, 2, 1503.3e6},
-    {DIATOMIC, 2 * CS_MO - CS_ME, 2741.0, 2.43, 2, 4, 1164.5e6},
-    {ATOM, CS_MN - CS_ME, 0.0, 0.0, 1, 9, 1873.1e6},
-    {ATOM, CS_MO - CS_ME, 0.0, 0.0, 1, 4, 1560.7e6},
-    {ELECTRON, CS_ME, 0.0, 0.0, 1, 2, 0.0},
-};
+#define CS_AIR_SPECIES                                             \
+  {                                                                \
+    {DIATOMIC, 2 * CS_MN, 3395.0, 2.88, 2, 1, 0.0},                \
+    {DIATOMIC, 2 * CS_MO, 2239.0, 2.08, 2, 3, 0.0},                \
+    {DIATOMIC, CS_MN + CS_MO, 2817.0, 2.45, 1, 4, 89.77e6},        \
+    {ATOM, CS_MN, 0.0, 0.0, 1, 4, 470.82e6},                       \
+    {ATOM, CS_MO, 0.0, 0.0, 1, 9, 246.79e6},                       \
+    {DIATOMIC, CS_MN + CS_MO - CS_ME, 3419.0, 2.87, 1, 1, 983.6e6}, \
+    {DIATOMIC, 2 * CS_MN - CS_ME, 3175.0, 2.78, 2, 2, 1503.3e6},   \
+    {DIATOMIC, 2 * CS_MO - CS_ME, 2741.0, 2.43, 2, 4, 1164.5e6},   \
+    {ATOM, CS_MN - CS_ME, 0.0, 0.0, 1, 9, 1873.1e6},               \
+    {ATOM, CS_MO - CS_ME, 0.0, 0.0, 1, 4, 1560.7e6},               \
+    {ELECTRON, CS_ME, 0.0, 0.0, 1, 2, 0.0},                        \
+  }
+__constant__ SpeciesData c_species_air[11] = CS_AIR_SPECIES;
+static const SpeciesData kSpeciesHost[11] = CS_AIR_SPECIES;   // host copy (derived constants)
 __constant__ SpeciesData c_species_perfect[1] = {
     {DIATOMIC, 28.9647, 0.0, 2.88, 2, 1, 0.0},
 };
@@ -72,6 +75,20 @@ __constant__ SpeciesData c_species_perfect[1] = {
 #define CS_EFF_O2 {1, 1, 1, 5, 5, 1, 1, 1, 5, 5, 0}
 #define CS_EFF_NO {1, 1, 22, 22, 22, 1, 1, 1, 22, 22, 0}
 __constant__ ReactionData c_reactions[21];
+
+// Constants derived on the host from the species table (so that the kernels evaluate no
+// logarithm or power of a constant):
+//  gc0[s]  = -1.5 ln(2 pi m k / h^2) - ln(k / p0) - ln g0 [+ ln(sigma theta_r) for diatomics],
+//            so that g_s/(R T) = h0/(R T) - (2.5 [+1]) ln T + gc0 [+ ln(1 - exp(-theta_v/T))]
+//  mwA[s][q], mwAB[s][q]: Millikan-White tau_sq p = exp(A T^-1/3 - AB), AB = A B + 18.42
+//  cbk[s]  = sqrt(8 R_u / (pi M_s)): mean molecular speed = cbk sqrt(T)
+struct GasConst {
+  double gc0[11];
+  double mwA[11][11];
+  double mwAB[11][11];
+  double cbk[11];
+};
+__constant__ GasConst c_gas;
 
 struct ReactionInit {
   int nr, r0, r1, np, p0, p1, p2, third;

@@ -24,8 +24,8 @@ struct Aux {
                        BETA = C + 1, GAM = BETA + 1, EV = GAM + 1, H = EV + 1, CVTR = H + 1,
                        CVVE = CVTR + 1, CV = CVVE + 1, MU = CV + 1, KT = MU + 1, KV = KT + 1,
                        RHOD = KV + 1, PREV = RHOD + 1, RELAX = PREV + 1, OMV = RELAX + 1,
-                       Y = OMV + 1, PRS = Y + NS, HS = PRS + NS, EVE = HS + NS, OM = EVE + NS,
-                       DOM = OM + NS, COUNT = DOM + NS;
+                       PY = OMV + 1, Y = PY + 1, PRS = Y + NS, HS = PRS + NS, EVE = HS + NS,
+                       OM = EVE + NS, DOM = OM + NS, COUNT = DOM + NS;
   static constexpr int NQ = NS + ND + 1 + (G::NTEMP == 2);
   static constexpr int NF = 1 + ND + 1 + (G::NTEMP == 2);
   static constexpr int NCI = NF + NS - 1;
@@ -63,6 +63,8 @@ struct DevGrid {
   double* dQc;
   double* red;            // reduction scratch
   double* Vdt;            // [N] V / dtau
+  double* invD;           // [2 + ns][N]: 1/D_F, 1/D_F,ev, 1/D_s
+  double* rhsF;           // [nF][N]: -(sum_s R_s, R_m, R_E, [R_ev])
   int* status;            // [0] code, [1] cell, [2] clip count
   const double* params;   // [0] cfl
 };
@@ -332,26 +334,45 @@ __device__ __forceinline__ void store_prim(const DevGrid& g, int c, const Prim<G
 // ---------------------------------------------------------------------------------------
 
 // g_s/(R_u T) and H_s/(R_u T) at the standard pressure, simplified form (translational,
-// rotational and vibrational enthalpy terms cancel between H/RT and S/R).
+// rotational and vibrational enthalpy terms cancel between H/RT and S/R); em = exp(-theta_v/T)
+// is supplied by the caller, iT = 1/T.
 template <class G>
-__device__ __forceinline__ void gibbs(int s, double T, double lnT, double& gRT, double& hRT) {
+__device__ __forceinline__ void gibbs(int s, double iT, double lnT, double em, double& gRT,
+                                      double& hRT) {
   const SpeciesData& d = G::sp(s);
-  const double m = d.M / kNa;
-  // ln[(2 pi m k T / h^2)^{3/2} k T / p0] = 1.5 ln(2 pi m k / h^2) + 2.5 ln T + ln(k/p0)
-  const double lntr = 1.5 * log(2.0 * kPi * m * kKb / (kH * kH)) + 2.5 * lnT + log(kKb / kPref);
-  double g = d.h0 / (kRu * T) - lntr - log(d.g0);
-  double h = 2.5 + d.h0 / (kRu * T);
+  const double hr = d.h0 * (iT / kRu);
+  double g = hr - 2.5 * lnT + c_gas.gc0[s];
+  double h = 2.5 + hr;
   if (d.kind == DIATOMIC) {
-    g -= lnT - log(d.sigma * d.thr);
+    g -= lnT;
     h += 1.0;
     if (d.thv > 0.0) {
-      const double x = d.thv / T, em = exp(-x);
-      g += log(1.0 - em);
-      h += x * em / (1.0 - em);
+      const double x = d.thv * iT, om = 1.0 - em;
+      g += log(om);
+      h += x * em / om;
     }
   }
   gRT = g;
   hRT = h;
+}
+
+// exp(-theta_v/T) of every diatomic species (0 for the others)
+template <class G>
+__device__ __forceinline__ void vib_exp(double iT, double* em) {
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    const SpeciesData& d = G::sp(s);
+    em[s] = (d.kind == DIATOMIC && d.thv > 0.0) ? exp(-d.thv * iT) : 0.0;
+  }
+}
+// harmonic-oscillator energy and heat capacity from em = exp(-theta/T)
+template <class G>
+__device__ __forceinline__ void vib_em(int s, double iT, double em, double& e, double& cv) {
+  const SpeciesData& d = G::sp(s);
+  if (d.kind != DIATOMIC || d.thv <= 0.0) { e = 0.0; cv = 0.0; return; }
+  const double x = d.thv * iT, den = 1.0 - em, R = kRu / d.M;
+  e = R * d.thv * em / den;
+  cv = R * x * x * em / (den * den);
 }
 
 __device__ __forceinline__ double rate_temp(int kind, double T, double Tv) {
@@ -360,9 +381,11 @@ __device__ __forceinline__ double rate_temp(int kind, double T, double Tv) {
 
 // omega[s]; optionally the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s, the full
 // fixed-T Jacobian J[s*NS+r] and the temperature derivatives wT[s], wTv[s].
+// emT/emTv: exp(-theta_v/T) and exp(-theta_v/Tv) of every species (vib_exp).
 template <class G, bool FULL>
-__device__ void chemistry(const double* rhos, double T, double Tv, double* omega, double* jd,
-                          double* J, double* wT, double* wTv) {
+__device__ void chemistry(const double* rhos, double T, double Tv, const double* emT,
+                          const double* emTv, double* omega, double* jd, double* J, double* wT,
+                          double* wTv) {
   constexpr int NS = G::NS;
   double X[NS], gT[NS], hT[NS], gV[NS], hV[NS];
 #pragma unroll
@@ -374,11 +397,14 @@ __device__ void chemistry(const double* rhos, double T, double Tv, double* omega
     wTv[s] = 0.0;
   }
   if (FULL) for (int k = 0; k < NS * NS; ++k) J[k] = 0.0;
-  const double lnT = log(T), lnTv = log(Tv);
+  const double lnT = log(T), lnTv = (G::NTEMP == 2) ? log(Tv) : lnT;
+  const double iT = 1.0 / T, iTv = (G::NTEMP == 2) ? 1.0 / Tv : iT;
+  const double lnTa = 0.5 * (lnT + lnTv), iTa = (G::NTEMP == 2) ? 1.0 / sqrt(T * Tv) : iT;
+  const double lnPT = log(kPref / kRu) - lnT, lnPTv = log(kPref / kRu) - lnTv;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    gibbs<G>(s, T, lnT, gT[s], hT[s]);
-    if (G::NTEMP == 2) gibbs<G>(s, Tv, lnTv, gV[s], hV[s]);
+    gibbs<G>(s, iT, lnT, emT[s], gT[s], hT[s]);
+    if (G::NTEMP == 2) gibbs<G>(s, iTv, lnTv, emTv[s], gV[s], hV[s]);
     else { gV[s] = gT[s]; hV[s] = hT[s]; }
   }
   for (int r = 0; r < G::NR; ++r) {
@@ -390,10 +416,13 @@ __device__ void chemistry(const double* rhos, double T, double Tv, double* omega
     int dn = 0;
     for (int a = 0; a < x.np; ++a) { sg += bv ? gV[x.p[a]] : gT[x.p[a]]; sh += bv ? hV[x.p[a]] : hT[x.p[a]]; ++dn; }
     for (int a = 0; a < x.nr; ++a) { sg -= bv ? gV[x.r[a]] : gT[x.r[a]]; sh -= bv ? hV[x.r[a]] : hT[x.r[a]]; --dn; }
-    const double lnKc = -sg + dn * log(kPref / (kRu * Tb));
-    const double lnTf = log(Tf), lnTb = log(Tb);
-    const double kf = exp(x.lnA + x.n * lnTf - x.theta / Tf);
-    const double kb = exp(x.lnA + x.n * lnTb - x.theta / Tb - lnKc);
+    const double lnKc = -sg + dn * (bv ? lnPTv : lnPT);
+    const double lnTf = x.tf == TK_T ? lnT : (x.tf == TK_V ? lnTv : lnTa);
+    const double iTf = x.tf == TK_T ? iT : (x.tf == TK_V ? iTv : iTa);
+    const double lnTb = x.tb == TK_T ? lnT : (x.tb == TK_V ? lnTv : lnTa);
+    const double iTb = x.tb == TK_T ? iT : (x.tb == TK_V ? iTv : iTa);
+    const double kf = exp(x.lnA + x.n * lnTf - x.theta * iTf);
+    const double kb = exp(x.lnA + x.n * lnTb - x.theta * iTb - lnKc);
     double M = 1.0;
     if (x.third) {
       M = 0.0;
@@ -405,12 +434,12 @@ __device__ void chemistry(const double* rhos, double T, double Tv, double* omega
     for (int a = 0; a < x.np; ++a) Pb *= X[x.p[a]];
     const double Rf = kf * Pf * M, Rb = kb * Pb * M;
     // temperature derivatives of ln k
-    const double dlf = x.n / Tf + x.theta / (Tf * Tf);
-    const double dlb = x.n / Tb + x.theta / (Tb * Tb) - (sh / Tb - dn / Tb);
-    const double fT = x.tf == TK_T ? 1.0 : (x.tf == TK_A ? 0.5 * Tf / T : 0.0);
-    const double fV = x.tf == TK_V ? 1.0 : (x.tf == TK_A ? 0.5 * Tf / Tv : 0.0);
-    const double bT = x.tb == TK_T ? 1.0 : (x.tb == TK_A ? 0.5 * Tb / T : 0.0);
-    const double bVv = x.tb == TK_V ? 1.0 : (x.tb == TK_A ? 0.5 * Tb / Tv : 0.0);
+    const double dlf = (x.n + x.theta * iTf) * iTf;
+    const double dlb = (x.n + x.theta * iTb - (sh - dn)) * iTb;
+    const double fT = x.tf == TK_T ? 1.0 : (x.tf == TK_A ? 0.5 * Tf * iT : 0.0);
+    const double fV = x.tf == TK_V ? 1.0 : (x.tf == TK_A ? 0.5 * Tf * iTv : 0.0);
+    const double bT = x.tb == TK_T ? 1.0 : (x.tb == TK_A ? 0.5 * Tb * iT : 0.0);
+    const double bVv = x.tb == TK_V ? 1.0 : (x.tb == TK_A ? 0.5 * Tb * iTv : 0.0);
     const double dRT = Rf * dlf * fT - Rb * dlb * bT;
     const double dRV = Rf * dlf * fV - Rb * dlb * bVv;
     const double net = Rf - Rb;
@@ -480,8 +509,10 @@ __device__ __forceinline__ void dT_drho(const Prim<G, ND>& w, int s, double evs,
 }
 
 // Millikan-White + Park vibrational relaxation and the vibrational source (2T).
+// emT/emTv: exp(-theta_v/T), exp(-theta_v/Tv) per species.
 template <class G, int ND>
-__device__ void vib_source(const Prim<G, ND>& w, const double* omega, double& omv, double& relax) {
+__device__ void vib_source(const Prim<G, ND>& w, const double* omega, const double* emT,
+                           const double* emTv, double& omv, double& relax) {
   constexpr int NS = G::NS;
   double X[NS], xs = 0.0, ph = 0.0;
 #pragma unroll
@@ -492,32 +523,30 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, double& om
     xs += X[s];
     ph += w.rhos[s] * Rs<G>(s) * w.T;
   }
-  const double patm = ph / kPref, nden = xs * kNa, T13 = pow(w.T, -1.0 / 3.0);
+  const double patm = ph / kPref, nden = xs * kNa, T13 = rcbrt(w.T);
+  const double iT = 1.0 / w.T, iTv = 1.0 / w.Tv, sqT = sqrt(w.T);
+  const double sv = 1e-21 * (50000.0 * iT) * (50000.0 * iT);
   double lt = 0.0, rc = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const SpeciesData& d = G::sp(s);
     if (d.kind == DIATOMIC && d.thv > 0.0) {
+      // 1/tau_MW = sum_q X_q / tau_sq / sum_q X_q, tau_sq = exp(A T^-1/3 - AB) / p_atm
       double num = 0.0, den = 0.0;
 #pragma unroll
       for (int q = 0; q < NS; ++q) {
         if (G::sp(q).kind == ELECTRON) continue;
-        const double Mq = G::sp(q).M;
-        const double mu = d.M * Mq / (d.M + Mq);
-        const double A = 1.16e-3 * sqrt(mu) * pow(d.thv, 4.0 / 3.0);
-        const double B = 0.015 * pow(mu, 0.25);
-        const double tsq = exp(A * (T13 - B) - 18.42) / patm;
         num += X[q];
-        den += X[q] / tsq;
+        den += X[q] * exp(c_gas.mwAB[s][q] - c_gas.mwA[s][q] * T13);
       }
-      const double cbar = sqrt(8.0 * kRu * w.T / (kPi * d.M));
-      const double sv = 1e-21 * (50000.0 / w.T) * (50000.0 / w.T);
-      const double tau = num / den + 1.0 / (nden * sv * cbar);
+      den *= patm;
+      const double tau = num / den + 1.0 / (nden * sv * c_gas.cbk[s] * sqT);
+      const double itau = 1.0 / tau;
       double eT, cT, eV, cV;
-      vib<G>(s, w.T, eT, cT);
-      vib<G>(s, w.Tv, eV, cV);
-      lt += w.rhos[s] * (eT - eV) / tau;
-      rc += w.rhos[s] * cV / tau;
+      vib_em<G>(s, iT, emT[s], eT, cT);
+      vib_em<G>(s, iTv, emTv[s], eV, cV);
+      lt += w.rhos[s] * (eT - eV) * itau;
+      rc += w.rhos[s] * cV * itau;
     }
     const double ep = (d.kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
     lt += omega[s] * ep;
@@ -548,17 +577,22 @@ __global__ void __launch_bounds__(128) k_primitive(DevGrid g) {
   double om[G::NS], jd[G::NS], wT[G::NS], wTv[G::NS];
   double omv = 0.0, relax = 0.0;
   if (g.react && G::NR > 0) {
-    chemistry<G, false>(w.rhos, w.T, w.Tv, om, jd, nullptr, wT, wTv);
+    double emT[G::NS], emTv[G::NS];
+    const double iT = 1.0 / w.T;
+    vib_exp<G>(iT, emT);
+    if (G::NTEMP == 2) vib_exp<G>(1.0 / w.Tv, emTv);
+    else for (int s = 0; s < G::NS; ++s) emTv[s] = emT[s];
+    chemistry<G, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
 #pragma unroll
     for (int s = 0; s < G::NS; ++s) {
       double ev = 0.0, cvv;
-      if (G::NTEMP == 1) vib<G>(s, w.T, ev, cvv);
+      if (G::NTEMP == 1) vib_em<G>(s, iT, emT[s], ev, cvv);
       else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
       double dT, dTv;
       dT_drho<G, ND>(w, s, ev, dT, dTv);
       jd[s] += wT[s] * dT + wTv[s] * dTv;
     }
-    if (G::NTEMP == 2) vib_source<G, ND>(w, om, omv, relax);
+    if (G::NTEMP == 2) vib_source<G, ND>(w, om, emT, emTv, omv, relax);
   } else {
 #pragma unroll
     for (int s = 0; s < G::NS; ++s) { om[s] = 0.0; jd[s] = 0.0; }
@@ -1150,11 +1184,26 @@ __global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
   }
   const double Vdt = sumdt / g.params[0];
   g.Vdt[c] = Vdt;
-  g.DF[c] = Vdt + sF;
-  g.DFev[c] = Vdt + sF + V * W[A::RELAX * N + c];
+  const double DF = Vdt + sF, DFev = Vdt + sF + V * W[A::RELAX * N + c];
+  g.DF[c] = DF;
+  g.DFev[c] = DFev;
+  g.invD[c] = 1.0 / DF;
+  g.invD[N + c] = 1.0 / DFev;
+  double py = 0.0, rr = 0.0;
 #pragma unroll
-  for (int s = 0; s < G::NS; ++s)
-    g.Ds[s * N + c] = Vdt + sC + V * fmax(0.0, -W[(A::DOM + s) * N + c]);
+  for (int s = 0; s < G::NS; ++s) {
+    const double Ds = Vdt + sC + V * fmax(0.0, -W[(A::DOM + s) * N + c]);
+    g.Ds[s * N + c] = Ds;
+    g.invD[(2 + s) * N + c] = 1.0 / Ds;
+    py += W[(A::Y + s) * N + c] * W[(A::PRS + s) * N + c];
+    rr += g.R[s * N + c];
+  }
+  // per-cell inputs of the sweeps: p_Y = sum_s Y_s dp/drho_s (frozen-composition pressure
+  // derivative of the flow block) and the flow right-hand side
+  g.W[A::PY * N + c] = py;
+  g.rhsF[c] = -rr;
+#pragma unroll
+  for (int q = 1; q < A::NF; ++q) g.rhsF[q * N + c] = -g.R[(G::NS + q - 1) * N + c];
   if (g.DLU) g.DLU[(size_t)c * A::NCI * A::NCI] = sCI;   // sum of coupled radii, read by k_ci_block
 }
 
@@ -1180,10 +1229,7 @@ __device__ __forceinline__ void load_state(const DevGrid& g, int c, CellState<G,
   s.rhoev = (G::NTEMP == 2) ? g.Q[(A::NQ - 1) * N + c] : 0.0;
   s.beta = W[A::BETA * N + c];
   s.prev = W[A::PREV * N + c];
-  double py = 0.0;
-#pragma unroll
-  for (int sp = 0; sp < G::NS; ++sp) py += W[(A::Y + sp) * N + c] * W[(A::PRS + sp) * N + c];
-  s.pY = py;
+  s.pY = W[A::PY * N + c];
 }
 
 // flow block: x = (drho, dm, drhoE, [drho e_v]) -> A(S) x
@@ -1239,16 +1285,10 @@ __global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, i
   const size_t N = g.N;
   double acc[NF], accs[NS];
   if (FWD) {
-    double rr = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const double r = g.R[s * N + c];
-      rr += r;
-      accs[s] = -r;
-    }
-    acc[0] = -rr;
+    for (int s = 0; s < NS; ++s) accs[s] = -g.R[s * N + c];
 #pragma unroll
-    for (int q = 1; q < NF; ++q) acc[q] = -g.R[(NS + q - 1) * N + c];
+    for (int q = 0; q < NF; ++q) acc[q] = g.rhsF[q * N + c];
   } else {
 #pragma unroll
     for (int q = 0; q < NF; ++q) acc[q] = 0.0;
@@ -1290,15 +1330,255 @@ __global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, i
   double* Y = FWD ? g.dQs : g.dQ;
 #pragma unroll
   for (int q = 0; q < NF; ++q) {
-    const double D = (G::NTEMP == 2 && q == NF - 1) ? g.DFev[c] : g.DF[c];
-    const double v = acc[q] / D;
+    const double iD = (G::NTEMP == 2 && q == NF - 1) ? g.invD[N + c] : g.invD[c];
+    const double v = acc[q] * iD;
     Y[q * N + c] = FWD ? v : g.dQs[q * N + c] + v;
   }
 #pragma unroll
   for (int sp = 0; sp < NS; ++sp) {
-    const double v = accs[sp] / g.Ds[sp * N + c];
+    const double v = accs[sp] * g.invD[(2 + sp) * N + c];
     Y[(NF + sp) * N + c] = FWD ? v : g.dQs[(NF + sp) * N + c] + v;
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// K6b: split LU-SGS sweeps in thread-block clusters (2D).  The flow block and every species
+// equation are independent operators (Sec. 2.3: "solved without specific order"), so each
+// gets its own cluster: cluster 0 sweeps the flow block, cluster 1+s species s.  In a cluster
+// of C CTAs, CTA r owns rows j in [r R, (r+1) R), one thread per row; at hyperplane h the
+// thread of row j updates cell (h - j, j).  The recurrence stays on chip: the previous cell of
+// the row (and the first cell, for the periodic wrap in i) is in registers, the row below /
+// above comes from shared memory, across a CTA boundary through distributed shared memory,
+// and one hardware cluster barrier separates consecutive hyperplanes.  Forward and backward
+// sweeps run in the same launch.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ unsigned cluster_ctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(r));
+  return r;
+}
+// generic address of the same shared variable in CTA `rank` of the cluster
+template <class T>
+__device__ __forceinline__ T* dsmem(T* p, unsigned rank) {
+  unsigned long long in = reinterpret_cast<unsigned long long>(p), out;
+  asm volatile("mapa.u64 %0, %1, %2;\n" : "=l"(out) : "l"(in), "r"(rank));
+  return reinterpret_cast<T*>(out);
+}
+
+constexpr int kClusterRows = 32;   // rows per CTA (one warp)
+
+template <class G, int NV>
+struct Xchg {
+  double v[2][kClusterRows][NV];
+};
+
+// one neighbour contribution of the flow block: nb on side s of direction d
+template <class G>
+__device__ __forceinline__ void flow_contrib(const CellState<G, 2>& w, double lam, const double* Sf,
+                                             const double* xn, int side, double* acc) {
+  constexpr int NF = Aux<G, 2>::NF;
+  double ax[NF];
+  jvp_flow<G, 2>(w, Sf, xn, ax);
+#pragma unroll
+  for (int q = 0; q < NF; ++q) {
+    if (side < 0) acc[q] += 0.5 * (ax[q] + lam * xn[q]);
+    else acc[q] -= 0.5 * (ax[q] - lam * xn[q]);
+  }
+}
+
+template <class G>
+__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF>& xc) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
+  const int t = threadIdx.x;
+  const int j = rank * R + t;
+  const bool row = t < R && j < g.nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double prevx[NF], firstx[NF];
+    CellState<G, 2> prevS, firstS;
+    double prevL = 0.0, firstL = 0.0;
+    for (int q = 0; q <= H; ++q) {
+      const int h = fwd ? q : H - q;
+      const int i = h - j;
+      const bool act = row && i >= 0 && i < ni;
+      // loads that do not depend on the other rows (issued before the barrier wait)
+      CellState<G, 2> me, jn;
+      double lam0 = 0.0, jlam = 0.0, iD = 0.0, iDev = 0.0, base[NF];
+      const double *Si = nullptr, *Sj = nullptr, *Sw = nullptr;
+      const int jj = fwd ? j - 1 : j + 1;
+      const bool hasj = act && jj >= 0 && jj < nj;
+      int c = 0;
+      if (act) {
+        c = i + ni * j;
+        load_state<G, 2>(g, c, me);
+        lam0 = g.lamF[c];
+        iD = g.invD[c];
+        iDev = g.invD[N + c];
+#pragma unroll
+        for (int v = 0; v < NF; ++v) base[v] = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
+        Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
+        Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
+        Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
+        if (hasj) {
+          const int cn = i + ni * jj;
+          load_state<G, 2>(g, cn, jn);
+          jlam = g.lamF[N + cn];
+        }
+      }
+      if (q > 0) cluster_wait();
+      if (act) {
+        double acc[NF];
+#pragma unroll
+        for (int v = 0; v < NF; ++v) acc[v] = fwd ? base[v] : 0.0;
+        if (fwd) {
+          if (i > 0) flow_contrib<G>(prevS, prevL, Si, prevx, -1, acc);
+          if (per && i == ni - 1) flow_contrib<G>(firstS, firstL, Sw, firstx, +1, acc);
+        } else {
+          if (per && i == 0) flow_contrib<G>(firstS, firstL, Sw, firstx, -1, acc);
+          if (i < ni - 1) flow_contrib<G>(prevS, prevL, Si, prevx, +1, acc);
+        }
+        if (hasj) {
+          const double* src;
+          const int par = (q - 1) & 1;
+          if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
+          double xn[NF];
+#pragma unroll
+          for (int v = 0; v < NF; ++v) xn[v] = src[v];
+          flow_contrib<G>(jn, jlam, Sj, xn, fwd ? -1 : +1, acc);
+        }
+        double x[NF];
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          const double d = (G::NTEMP == 2 && v == NF - 1) ? iDev : iD;
+          x[v] = fwd ? acc[v] * d : base[v] + acc[v] * d;
+          (fwd ? g.dQs : g.dQ)[v * N + c] = x[v];
+          xc.v[q & 1][t][v] = x[v];
+          prevx[v] = x[v];
+        }
+        prevS = me;
+        prevL = lam0;
+        if (i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) firstx[v] = x[v];
+          firstS = me;
+          firstL = lam0;
+        }
+      }
+      cluster_arrive();
+    }
+    cluster_wait();
+    (void)C;
+  }
+}
+
+template <class G>
+__device__ void sweep_species_cluster(const DevGrid& g, int R, int s, Xchg<G, 1>& xc) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank();
+  const int t = threadIdx.x;
+  const int j = rank * R + t;
+  const bool row = t < R && j < g.nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const double* X = g.dQs + (size_t)(NF + s) * N;
+  double* Yf = g.dQs + (size_t)(NF + s) * N;
+  double* Yb = g.dQ + (size_t)(NF + s) * N;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double prevx = 0.0, firstx = 0.0, prevU[2] = {0, 0}, firstU[2] = {0, 0}, prevL = 0.0, firstL = 0.0;
+    for (int q = 0; q <= H; ++q) {
+      const int h = fwd ? q : H - q;
+      const int i = h - j;
+      const bool act = row && i >= 0 && i < ni;
+      const int jj = fwd ? j - 1 : j + 1;
+      const bool hasj = act && jj >= 0 && jj < nj;
+      double u0 = 0, u1 = 0, lam0 = 0, iD = 0, base = 0, ju0 = 0, ju1 = 0, jlam = 0;
+      const double *Si = nullptr, *Sj = nullptr, *Sw = nullptr;
+      int c = 0;
+      if (act) {
+        c = i + ni * j;
+        u0 = g.W[A::U * N + c];
+        u1 = g.W[(A::U + 1) * N + c];
+        lam0 = g.lamC[c];
+        iD = g.invD[(2 + s) * N + c];
+        base = fwd ? -g.R[(size_t)s * N + c] : X[c];
+        Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
+        Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
+        Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
+        if (hasj) {
+          const int cn = i + ni * jj;
+          ju0 = g.W[A::U * N + cn];
+          ju1 = g.W[(A::U + 1) * N + cn];
+          jlam = g.lamC[N + cn];
+        }
+      }
+      if (q > 0) cluster_wait();
+      if (act) {
+        double acc = fwd ? base : 0.0;
+        auto contrib = [&](double ua, double ub, double lam, const double* Sf, double xn, int side) {
+          const double U = ua * Sf[0] + ub * Sf[1];
+          if (side < 0) acc += 0.5 * (U * xn + lam * xn);
+          else acc -= 0.5 * (U * xn - lam * xn);
+        };
+        if (fwd) {
+          if (i > 0) contrib(prevU[0], prevU[1], prevL, Si, prevx, -1);
+          if (per && i == ni - 1) contrib(firstU[0], firstU[1], firstL, Sw, firstx, +1);
+        } else {
+          if (per && i == 0) contrib(firstU[0], firstU[1], firstL, Sw, firstx, -1);
+          if (i < ni - 1) contrib(prevU[0], prevU[1], prevL, Si, prevx, +1);
+        }
+        if (hasj) {
+          const int par = (q - 1) & 1;
+          double xn;
+          if (fwd) xn = (t > 0) ? xc.v[par][t - 1][0] : *dsmem(&xc.v[par][R - 1][0], rank - 1);
+          else xn = (t < R - 1) ? xc.v[par][t + 1][0] : *dsmem(&xc.v[par][0][0], rank + 1);
+          contrib(ju0, ju1, jlam, Sj, xn, fwd ? -1 : +1);
+        }
+        const double x = fwd ? acc * iD : base + acc * iD;
+        (fwd ? Yf : Yb)[c] = x;
+        xc.v[q & 1][t][0] = x;
+        prevx = x;
+        prevU[0] = u0;
+        prevU[1] = u1;
+        prevL = lam0;
+        if (i == (fwd ? 0 : ni - 1)) {
+          firstx = x;
+          firstU[0] = u0;
+          firstU[1] = u1;
+          firstL = lam0;
+        }
+      }
+      cluster_arrive();
+    }
+    cluster_wait();
+  }
+}
+
+template <class G>
+__global__ void __launch_bounds__(kClusterRows) k_split_cluster(DevGrid g, int R) {
+  __shared__ Xchg<G, Aux<G, 2>::NF> xf;
+  const int comp = blockIdx.x / (int)cluster_nctarank();   // uniform within a cluster
+  if (comp == 0) sweep_flow_cluster<G>(g, R, xf);
+  else sweep_species_cluster<G>(g, R, comp - 1, *reinterpret_cast<Xchg<G, 1>*>(&xf));
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1399,8 +1679,11 @@ __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
       set_status(g, ST_NONPHYSICAL, c);
       return;
     }
-    double om[NS], jd[NS], J[NS * NS], wT[NS], wTv[NS];
-    chemistry<G, true>(w.rhos, w.T, w.Tv, om, jd, J, wT, wTv);
+    double om[NS], jd[NS], J[NS * NS], wT[NS], wTv[NS], emT[NS], emTv[NS];
+    vib_exp<G>(1.0 / w.T, emT);
+    if (G::NTEMP == 2) vib_exp<G>(1.0 / w.Tv, emTv);
+    else for (int s = 0; s < NS; ++s) emTv[s] = emT[s];
+    chemistry<G, true>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, J, wT, wTv);
     // temperature derivatives with respect to the full conserved variables
     double dT[NQ], dTv[NQ];
     double ke = 0.0;

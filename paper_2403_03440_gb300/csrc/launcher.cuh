@@ -25,7 +25,15 @@ struct Launcher {
   virtual void flux(const DevGrid& g, cudaStream_t st) = 0;
   virtual void assemble(const DevGrid& g, cudaStream_t st, int stag, double* out) = 0;
   virtual void spectral(const DevGrid& g, cudaStream_t st) = 0;
-  void sweep_split(const DevGrid& g, cudaStream_t st) { sweep_split_dir(g, st, true); sweep_split_dir(g, st, false); }
+  // both sweeps; returns launches (the cluster path does both in one launch when available)
+  int sweep_split(const DevGrid& g, cudaStream_t st) {
+    const int n = use_cluster ? sweep_split_cluster(g, st) : 0;
+    if (n) return n;
+    return sweep_split_dir(g, st, true) + sweep_split_dir(g, st, false);
+  }
+  virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st) = 0;
+  bool use_cluster = true;
+  bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;   // returns launches
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
@@ -71,7 +79,29 @@ struct LauncherT : Launcher {
       h[r].tb = x.tb;
       for (int s = 0; s < 11; ++s) h[r].eff[s] = effs[x.effset][s];
     }
-    return cudaMemcpyToSymbol(c_reactions, h, sizeof h);
+    cudaError_t e = cudaMemcpyToSymbol(c_reactions, h, sizeof h);
+    if (e != cudaSuccess) return e;
+    // species-derived constants (see GasConst)
+    GasConst gc;
+    std::memset(&gc, 0, sizeof gc);
+    const SpeciesData* sp = G::PERFECT ? nullptr : kSpeciesHost;
+    for (int s = 0; s < G::NS && sp; ++s) {
+      const double m = sp[s].M / kNa;
+      double v = -1.5 * log(2.0 * kPi * m * kKb / (kH * kH)) - log(kKb / kPref) - log(sp[s].g0);
+      if (sp[s].kind == DIATOMIC) v += log(sp[s].sigma * sp[s].thr);
+      gc.gc0[s] = v;
+      gc.cbk[s] = sqrt(8.0 * kRu / (kPi * sp[s].M));
+      for (int q = 0; q < G::NS; ++q) {
+        if (sp[s].kind != DIATOMIC || sp[s].thv <= 0.0 || sp[q].kind == ELECTRON) continue;
+        const double mu = sp[s].M * sp[q].M / (sp[s].M + sp[q].M);
+        const double A = 1.16e-3 * sqrt(mu) * pow(sp[s].thv, 4.0 / 3.0);
+        const double B = 0.015 * pow(mu, 0.25);
+        // tau_sq p = exp(A (T^-1/3 - B) - 18.42); store the exponent of 1/(tau_sq p)
+        gc.mwA[s][q] = A;
+        gc.mwAB[s][q] = A * B + 18.42;
+      }
+    }
+    return cudaMemcpyToSymbol(c_gas, &gc, sizeof gc);
   }
 
   void freestream(const DevGrid& g, cudaStream_t st, const double* in, double* fsQ) override {
@@ -113,6 +143,66 @@ struct LauncherT : Launcher {
       off = 0;
       count = g.nj * g.nk;
     }
+  }
+
+  // Cluster size for the cluster sweep (0: not available for this grid / device).
+  int cluster_size(const DevGrid& g) {
+    if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    if (probed_ >= 0) return probed_;
+    probed_ = 0;
+    auto kern = k_split_cluster<G>;
+    for (int C : {16, 8, 4, 2}) {
+      const int R = (g.nj + C - 1) / C;
+      if (R > kClusterRows) continue;
+      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(C * (1 + G::NS));
+      cfg.blockDim = dim3(kClusterRows);
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
+        probed_ = C;
+        break;
+      }
+      cudaGetLastError();
+    }
+    return probed_;
+  }
+  int probed_ = -1;
+
+  // one launch: both sweeps of the flow block and of every species (returns launches)
+  int sweep_split_cluster(const DevGrid& g, cudaStream_t st) override {
+    sweep_split_cluster_ok = false;
+    if (ND != 2) return 0;
+    const int C = cluster_size(g);
+    if (C == 0) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(C * (1 + G::NS));
+    cfg.blockDim = dim3(kClusterRows);
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int R = (g.nj + C - 1) / C;
+    if (cudaLaunchKernelEx(&cfg, k_split_cluster<G>, g, R) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    sweep_split_cluster_ok = true;
+    return 1;
   }
 
   int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) override {

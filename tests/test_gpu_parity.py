@@ -274,3 +274,20 @@ def test_device_and_host_buffers_agree():
     gpu.set_state(torch.from_numpy(Q).cuda())      # same temperature warm start as the first call
     gpu.residual(R_out=Rd)
     assert np.array_equal(Rd.cpu().numpy(), Rh)
+
+
+@pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "ragged_box_perfect", "tiny_periodic_air5"])
+def test_cluster_sweep_equals_hyperplane_sweep(name):
+    """The one-launch cluster sweep (2D) and the one-launch-per-hyperplane sweep perform the
+    same arithmetic in the same order: their increments are identical."""
+    ref, gpu, Q = make_pair(name, seed=7)
+    gpu.residual(want_R=False)
+    a = gpu.lusgs_split(8.0)
+    gpu.set_option("cluster_sweep", 0)
+    gpu.set_state(Q)
+    gpu.residual(want_R=False)
+    b = gpu.lusgs_split(8.0)
+    gpu.set_option("cluster_sweep", 1)
+    assert np.array_equal(a, b)
+    ref.residual()
+    assert rel(a[:ref.nF], ref.lusgs_split(8.0)[:ref.nF]) < TOL
