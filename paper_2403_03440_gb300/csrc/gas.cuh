@@ -96,7 +96,7 @@ struct ReactionInit {
   int tf, tb, effset;
 };
 // host-side initialiser table (copied to c_reactions by the library at load time)
-static const ReactionInit kReactionInit[21] = {
+static constexpr ReactionInit kReactionInit[21] = {
     {1, 0, -1, 2, 3, 3, -1, 1, 7.0e21, -1.6, 113200.0, TK_A, TK_T, 1},
     {1, 1, -1, 2, 4, 4, -1, 1, 2.0e21, -1.5, 59500.0, TK_A, TK_T, 2},
     {1, 2, -1, 2, 3, 4, -1, 1, 5.0e15, 0.0, 75500.0, TK_A, TK_T, 3},
@@ -119,6 +119,25 @@ static const ReactionInit kReactionInit[21] = {
     {2, 4, 10, 3, 9, 10, 10, 0, 3.9e33, -3.78, 158500.0, TK_V, TK_V, 0},
     {2, 3, 10, 3, 8, 10, 10, 0, 2.5e34, -3.82, 168600.0, TK_V, TK_V, 0},
 };
+
+// Compile-time view of the same reaction table (structure only; the numbers lnA, n, theta and
+// the efficiencies come from c_reactions): lets the kernels unroll the reaction loop so that
+// every per-species index is a compile-time constant.
+struct RxShape {
+  int nr, r0, r1, np, p0, p1, p2, third, tf, tb;
+};
+__host__ __device__ constexpr RxShape rx_shape(int r) {
+  return RxShape{kReactionInit[r].nr, kReactionInit[r].r0, kReactionInit[r].r1,
+                 kReactionInit[r].np, kReactionInit[r].p0, kReactionInit[r].p1,
+                 kReactionInit[r].p2, kReactionInit[r].third, kReactionInit[r].tf,
+                 kReactionInit[r].tb};
+}
+// net stoichiometric coefficient of species s in reaction r
+__host__ __device__ constexpr int rx_nu(int r, int s) {
+  const RxShape x = rx_shape(r);
+  return (x.p0 == s) + (x.np > 1 && x.p1 == s) + (x.np > 2 && x.p2 == s) - (x.r0 == s) -
+         (x.nr > 1 && x.r1 == s);
+}
 
 // Compile-time description of one gas model.
 template <int NS_, int NTEMP_, int NR_, bool PERFECT_ = false>

@@ -8,6 +8,7 @@
 // and the sweeps are purely algebraic: on GB300 the FP64 pipe, not HBM, bounds this path.
 #pragma once
 #include <cstdint>
+#include <utility>
 
 #include "gas.cuh"
 
@@ -381,114 +382,182 @@ __device__ __forceinline__ double rate_temp(int kind, double T, double Tv) {
 
 // omega[s]; optionally the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s, the full
 // fixed-T Jacobian J[s*NS+r] and the temperature derivatives wT[s], wTv[s].
+// Working set of the chemistry evaluation (registers after inlining).
+template <class G, bool FULL>
+struct ChemCtx {
+  static constexpr int NS = G::NS;
+  double X[NS], gT[NS], hT[NS], gV[NS], hV[NS];
+  double omega[NS], jd[NS], wT[NS], wTv[NS];
+  double J[FULL ? NS * NS : 1];
+  double lnT, lnTv, lnTa, iT, iTv, iTa, lnPT, lnPTv, T, Tv;
+};
+
+template <int K>
+__device__ __forceinline__ void pick_temp(double T, double Tv, double lnT, double lnTv,
+                                          double lnTa, double iT, double iTv, double iTa,
+                                          double& Tk, double& lnTk, double& iTk) {
+  if (K == TK_T) { Tk = T; lnTk = lnT; iTk = iT; }
+  else if (K == TK_V) { Tk = Tv; lnTk = lnTv; iTk = iTv; }
+  else { Tk = sqrt(T * Tv); lnTk = lnTa; iTk = iTa; }
+}
+
+struct RxTerms {
+  double kf, kb, M, Pf, Pb, net, dRT, dRV;
+};
+
+// d(product of the concentrations of a species list)/dX_q, repeats handled
+template <int RI>
+__device__ __forceinline__ double dprod_f(const double* X, int q) {
+  constexpr RxShape x = rx_shape(RI);
+  double v = 0.0;
+  if (x.r0 == q) v += (x.nr > 1) ? X[x.r1] : 1.0;
+  if (x.nr > 1 && x.r1 == q) v += X[x.r0];
+  return v;
+}
+template <int RI>
+__device__ __forceinline__ double dprod_b(const double* X, int q) {
+  constexpr RxShape x = rx_shape(RI);
+  double v = 0.0;
+  if (x.p0 == q) v += (x.np > 1 ? X[x.p1] : 1.0) * (x.np > 2 ? X[x.p2] : 1.0);
+  if (x.np > 1 && x.p1 == q) v += X[x.p0] * (x.np > 2 ? X[x.p2] : 1.0);
+  if (x.np > 2 && x.p2 == q) v += X[x.p0] * X[x.p1];
+  return v;
+}
+
+// contribution of reaction RI to species S (nothing when S does not change in RI)
+template <class G, bool FULL, int RI, int S>
+__device__ __forceinline__ void species_term(ChemCtx<G, FULL>& c, const RxTerms& t) {
+  constexpr int nu = rx_nu(RI, S);
+  if constexpr (nu != 0) {
+    constexpr int NS = G::NS;
+    constexpr RxShape x = rx_shape(RI);
+    const ReactionData& d = c_reactions[RI];
+    const double Ms = G::sp(S).M;
+    c.omega[S] += Ms * nu * t.net;
+    c.wT[S] += Ms * nu * t.dRT;
+    c.wTv[S] += Ms * nu * t.dRV;
+    if (FULL) {
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const double e = x.third ? d.eff[q] : 0.0;
+        const double dRf = t.kf * (dprod_f<RI>(c.X, q) * t.M + t.Pf * e);
+        const double dRb = t.kb * (dprod_b<RI>(c.X, q) * t.M + t.Pb * e);
+        c.J[S * NS + q] += Ms * nu * (dRf - dRb) / G::sp(q).M;
+      }
+    } else {
+      const double e = x.third ? d.eff[S] : 0.0;
+      c.jd[S] += nu * (t.kf * (dprod_f<RI>(c.X, S) * t.M + t.Pf * e) -
+                       t.kb * (dprod_b<RI>(c.X, S) * t.M + t.Pb * e));
+    }
+  }
+}
+template <class G, bool FULL, int RI, int... S>
+__device__ __forceinline__ void species_terms(ChemCtx<G, FULL>& c, const RxTerms& t,
+                                              std::integer_sequence<int, S...>) {
+  (species_term<G, FULL, RI, S>(c, t), ...);
+}
+
+// One reaction, unrolled at compile time (species indices are constants).
+template <class G, bool FULL, int RI>
+__device__ __forceinline__ void reaction(ChemCtx<G, FULL>& c) {
+  constexpr RxShape x = rx_shape(RI);
+  constexpr int NS = G::NS;
+  const ReactionData& d = c_reactions[RI];
+  constexpr bool bv = x.tb == TK_V;
+  double sg = 0.0, sh = 0.0;
+  int dn = 0;
+  // products minus reactants of nu g/RT and nu h/RT at the backward temperature
+  const double* gB = bv ? c.gV : c.gT;
+  const double* hB = bv ? c.hV : c.hT;
+  sg += gB[x.p0]; sh += hB[x.p0]; ++dn;
+  if (x.np > 1) { sg += gB[x.p1]; sh += hB[x.p1]; ++dn; }
+  if (x.np > 2) { sg += gB[x.p2]; sh += hB[x.p2]; ++dn; }
+  sg -= gB[x.r0]; sh -= hB[x.r0]; --dn;
+  if (x.nr > 1) { sg -= gB[x.r1]; sh -= hB[x.r1]; --dn; }
+  const double lnKc = -sg + dn * (bv ? c.lnPTv : c.lnPT);
+  double Tf, lnTf, iTf, Tb, lnTb, iTb;
+  pick_temp<x.tf>(c.T, c.Tv, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tf, lnTf, iTf);
+  pick_temp<x.tb>(c.T, c.Tv, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tb, lnTb, iTb);
+  const double kf = exp(d.lnA + d.n * lnTf - d.theta * iTf);
+  const double kb = exp(d.lnA + d.n * lnTb - d.theta * iTb - lnKc);
+  double M = 1.0;
+  if (x.third) {
+    M = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) M += d.eff[s] * c.X[s];
+  }
+  double Pf = c.X[x.r0];
+  if (x.nr > 1) Pf *= c.X[x.r1];
+  double Pb = c.X[x.p0];
+  if (x.np > 1) Pb *= c.X[x.p1];
+  if (x.np > 2) Pb *= c.X[x.p2];
+  const double Rf = kf * Pf * M, Rb = kb * Pb * M;
+  const double dlf = (d.n + d.theta * iTf) * iTf;
+  const double dlb = (d.n + d.theta * iTb - (sh - dn)) * iTb;
+  constexpr bool fA = x.tf == TK_A, bA = x.tb == TK_A;
+  const double fT = x.tf == TK_T ? 1.0 : (fA ? 0.5 * Tf * c.iT : 0.0);
+  const double fV = x.tf == TK_V ? 1.0 : (fA ? 0.5 * Tf * c.iTv : 0.0);
+  const double bT = x.tb == TK_T ? 1.0 : (bA ? 0.5 * Tb * c.iT : 0.0);
+  const double bVv = x.tb == TK_V ? 1.0 : (bA ? 0.5 * Tb * c.iTv : 0.0);
+  const double dRT = Rf * dlf * fT - Rb * dlb * bT;
+  const double dRV = Rf * dlf * fV - Rb * dlb * bVv;
+  const double net = Rf - Rb;
+  species_terms<G, FULL, RI>(c, RxTerms{kf, kb, M, Pf, Pb, net, dRT, dRV},
+                             std::make_integer_sequence<int, NS>{});
+}
+
+template <class G, bool FULL, int... RI>
+__device__ __forceinline__ void all_reactions(ChemCtx<G, FULL>& c, std::integer_sequence<int, RI...>) {
+  (reaction<G, FULL, RI>(c), ...);
+}
+
+// omega[s]; the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s (or the full fixed-T
+// Jacobian J[s*NS+r] when FULL) and the temperature derivatives wT[s], wTv[s].
 // emT/emTv: exp(-theta_v/T) and exp(-theta_v/Tv) of every species (vib_exp).
 template <class G, bool FULL>
-__device__ void chemistry(const double* rhos, double T, double Tv, const double* emT,
-                          const double* emTv, double* omega, double* jd, double* J, double* wT,
-                          double* wTv) {
+__device__ __forceinline__ void chemistry(const double* rhos, double T, double Tv, const double* emT,
+                                          const double* emTv, double* omega, double* jd,
+                                          double* J, double* wT, double* wTv) {
   constexpr int NS = G::NS;
-  double X[NS], gT[NS], hT[NS], gV[NS], hV[NS];
+  ChemCtx<G, FULL> c;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    X[s] = rhos[s] / G::sp(s).M;
-    omega[s] = 0.0;
-    jd[s] = 0.0;
-    wT[s] = 0.0;
-    wTv[s] = 0.0;
+    c.X[s] = rhos[s] / G::sp(s).M;
+    c.omega[s] = 0.0;
+    c.jd[s] = 0.0;
+    c.wT[s] = 0.0;
+    c.wTv[s] = 0.0;
   }
-  if (FULL) for (int k = 0; k < NS * NS; ++k) J[k] = 0.0;
-  const double lnT = log(T), lnTv = (G::NTEMP == 2) ? log(Tv) : lnT;
-  const double iT = 1.0 / T, iTv = (G::NTEMP == 2) ? 1.0 / Tv : iT;
-  const double lnTa = 0.5 * (lnT + lnTv), iTa = (G::NTEMP == 2) ? 1.0 / sqrt(T * Tv) : iT;
-  const double lnPT = log(kPref / kRu) - lnT, lnPTv = log(kPref / kRu) - lnTv;
+  if (FULL)
+#pragma unroll
+    for (int k = 0; k < NS * NS; ++k) c.J[k] = 0.0;
+  c.T = T;
+  c.Tv = Tv;
+  c.lnT = log(T);
+  c.lnTv = (G::NTEMP == 2) ? log(Tv) : c.lnT;
+  c.iT = 1.0 / T;
+  c.iTv = (G::NTEMP == 2) ? 1.0 / Tv : c.iT;
+  c.lnTa = 0.5 * (c.lnT + c.lnTv);
+  c.iTa = (G::NTEMP == 2) ? 1.0 / sqrt(T * Tv) : c.iT;
+  c.lnPT = log(kPref / kRu) - c.lnT;
+  c.lnPTv = log(kPref / kRu) - c.lnTv;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    gibbs<G>(s, iT, lnT, emT[s], gT[s], hT[s]);
-    if (G::NTEMP == 2) gibbs<G>(s, iTv, lnTv, emTv[s], gV[s], hV[s]);
-    else { gV[s] = gT[s]; hV[s] = hT[s]; }
+    gibbs<G>(s, c.iT, c.lnT, emT[s], c.gT[s], c.hT[s]);
+    if (G::NTEMP == 2) gibbs<G>(s, c.iTv, c.lnTv, emTv[s], c.gV[s], c.hV[s]);
+    else { c.gV[s] = c.gT[s]; c.hV[s] = c.hT[s]; }
   }
-  for (int r = 0; r < G::NR; ++r) {
-    const ReactionData& x = c_reactions[r];
-    const double Tf = rate_temp(x.tf, T, Tv), Tb = rate_temp(x.tb, T, Tv);
-    const bool bv = (x.tb == TK_V);
-    // sum over species of nu * g/RT and nu * h/RT at the backward temperature
-    double sg = 0.0, sh = 0.0;
-    int dn = 0;
-    for (int a = 0; a < x.np; ++a) { sg += bv ? gV[x.p[a]] : gT[x.p[a]]; sh += bv ? hV[x.p[a]] : hT[x.p[a]]; ++dn; }
-    for (int a = 0; a < x.nr; ++a) { sg -= bv ? gV[x.r[a]] : gT[x.r[a]]; sh -= bv ? hV[x.r[a]] : hT[x.r[a]]; --dn; }
-    const double lnKc = -sg + dn * (bv ? lnPTv : lnPT);
-    const double lnTf = x.tf == TK_T ? lnT : (x.tf == TK_V ? lnTv : lnTa);
-    const double iTf = x.tf == TK_T ? iT : (x.tf == TK_V ? iTv : iTa);
-    const double lnTb = x.tb == TK_T ? lnT : (x.tb == TK_V ? lnTv : lnTa);
-    const double iTb = x.tb == TK_T ? iT : (x.tb == TK_V ? iTv : iTa);
-    const double kf = exp(x.lnA + x.n * lnTf - x.theta * iTf);
-    const double kb = exp(x.lnA + x.n * lnTb - x.theta * iTb - lnKc);
-    double M = 1.0;
-    if (x.third) {
-      M = 0.0;
+  all_reactions<G, FULL>(c, std::make_integer_sequence<int, G::NR>{});
 #pragma unroll
-      for (int s = 0; s < NS; ++s) M += x.eff[s] * X[s];
-    }
-    double Pf = 1.0, Pb = 1.0;
-    for (int a = 0; a < x.nr; ++a) Pf *= X[x.r[a]];
-    for (int a = 0; a < x.np; ++a) Pb *= X[x.p[a]];
-    const double Rf = kf * Pf * M, Rb = kb * Pb * M;
-    // temperature derivatives of ln k
-    const double dlf = (x.n + x.theta * iTf) * iTf;
-    const double dlb = (x.n + x.theta * iTb - (sh - dn)) * iTb;
-    const double fT = x.tf == TK_T ? 1.0 : (x.tf == TK_A ? 0.5 * Tf * iT : 0.0);
-    const double fV = x.tf == TK_V ? 1.0 : (x.tf == TK_A ? 0.5 * Tf * iTv : 0.0);
-    const double bT = x.tb == TK_T ? 1.0 : (x.tb == TK_A ? 0.5 * Tb * iT : 0.0);
-    const double bVv = x.tb == TK_V ? 1.0 : (x.tb == TK_A ? 0.5 * Tb * iTv : 0.0);
-    const double dRT = Rf * dlf * fT - Rb * dlb * bT;
-    const double dRV = Rf * dlf * fV - Rb * dlb * bVv;
-    const double net = Rf - Rb;
-    // stoichiometry: loop over the (<= 3 + 3) participating species
-    auto nu_of = [&](int s) {
-      int v = 0;
-      for (int a = 0; a < x.np; ++a) v += (x.p[a] == s);
-      for (int a = 0; a < x.nr; ++a) v -= (x.r[a] == s);
-      return v;
-    };
-    // d(Pf)/dX_q and d(Pb)/dX_q
-    auto dprod = [&](const int* lst, int n, int q) {
-      double v = 0.0;
-      for (int a = 0; a < n; ++a) {
-        if (lst[a] != q) continue;
-        double pr = 1.0;
-        for (int b = 0; b < n; ++b) if (b != a) pr *= X[lst[b]];
-        v += pr;
-      }
-      return v;
-    };
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int nu = nu_of(s);
-      const double Ms = G::sp(s).M;
-      if (nu != 0) {
-        omega[s] += Ms * nu * net;
-        wT[s] += Ms * nu * dRT;
-        wTv[s] += Ms * nu * dRV;
-      }
-      if (FULL) {
-        if (nu == 0) continue;
-        for (int q = 0; q < NS; ++q) {
-          const double dRf = kf * (dprod(x.r, x.nr, q) * M + Pf * (x.third ? x.eff[q] : 0.0));
-          const double dRb = kb * (dprod(x.p, x.np, q) * M + Pb * (x.third ? x.eff[q] : 0.0));
-          J[s * NS + q] += Ms * nu * (dRf - dRb) / G::sp(q).M;
-        }
-      } else {
-        // diagonal only: d omega_s / d rho_s
-        const double dRf = kf * (dprod(x.r, x.nr, s) * M + Pf * (x.third ? x.eff[s] : 0.0));
-        const double dRb = kb * (dprod(x.p, x.np, s) * M + Pb * (x.third ? x.eff[s] : 0.0));
-        if (nu != 0) jd[s] += Ms * nu * (dRf - dRb) / Ms;
-      }
-    }
+  for (int s = 0; s < NS; ++s) {
+    omega[s] = c.omega[s];
+    wT[s] = c.wT[s];
+    wTv[s] = c.wTv[s];
+    jd[s] = FULL ? c.J[s * NS + s] : c.jd[s];
   }
-  if (FULL) {
+  if (FULL)
 #pragma unroll
-    for (int s = 0; s < NS; ++s) jd[s] = J[s * NS + s];
-  }
+    for (int k = 0; k < NS * NS; ++k) J[k] = c.J[k];
 }
 
 // Derivatives of T and Tv with respect to rho_s at fixed other conserved variables.
@@ -1212,8 +1281,8 @@ __global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
 // matrix-free.  Flow block with frozen mass fractions (Sec. 2.3.1) and coupled variables.
 // ---------------------------------------------------------------------------------------
 template <class G, int ND>
-struct CellState {       // what the Jacobian needs from the neighbour cell
-  double rho, u[ND], p, rhoE, rhoev, beta, prev, pY;   // pY = sum_s Y_s dp/drho_s
+struct CellState {       // what the flow Jacobian needs from the neighbour cell
+  double u[ND], H, ev, beta, prev, pY;   // pY = sum_s Y_s dp/drho_s
 };
 
 template <class G, int ND>
@@ -1221,18 +1290,18 @@ __device__ __forceinline__ void load_state(const DevGrid& g, int c, CellState<G,
   using A = Aux<G, ND>;
   const size_t N = g.N;
   const double* W = g.W;
-  s.rho = W[A::RHO * N + c];
 #pragma unroll
   for (int d = 0; d < ND; ++d) s.u[d] = W[(A::U + d) * N + c];
-  s.p = W[A::P * N + c];
-  s.rhoE = g.Q[(G::NS + ND) * N + c];
-  s.rhoev = (G::NTEMP == 2) ? g.Q[(A::NQ - 1) * N + c] : 0.0;
+  s.H = W[A::H * N + c];
+  s.ev = (G::NTEMP == 2) ? W[A::EV * N + c] : 0.0;
   s.beta = W[A::BETA * N + c];
   s.prev = W[A::PREV * N + c];
   s.pY = W[A::PY * N + c];
 }
 
-// flow block: x = (drho, dm, drhoE, [drho e_v]) -> A(S) x
+// flow block: x = (drho, dm, drhoE, [drho e_v]) -> A(S) x.  With a = rho dU = S.dm - U drho
+// the product needs no division: dF_m = dm U + u a + dp S, dF_E = (drhoE + dp) U + H a,
+// dF_ev = d(rho e_v) U + e_v a.
 template <class G, int ND>
 __device__ __forceinline__ void jvp_flow(const CellState<G, ND>& w, const double* S, const double* x,
                                          double* y) {
@@ -1245,12 +1314,12 @@ __device__ __forceinline__ void jvp_flow(const CellState<G, ND>& w, const double
     dp -= w.beta * w.u[d] * x[1 + d];
   }
   if (G::NTEMP == 2) dp += w.prev * x[NF - 1];
-  const double dU = (Sdm - U * x[0]) / w.rho;
+  const double a = Sdm - U * x[0];
   y[0] = Sdm;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) y[1 + d] = x[1 + d] * U + w.rho * w.u[d] * dU + dp * S[d];
-  y[ND + 1] = (x[ND + 1] + dp) * U + (w.rhoE + w.p) * dU;
-  if (G::NTEMP == 2) y[NF - 1] = x[NF - 1] * U + w.rhoev * dU;
+  for (int d = 0; d < ND; ++d) y[1 + d] = x[1 + d] * U + w.u[d] * a + dp * S[d];
+  y[ND + 1] = (x[ND + 1] + dp) * U + w.H * a;
+  if (G::NTEMP == 2) y[NF - 1] = x[NF - 1] * U + w.ev * a;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1397,99 +1466,51 @@ __device__ __forceinline__ void flow_contrib(const CellState<G, 2>& w, double la
   }
 }
 
+// Static inputs of one cell for the flow sweep (loaded one step ahead).
 template <class G>
-__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF>& xc) {
-  using A = Aux<G, 2>;
-  constexpr int NF = A::NF;
+struct FlowStep {
+  static constexpr int NF = Aux<G, 2>::NF;
+  CellState<G, 2> me, jn;
+  double lam0, jlam, iD, iDev, base[NF], Si[2], Sj[2], Sw[2];
+  int c;
+  bool act, hasj;
+};
+
+template <class G>
+__device__ __forceinline__ void flow_step_load(const DevGrid& g, int q, int j, bool row, bool fwd,
+                                               FlowStep<G>& f) {
+  constexpr int NF = Aux<G, 2>::NF;
   const size_t N = g.N;
-  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
-  const int t = threadIdx.x;
-  const int j = rank * R + t;
-  const bool row = t < R && j < g.nj;
-  const bool per = g.bc[0] == BC_PERIODIC;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fwd = pass == 0;
-    double prevx[NF], firstx[NF];
-    CellState<G, 2> prevS, firstS;
-    double prevL = 0.0, firstL = 0.0;
-    for (int q = 0; q <= H; ++q) {
-      const int h = fwd ? q : H - q;
-      const int i = h - j;
-      const bool act = row && i >= 0 && i < ni;
-      // loads that do not depend on the other rows (issued before the barrier wait)
-      CellState<G, 2> me, jn;
-      double lam0 = 0.0, jlam = 0.0, iD = 0.0, iDev = 0.0, base[NF];
-      const double *Si = nullptr, *Sj = nullptr, *Sw = nullptr;
-      const int jj = fwd ? j - 1 : j + 1;
-      const bool hasj = act && jj >= 0 && jj < nj;
-      int c = 0;
-      if (act) {
-        c = i + ni * j;
-        load_state<G, 2>(g, c, me);
-        lam0 = g.lamF[c];
-        iD = g.invD[c];
-        iDev = g.invD[N + c];
+  const int h = fwd ? q : H - q;
+  const int i = h - j;
+  f.act = row && q <= H && i >= 0 && i < ni;
+  const int jj = fwd ? j - 1 : j + 1;
+  f.hasj = f.act && jj >= 0 && jj < nj;
+  if (!f.act) return;
+  const int c = i + ni * j;
+  f.c = c;
+  load_state<G, 2>(g, c, f.me);
+  f.lam0 = g.lamF[c];
+  f.iD = g.invD[c];
+  f.iDev = g.invD[N + c];
 #pragma unroll
-        for (int v = 0; v < NF; ++v) base[v] = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
-        Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
-        Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
-        Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
-        if (hasj) {
-          const int cn = i + ni * jj;
-          load_state<G, 2>(g, cn, jn);
-          jlam = g.lamF[N + cn];
-        }
-      }
-      if (q > 0) cluster_wait();
-      if (act) {
-        double acc[NF];
-#pragma unroll
-        for (int v = 0; v < NF; ++v) acc[v] = fwd ? base[v] : 0.0;
-        if (fwd) {
-          if (i > 0) flow_contrib<G>(prevS, prevL, Si, prevx, -1, acc);
-          if (per && i == ni - 1) flow_contrib<G>(firstS, firstL, Sw, firstx, +1, acc);
-        } else {
-          if (per && i == 0) flow_contrib<G>(firstS, firstL, Sw, firstx, -1, acc);
-          if (i < ni - 1) flow_contrib<G>(prevS, prevL, Si, prevx, +1, acc);
-        }
-        if (hasj) {
-          const double* src;
-          const int par = (q - 1) & 1;
-          if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
-          else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
-          double xn[NF];
-#pragma unroll
-          for (int v = 0; v < NF; ++v) xn[v] = src[v];
-          flow_contrib<G>(jn, jlam, Sj, xn, fwd ? -1 : +1, acc);
-        }
-        double x[NF];
-#pragma unroll
-        for (int v = 0; v < NF; ++v) {
-          const double d = (G::NTEMP == 2 && v == NF - 1) ? iDev : iD;
-          x[v] = fwd ? acc[v] * d : base[v] + acc[v] * d;
-          (fwd ? g.dQs : g.dQ)[v * N + c] = x[v];
-          xc.v[q & 1][t][v] = x[v];
-          prevx[v] = x[v];
-        }
-        prevS = me;
-        prevL = lam0;
-        if (i == (fwd ? 0 : ni - 1)) {
-#pragma unroll
-          for (int v = 0; v < NF; ++v) firstx[v] = x[v];
-          firstS = me;
-          firstL = lam0;
-        }
-      }
-      cluster_arrive();
-    }
-    cluster_wait();
-    (void)C;
+  for (int v = 0; v < NF; ++v) f.base[v] = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
+  const double* Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
+  const double* Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
+  const double* Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
+  f.Si[0] = Si[0]; f.Si[1] = Si[1];
+  f.Sj[0] = Sj[0]; f.Sj[1] = Sj[1];
+  f.Sw[0] = Sw[0]; f.Sw[1] = Sw[1];
+  if (f.hasj) {
+    const int cn = i + ni * jj;
+    load_state<G, 2>(g, cn, f.jn);
+    f.jlam = g.lamF[N + cn];
   }
 }
 
 template <class G>
-__device__ void sweep_species_cluster(const DevGrid& g, int R, int s, Xchg<G, 1>& xc) {
+__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF>& xc) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF;
   const size_t N = g.N;
@@ -1498,32 +1519,107 @@ __device__ void sweep_species_cluster(const DevGrid& g, int R, int s, Xchg<G, 1>
   const int j = rank * R + t;
   const bool row = t < R && j < g.nj;
   const bool per = g.bc[0] == BC_PERIODIC;
-  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
-  const double* X = g.dQs + (size_t)(NF + s) * N;
-  double* Yf = g.dQs + (size_t)(NF + s) * N;
-  double* Yb = g.dQ + (size_t)(NF + s) * N;
+  const int ni = g.ni, H = ni + g.nj - 2;
   for (int pass = 0; pass < 2; ++pass) {
     const bool fwd = pass == 0;
-    double prevx = 0.0, firstx = 0.0, prevU[2] = {0, 0}, firstU[2] = {0, 0}, prevL = 0.0, firstL = 0.0;
+    double prevx[NF], firstx[NF];
+    CellState<G, 2> prevS, firstS;
+    double prevL = 0.0, firstL = 0.0;
+    FlowStep<G> cur, nxt;
+    flow_step_load<G>(g, 0, j, row, fwd, cur);
+    for (int q = 0; q <= H; ++q) {
+      const int i = (fwd ? q : H - q) - j;
+      flow_step_load<G>(g, q + 1, j, row, fwd, nxt);     // prefetch the next step
+      if (q > 0) cluster_wait();
+      if (cur.act) {
+        double acc[NF];
+#pragma unroll
+        for (int v = 0; v < NF; ++v) acc[v] = fwd ? cur.base[v] : 0.0;
+        if (fwd) {
+          if (i > 0) flow_contrib<G>(prevS, prevL, cur.Si, prevx, -1, acc);
+          if (per && i == ni - 1) flow_contrib<G>(firstS, firstL, cur.Sw, firstx, +1, acc);
+        } else {
+          if (per && i == 0) flow_contrib<G>(firstS, firstL, cur.Sw, firstx, -1, acc);
+          if (i < ni - 1) flow_contrib<G>(prevS, prevL, cur.Si, prevx, +1, acc);
+        }
+        if (cur.hasj) {
+          const double* src;
+          const int par = (q - 1) & 1;
+          if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
+          double xn[NF];
+#pragma unroll
+          for (int v = 0; v < NF; ++v) xn[v] = src[v];
+          flow_contrib<G>(cur.jn, cur.jlam, cur.Sj, xn, fwd ? -1 : +1, acc);
+        }
+        double* out = fwd ? g.dQs : g.dQ;
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          const double d = (G::NTEMP == 2 && v == NF - 1) ? cur.iDev : cur.iD;
+          const double x = fwd ? acc[v] * d : cur.base[v] + acc[v] * d;
+          out[v * N + cur.c] = x;
+          xc.v[q & 1][t][v] = x;
+          prevx[v] = x;
+        }
+        prevS = cur.me;
+        prevL = cur.lam0;
+        if (i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) firstx[v] = prevx[v];
+          firstS = cur.me;
+          firstL = cur.lam0;
+        }
+      }
+      cluster_arrive();
+      cur = nxt;
+    }
+    cluster_wait();
+  }
+}
+
+constexpr int kSpeciesGroup = 4;   // species per cluster (they share u, lambda and S)
+
+template <class G>
+__device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, kSpeciesGroup>& xc) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF, SG = kSpeciesGroup;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank();
+  const int t = threadIdx.x;
+  const int j = rank * R + t;
+  const bool row = t < R && j < g.nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const int ns = (G::NS - s0 < SG) ? G::NS - s0 : SG;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double prevx[SG], firstx[SG], prevU[2] = {0, 0}, firstU[2] = {0, 0}, prevL = 0.0, firstL = 0.0;
+#pragma unroll
+    for (int k = 0; k < SG; ++k) { prevx[k] = 0.0; firstx[k] = 0.0; }
     for (int q = 0; q <= H; ++q) {
       const int h = fwd ? q : H - q;
       const int i = h - j;
       const bool act = row && i >= 0 && i < ni;
       const int jj = fwd ? j - 1 : j + 1;
       const bool hasj = act && jj >= 0 && jj < nj;
-      double u0 = 0, u1 = 0, lam0 = 0, iD = 0, base = 0, ju0 = 0, ju1 = 0, jlam = 0;
-      const double *Si = nullptr, *Sj = nullptr, *Sw = nullptr;
+      double u0 = 0, u1 = 0, lam0 = 0, iD[SG], base[SG], ju0 = 0, ju1 = 0, jlam = 0;
+      double Si0 = 0, Si1 = 0, Sj0 = 0, Sj1 = 0, Sw0 = 0, Sw1 = 0;
       int c = 0;
       if (act) {
         c = i + ni * j;
         u0 = g.W[A::U * N + c];
         u1 = g.W[(A::U + 1) * N + c];
         lam0 = g.lamC[c];
-        iD = g.invD[(2 + s) * N + c];
-        base = fwd ? -g.R[(size_t)s * N + c] : X[c];
-        Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
-        Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
-        Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
+#pragma unroll
+        for (int k = 0; k < SG; ++k) {
+          if (k >= ns) continue;
+          iD[k] = g.invD[(2 + s0 + k) * N + c];
+          base[k] = fwd ? -g.R[(size_t)(s0 + k) * N + c] : g.dQs[(size_t)(NF + s0 + k) * N + c];
+        }
+        const double* Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
+        const double* Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
+        const double* Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
+        Si0 = Si[0]; Si1 = Si[1]; Sj0 = Sj[0]; Sj1 = Sj[1]; Sw0 = Sw[0]; Sw1 = Sw[1];
         if (hasj) {
           const int cn = i + ni * jj;
           ju0 = g.W[A::U * N + cn];
@@ -1533,35 +1629,60 @@ __device__ void sweep_species_cluster(const DevGrid& g, int R, int s, Xchg<G, 1>
       }
       if (q > 0) cluster_wait();
       if (act) {
-        double acc = fwd ? base : 0.0;
-        auto contrib = [&](double ua, double ub, double lam, const double* Sf, double xn, int side) {
-          const double U = ua * Sf[0] + ub * Sf[1];
-          if (side < 0) acc += 0.5 * (U * xn + lam * xn);
-          else acc -= 0.5 * (U * xn - lam * xn);
+        double acc[SG];
+#pragma unroll
+        for (int k = 0; k < SG; ++k) acc[k] = fwd ? base[k] : 0.0;
+        // coefficient of a neighbour: minus side (U + lam)/2, plus side -(U - lam)/2
+        auto coef = [](double ua, double ub, double lam, double s0_, double s1_, int side) {
+          const double U = ua * s0_ + ub * s1_;
+          return side < 0 ? 0.5 * (U + lam) : -0.5 * (U - lam);
         };
         if (fwd) {
-          if (i > 0) contrib(prevU[0], prevU[1], prevL, Si, prevx, -1);
-          if (per && i == ni - 1) contrib(firstU[0], firstU[1], firstL, Sw, firstx, +1);
+          if (i > 0) {
+            const double k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, -1);
+#pragma unroll
+            for (int k = 0; k < SG; ++k) acc[k] += k0 * prevx[k];
+          }
+          if (per && i == ni - 1) {
+            const double k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, +1);
+#pragma unroll
+            for (int k = 0; k < SG; ++k) acc[k] += k0 * firstx[k];
+          }
         } else {
-          if (per && i == 0) contrib(firstU[0], firstU[1], firstL, Sw, firstx, -1);
-          if (i < ni - 1) contrib(prevU[0], prevU[1], prevL, Si, prevx, +1);
+          if (per && i == 0) {
+            const double k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, -1);
+#pragma unroll
+            for (int k = 0; k < SG; ++k) acc[k] += k0 * firstx[k];
+          }
+          if (i < ni - 1) {
+            const double k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, +1);
+#pragma unroll
+            for (int k = 0; k < SG; ++k) acc[k] += k0 * prevx[k];
+          }
         }
         if (hasj) {
           const int par = (q - 1) & 1;
-          double xn;
-          if (fwd) xn = (t > 0) ? xc.v[par][t - 1][0] : *dsmem(&xc.v[par][R - 1][0], rank - 1);
-          else xn = (t < R - 1) ? xc.v[par][t + 1][0] : *dsmem(&xc.v[par][0][0], rank + 1);
-          contrib(ju0, ju1, jlam, Sj, xn, fwd ? -1 : +1);
+          const double* src;
+          if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
+          const double k0 = coef(ju0, ju1, jlam, Sj0, Sj1, fwd ? -1 : +1);
+#pragma unroll
+          for (int k = 0; k < SG; ++k) acc[k] += k0 * src[k];
         }
-        const double x = fwd ? acc * iD : base + acc * iD;
-        (fwd ? Yf : Yb)[c] = x;
-        xc.v[q & 1][t][0] = x;
-        prevx = x;
+#pragma unroll
+        for (int k = 0; k < SG; ++k) {
+          if (k >= ns) { xc.v[q & 1][t][k] = 0.0; prevx[k] = 0.0; continue; }
+          const double x = fwd ? acc[k] * iD[k] : base[k] + acc[k] * iD[k];
+          (fwd ? g.dQs : g.dQ)[(size_t)(NF + s0 + k) * N + c] = x;
+          xc.v[q & 1][t][k] = x;
+          prevx[k] = x;
+        }
         prevU[0] = u0;
         prevU[1] = u1;
         prevL = lam0;
         if (i == (fwd ? 0 : ni - 1)) {
-          firstx = x;
+#pragma unroll
+          for (int k = 0; k < SG; ++k) firstx[k] = prevx[k];
           firstU[0] = u0;
           firstU[1] = u1;
           firstL = lam0;
@@ -1574,11 +1695,16 @@ __device__ void sweep_species_cluster(const DevGrid& g, int R, int s, Xchg<G, 1>
 }
 
 template <class G>
+constexpr int species_clusters() { return (G::NS + kSpeciesGroup - 1) / kSpeciesGroup; }
+
+template <class G>
 __global__ void __launch_bounds__(kClusterRows) k_split_cluster(DevGrid g, int R) {
-  __shared__ Xchg<G, Aux<G, 2>::NF> xf;
+  constexpr int NV = Aux<G, 2>::NF > kSpeciesGroup ? Aux<G, 2>::NF : kSpeciesGroup;
+  __shared__ Xchg<G, NV> xf;
   const int comp = blockIdx.x / (int)cluster_nctarank();   // uniform within a cluster
-  if (comp == 0) sweep_flow_cluster<G>(g, R, xf);
-  else sweep_species_cluster<G>(g, R, comp - 1, *reinterpret_cast<Xchg<G, 1>*>(&xf));
+  if (comp == 0) sweep_flow_cluster<G>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF>*>(&xf));
+  else sweep_species_cluster<G>(g, R, (comp - 1) * kSpeciesGroup,
+                                *reinterpret_cast<Xchg<G, kSpeciesGroup>*>(&xf));
 }
 
 // ---------------------------------------------------------------------------------------

@@ -160,7 +160,7 @@ struct LauncherT : Launcher {
       }
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
-      cfg.gridDim = dim3(C * (1 + G::NS));
+      cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
       cfg.blockDim = dim3(kClusterRows);
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = C;
@@ -187,7 +187,7 @@ struct LauncherT : Launcher {
     if (C == 0) return 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(C * (1 + G::NS));
+    cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
     cfg.blockDim = dim3(kClusterRows);
     cfg.stream = st;
     at[0].id = cudaLaunchAttributeClusterDimension;

@@ -279,7 +279,8 @@ def test_device_and_host_buffers_agree():
 @pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "ragged_box_perfect", "tiny_periodic_air5"])
 def test_cluster_sweep_equals_hyperplane_sweep(name):
     """The one-launch cluster sweep (2D) and the one-launch-per-hyperplane sweep perform the
-    same arithmetic in the same order: their increments are identical."""
+    same arithmetic in the same order (the compiler may contract multiply-adds differently
+    in the two kernels, so they agree to rounding)."""
     ref, gpu, Q = make_pair(name, seed=7)
     gpu.residual(want_R=False)
     a = gpu.lusgs_split(8.0)
@@ -288,6 +289,7 @@ def test_cluster_sweep_equals_hyperplane_sweep(name):
     gpu.residual(want_R=False)
     b = gpu.lusgs_split(8.0)
     gpu.set_option("cluster_sweep", 1)
-    assert np.array_equal(a, b)
+    assert rel(a[:ref.nF], b[:ref.nF]) < 1e-13
+    assert rel(a[ref.nF:], b[ref.nF:], ns=ref.ns) < 1e-13
     ref.residual()
     assert rel(a[:ref.nF], ref.lusgs_split(8.0)[:ref.nF]) < TOL
