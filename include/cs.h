@@ -166,6 +166,25 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * hyperplane.  Both give the same arithmetic.  Errors: CS_ERR_ARG for an unknown name. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
+/* Residual monitors without device allocation (no counterpart in the paper: a service for
+ * callers that cannot allocate device memory, e.g. an application whose memory pool already
+ * holds the device, or monitoring code that must not let cudaMalloc / cudaFree synchronise the
+ * device).  Computes norms_host[0] = r_species and norms_host[1] = r_energy exactly as
+ * cs_residual does, from a residual R_dev (device, [nq][ncell], species rows first, energy row
+ * nspecies + ndim) and cell volumes V_dev (device, [ncell]) owned by the caller.  Its scratch is
+ * a static device array of CS_NORMS_STATIC_MAX_BLOCKS x 2 doubles (256 KiB) that every GPU
+ * loading the library keeps until exit; ncell above CS_NORMS_STATIC_MAX_CELLS is rejected with
+ * CS_ERR_ARG.  It allocates nothing: the first call on a device looks up the array's device
+ * address (make that first call before any stream capture).  All calls share the array, so
+ * calls that overlap on the GPU race; the call synchronises cuda_stream (NULL: legacy default
+ * stream) before returning.  Errors: CS_ERR_ARG (null pointer, size, nspecies, ndim),
+ * CS_ERR_CUDA. */
+#define CS_NORMS_STATIC_MAX_BLOCKS 16384
+#define CS_NORMS_STATIC_MAX_CELLS (CS_NORMS_STATIC_MAX_BLOCKS * 256)
+cs_status cs_residual_norms_static(const double *R_dev, const double *V_dev, int ncell,
+                                   int nspecies, int ndim, void *cuda_stream,
+                                   double norms_host[2]);
+
 const char *cs_last_error(cs_grid g);
 
 #ifdef __cplusplus

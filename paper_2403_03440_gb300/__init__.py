@@ -17,7 +17,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libcs_gb300.so")
 SOURCES = ["launch_air11_2d.cu", "launch_air11_3d.cu", "launch_air5_2d.cu", "launch_air5_3d.cu",
-           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu"]
+           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 
@@ -97,7 +97,8 @@ class cs_step_stats(C.Structure):
 EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary",
            "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
-           "cs_gas_info", "cs_profile", "cs_set_option", "cs_last_error"]
+           "cs_gas_info", "cs_profile", "cs_set_option", "cs_residual_norms_static",
+           "cs_last_error"]
 
 _lib = None
 
