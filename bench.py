@@ -35,35 +35,32 @@ MECH = inputs.MECH_AIR11
 MACH, T_INF, P_INF, T_WALL = 15.0, 300.0, 500.0, 500.0
 CFL, CFL_START, RAMP = 2.0, 0.5, 100
 WORKLOAD = "cylinder-384x256-air11-2T-mach15-CS1-fp64"
-# HBM bytes a phase must move per cell and iteration (FP64 words x 8), from the arrays each
-# kernel reads and writes once (section "Roofline"): used for the roofline of
-# memory-bound phases.
-ALGO_BYTES_PER_CELL = {
-    # primitive: Q (17) + warm-start T, Tv (2) in; aux record (23 + 6*11 = 89) out
-    "primitive": 8 * (17 + 2 + 89),
-    # gradient: 15 gradient variables of the cell in, 15*2 gradients out (neighbours cached)
-    "gradient": 8 * (15 + 30),
-    # flux: per face ~ 2 x (reconstruction 17 + gradient 30 + transport/enthalpy 26) in, 17 out;
-    # two faces per cell
-    "flux": 8 * 2 * (17 + 30 + 26 + 17),
-    "assemble": 8 * (2 * 2 * 17 + 12 + 17),
-    "spectral": 8 * (16 + 11 + 3 * 3 + 2 + 11),
-    "sweep_fwd": 8 * (17 + 16 + 10 + 3 + 16),
-    "sweep_bwd": 8 * (16 + 10 + 3 + 2 * 16),
-    "correct": 8 * (17 + 16 + 17),
+# FP64 floating-point operations per cell and iteration of each phase (2 x DFMA + DMUL + DADD
+# thread instructions counted by ncu on this workload, divided by the cell count; the
+# primitive phase varies with the Newton iteration count).  On GB300 every residual kernel
+# runs with its FP64 pipe 70-86 % busy, so the roofline of this path is the FP64 ALU, not HBM.
+FP64_FLOPS_PER_CELL = {
+    "primitive": 11883.0,
+    "gradient": 402.0,
+    "flux": 2299.0,
+    "assemble": 137.0,
+    "spectral": 358.0,
+    "sweep_fwd": 474.0,        # both sweeps of all components (one cluster launch)
+    "sweep_bwd": 0.0,
+    "correct": 82.0,
 }
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+DRAM_BYTES_PER_LAUNCH = {
+    "primitive": 39.6e6, "flux": 2 * 65.8e6, "sweep_fwd": 36.7e6, "gradient": 17.4e6,
+    "spectral": 54.0e6, "assemble": 33.9e6, "correct": 24.4e6,
+}
+# GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA microbenchmark measured
+# 1.20 TFLOP/s on this machine)
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
-
-
-def peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            return json.load(f), "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
 class ClockSampler:
@@ -128,9 +125,12 @@ def make_case(P):
     return nodes, fs
 
 
+PRECISION = 0   # 0: FP64 operator, 1: FP32 operator (mixed); set by --precision
+
+
 def step_kwargs(iters):
     return dict(scheme=0, correction=1, clip=1, cfl=CFL, cfl_start=CFL_START, ramp_iters=RAMP,
-                iters=iters)
+                iters=iters, precision=PRECISION)
 
 
 def oracle_rate(iters, seconds_cap=30.0):
@@ -143,8 +143,10 @@ def oracle_rate(iters, seconds_cap=30.0):
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
     done, t0 = 0, time.perf_counter()
+    kw = step_kwargs(1)
+    kw.pop("precision")
     while done < iters:
-        g.step(**step_kwargs(1))
+        g.step(**kw)
         done += 1
         if time.perf_counter() - t0 > seconds_cap:
             break
@@ -163,11 +165,13 @@ def run_reference(args, rank):
     g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
+    kw = step_kwargs(1)
+    kw.pop("precision")
     for _ in range(args.warmup):
-        g.step(**step_kwargs(1))
+        g.step(**kw)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        g.step(**step_kwargs(1))
+        g.step(**kw)
     dt = time.perf_counter() - t0
     v = NI * NJ * args.steps / dt / 1e6
     line = {
@@ -191,7 +195,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
+    global PRECISION, WORKLOAD
+    if args.precision == "mixed":
+        PRECISION = 1
+        WORKLOAD = WORKLOAD.replace("fp64", "mixed-fp32-operator")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -258,16 +267,17 @@ def main():
     nbytes = Qh.nbytes
 
     # ---- roofline of the dominant phase (live CUDA-event timing inside the timed region) ----
-    pk, pk_kind = peaks()
     dom = max(prof, key=lambda p: prof[p][0])
     dom_ms = prof[dom][0] / args.steps
     launches = sum(v[1] for v in prof.values())
-    algo_bytes = ALGO_BYTES_PER_CELL[dom] * N
-    achieved = algo_bytes / (dom_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": None, "kernel_phase": dom,
-            "peak_kind": pk_kind,
-            "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof}}
+    flops = FP64_FLOPS_PER_CELL[dom] * N
+    achieved = flops / (dom_ms / 1e3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
+            "kernel_phase": dom, "peak_kind": "nominal FP64 of the recipe (1.25 TFLOP/s)",
+            "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof},
+            "phases_fp64_frac": {p: (FP64_FLOPS_PER_CELL[p] * N / (prof[p][0] / args.steps / 1e3) / 1e9
+                                     / FP64_PEAK_GFLOPS) if prof[p][0] > 0 else None for p in prof}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -278,7 +288,8 @@ def main():
         line = {
             "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if PRECISION == 0 else "f64 residual/update, f32 operator",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "species": 11, "temperatures": 2,
                        "scheme": "CS-1 split LU-SGS", "cfl": CFL,

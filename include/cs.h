@@ -52,7 +52,10 @@ enum { CS_BC_PERIODIC = 0, CS_BC_WALL = 1, CS_BC_FARFIELD = 2, CS_BC_OUTFLOW = 3
  * reactions (Sec. 3.2 / 3.3 of the paper: Park's model). */
 enum { CS_MECH_PERFECT = 0, CS_MECH_AIR5 = 1, CS_MECH_AIR11 = 2 };
 enum { CS_SCHEME_SPLIT = 0, CS_SCHEME_COUPLED = 1 };
-enum { CS_FP64 = 0 };
+/* Precision of the implicit operator: CS_FP64 everywhere, or CS_MIXED = the LU-SGS sweeps of
+ * the split operator compute in FP32 (from FP64 spectral radii, diagonals and right-hand side,
+ * into FP64 increments) while the residual, the corrections and the update stay FP64. */
+enum { CS_FP64 = 0, CS_MIXED = 1 };
 
 typedef struct cs_grid_s *cs_grid;
 
@@ -85,7 +88,7 @@ typedef struct {
   double cfl;              /* target CFL */
   double cfl_start;        /* first CFL of the geometric ramp */
   int ramp_iters;          /* ramp length in iterations (0: no ramp) */
-  int precision;           /* CS_FP64 */
+  int precision;           /* CS_FP64 or CS_MIXED (split scheme) */
   int iters;               /* iterations to run */
 } cs_step_opts;
 
@@ -128,7 +131,8 @@ cs_status cs_residual(cs_grid g, double *R_out, double norms_host[3]);
 
 /* Split operator (Sec. 2.3.1-2.3.2) solved by LU-SGS (Sec. 2.2) with the local time step of
  * the given CFL; uses R of the last cs_residual.  dQ_out (host or device,
- * [nsplit][ncell], nullable).  precision: CS_FP64.  Errors: CS_ERR_STATE (no residual). */
+ * [nsplit][ncell], nullable).  precision: CS_FP64 or CS_MIXED.  Errors: CS_ERR_STATE (no
+ * residual). */
 cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double *dQ_out);
 
 /* Coupled (CI) operator: unified spectral radius, dense diagonal blocks with the source

@@ -515,13 +515,14 @@ static cs_status set_cfl(cs_grid g, double cfl) {
 
 extern "C" cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double* dQ_out) {
   if (!g) return CS_ERR_ARG;
-  if (precision != CS_FP64) return fail(g, CS_ERR_ARG, "unsupported precision %d", precision);
+  if (precision != CS_FP64 && precision != CS_MIXED)
+    return fail(g, CS_ERR_ARG, "unsupported precision %d", precision);
   if (!g->have_R) return fail(g, CS_ERR_STATE, "cs_lusgs_split before cs_residual");
   cs_status st = begin(g);
   if (st) return st;
   if ((st = set_cfl(g, cfl))) return st;
   g->L->spectral(g->g, g->stream);
-  g->L->sweep_split(g->g, g->stream);
+  g->L->sweep_split(g->g, g->stream, precision == CS_MIXED);
   if (dQ_out)
     CUDA_TRY(g, cudaMemcpyAsync(dQ_out, g->g.dQ, (size_t)(g->L->nF + g->L->ns) * g->g.N * sizeof(double),
                                 cudaMemcpyDefault, g->stream));
@@ -591,7 +592,8 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
   if (!g->have_bc) return fail(g, CS_ERR_STATE, "cs_step before cs_set_boundary");
   if (o->scheme != CS_SCHEME_SPLIT && o->scheme != CS_SCHEME_COUPLED) return CS_ERR_ARG;
   if (o->scheme == CS_SCHEME_SPLIT && o->correction != 1 && o->correction != 2) return CS_ERR_ARG;
-  if (o->precision != CS_FP64 || o->iters < 0) return CS_ERR_ARG;
+  if ((o->precision != CS_FP64 && o->precision != CS_MIXED) || o->iters < 0) return CS_ERR_ARG;
+  const bool mixed = o->precision == CS_MIXED;
   cs_status st = CS_OK;
   if (o->scheme == CS_SCHEME_COUPLED && (st = ensure_ci(g))) return fail(g, st, "allocation");
   if ((st = begin(g))) return st;
@@ -620,11 +622,11 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
     if (o->scheme == CS_SCHEME_SPLIT) {
       prof_record(g, slot, 5);
       // the cluster path runs both sweeps in one launch (timed as phase 5)
-      nf = g->L->use_cluster ? g->L->sweep_split_cluster(d, g->stream) : 0;
+      nf = g->L->use_cluster ? g->L->sweep_split_cluster(d, g->stream, mixed) : 0;
       nb = 0;
-      if (!nf) nf = g->L->sweep_split_dir(d, g->stream, true);
+      if (!nf) nf = g->L->sweep_split_dir(d, g->stream, true, mixed);
       prof_record(g, slot, 6);
-      if (!g->L->use_cluster || !g->L->sweep_split_cluster_ok) nb = g->L->sweep_split_dir(d, g->stream, false);
+      if (!g->L->use_cluster || !g->L->sweep_split_cluster_ok) nb = g->L->sweep_split_dir(d, g->stream, false, mixed);
       prof_record(g, slot, 7);
       g->L->correct(d, g->stream, o->correction, o->clip, d.dQ);
     } else {

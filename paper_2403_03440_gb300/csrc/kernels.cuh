@@ -1280,33 +1280,33 @@ __global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
 // Flux Jacobian times a vector at a cell state (Sec. 2.3 Eq. (convectiveJacobian)),
 // matrix-free.  Flow block with frozen mass fractions (Sec. 2.3.1) and coupled variables.
 // ---------------------------------------------------------------------------------------
-template <class G, int ND>
+template <class G, int ND, class T = double>
 struct CellState {       // what the flow Jacobian needs from the neighbour cell
-  double u[ND], H, ev, beta, prev, pY;   // pY = sum_s Y_s dp/drho_s
+  T u[ND], H, ev, beta, prev, pY;   // pY = sum_s Y_s dp/drho_s
 };
 
-template <class G, int ND>
-__device__ __forceinline__ void load_state(const DevGrid& g, int c, CellState<G, ND>& s) {
+template <class G, int ND, class T>
+__device__ __forceinline__ void load_state(const DevGrid& g, int c, CellState<G, ND, T>& s) {
   using A = Aux<G, ND>;
   const size_t N = g.N;
   const double* W = g.W;
 #pragma unroll
-  for (int d = 0; d < ND; ++d) s.u[d] = W[(A::U + d) * N + c];
-  s.H = W[A::H * N + c];
-  s.ev = (G::NTEMP == 2) ? W[A::EV * N + c] : 0.0;
-  s.beta = W[A::BETA * N + c];
-  s.prev = W[A::PREV * N + c];
-  s.pY = W[A::PY * N + c];
+  for (int d = 0; d < ND; ++d) s.u[d] = (T)W[(A::U + d) * N + c];
+  s.H = (T)W[A::H * N + c];
+  s.ev = (G::NTEMP == 2) ? (T)W[A::EV * N + c] : T(0);
+  s.beta = (T)W[A::BETA * N + c];
+  s.prev = (T)W[A::PREV * N + c];
+  s.pY = (T)W[A::PY * N + c];
 }
 
 // flow block: x = (drho, dm, drhoE, [drho e_v]) -> A(S) x.  With a = rho dU = S.dm - U drho
 // the product needs no division: dF_m = dm U + u a + dp S, dF_E = (drhoE + dp) U + H a,
-// dF_ev = d(rho e_v) U + e_v a.
-template <class G, int ND>
-__device__ __forceinline__ void jvp_flow(const CellState<G, ND>& w, const double* S, const double* x,
-                                         double* y) {
+// dF_ev = d(rho e_v) U + e_v a.  T is the compute type of the operator (FP64, or FP32 in the
+// mixed-precision form).
+template <class G, int ND, class T>
+__device__ __forceinline__ void jvp_flow(const CellState<G, ND, T>& w, const T* S, const T* x, T* y) {
   constexpr int NF = Aux<G, ND>::NF;
-  double U = 0.0, Sdm = 0.0, dp = w.pY * x[0] + w.beta * x[ND + 1];
+  T U = 0, Sdm = 0, dp = w.pY * x[0] + w.beta * x[ND + 1];
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
     U += w.u[d] * S[d];
@@ -1314,7 +1314,7 @@ __device__ __forceinline__ void jvp_flow(const CellState<G, ND>& w, const double
     dp -= w.beta * w.u[d] * x[1 + d];
   }
   if (G::NTEMP == 2) dp += w.prev * x[NF - 1];
-  const double a = Sdm - U * x[0];
+  const T a = Sdm - U * x[0];
   y[0] = Sdm;
 #pragma unroll
   for (int d = 0; d < ND; ++d) y[1 + d] = x[1 + d] * U + w.u[d] * a + dp * S[d];
@@ -1343,7 +1343,7 @@ __device__ __forceinline__ bool hyperplane_cell(const DevGrid& g, int h, int t, 
   return i >= 0 && i < g.ni;
 }
 
-template <class G, int ND, bool FWD>
+template <class G, int ND, bool FWD, class T>
 __global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, int cnt) {
   using A = Aux<G, ND>;
   constexpr int NS = G::NS, NF = A::NF;
@@ -1352,17 +1352,17 @@ __global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, i
   if (t >= cnt || !hyperplane_cell<G, ND>(g, h, t + off, i, j, k)) return;
   const int c = cell_of(g, i, j, k);
   const size_t N = g.N;
-  double acc[NF], accs[NS];
+  T acc[NF], accs[NS];
   if (FWD) {
 #pragma unroll
-    for (int s = 0; s < NS; ++s) accs[s] = -g.R[s * N + c];
+    for (int s = 0; s < NS; ++s) accs[s] = (T)(-g.R[s * N + c]);
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] = g.rhsF[q * N + c];
+    for (int q = 0; q < NF; ++q) acc[q] = (T)g.rhsF[q * N + c];
   } else {
 #pragma unroll
-    for (int q = 0; q < NF; ++q) acc[q] = 0.0;
+    for (int q = 0; q < NF; ++q) acc[q] = 0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) accs[s] = 0.0;
+    for (int s = 0; s < NS; ++s) accs[s] = 0;
   }
   const double* X = FWD ? g.dQs : g.dQ;     // solution being built by this sweep
 #pragma unroll
@@ -1372,41 +1372,44 @@ __global__ void __launch_bounds__(64) k_sweep_split(DevGrid g, int h, int off, i
       bool lower;
       const int nb = neighbour(g, i, j, k, d, s, lower);
       if (nb < 0 || lower != FWD) continue;
-      const double* Sf = face_vec(g, d, i, j, k, s);
-      CellState<G, ND> w;
-      load_state<G, ND>(g, nb, w);
-      double xn[NF], ax[NF];
+      const double* Sd = face_vec(g, d, i, j, k, s);
+      T Sf[ND];
 #pragma unroll
-      for (int q = 0; q < NF; ++q) xn[q] = X[q * N + nb];
-      jvp_flow<G, ND>(w, Sf, xn, ax);
-      const double l = g.lamF[d * N + nb];
+      for (int q = 0; q < ND; ++q) Sf[q] = (T)Sd[q];
+      CellState<G, ND, T> w;
+      load_state<G, ND, T>(g, nb, w);
+      T xn[NF], ax[NF];
+#pragma unroll
+      for (int q = 0; q < NF; ++q) xn[q] = (T)X[q * N + nb];
+      jvp_flow<G, ND, T>(w, Sf, xn, ax);
+      const T l = (T)g.lamF[d * N + nb];
 #pragma unroll
       for (int q = 0; q < NF; ++q) {
-        if (s < 0) acc[q] += 0.5 * (ax[q] + l * xn[q]);
-        else acc[q] -= 0.5 * (ax[q] - l * xn[q]);
+        if (s < 0) acc[q] += T(0.5) * (ax[q] + l * xn[q]);
+        else acc[q] -= T(0.5) * (ax[q] - l * xn[q]);
       }
-      double U = 0.0;
+      T U = 0;
 #pragma unroll
       for (int q = 0; q < ND; ++q) U += w.u[q] * Sf[q];
-      const double lc = g.lamC[d * N + nb];
+      const T lc = (T)g.lamC[d * N + nb];
 #pragma unroll
       for (int sp = 0; sp < NS; ++sp) {
-        const double xs = X[(NF + sp) * N + nb];
-        if (s < 0) accs[sp] += 0.5 * (U * xs + lc * xs);
-        else accs[sp] -= 0.5 * (U * xs - lc * xs);
+        const T xs = (T)X[(NF + sp) * N + nb];
+        if (s < 0) accs[sp] += T(0.5) * (U * xs + lc * xs);
+        else accs[sp] -= T(0.5) * (U * xs - lc * xs);
       }
     }
   double* Y = FWD ? g.dQs : g.dQ;
 #pragma unroll
   for (int q = 0; q < NF; ++q) {
-    const double iD = (G::NTEMP == 2 && q == NF - 1) ? g.invD[N + c] : g.invD[c];
-    const double v = acc[q] * iD;
-    Y[q * N + c] = FWD ? v : g.dQs[q * N + c] + v;
+    const T iD = (T)((G::NTEMP == 2 && q == NF - 1) ? g.invD[N + c] : g.invD[c]);
+    const T v = acc[q] * iD;
+    Y[q * N + c] = FWD ? (double)v : (double)((T)g.dQs[q * N + c] + v);
   }
 #pragma unroll
   for (int sp = 0; sp < NS; ++sp) {
-    const double v = accs[sp] * g.invD[(2 + sp) * N + c];
-    Y[(NF + sp) * N + c] = FWD ? v : g.dQs[(NF + sp) * N + c] + v;
+    const T v = accs[sp] * (T)g.invD[(2 + sp) * N + c];
+    Y[(NF + sp) * N + c] = FWD ? (double)v : (double)((T)g.dQs[(NF + sp) * N + c] + v);
   }
 }
 
@@ -1445,40 +1448,52 @@ __device__ __forceinline__ T* dsmem(T* p, unsigned rank) {
   return reinterpret_cast<T*>(out);
 }
 
-constexpr int kClusterRows = 32;   // rows per CTA (one warp)
+constexpr int kClusterRows = 32;   // max rows per CTA
+constexpr int kClusterWarps = 1;   // warps per CTA (8 warps measured slower than 1: the per-step
+                                   // cost is load latency and FP64 dependency depth)
+// Row handled by this thread of the CTA (rows t = warp + kClusterWarps k for the first lane of
+// each of the rpw lane groups), or -1 for a thread that only takes part in the barriers.
+__device__ __forceinline__ int cluster_row(int R) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int rpw = (R + kClusterWarps - 1) / kClusterWarps;     // rows per warp (<= 4)
+  const int stride = 32 / rpw;
+  if (lane % stride != 0) return -1;
+  const int t = warp + kClusterWarps * (lane / stride);
+  return t < R ? t : -1;
+}
 
-template <class G, int NV>
+template <class G, int NV, class T>
 struct Xchg {
-  double v[2][kClusterRows][NV];
+  T v[2][kClusterRows][NV];
 };
 
 // one neighbour contribution of the flow block: nb on side s of direction d
-template <class G>
-__device__ __forceinline__ void flow_contrib(const CellState<G, 2>& w, double lam, const double* Sf,
-                                             const double* xn, int side, double* acc) {
+template <class G, class T>
+__device__ __forceinline__ void flow_contrib(const CellState<G, 2, T>& w, T lam, const T* Sf,
+                                             const T* xn, int side, T* acc) {
   constexpr int NF = Aux<G, 2>::NF;
-  double ax[NF];
-  jvp_flow<G, 2>(w, Sf, xn, ax);
+  T ax[NF];
+  jvp_flow<G, 2, T>(w, Sf, xn, ax);
 #pragma unroll
   for (int q = 0; q < NF; ++q) {
-    if (side < 0) acc[q] += 0.5 * (ax[q] + lam * xn[q]);
-    else acc[q] -= 0.5 * (ax[q] - lam * xn[q]);
+    if (side < 0) acc[q] += T(0.5) * (ax[q] + lam * xn[q]);
+    else acc[q] -= T(0.5) * (ax[q] - lam * xn[q]);
   }
 }
 
 // Static inputs of one cell for the flow sweep (loaded one step ahead).
-template <class G>
+template <class G, class T>
 struct FlowStep {
   static constexpr int NF = Aux<G, 2>::NF;
-  CellState<G, 2> me, jn;
-  double lam0, jlam, iD, iDev, base[NF], Si[2], Sj[2], Sw[2];
+  CellState<G, 2, T> me, jn;
+  T lam0, jlam, iD, iDev, base[NF], Si[2], Sj[2], Sw[2];
   int c;
   bool act, hasj;
 };
 
-template <class G>
+template <class G, class T>
 __device__ __forceinline__ void flow_step_load(const DevGrid& g, int q, int j, bool row, bool fwd,
-                                               FlowStep<G>& f) {
+                                               FlowStep<G, T>& f) {
   constexpr int NF = Aux<G, 2>::NF;
   const size_t N = g.N;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
@@ -1490,74 +1505,74 @@ __device__ __forceinline__ void flow_step_load(const DevGrid& g, int q, int j, b
   if (!f.act) return;
   const int c = i + ni * j;
   f.c = c;
-  load_state<G, 2>(g, c, f.me);
-  f.lam0 = g.lamF[c];
-  f.iD = g.invD[c];
-  f.iDev = g.invD[N + c];
+  load_state<G, 2, T>(g, c, f.me);
+  f.lam0 = (T)g.lamF[c];
+  f.iD = (T)g.invD[c];
+  f.iDev = (T)g.invD[N + c];
 #pragma unroll
-  for (int v = 0; v < NF; ++v) f.base[v] = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
+  for (int v = 0; v < NF; ++v) f.base[v] = (T)(fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c]);
   const double* Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
   const double* Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
   const double* Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
-  f.Si[0] = Si[0]; f.Si[1] = Si[1];
-  f.Sj[0] = Sj[0]; f.Sj[1] = Sj[1];
-  f.Sw[0] = Sw[0]; f.Sw[1] = Sw[1];
+  f.Si[0] = (T)Si[0]; f.Si[1] = (T)Si[1];
+  f.Sj[0] = (T)Sj[0]; f.Sj[1] = (T)Sj[1];
+  f.Sw[0] = (T)Sw[0]; f.Sw[1] = (T)Sw[1];
   if (f.hasj) {
     const int cn = i + ni * jj;
-    load_state<G, 2>(g, cn, f.jn);
-    f.jlam = g.lamF[N + cn];
+    load_state<G, 2, T>(g, cn, f.jn);
+    f.jlam = (T)g.lamF[N + cn];
   }
 }
 
-template <class G>
-__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF>& xc) {
+template <class G, class T>
+__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF, T>& xc) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF;
   const size_t N = g.N;
   const unsigned rank = cluster_ctarank();
-  const int t = threadIdx.x;
+  const int t = cluster_row(R);
   const int j = rank * R + t;
-  const bool row = t < R && j < g.nj;
+  const bool row = t >= 0 && j < g.nj;
   const bool per = g.bc[0] == BC_PERIODIC;
   const int ni = g.ni, H = ni + g.nj - 2;
   for (int pass = 0; pass < 2; ++pass) {
     const bool fwd = pass == 0;
-    double prevx[NF], firstx[NF];
-    CellState<G, 2> prevS, firstS;
-    double prevL = 0.0, firstL = 0.0;
-    FlowStep<G> cur, nxt;
-    flow_step_load<G>(g, 0, j, row, fwd, cur);
+    T prevx[NF], firstx[NF];
+    CellState<G, 2, T> prevS, firstS;
+    T prevL = 0, firstL = 0;
+    FlowStep<G, T> cur, nxt;
+    flow_step_load<G, T>(g, 0, j, row, fwd, cur);
     for (int q = 0; q <= H; ++q) {
       const int i = (fwd ? q : H - q) - j;
-      flow_step_load<G>(g, q + 1, j, row, fwd, nxt);     // prefetch the next step
+      flow_step_load<G, T>(g, q + 1, j, row, fwd, nxt);     // prefetch the next step
       if (q > 0) cluster_wait();
       if (cur.act) {
-        double acc[NF];
+        T acc[NF];
 #pragma unroll
-        for (int v = 0; v < NF; ++v) acc[v] = fwd ? cur.base[v] : 0.0;
+        for (int v = 0; v < NF; ++v) acc[v] = fwd ? cur.base[v] : T(0);
         if (fwd) {
-          if (i > 0) flow_contrib<G>(prevS, prevL, cur.Si, prevx, -1, acc);
-          if (per && i == ni - 1) flow_contrib<G>(firstS, firstL, cur.Sw, firstx, +1, acc);
+          if (i > 0) flow_contrib<G, T>(prevS, prevL, cur.Si, prevx, -1, acc);
+          if (per && i == ni - 1) flow_contrib<G, T>(firstS, firstL, cur.Sw, firstx, +1, acc);
         } else {
-          if (per && i == 0) flow_contrib<G>(firstS, firstL, cur.Sw, firstx, -1, acc);
-          if (i < ni - 1) flow_contrib<G>(prevS, prevL, cur.Si, prevx, +1, acc);
+          if (per && i == 0) flow_contrib<G, T>(firstS, firstL, cur.Sw, firstx, -1, acc);
+          if (i < ni - 1) flow_contrib<G, T>(prevS, prevL, cur.Si, prevx, +1, acc);
         }
         if (cur.hasj) {
-          const double* src;
+          const T* src;
           const int par = (q - 1) & 1;
           if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
           else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
-          double xn[NF];
+          T xn[NF];
 #pragma unroll
           for (int v = 0; v < NF; ++v) xn[v] = src[v];
-          flow_contrib<G>(cur.jn, cur.jlam, cur.Sj, xn, fwd ? -1 : +1, acc);
+          flow_contrib<G, T>(cur.jn, cur.jlam, cur.Sj, xn, fwd ? -1 : +1, acc);
         }
         double* out = fwd ? g.dQs : g.dQ;
 #pragma unroll
         for (int v = 0; v < NF; ++v) {
-          const double d = (G::NTEMP == 2 && v == NF - 1) ? cur.iDev : cur.iD;
-          const double x = fwd ? acc[v] * d : cur.base[v] + acc[v] * d;
-          out[v * N + cur.c] = x;
+          const T d = (G::NTEMP == 2 && v == NF - 1) ? cur.iDev : cur.iD;
+          const T x = fwd ? acc[v] * d : cur.base[v] + acc[v] * d;
+          out[v * N + cur.c] = (double)x;
           xc.v[q & 1][t][v] = x;
           prevx[v] = x;
         }
@@ -1579,101 +1594,101 @@ __device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::N
 
 constexpr int kSpeciesGroup = 4;   // species per cluster (they share u, lambda and S)
 
-template <class G>
-__device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, kSpeciesGroup>& xc) {
+template <class G, class T>
+__device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, kSpeciesGroup, T>& xc) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF, SG = kSpeciesGroup;
   const size_t N = g.N;
   const unsigned rank = cluster_ctarank();
-  const int t = threadIdx.x;
+  const int t = cluster_row(R);
   const int j = rank * R + t;
-  const bool row = t < R && j < g.nj;
+  const bool row = t >= 0 && j < g.nj;
   const bool per = g.bc[0] == BC_PERIODIC;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
   const int ns = (G::NS - s0 < SG) ? G::NS - s0 : SG;
   for (int pass = 0; pass < 2; ++pass) {
     const bool fwd = pass == 0;
-    double prevx[SG], firstx[SG], prevU[2] = {0, 0}, firstU[2] = {0, 0}, prevL = 0.0, firstL = 0.0;
+    T prevx[SG], firstx[SG], prevU[2] = {0, 0}, firstU[2] = {0, 0}, prevL = 0, firstL = 0;
 #pragma unroll
-    for (int k = 0; k < SG; ++k) { prevx[k] = 0.0; firstx[k] = 0.0; }
+    for (int k = 0; k < SG; ++k) { prevx[k] = 0; firstx[k] = 0; }
     for (int q = 0; q <= H; ++q) {
       const int h = fwd ? q : H - q;
       const int i = h - j;
       const bool act = row && i >= 0 && i < ni;
       const int jj = fwd ? j - 1 : j + 1;
       const bool hasj = act && jj >= 0 && jj < nj;
-      double u0 = 0, u1 = 0, lam0 = 0, iD[SG], base[SG], ju0 = 0, ju1 = 0, jlam = 0;
-      double Si0 = 0, Si1 = 0, Sj0 = 0, Sj1 = 0, Sw0 = 0, Sw1 = 0;
+      T u0 = 0, u1 = 0, lam0 = 0, iD[SG], base[SG], ju0 = 0, ju1 = 0, jlam = 0;
+      T Si0 = 0, Si1 = 0, Sj0 = 0, Sj1 = 0, Sw0 = 0, Sw1 = 0;
       int c = 0;
       if (act) {
         c = i + ni * j;
-        u0 = g.W[A::U * N + c];
-        u1 = g.W[(A::U + 1) * N + c];
-        lam0 = g.lamC[c];
+        u0 = (T)g.W[A::U * N + c];
+        u1 = (T)g.W[(A::U + 1) * N + c];
+        lam0 = (T)g.lamC[c];
 #pragma unroll
         for (int k = 0; k < SG; ++k) {
           if (k >= ns) continue;
-          iD[k] = g.invD[(2 + s0 + k) * N + c];
-          base[k] = fwd ? -g.R[(size_t)(s0 + k) * N + c] : g.dQs[(size_t)(NF + s0 + k) * N + c];
+          iD[k] = (T)g.invD[(2 + s0 + k) * N + c];
+          base[k] = (T)(fwd ? -g.R[(size_t)(s0 + k) * N + c] : g.dQs[(size_t)(NF + s0 + k) * N + c]);
         }
         const double* Si = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? i : i + 1, j, 0);
         const double* Sj = g.S[1] + 3 * (size_t)face_of(g, 1, i, fwd ? j : j + 1, 0);
         const double* Sw = g.S[0] + 3 * (size_t)face_of(g, 0, fwd ? ni : 0, j, 0);
-        Si0 = Si[0]; Si1 = Si[1]; Sj0 = Sj[0]; Sj1 = Sj[1]; Sw0 = Sw[0]; Sw1 = Sw[1];
+        Si0 = (T)Si[0]; Si1 = (T)Si[1]; Sj0 = (T)Sj[0]; Sj1 = (T)Sj[1]; Sw0 = (T)Sw[0]; Sw1 = (T)Sw[1];
         if (hasj) {
           const int cn = i + ni * jj;
-          ju0 = g.W[A::U * N + cn];
-          ju1 = g.W[(A::U + 1) * N + cn];
-          jlam = g.lamC[N + cn];
+          ju0 = (T)g.W[A::U * N + cn];
+          ju1 = (T)g.W[(A::U + 1) * N + cn];
+          jlam = (T)g.lamC[N + cn];
         }
       }
       if (q > 0) cluster_wait();
       if (act) {
-        double acc[SG];
+        T acc[SG];
 #pragma unroll
-        for (int k = 0; k < SG; ++k) acc[k] = fwd ? base[k] : 0.0;
+        for (int k = 0; k < SG; ++k) acc[k] = fwd ? base[k] : T(0);
         // coefficient of a neighbour: minus side (U + lam)/2, plus side -(U - lam)/2
-        auto coef = [](double ua, double ub, double lam, double s0_, double s1_, int side) {
-          const double U = ua * s0_ + ub * s1_;
-          return side < 0 ? 0.5 * (U + lam) : -0.5 * (U - lam);
+        auto coef = [](T ua, T ub, T lam, T s0_, T s1_, int side) {
+          const T U = ua * s0_ + ub * s1_;
+          return side < 0 ? T(0.5) * (U + lam) : T(-0.5) * (U - lam);
         };
         if (fwd) {
           if (i > 0) {
-            const double k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, -1);
+            const T k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, -1);
 #pragma unroll
             for (int k = 0; k < SG; ++k) acc[k] += k0 * prevx[k];
           }
           if (per && i == ni - 1) {
-            const double k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, +1);
+            const T k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, +1);
 #pragma unroll
             for (int k = 0; k < SG; ++k) acc[k] += k0 * firstx[k];
           }
         } else {
           if (per && i == 0) {
-            const double k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, -1);
+            const T k0 = coef(firstU[0], firstU[1], firstL, Sw0, Sw1, -1);
 #pragma unroll
             for (int k = 0; k < SG; ++k) acc[k] += k0 * firstx[k];
           }
           if (i < ni - 1) {
-            const double k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, +1);
+            const T k0 = coef(prevU[0], prevU[1], prevL, Si0, Si1, +1);
 #pragma unroll
             for (int k = 0; k < SG; ++k) acc[k] += k0 * prevx[k];
           }
         }
         if (hasj) {
           const int par = (q - 1) & 1;
-          const double* src;
+          const T* src;
           if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
           else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
-          const double k0 = coef(ju0, ju1, jlam, Sj0, Sj1, fwd ? -1 : +1);
+          const T k0 = coef(ju0, ju1, jlam, Sj0, Sj1, fwd ? -1 : +1);
 #pragma unroll
           for (int k = 0; k < SG; ++k) acc[k] += k0 * src[k];
         }
 #pragma unroll
         for (int k = 0; k < SG; ++k) {
-          if (k >= ns) { xc.v[q & 1][t][k] = 0.0; prevx[k] = 0.0; continue; }
-          const double x = fwd ? acc[k] * iD[k] : base[k] + acc[k] * iD[k];
-          (fwd ? g.dQs : g.dQ)[(size_t)(NF + s0 + k) * N + c] = x;
+          if (k >= ns) { xc.v[q & 1][t][k] = 0; prevx[k] = 0; continue; }
+          const T x = fwd ? acc[k] * iD[k] : base[k] + acc[k] * iD[k];
+          (fwd ? g.dQs : g.dQ)[(size_t)(NF + s0 + k) * N + c] = (double)x;
           xc.v[q & 1][t][k] = x;
           prevx[k] = x;
         }
@@ -1697,14 +1712,14 @@ __device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, k
 template <class G>
 constexpr int species_clusters() { return (G::NS + kSpeciesGroup - 1) / kSpeciesGroup; }
 
-template <class G>
-__global__ void __launch_bounds__(kClusterRows) k_split_cluster(DevGrid g, int R) {
+template <class G, class T>
+__global__ void __launch_bounds__(32 * kClusterWarps) k_split_cluster(DevGrid g, int R) {
   constexpr int NV = Aux<G, 2>::NF > kSpeciesGroup ? Aux<G, 2>::NF : kSpeciesGroup;
-  __shared__ Xchg<G, NV> xf;
+  __shared__ Xchg<G, NV, double> xf;   // sized for the widest use
   const int comp = blockIdx.x / (int)cluster_nctarank();   // uniform within a cluster
-  if (comp == 0) sweep_flow_cluster<G>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF>*>(&xf));
-  else sweep_species_cluster<G>(g, R, (comp - 1) * kSpeciesGroup,
-                                *reinterpret_cast<Xchg<G, kSpeciesGroup>*>(&xf));
+  if (comp == 0) sweep_flow_cluster<G, T>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF, T>*>(&xf));
+  else sweep_species_cluster<G, T>(g, R, (comp - 1) * kSpeciesGroup,
+                                   *reinterpret_cast<Xchg<G, kSpeciesGroup, T>*>(&xf));
 }
 
 // ---------------------------------------------------------------------------------------

@@ -26,15 +26,16 @@ struct Launcher {
   virtual void assemble(const DevGrid& g, cudaStream_t st, int stag, double* out) = 0;
   virtual void spectral(const DevGrid& g, cudaStream_t st) = 0;
   // both sweeps; returns launches (the cluster path does both in one launch when available)
-  int sweep_split(const DevGrid& g, cudaStream_t st) {
-    const int n = use_cluster ? sweep_split_cluster(g, st) : 0;
+  // mixed = true: the sweeps compute in FP32 (from FP64 inputs, into FP64 increments)
+  int sweep_split(const DevGrid& g, cudaStream_t st, bool mixed = false) {
+    const int n = use_cluster ? sweep_split_cluster(g, st, mixed) : 0;
     if (n) return n;
-    return sweep_split_dir(g, st, true) + sweep_split_dir(g, st, false);
+    return sweep_split_dir(g, st, true, mixed) + sweep_split_dir(g, st, false, mixed);
   }
-  virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st) = 0;
+  virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed = false) = 0;
   bool use_cluster = true;
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
-  virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;   // returns launches
+  virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
   virtual int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;
@@ -146,11 +147,12 @@ struct LauncherT : Launcher {
   }
 
   // Cluster size for the cluster sweep (0: not available for this grid / device).
-  int cluster_size(const DevGrid& g) {
+  template <class T>
+  int cluster_size(const DevGrid& g, int& probed) {
     if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
-    if (probed_ >= 0) return probed_;
-    probed_ = 0;
-    auto kern = k_split_cluster<G>;
+    if (probed >= 0) return probed;
+    probed = 0;
+    auto kern = k_split_cluster<G, T>;
     for (int C : {16, 8, 4, 2}) {
       const int R = (g.nj + C - 1) / C;
       if (R > kClusterRows) continue;
@@ -161,7 +163,7 @@ struct LauncherT : Launcher {
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
-      cfg.blockDim = dim3(kClusterRows);
+      cfg.blockDim = dim3(32 * kClusterWarps);
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = C;
       at[0].val.clusterDim.y = 1;
@@ -170,25 +172,29 @@ struct LauncherT : Launcher {
       cfg.numAttrs = 1;
       int n = 0;
       if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
-        probed_ = C;
+        probed = C;
         break;
       }
       cudaGetLastError();
     }
-    return probed_;
+    return probed;
   }
-  int probed_ = -1;
+  int probed64_ = -1, probed32_ = -1;
 
   // one launch: both sweeps of the flow block and of every species (returns launches)
-  int sweep_split_cluster(const DevGrid& g, cudaStream_t st) override {
+  int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed) override {
+    return mixed ? sweep_cluster_t<float>(g, st, probed32_) : sweep_cluster_t<double>(g, st, probed64_);
+  }
+  template <class T>
+  int sweep_cluster_t(const DevGrid& g, cudaStream_t st, int& probed) {
     sweep_split_cluster_ok = false;
     if (ND != 2) return 0;
-    const int C = cluster_size(g);
+    const int C = cluster_size<T>(g, probed);
     if (C == 0) return 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
     cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
-    cfg.blockDim = dim3(kClusterRows);
+    cfg.blockDim = dim3(32 * kClusterWarps);
     cfg.stream = st;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
@@ -197,7 +203,7 @@ struct LauncherT : Launcher {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const int R = (g.nj + C - 1) / C;
-    if (cudaLaunchKernelEx(&cfg, k_split_cluster<G>, g, R) != cudaSuccess) {
+    if (cudaLaunchKernelEx(&cfg, k_split_cluster<G, T>, g, R) != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
@@ -205,7 +211,7 @@ struct LauncherT : Launcher {
     return 1;
   }
 
-  int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd) override {
+  int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed) override {
     const int H = g.ni + g.nj + (ND == 3 ? g.nk : 1) - 2;
     int launches = 0;
     for (int t = 0; t <= H; ++t) {
@@ -213,8 +219,14 @@ struct LauncherT : Launcher {
       int off, cnt;
       plane_range(g, h, off, cnt);
       if (cnt <= 0) continue;
-      if (fwd) k_sweep_split<G, ND, true><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
-      else k_sweep_split<G, ND, false><<<blocks(cnt, 32), 32, 0, st>>>(g, h, off, cnt);
+      const int nb = blocks(cnt, 32);
+      if (mixed) {
+        if (fwd) k_sweep_split<G, ND, true, float><<<nb, 32, 0, st>>>(g, h, off, cnt);
+        else k_sweep_split<G, ND, false, float><<<nb, 32, 0, st>>>(g, h, off, cnt);
+      } else {
+        if (fwd) k_sweep_split<G, ND, true, double><<<nb, 32, 0, st>>>(g, h, off, cnt);
+        else k_sweep_split<G, ND, false, double><<<nb, 32, 0, st>>>(g, h, off, cnt);
+      }
       ++launches;
     }
     return launches;
