@@ -165,9 +165,11 @@ cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
  * and enables (enable = 1) or disables timing. */
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
 
-/* Implementation options (not part of the method): "cluster_sweep" = 1 (default) runs the 2D
- * split sweeps as one cluster launch where the device supports it, 0 forces one launch per
- * hyperplane.  Both give the same arithmetic.  Errors: CS_ERR_ARG for an unknown name. */
+/* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
+ * split sweeps as one thread-block-cluster launch, choosing per precision between 2 (cluster
+ * kernel over hyperplane-ordered cell records, faster in FP32) and 1 (cluster kernel reading
+ * the cell arrays directly, faster in FP64); 0 runs one launch per hyperplane.  All give the
+ * same arithmetic up to rounding.  Errors: CS_ERR_ARG for an unknown name. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Residual monitors without device allocation (no counterpart in the paper: a service for

@@ -1,0 +1,91 @@
+"""Run a cylinder case to a residual drop and report iterations, device time and the
+stagnation heat flux history (the second half of the benchmark metric: time to a 1e-8
+residual drop, split vs coupled, FP64 vs mixed-precision operator).
+
+Usage (GPU):
+    python -m paper_2403_03440_gb300.convergence --case c1 --scheme cs1 --max-iters 20000
+prints one JSON line.  The residual monitors are r_species and r_energy of cs_residual, each
+divided by its value at the first iteration; the drop is reached when both are <= tol.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+import paper_2403_03440_gb300 as P  # noqa: E402
+
+CASES = {
+    # 2D Mach 10 cylinder, 48 x 32, 5-species one-temperature air
+    "c1": dict(ni=48, nj=32, mech=inputs.MECH_AIR5, mach=10.0, dr1=5e-5),
+    # 2D Mach 15 cylinder, 384 x 256, 11-species two-temperature air
+    "c2": dict(ni=384, nj=256, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5 / 8),
+}
+SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1)}
+
+
+def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1):
+    c = CASES[case]
+    nodes = inputs.cylinder_ogrid(c["ni"], c["nj"], dr1=c["dr1"])
+    fs = inputs.freestream(c["mech"], T=300.0, p=500.0, mach=c["mach"])
+    g = P.Grid(nodes, inputs.cylinder_bc(), c["mech"], limiter=limiter)
+    g.set_boundary(fs, Tw=500.0)
+    g.init_freestream()
+    sch, corr = SCHEMES[scheme]
+    kw = dict(scheme=sch, correction=corr, clip=clip, cfl=cfl, cfl_start=cfl_start,
+              ramp_iters=ramp, precision=precision)
+    first = g.step(iters=1, **kw)
+    r0 = (first["r_species"], first["r_energy"])
+    hist = [(1, 1.0, 1.0, first["q_stag"])]
+    done, status = 1, "max_iters"
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while done < max_iters:
+        try:
+            st = g.step(iters=chunk, **kw)
+        except P.CSError as e:
+            status = f"error: {e}"
+            break
+        done += st["iters_done"]
+        rs, re = st["r_species"] / r0[0], st["r_energy"] / r0[1]
+        hist.append((done, rs, re, st["q_stag"]))
+        if rs <= tol and re <= tol:
+            status = "converged"
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    best = min(max(h[1], h[2]) for h in hist)
+    return dict(case=case, scheme=scheme, precision="mixed" if precision else "fp64", cfl=cfl,
+                limiter=limiter, tol=tol, status=status, iterations=done, seconds=dt,
+                ms_per_iter=1e3 * dt / max(done - 1, 1), min_drop=best,
+                q_stag_final=hist[-1][3], cells=c["ni"] * c["nj"],
+                history=hist[:: max(1, len(hist) // 50)] + [hist[-1]])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="c1", choices=list(CASES))
+    ap.add_argument("--scheme", default="cs1", choices=list(SCHEMES))
+    ap.add_argument("--cfl", type=float, default=10.0)
+    ap.add_argument("--cfl-start", type=float, default=1.0)
+    ap.add_argument("--ramp", type=int, default=100)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iters", type=int, default=20000)
+    ap.add_argument("--chunk", type=int, default=100)
+    ap.add_argument("--limiter", type=int, default=1)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    a = ap.parse_args()
+    P.build()
+    out = run(a.case, a.scheme, a.cfl, a.cfl_start, a.ramp, a.tol, a.max_iters, a.chunk,
+              a.limiter, 1 if a.precision == "mixed" else 0)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -347,6 +347,31 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   ALLOC(d.Vdt, N);
   ALLOC(d.invD, (size_t)(2 + L->ns) * N);
   ALLOC(d.rhsF, (size_t)L->nF * N);
+  d.woff = nullptr;
+  d.wrec = d.wrecs = d.wbase = nullptr;
+  if (nd == 2) {
+    // hyperplane offsets of the wavefront-ordered sweep records (2D)
+    const int H = d.ni + d.nj - 2;
+    std::vector<int> off(H + 2, 0);
+    for (int h = 0; h <= H; ++h) {
+      const int jlo = h - d.ni + 1 > 0 ? h - d.ni + 1 : 0, jhi = h < d.nj - 1 ? h : d.nj - 1;
+      off[h + 1] = off[h] + (jhi - jlo + 1);
+    }
+    int* woff;
+    ALLOC(woff, H + 2);
+    if (cudaMemcpyAsync(woff, off.data(), (H + 2) * sizeof(int), cudaMemcpyHostToDevice, g->stream) != cudaSuccess)
+      return CS_ERR_CUDA;
+    if (cudaStreamSynchronize(g->stream) != cudaSuccess) return CS_ERR_CUDA;
+    d.woff = woff;
+    const size_t groups = (L->ns + 3) / 4;
+    double *wr, *wrs, *wb;
+    ALLOC(wr, (size_t)kRecF * N);
+    ALLOC(wrs, groups * kRecS * N);
+    ALLOC(wb, (8 + 4 * groups) * N);
+    d.wrec = wr;
+    d.wrecs = wrs;
+    d.wbase = wb;
+  }
   ALLOC(d.dQs, (size_t)(L->nF + L->ns) * N);
   ALLOC(d.dQ, (size_t)(L->nF + L->ns) * N);
   ALLOC(d.dQcs, (size_t)L->nci * N);
@@ -707,6 +732,7 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!g || !name) return CS_ERR_ARG;
   if (!strcmp(name, "cluster_sweep")) {
     g->L->use_cluster = value != 0.0;
+    g->L->cluster_kind = value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1);
     return CS_OK;
   }
   return fail(g, CS_ERR_ARG, "unknown option %s", name);

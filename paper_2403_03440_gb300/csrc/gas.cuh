@@ -82,11 +82,13 @@ __constant__ ReactionData c_reactions[21];
 //            so that g_s/(R T) = h0/(R T) - (2.5 [+1]) ln T + gc0 [+ ln(1 - exp(-theta_v/T))]
 //  mwA[s][q], mwAB[s][q]: Millikan-White tau_sq p = exp(A T^-1/3 - AB), AB = A B + 18.42
 //  cbk[s]  = sqrt(8 R_u / (pi M_s)): mean molecular speed = cbk sqrt(T)
+//  Rs[s] = R_u / M_s, hf[s] = h0_s / M_s, invM[s] = 1 / M_s (no division in the kernels)
 struct GasConst {
   double gc0[11];
   double mwA[11][11];
   double mwAB[11][11];
   double cbk[11];
+  double Rs[11], hf[11], invM[11];
 };
 __constant__ GasConst c_gas;
 
@@ -155,7 +157,7 @@ using GasAir11 = Gas<11, 2, 21>;
 // ---- species thermodynamics -------------------------------------------------------------
 
 template <class G>
-__device__ __forceinline__ double Rs(int s) { return kRu / G::sp(s).M; }
+__device__ __forceinline__ double Rs(int s) { return c_gas.Rs[s]; }
 
 // trans(-rot) heat capacity per unit mass
 template <class G>
@@ -166,20 +168,21 @@ __device__ __forceinline__ double cvtr(int s) {
   return G::NTEMP == 1 ? 1.5 * Rs<G>(s) : 0.0;
 }
 
-// Harmonic-oscillator energy and heat capacity per unit mass at temperature T; one exp.
+// Harmonic-oscillator energy and heat capacity per unit mass at temperature T: one exp and
+// one reciprocal (R theta em / (1 - em), R x^2 em / (1 - em)^2 with x = theta/T, em = e^-x).
 template <class G>
 __device__ __forceinline__ void vib(int s, double T, double& e, double& cv) {
   const SpeciesData& d = G::sp(s);
   if (d.kind != DIATOMIC || d.thv <= 0.0) { e = 0.0; cv = 0.0; return; }
   const double x = d.thv / T;
   const double em = exp(-x);
-  const double den = 1.0 - em;
-  const double R = kRu / d.M;
-  e = R * d.thv * em / den;
-  cv = R * x * x * em / (den * den);
+  const double r = 1.0 / (1.0 - em);
+  const double Rem = c_gas.Rs[s] * em * r;
+  e = Rem * d.thv;
+  cv = Rem * x * x * r;
 }
 
 template <class G>
-__device__ __forceinline__ double hf(int s) { return G::sp(s).h0 / G::sp(s).M; }
+__device__ __forceinline__ double hf(int s) { return c_gas.hf[s]; }
 
 }  // namespace cs

@@ -66,6 +66,11 @@ struct DevGrid {
   double* Vdt;            // [N] V / dtau
   double* invD;           // [2 + ns][N]: 1/D_F, 1/D_F,ev, 1/D_s
   double* rhsF;           // [nF][N]: -(sum_s R_s, R_m, R_E, [R_ev])
+  // 2D wavefront sweep: per-cell sweep records in hyperplane order (w = woff[h] + j - jlo(h))
+  const int* woff;        // [H + 2]
+  void* wrec;             // flow records [N][kRecF] (compute type)
+  void* wrecs;            // species-group records [groups][N][kRecS]
+  void* wbase;            // forward results in hyperplane order: flow [N][8], species [groups][N][4]
   int* status;            // [0] code, [1] cell, [2] clip count
   const double* params;   // [0] cfl
 };
@@ -153,21 +158,32 @@ __device__ __forceinline__ void mix_pool(const double* Y, double Tv, double& e, 
   }
 }
 
-// Safeguarded Newton for a monotone energy: returns 0 on convergence, 1 otherwise.
+// Safeguarded Newton for a monotone energy: returns 0 on convergence, 1 otherwise.  The
+// energies at the bracket ends [kTmin, kTmax] are evaluated only when a Newton step leaves the
+// bracket (a state below / above them is clamped to the end, as in a plain bracketed solve).
 template <class G, bool POOL>
 __device__ int solve_temperature(const double* Y, double target, double guess, double& Tout) {
   double lo = kTmin, hi = kTmax, e, cv;
-  if (POOL) mix_pool<G>(Y, lo, e, cv); else mix_e1<G>(Y, lo, e, cv);
-  if (e >= target) { Tout = lo; return 0; }
-  if (POOL) mix_pool<G>(Y, hi, e, cv); else mix_e1<G>(Y, hi, e, cv);
-  if (e <= target) { Tout = hi; return 1; }
+  bool lo_checked = false, hi_checked = false;
   double T = (guess > lo && guess < hi) ? guess : 1000.0;
   for (int it = 0; it < 200; ++it) {
     if (POOL) mix_pool<G>(Y, T, e, cv); else mix_e1<G>(Y, T, e, cv);
     const double f = e - target;
     if (f > 0) hi = T; else lo = T;
     double Tn = (cv > 0) ? T - f / cv : 0.5 * (lo + hi);
-    if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+    if (!(Tn > lo && Tn < hi)) {
+      if (Tn <= lo && lo == kTmin && !lo_checked) {
+        lo_checked = true;
+        if (POOL) mix_pool<G>(Y, kTmin, e, cv); else mix_e1<G>(Y, kTmin, e, cv);
+        if (e >= target) { Tout = kTmin; return 0; }
+      }
+      if (Tn >= hi && hi == kTmax && !hi_checked) {
+        hi_checked = true;
+        if (POOL) mix_pool<G>(Y, kTmax, e, cv); else mix_e1<G>(Y, kTmax, e, cv);
+        if (e <= target) { Tout = kTmax; return 1; }
+      }
+      Tn = 0.5 * (lo + hi);
+    }
     if (fabs(Tn - T) <= 1e-12 * T) { Tout = Tn; return 0; }
     T = Tn;
   }
@@ -371,9 +387,9 @@ template <class G>
 __device__ __forceinline__ void vib_em(int s, double iT, double em, double& e, double& cv) {
   const SpeciesData& d = G::sp(s);
   if (d.kind != DIATOMIC || d.thv <= 0.0) { e = 0.0; cv = 0.0; return; }
-  const double x = d.thv * iT, den = 1.0 - em, R = kRu / d.M;
-  e = R * d.thv * em / den;
-  cv = R * x * x * em / (den * den);
+  const double x = d.thv * iT, r = 1.0 / (1.0 - em), Rem = c_gas.Rs[s] * em * r;
+  e = Rem * d.thv;
+  cv = Rem * x * x * r;
 }
 
 __device__ __forceinline__ double rate_temp(int kind, double T, double Tv) {
@@ -442,7 +458,7 @@ __device__ __forceinline__ void species_term(ChemCtx<G, FULL>& c, const RxTerms&
         const double e = x.third ? d.eff[q] : 0.0;
         const double dRf = t.kf * (dprod_f<RI>(c.X, q) * t.M + t.Pf * e);
         const double dRb = t.kb * (dprod_b<RI>(c.X, q) * t.M + t.Pb * e);
-        c.J[S * NS + q] += Ms * nu * (dRf - dRb) / G::sp(q).M;
+        c.J[S * NS + q] += Ms * nu * (dRf - dRb) * c_gas.invM[q];
       }
     } else {
       const double e = x.third ? d.eff[S] : 0.0;
@@ -522,7 +538,7 @@ __device__ __forceinline__ void chemistry(const double* rhos, double T, double T
   ChemCtx<G, FULL> c;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    c.X[s] = rhos[s] / G::sp(s).M;
+    c.X[s] = rhos[s] * c_gas.invM[s];
     c.omega[s] = 0.0;
     c.jd[s] = 0.0;
     c.wT[s] = 0.0;
@@ -588,7 +604,7 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, const doub
   for (int s = 0; s < NS; ++s) {
     X[s] = 0.0;
     if (G::sp(s).kind == ELECTRON) continue;
-    X[s] = w.rhos[s] / G::sp(s).M;
+    X[s] = w.rhos[s] * c_gas.invM[s];
     xs += X[s];
     ph += w.rhos[s] * Rs<G>(s) * w.T;
   }
@@ -1707,6 +1723,456 @@ __device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, k
     }
     cluster_wait();
   }
+}
+
+
+// ---------------------------------------------------------------------------------------
+// K6c: 2D split sweeps, wavefront-record cluster kernel.  Same arithmetic as K6/K6b; the
+// layout is built for GB300, where a dependent FP64 operation costs ~70 cycles and a scattered
+// global load ~1 us: (1) k_pack_wave writes each cell's sweep inputs into a record, records
+// stored hyperplane by hyperplane, so that the rows one CTA needs at a step are contiguous;
+// (2) every CTA streams its chunk of records into a shared-memory ring with cp.async, kWaveD
+// steps ahead; (3) between the cluster barrier's wait and arrive a row does only the coupling
+// of the neighbouring row (an explicit NF x NF matrix built beforehand) and the diagonal
+// scaling; the contribution of the row's previous cell and the next step's matrices are
+// computed after the arrive, overlapping the barrier latency; (4) the value of a CTA's
+// boundary row is pushed into the neighbouring CTA's shared memory before the arrive.
+// ---------------------------------------------------------------------------------------
+constexpr int kRecF = 24;            // flow record (compute-type values)
+constexpr int kRecS = 20;            // species-group record
+constexpr int kWaveD = 3;            // prefetch distance (steps)
+constexpr int kWaveSlots = kWaveD + 1;
+constexpr int kWaveRows = 32;        // max rows per CTA
+
+// flow record fields
+enum { RF_U = 0, RF_H = 2, RF_EV = 3, RF_BETA = 4, RF_PREV = 5, RF_PY = 6, RF_L0 = 7, RF_L1 = 8,
+       RF_ID = 9, RF_IDEV = 10, RF_RHS = 11, RF_SIM = 16, RF_SIP = 18, RF_SJM = 20, RF_SJP = 22 };
+// species-group record fields
+enum { RS_U = 0, RS_L0 = 2, RS_L1 = 3, RS_SIM = 4, RS_SIP = 6, RS_SJM = 8, RS_SJP = 10,
+       RS_RHS = 12, RS_ID = 16 };
+
+__device__ __forceinline__ int wave_jlo(int h, int ni) { return h - ni + 1 > 0 ? h - ni + 1 : 0; }
+__device__ __forceinline__ int wave_jhi(int h, int nj) { return h < nj - 1 ? h : nj - 1; }
+
+template <class G, class T>
+__global__ void __launch_bounds__(128) k_pack_wave(DevGrid g) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF, NS = G::NS, SG = kSpeciesGroup;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  const int ni = g.ni, i = c % ni, j = c / ni, h = i + j;
+  const size_t w = (size_t)g.woff[h] + (j - wave_jlo(h, ni));
+  const double* W = g.W;
+  const double* Si0 = g.S[0] + 3 * (size_t)face_of(g, 0, i, j, 0);
+  const double* Si1 = g.S[0] + 3 * (size_t)face_of(g, 0, i + 1, j, 0);
+  const double* Sj0 = g.S[1] + 3 * (size_t)face_of(g, 1, i, j, 0);
+  const double* Sj1 = g.S[1] + 3 * (size_t)face_of(g, 1, i, j + 1, 0);
+  T* r = static_cast<T*>(g.wrec) + w * kRecF;
+  r[RF_U] = (T)W[A::U * N + c];
+  r[RF_U + 1] = (T)W[(A::U + 1) * N + c];
+  r[RF_H] = (T)W[A::H * N + c];
+  r[RF_EV] = (G::NTEMP == 2) ? (T)W[A::EV * N + c] : T(0);
+  r[RF_BETA] = (T)W[A::BETA * N + c];
+  r[RF_PREV] = (T)W[A::PREV * N + c];
+  r[RF_PY] = (T)W[A::PY * N + c];
+  r[RF_L0] = (T)g.lamF[c];
+  r[RF_L1] = (T)g.lamF[N + c];
+  r[RF_ID] = (T)g.invD[c];
+  r[RF_IDEV] = (T)g.invD[N + c];
+#pragma unroll
+  for (int v = 0; v < 5; ++v) r[RF_RHS + v] = v < NF ? (T)g.rhsF[v * N + c] : T(0);
+  r[RF_SIM] = (T)Si0[0]; r[RF_SIM + 1] = (T)Si0[1];
+  r[RF_SIP] = (T)Si1[0]; r[RF_SIP + 1] = (T)Si1[1];
+  r[RF_SJM] = (T)Sj0[0]; r[RF_SJM + 1] = (T)Sj0[1];
+  r[RF_SJP] = (T)Sj1[0]; r[RF_SJP + 1] = (T)Sj1[1];
+  constexpr int NGRP = (NS + SG - 1) / SG;
+#pragma unroll
+  for (int gi = 0; gi < NGRP; ++gi) {
+    T* q = static_cast<T*>(g.wrecs) + ((size_t)gi * N + w) * kRecS;
+    q[RS_U] = r[RF_U];
+    q[RS_U + 1] = r[RF_U + 1];
+    q[RS_L0] = (T)g.lamC[c];
+    q[RS_L1] = (T)g.lamC[N + c];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) q[RS_SIM + k] = r[RF_SIM + k];
+#pragma unroll
+    for (int k = 0; k < SG; ++k) {
+      const int s = gi * SG + k;
+      q[RS_RHS + k] = s < NS ? (T)(-g.R[(size_t)s * N + c]) : T(0);
+      q[RS_ID + k] = s < NS ? (T)g.invD[(2 + s) * N + c] : T(0);
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Copy the records of rows [j0-1, j0+R] of hyperplane h (those that exist) into a ring slot of
+// (R+2) records; slot row index = j - (j0 - 1).  Whole warp; the caller commits the group.
+template <class T>
+__device__ __forceinline__ void wave_fetch(const T* src, int rec, const int* woff, int h, int H,
+                                           int ni, int nj, int j0, int R, T* slot) {
+  if (h >= 0 && h <= H) {
+    const int jlo = wave_jlo(h, ni), jhi = wave_jhi(h, nj);
+    const int lo = max(j0 - 1, jlo), hi = min(j0 + R, jhi);
+    if (lo <= hi) {
+      const T* from = src + ((size_t)woff[h] + (lo - jlo)) * rec;
+      T* to = slot + (size_t)(lo - (j0 - 1)) * rec;
+      const int pieces = (hi - lo + 1) * rec * (int)sizeof(T) / 16;
+      for (int k = threadIdx.x; k < pieces; k += 32)
+        cp_async16(reinterpret_cast<char*>(to) + 16 * k, reinterpret_cast<const char*>(from) + 16 * k);
+    }
+  }
+}
+
+template <class G, class T>
+__device__ __forceinline__ void rec_state(const T* r, CellState<G, 2, T>& w) {
+  w.u[0] = r[RF_U];
+  w.u[1] = r[RF_U + 1];
+  w.H = r[RF_H];
+  w.ev = r[RF_EV];
+  w.beta = r[RF_BETA];
+  w.prev = r[RF_PREV];
+  w.pY = r[RF_PY];
+}
+
+// coupling matrix M of a neighbour (state w, radius lam, face S): minus side M = (A + lam)/2,
+// plus side M = -(A - lam)/2, with A(S) the frozen-composition flow Jacobian of Sec. 2.3.1
+// written out entry by entry (the matrix jvp_flow applies: columns rho, m_1, m_2, rhoE,
+// [rho e_v])
+template <class G, class T>
+__device__ __forceinline__ void wave_matrix(const CellState<G, 2, T>& w, T lam, const T* S, int side,
+                                            T (*M)[Aux<G, 2>::NF]) {
+  constexpr int NF = Aux<G, 2>::NF;
+  constexpr bool TWO = G::NTEMP == 2;
+  const T U = w.u[0] * S[0] + w.u[1] * S[1];
+  T A[NF][NF];
+  A[0][0] = 0;
+  A[1][0] = w.pY * S[0] - w.u[0] * U;
+  A[2][0] = w.pY * S[1] - w.u[1] * U;
+  A[3][0] = (w.pY - w.H) * U;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T bu = w.beta * w.u[k];
+    A[0][1 + k] = S[k];
+    A[1][1 + k] = w.u[0] * S[k] - bu * S[0] + (k == 0 ? U : T(0));
+    A[2][1 + k] = w.u[1] * S[k] - bu * S[1] + (k == 1 ? U : T(0));
+    A[3][1 + k] = w.H * S[k] - bu * U;
+  }
+  A[0][3] = 0;
+  A[1][3] = w.beta * S[0];
+  A[2][3] = w.beta * S[1];
+  A[3][3] = (T(1) + w.beta) * U;
+  if (TWO) {
+    A[NF - 1][0] = -w.ev * U;
+    A[NF - 1][1] = w.ev * S[0];
+    A[NF - 1][2] = w.ev * S[1];
+    A[NF - 1][3] = 0;
+    A[0][NF - 1] = 0;
+    A[1][NF - 1] = w.prev * S[0];
+    A[2][NF - 1] = w.prev * S[1];
+    A[3][NF - 1] = w.prev * U;
+    A[NF - 1][NF - 1] = U;
+  }
+  const T h = side < 0 ? T(0.5) : T(-0.5), l = side < 0 ? lam : -lam;
+#pragma unroll
+  for (int r = 0; r < NF; ++r)
+#pragma unroll
+    for (int c = 0; c < NF; ++c) M[r][c] = h * (A[r][c] + (r == c ? l : T(0)));
+}
+
+// contribution of x (at a cell with state w, radius lam) to the neighbour across face S on its
+// side `side`: minus side (A x + lam x)/2, plus side -(A x - lam x)/2
+template <class G, class T>
+__device__ __forceinline__ void wave_contrib(const CellState<G, 2, T>& w, T lam, const T* S, int side,
+                                             const T* x, T* out) {
+  constexpr int NF = Aux<G, 2>::NF;
+  T ax[NF];
+  jvp_flow<G, 2, T>(w, S, x, ax);
+#pragma unroll
+  for (int v = 0; v < NF; ++v)
+    out[v] = side < 0 ? T(0.5) * (ax[v] + lam * x[v]) : T(-0.5) * (ax[v] - lam * x[v]);
+}
+
+template <class G, class T>
+struct WaveSmemF {
+  T ring[kWaveSlots][kWaveRows + 2][kRecF];
+  T base[kWaveSlots][kWaveRows + 2][8];
+  T x[2][kWaveRows][Aux<G, 2>::NF];
+  T mbox[2][Aux<G, 2>::NF];
+};
+
+template <class G, class T>
+__device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
+  const int t = threadIdx.x;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const int j0 = rank * R, j = j0 + t;
+  const bool row = t < R && j < nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const T* rec = static_cast<const T*>(g.wrec);
+  T* base = static_cast<T*>(g.wbase);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    const int hs = fwd ? 1 : -1;      // hyperplane step
+    auto hof = [&](int q) { return fwd ? q : H - q; };
+    if (!fwd) __threadfence();   // forward results in `base` are read back through cp.async
+    for (int q = 0; q < kWaveD; ++q) {
+      wave_fetch<T>(rec, kRecF, g.woff, hof(q), H, ni, nj, j0, R, &sm.ring[q % kWaveSlots][0][0]);
+      if (!fwd) wave_fetch<T>(base, 8, g.woff, hof(q), H, ni, nj, j0, R, &sm.base[q % kWaveSlots][0][0]);
+      cp_async_commit();
+    }
+    T acc[NF], Mj[NF][NF], carry[NF], wrapc[NF], x[NF];
+    T iD = 0, iDev = 0, lam0 = 0, Sn[2] = {0, 0}, Sw[2] = {0, 0};
+    CellState<G, 2, T> ws;
+    bool act = false, hasj = false;
+    int cidx = 0, wcur = 0;
+#pragma unroll
+    for (int v = 0; v < NF; ++v) { carry[v] = 0; wrapc[v] = 0; x[v] = 0; }
+    // per-step set-up from the records (step q); also used for the first step
+    auto setup = [&](int q) {
+      cp_async_wait<kWaveD - 1>();
+      __syncwarp();
+      const int h = hof(q), i = h - j;
+      act = row && q <= H && i >= 0 && i < ni;
+      const int jj = j - hs;
+      hasj = act && jj >= 0 && jj < nj;
+      if (!act) return;
+      const T* me = sm.ring[q % kWaveSlots][t + 1];
+      rec_state<G, T>(me, ws);
+      lam0 = me[RF_L0];
+      Sn[0] = me[fwd ? RF_SIP : RF_SIM];          // face towards the next cell of the row
+      Sn[1] = me[(fwd ? RF_SIP : RF_SIM) + 1];
+      Sw[0] = me[fwd ? RF_SIM : RF_SIP];          // face across the periodic cut
+      Sw[1] = me[(fwd ? RF_SIM : RF_SIP) + 1];
+      iD = me[RF_ID];
+      iDev = me[RF_IDEV];
+      cidx = i + ni * j;
+      wcur = g.woff[h] + (j - wave_jlo(h, ni));
+      const bool prev_exists = fwd ? i > 0 : i < ni - 1;
+      const bool wrap = per && (fwd ? i == ni - 1 : i == 0);
+#pragma unroll
+      for (int v = 0; v < NF; ++v) {
+        acc[v] = fwd ? me[RF_RHS + v] : T(0);
+        if (prev_exists) acc[v] += carry[v];
+        if (wrap) acc[v] += wrapc[v];
+      }
+      if (hasj) {
+        const T* nb = sm.ring[(q + kWaveSlots - 1) % kWaveSlots][fwd ? t : t + 2];
+        CellState<G, 2, T> wn;
+        rec_state<G, T>(nb, wn);
+        wave_matrix<G, T>(wn, nb[RF_L1], me + (fwd ? RF_SJM : RF_SJP), fwd ? -1 : +1, Mj);
+      }
+    };
+    setup(0);
+    for (int q = 0; q <= H; ++q) {
+      const int h = hof(q), i = h - j;
+      if (q > 0) cluster_wait();
+      if (act) {
+        if (hasj) {
+          const bool remote = fwd ? t == 0 : t == R - 1;
+          const T* src = remote ? sm.mbox[(q - 1) & 1] : sm.x[(q - 1) & 1][fwd ? t - 1 : t + 1];
+          T xn[NF];
+#pragma unroll
+          for (int v = 0; v < NF; ++v) xn[v] = src[v];
+#pragma unroll
+          for (int r = 0; r < NF; ++r)
+#pragma unroll
+            for (int c = 0; c < NF; ++c) acc[r] += Mj[r][c] * xn[c];
+        }
+        const T* bse = sm.base[q % kWaveSlots][t + 1];
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          const T d = (G::NTEMP == 2 && v == NF - 1) ? iDev : iD;
+          x[v] = fwd ? acc[v] * d : bse[v] + acc[v] * d;
+          sm.x[q & 1][t][v] = x[v];
+        }
+        // push the CTA-boundary row to the neighbouring CTA
+        if (fwd ? (t == R - 1 && rank + 1 < C) : (t == 0 && rank > 0)) {
+          T* dst = dsmem(&sm.mbox[q & 1][0], fwd ? rank + 1 : rank - 1);
+#pragma unroll
+          for (int v = 0; v < NF; ++v) dst[v] = x[v];
+        }
+      }
+      cluster_arrive();
+      if (act) {
+        double* out = fwd ? g.dQs : g.dQ;
+#pragma unroll
+        for (int v = 0; v < NF; ++v) out[v * N + cidx] = (double)x[v];
+        if (fwd) {
+          T* b = base + (size_t)wcur * 8;
+#pragma unroll
+          for (int v = 0; v < NF; ++v) b[v] = x[v];
+        }
+        // contribution of this cell to the next cell of the row (minus side of that cell in
+        // the forward sweep, plus side in the backward sweep) and across the periodic cut
+        const bool next_exists = fwd ? i < ni - 1 : i > 0;
+        if (next_exists) wave_contrib<G, T>(ws, lam0, Sn, fwd ? -1 : +1, x, carry);
+        if (per && i == (fwd ? 0 : ni - 1)) wave_contrib<G, T>(ws, lam0, Sw, fwd ? +1 : -1, x, wrapc);
+      }
+      // prefetch step q + D, then prepare step q + 1
+      if (q + kWaveD <= H) {
+        wave_fetch<T>(rec, kRecF, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
+                      &sm.ring[(q + kWaveD) % kWaveSlots][0][0]);
+        if (!fwd)
+          wave_fetch<T>(base, 8, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
+                        &sm.base[(q + kWaveD) % kWaveSlots][0][0]);
+      }
+      cp_async_commit();        // one group per step, possibly empty
+      setup(q + 1);
+    }
+    cluster_wait();
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+}
+
+
+template <class G, class T>
+struct WaveSmemS {
+  T ring[kWaveSlots][kWaveRows + 2][kRecS];
+  T base[kWaveSlots][kWaveRows + 2][kSpeciesGroup];
+  T x[2][kWaveRows][kSpeciesGroup];
+  T mbox[2][kSpeciesGroup];
+};
+
+// scalar coupling of a neighbour in the component operator: minus side (U + lam)/2, plus
+// side -(U - lam)/2, U = u_nb . S_f (Sec. 2.3.2)
+template <class T>
+__device__ __forceinline__ T wave_coef(const T* u, T lam, const T* S, int side) {
+  const T U = u[0] * S[0] + u[1] * S[1];
+  return side < 0 ? T(0.5) * (U + lam) : T(-0.5) * (U - lam);
+}
+
+template <class G, class T>
+__device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& sm) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF, SG = kSpeciesGroup, NS = G::NS;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
+  const int t = threadIdx.x;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const int j0 = rank * R, j = j0 + t;
+  const bool row = t < R && j < nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int s0 = grp * SG;
+  const int ns = (NS - s0 < SG) ? NS - s0 : SG;
+  const T* rec = static_cast<const T*>(g.wrecs) + (size_t)grp * N * kRecS;
+  T* base = static_cast<T*>(g.wbase) + (size_t)N * 8 + (size_t)grp * N * SG;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    const int hs = fwd ? 1 : -1;
+    auto hof = [&](int q) { return fwd ? q : H - q; };
+    if (!fwd) __threadfence();
+    for (int q = 0; q < kWaveD; ++q) {
+      wave_fetch<T>(rec, kRecS, g.woff, hof(q), H, ni, nj, j0, R, &sm.ring[q % kWaveSlots][0][0]);
+      if (!fwd) wave_fetch<T>(base, SG, g.woff, hof(q), H, ni, nj, j0, R, &sm.base[q % kWaveSlots][0][0]);
+      cp_async_commit();
+    }
+    T acc[SG], iD[SG], carry[SG], wrapc[SG], x[SG], kj = 0, ki = 0, kw = 0;
+    bool act = false, hasj = false;
+    int cidx = 0, wcur = 0;
+#pragma unroll
+    for (int k = 0; k < SG; ++k) { carry[k] = 0; wrapc[k] = 0; x[k] = 0; iD[k] = 0; acc[k] = 0; }
+    auto setup = [&](int q) {
+      cp_async_wait<kWaveD - 1>();
+      __syncwarp();
+      const int h = hof(q), i = h - j;
+      act = row && q <= H && i >= 0 && i < ni;
+      const int jj = j - hs;
+      hasj = act && jj >= 0 && jj < nj;
+      if (!act) return;
+      const T* me = sm.ring[q % kWaveSlots][t + 1];
+      cidx = i + ni * j;
+      wcur = g.woff[h] + (j - wave_jlo(h, ni));
+      const bool prev_exists = fwd ? i > 0 : i < ni - 1;
+      const bool wrap = per && (fwd ? i == ni - 1 : i == 0);
+#pragma unroll
+      for (int k = 0; k < SG; ++k) {
+        iD[k] = me[RS_ID + k];
+        acc[k] = fwd ? me[RS_RHS + k] : T(0);
+        if (prev_exists) acc[k] += carry[k];
+        if (wrap) acc[k] += wrapc[k];
+      }
+      if (hasj) {
+        const T* nb = sm.ring[(q + kWaveSlots - 1) % kWaveSlots][fwd ? t : t + 2];
+        kj = wave_coef<T>(nb + RS_U, nb[RS_L1], me + (fwd ? RS_SJM : RS_SJP), fwd ? -1 : +1);
+      }
+      ki = wave_coef<T>(me + RS_U, me[RS_L0], me + (fwd ? RS_SIP : RS_SIM), fwd ? -1 : +1);
+      kw = wave_coef<T>(me + RS_U, me[RS_L0], me + (fwd ? RS_SIM : RS_SIP), fwd ? +1 : -1);
+    };
+    setup(0);
+    for (int q = 0; q <= H; ++q) {
+      const int h = hof(q), i = h - j;
+      if (q > 0) cluster_wait();
+      if (act) {
+        if (hasj) {
+          const bool remote = fwd ? t == 0 : t == R - 1;
+          const T* src = remote ? sm.mbox[(q - 1) & 1] : sm.x[(q - 1) & 1][fwd ? t - 1 : t + 1];
+#pragma unroll
+          for (int k = 0; k < SG; ++k) acc[k] += kj * src[k];
+        }
+        const T* bse = sm.base[q % kWaveSlots][t + 1];
+#pragma unroll
+        for (int k = 0; k < SG; ++k) {
+          x[k] = fwd ? acc[k] * iD[k] : bse[k] + acc[k] * iD[k];
+          sm.x[q & 1][t][k] = x[k];
+        }
+        if (fwd ? (t == R - 1 && rank + 1 < C) : (t == 0 && rank > 0)) {
+          T* dst = dsmem(&sm.mbox[q & 1][0], fwd ? rank + 1 : rank - 1);
+#pragma unroll
+          for (int k = 0; k < SG; ++k) dst[k] = x[k];
+        }
+      }
+      cluster_arrive();
+      if (act) {
+        double* out = fwd ? g.dQs : g.dQ;
+#pragma unroll
+        for (int k = 0; k < SG; ++k)
+          if (k < ns) out[(size_t)(NF + s0 + k) * N + cidx] = (double)x[k];
+        if (fwd) {
+          T* b = base + (size_t)wcur * SG;
+#pragma unroll
+          for (int k = 0; k < SG; ++k) b[k] = x[k];
+        }
+#pragma unroll
+        for (int k = 0; k < SG; ++k) carry[k] = ki * x[k];
+        if (per && i == (fwd ? 0 : ni - 1))
+#pragma unroll
+          for (int k = 0; k < SG; ++k) wrapc[k] = kw * x[k];
+      }
+      if (q + kWaveD <= H) {
+        wave_fetch<T>(rec, kRecS, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
+                      &sm.ring[(q + kWaveD) % kWaveSlots][0][0]);
+        if (!fwd)
+          wave_fetch<T>(base, SG, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
+                        &sm.base[(q + kWaveD) % kWaveSlots][0][0]);
+      }
+      cp_async_commit();
+      setup(q + 1);
+    }
+    cluster_wait();
+    cp_async_wait<0>();
+    __syncwarp();
+  }
+}
+
+template <class G, class T>
+__global__ void __launch_bounds__(32) k_split_wave(DevGrid g, int R) {
+  constexpr size_t BF = sizeof(WaveSmemF<G, T>), BS = sizeof(WaveSmemS<G, T>);
+  __shared__ __align__(16) char smem[BF > BS ? BF : BS];
+  const int comp = blockIdx.x / (int)cluster_nctarank();   // uniform within a cluster
+  if (comp == 0) wave_flow<G, T>(g, R, *reinterpret_cast<WaveSmemF<G, T>*>(smem));
+  else wave_species<G, T>(g, R, comp - 1, *reinterpret_cast<WaveSmemS<G, T>*>(smem));
 }
 
 template <class G>

@@ -34,6 +34,7 @@ struct Launcher {
   }
   virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed = false) = 0;
   bool use_cluster = true;
+  int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
@@ -85,8 +86,14 @@ struct LauncherT : Launcher {
     // species-derived constants (see GasConst)
     GasConst gc;
     std::memset(&gc, 0, sizeof gc);
-    const SpeciesData* sp = G::PERFECT ? nullptr : kSpeciesHost;
-    for (int s = 0; s < G::NS && sp; ++s) {
+    static const SpeciesData kPerfectHost = {DIATOMIC, 28.9647, 0.0, 2.88, 2, 1, 0.0};
+    const SpeciesData* sp = G::PERFECT ? &kPerfectHost : kSpeciesHost;
+    for (int s = 0; s < G::NS; ++s) {
+      gc.Rs[s] = kRu / sp[s].M;
+      gc.hf[s] = sp[s].h0 / sp[s].M;
+      gc.invM[s] = 1.0 / sp[s].M;
+    }
+    for (int s = 0; s < G::NS && !G::PERFECT; ++s) {
       const double m = sp[s].M / kNa;
       double v = -1.5 * log(2.0 * kPi * m * kKb / (kH * kH)) - log(kKb / kPref) - log(sp[s].g0);
       if (sp[s].kind == DIATOMIC) v += log(sp[s].sigma * sp[s].thr);
@@ -183,7 +190,75 @@ struct LauncherT : Launcher {
 
   // one launch: both sweeps of the flow block and of every species (returns launches)
   int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed) override {
+    // measured on GB300: the wavefront-record kernel is the faster one in FP32, the
+    // direct-load kernel in FP64 (fewer dependent FP64 operations per step)
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
+    if (kind == 2 && g.wrec) {
+      const int n = mixed ? sweep_wave_t<float>(g, st, wprobed32_) : sweep_wave_t<double>(g, st, wprobed64_);
+      if (n) return n;
+    }
     return mixed ? sweep_cluster_t<float>(g, st, probed32_) : sweep_cluster_t<double>(g, st, probed64_);
+  }
+  int wprobed64_ = -1, wprobed32_ = -1;
+
+  // wavefront-record kernel: cluster size with at most kWaveRows rows per CTA
+  template <class T>
+  int wave_cluster_size(const DevGrid& g, int& probed) {
+    if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    if (probed >= 0) return probed;
+    probed = 0;
+    auto kern = k_split_wave<G, T>;
+    for (int C : {16, 8, 4, 2, 1}) {
+      const int R = (g.nj + C - 1) / C;
+      if (R > kWaveRows) continue;
+      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
+      cfg.blockDim = dim3(32);
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
+        probed = C;
+        break;
+      }
+      cudaGetLastError();
+    }
+    return probed;
+  }
+
+  template <class T>
+  int sweep_wave_t(const DevGrid& g, cudaStream_t st, int& probed) {
+    sweep_split_cluster_ok = false;
+    const int C = wave_cluster_size<T>(g, probed);
+    if (C == 0) return 0;
+    k_pack_wave<G, T><<<blocks(g.N, 128), 128, 0, st>>>(g);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
+    cfg.blockDim = dim3(32);
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int R = (g.nj + C - 1) / C;
+    if (cudaLaunchKernelEx(&cfg, k_split_wave<G, T>, g, R) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    sweep_split_cluster_ok = true;
+    return 2;
   }
   template <class T>
   int sweep_cluster_t(const DevGrid& g, cudaStream_t st, int& probed) {

@@ -282,15 +282,17 @@ def test_cluster_sweep_equals_hyperplane_sweep(name):
     same arithmetic in the same order (the compiler may contract multiply-adds differently
     in the two kernels, so they agree to rounding)."""
     ref, gpu, Q = make_pair(name, seed=7)
-    gpu.residual(want_R=False)
-    a = gpu.lusgs_split(8.0)
-    gpu.set_option("cluster_sweep", 0)
-    gpu.set_state(Q)
-    gpu.residual(want_R=False)
-    b = gpu.lusgs_split(8.0)
-    gpu.set_option("cluster_sweep", 1)
-    assert rel(a[:ref.nF], b[:ref.nF]) < 1e-13
-    assert rel(a[ref.nF:], b[ref.nF:], ns=ref.ns) < 1e-13
+    out = {}
+    for mode in (2, 1, 0):               # wavefront-record cluster, direct cluster, per hyperplane
+        gpu.set_option("cluster_sweep", mode)
+        gpu.set_state(Q)
+        gpu.residual(want_R=False)
+        out[mode] = gpu.lusgs_split(8.0)
+    gpu.set_option("cluster_sweep", 3)
+    a, b = out[2], out[0]
+    for m in (1, 2):
+        assert rel(out[m][:ref.nF], b[:ref.nF]) < 1e-13, m
+        assert rel(out[m][ref.nF:], b[ref.nF:], ns=ref.ns) < 1e-13, m
     ref.residual()
     assert rel(a[:ref.nF], ref.lusgs_split(8.0)[:ref.nF]) < TOL
 
