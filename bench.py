@@ -1,7 +1,7 @@
 """Benchmark: pseudo-time iterations of the component-splitting LU-SGS scheme on one GB300.
 
 Workload (one "step" = one full pseudo-time iteration: residual, split LU-SGS operator,
-CS-1 correction and update): 2D Mach 15 flow over a cylinder, 384 x 256 cell O-grid,
+CS-1 correction and update): 2D Mach 15 flow over a cylinder, 384 x 256 cells over the windward half,
 11-species two-temperature ionised air with 21 reactions, FP64.  Synthetic, seeded: the run
 starts from the uniform freestream.
 
@@ -34,7 +34,7 @@ NI, NJ = 384, 256
 MECH = inputs.MECH_AIR11
 MACH, T_INF, P_INF, T_WALL = 15.0, 300.0, 500.0, 500.0
 CFL, CFL_START, RAMP = 2.0, 0.5, 100
-WORKLOAD = "cylinder-384x256-air11-2T-mach15-CS1-fp64"
+WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # FP64 floating-point operations per cell and iteration of each phase (2 x DFMA + DMUL + DADD
 # thread instructions counted by ncu on this workload, divided by the cell count; the
 # primitive phase varies with the Newton iteration count).  On GB300 every residual kernel
@@ -120,7 +120,7 @@ class ClockSampler:
 
 
 def make_case(P):
-    nodes = inputs.cylinder_ogrid(NI, NJ, dr1=5e-5 / 8)
+    nodes = inputs.cylinder_half(NI, NJ, dr1=5e-5 / 8)
     fs = inputs.freestream(MECH, T=T_INF, p=P_INF, mach=MACH)
     return nodes, fs
 
@@ -139,7 +139,7 @@ def oracle_rate(iters, seconds_cap=30.0):
     import oracle
     oracle.build()
     nodes, fs = make_case(None)
-    g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), MECH)
+    g = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
     done, t0 = 0, time.perf_counter()
@@ -162,7 +162,7 @@ def run_reference(args, rank):
     import oracle
     oracle.build()
     nodes, fs = make_case(None)
-    g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), MECH)
+    g = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
     kw = step_kwargs(1)
@@ -220,7 +220,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     nodes, fs = make_case(P)
-    g = P.Grid(nodes, inputs.cylinder_bc(), MECH)
+    g = P.Grid(nodes, inputs.cylinder_half_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.init_freestream()
     N = g.ncell

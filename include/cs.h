@@ -169,7 +169,13 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * split sweeps as one thread-block-cluster launch, choosing per precision between 2 (cluster
  * kernel over hyperplane-ordered cell records, faster in FP32) and 1 (cluster kernel reading
  * the cell arrays directly, faster in FP64); 0 runs one launch per hyperplane.  All give the
- * same arithmetic up to rounding.  Errors: CS_ERR_ARG for an unknown name. */
+ * same arithmetic up to rounding.
+ * Method option: "h_correction" = 1 (default) widens the entropy fix of every face's Roe flux
+ * to at least twice the face's multidimensional H-correction (Sanders, Morano and Druguet,
+ * J. Comput. Phys. 145, 1998; the paper names Roe's scheme, Sec. 3.2, but not its entropy
+ * fix), which keeps the bow shock of a blunt body free of the carbuncle instability; 0 keeps
+ * only the one-dimensional fix entropy_fix (|u_n| + c).
+ * Errors: CS_ERR_ARG for an unknown name. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Residual monitors without device allocation (no counterpart in the paper: a service for

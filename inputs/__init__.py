@@ -68,6 +68,33 @@ def cylinder_bc():
     return [BC_PERIODIC, BC_PERIODIC, BC_WALL, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC]
 
 
+def cylinder_half(ni, nj, radius=0.05, r_out=0.2, dr1=5e-5):
+    """2D grid over the windward half of a cylinder: i circumferential (clockwise, from the
+    upper shoulder to the lower one), j radial outward.  Both i ends are supersonic outflow
+    boundaries, so the grid holds no wake and the flow has a steady state.
+
+    The span is 180 degrees shifted by half a cell so that cell i = ni/2 is centred on the
+    windward stagnation line (angle pi) for even ni.  Returns nodes of shape (2, nj+1, ni+1).
+    """
+    q = geometric_ratio(nj, dr1, r_out - radius)
+    r = np.empty(nj + 1)
+    r[0] = radius
+    for j in range(nj):
+        r[j + 1] = r[j] + dr1 * q ** j
+    r[nj] = r_out
+    dth = math.pi / ni
+    theta = math.pi + (ni // 2 + 0.5 - np.arange(ni + 1)) * dth
+    nodes = np.empty((2, nj + 1, ni + 1))
+    nodes[0] = r[:, None] * np.cos(theta)[None, :]
+    nodes[1] = r[:, None] * np.sin(theta)[None, :]
+    return nodes
+
+
+def cylinder_half_bc():
+    """imin, imax, jmin, jmax, kmin, kmax boundary codes of the half-cylinder grid."""
+    return [BC_OUTFLOW, BC_OUTFLOW, BC_WALL, BC_FARFIELD, BC_PERIODIC, BC_PERIODIC]
+
+
 def sphere_cone(ni, nj, nk, nose=0.05, half_angle_deg=7.0, length=0.5, standoff=None, dr1=None):
     """3D sphere-cone grid: i along the body from the nose (axis) to the base, j normal to the
     wall, k circumferential (periodic).  Nodes at i=0 lie on the symmetry axis (degenerate

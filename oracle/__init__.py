@@ -41,6 +41,7 @@ def lib():
                                  C.c_double, _dp, C.POINTER(C.c_void_p)]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_set_reacting.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_hcorr.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_boundary.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                        _dp, _dp, C.c_double]
         L.orc_freestream_state.argtypes = [C.c_void_p, _dp]
@@ -233,6 +234,9 @@ class OracleGrid:
 
     def set_reacting(self, on):
         lib().orc_set_reacting(self._h, int(bool(on)))
+
+    def set_hcorr(self, on):
+        lib().orc_set_hcorr(self._h, int(bool(on)))
 
     def set_boundary(self, fs, Tw=500.0):
         Y = _f64(fs["Y"])

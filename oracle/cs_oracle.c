@@ -664,6 +664,7 @@ typedef struct {
     gas_t gas;
     int nd, n[3], bc[6], limiter;
     double efix;
+    int hcorr;                       /* H-correction of the entropy fix on/off */
     int ncell, nf[3];                /* faces per direction */
     int nq, nF, nsplit, nci;
     double *node[3];
@@ -826,7 +827,14 @@ static void cell_coords(const orc_grid *G, int c, int *o)
  * Inviscid flux (Sec. 3.2: MUSCL reconstruction with the minmod limiter + Roe's scheme).
  * Reading: reconstructed variables per cell are w = (rho_s, u, p, Gam = rho*e/p, beta,
  * [e_v]); the face state needs no temperature solve.  Roe average with sqrt(rho) weights;
- * Harten's entropy fix on all three wave speeds.
+ * Harten's entropy fix on all three wave speeds, with the width
+ *   delta = max(eps (|u_n| + c), 2 eta_H),
+ * so that a wave speed of zero is raised to eta_H, where eta_H is the multidimensional H-correction of Sanders, Morano and Druguet (J. Comput.
+ * Phys. 145, 1998): the largest eta over this face and the faces of the other directions that
+ * bound its two cells, eta = (|jump of u.n| + |jump of c|) / 2 between the two cell-centre
+ * states of a face (the largest jump of u_n - c, u_n, u_n + c).  Faces on a non-periodic
+ * boundary have eta = 0.  The paper does not state its entropy fix; without the H term Roe's
+ * scheme develops the carbuncle instability on the stagnation line of a blunt body.
  * ------------------------------------------------------------------------------------- */
 typedef struct { double rhos[NSMAX], u[3], p, Gam, beta, ev; } recon_t;
 
@@ -882,8 +890,10 @@ static double harten(double lam, double delta)
     return (a < delta) ? (lam * lam + delta * delta) / (2.0 * delta) : a;
 }
 
-/* Roe numerical flux through face vector S (oriented from L to R), F = flux * |S| */
-static void roe_flux(const orc_grid *G, const recon_t *L, const recon_t *R, const double *S, double *F)
+/* Roe numerical flux through face vector S (oriented from L to R), F = flux * |S|; etaH is the
+ * face's H-correction width (0 for none) */
+static void roe_flux(const orc_grid *G, const recon_t *L, const recon_t *R, const double *S,
+                     double etaH, double *F)
 {
     int ns = G->gas.ns, nd = G->nd, nq = G->nq;
     double QL[NQMAX], QR[NQMAX], FL[NQMAX], FR[NQMAX];
@@ -915,6 +925,7 @@ static void roe_flux(const orc_grid *G, const recon_t *L, const recon_t *R, cons
     double c2 = (1.0 + bt) * prt + 0.5 * bt * wl * wr * du2;
     double ct = sqrt(c2);
     double delta = G->efix * (fabs(un) + ct);
+    if (2.0 * etaH > delta) delta = 2.0 * etaH;
     double l1 = harten(un - ct, delta), l2 = harten(un, delta), l3 = harten(un + ct, delta);
     double dp = R->p - L->p;
     double ap = (dp + rt * ct * dun) / (2.0 * c2), am = (dp - rt * ct * dun) / (2.0 * c2);
@@ -976,8 +987,54 @@ static int recon_ok(const orc_grid *G, const recon_t *r)
     return rho > 0.0;
 }
 
+/* eta of the face with vector S between cells a and b: half the largest jump of the three
+ * wave speeds u.n - c, u.n, u.n + c, which is (|jump of u.n| + |jump of c|) / 2 */
+static double eta_cells(const orc_grid *G, int a, int b, const double *S)
+{
+    double area = 0.0, dun = 0.0;
+    for (int d = 0; d < G->nd; d++) area += S[d] * S[d];
+    area = sqrt(area);
+    for (int d = 0; d < G->nd; d++) dun += (G->w[b].u[d] - G->w[a].u[d]) * (S[d] / area);
+    return 0.5 * (fabs(dun) + fabs(G->w[b].c - G->w[a].c));
+}
+
+/* H-correction width of the direction-d face with face coordinates o (o[d] = 0..n[d]) */
+static double eta_h(const orc_grid *G, int d, const int *o)
+{
+    int cells[2], nc = 0, n = G->n[d];
+    int oa[3] = {o[0], o[1], o[2]}, ob[3] = {o[0], o[1], o[2]};
+    if (o[d] > 0 && o[d] < n) {
+        oa[d] = o[d] - 1;
+    } else if (G->bc[2 * d] == BC_PERIODIC) {
+        oa[d] = n - 1;
+        ob[d] = 0;
+    } else {
+        oa[d] = (o[d] == 0) ? -1 : n - 1;
+        ob[d] = (o[d] == 0) ? 0 : -1;
+    }
+    if (oa[d] >= 0) cells[nc++] = cidx(G, oa[0], oa[1], G->nd == 3 ? oa[2] : 0);
+    if (ob[d] >= 0) cells[nc++] = cidx(G, ob[0], ob[1], G->nd == 3 ? ob[2] : 0);
+    double eta = 0.0;
+    if (nc == 2) eta = eta_cells(G, cells[0], cells[1], &G->S[d][3 * fidx(G, d, o[0], o[1], G->nd == 3 ? o[2] : 0)]);
+    for (int m = 0; m < nc; m++) {
+        int oc[3];
+        cell_coords(G, cells[m], oc);
+        for (int e = 0; e < G->nd; e++) {
+            if (e == d) continue;
+            for (int s = -1; s <= 1; s += 2) {
+                int nb = neighbour(G, oc, e, s, NULL);
+                if (nb < 0) continue;
+                double x = eta_cells(G, cells[m], nb, &G->S[e][3 * face_of(G, oc, e, s)]);
+                if (x > eta) eta = x;
+            }
+        }
+    }
+    return eta;
+}
+
 /* inviscid flux at the interior face between cells a (minus side) and b (plus side) */
-static void inviscid_interior(const orc_grid *G, int a, int b, int d, const double *S, double *F)
+static void inviscid_interior(const orc_grid *G, int a, int b, int d, const double *S,
+                              double etaH, double *F)
 {
     int nr = nrecon(G);
     double wa[NQMAX + 4], wb[NQMAX + 4], wam[NQMAX + 4], wbp[NQMAX + 4], vl[NQMAX + 4], vr[NQMAX + 4];
@@ -1001,11 +1058,12 @@ static void inviscid_interior(const orc_grid *G, int a, int b, int d, const doub
         recon_unpack(G, wa, &L);
         recon_unpack(G, wb, &R);
     }
-    roe_flux(G, &L, &R, S, F);
+    roe_flux(G, &L, &R, S, etaH, F);
 }
 
 /* inviscid flux at a boundary face of cell c (side s of d) */
-static void inviscid_boundary(const orc_grid *G, int c, int d, int s, const double *S, double *F)
+static void inviscid_boundary(const orc_grid *G, int c, int d, int s, const double *S,
+                              double etaH, double *F)
 {
     int nq = G->nq, ns = G->gas.ns, nd = G->nd;
     prim_t gw;
@@ -1022,8 +1080,8 @@ static void inviscid_boundary(const orc_grid *G, int c, int d, int s, const doub
     recon_t I, Gh;
     recon_unpack(G, vi, &I);
     recon_unpack(G, vg, &Gh);
-    if (s > 0) roe_flux(G, &I, &Gh, S, F);
-    else roe_flux(G, &Gh, &I, S, F);
+    if (s > 0) roe_flux(G, &I, &Gh, S, etaH, F);
+    else roe_flux(G, &Gh, &I, S, etaH, F);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -1252,12 +1310,13 @@ static int residual(orc_grid *G)
                     int o[3] = {i, j, k}, lo = o[d] - 1, hi = o[d], n = G->n[d];
                     int per = (G->bc[2 * d] == BC_PERIODIC);
                     double Fi[NQMAX], Fv[NQMAX];
+                    double etaH = G->hcorr ? eta_h(G, d, o) : 0.0;
                     if (lo >= 0 && hi < n) {
                         int oa[3] = {o[0], o[1], o[2]};
                         oa[d] = lo;
                         int a = cidx(G, oa[0], oa[1], nd == 3 ? oa[2] : 0);
                         int b = cidx(G, o[0], o[1], nd == 3 ? o[2] : 0);
-                        inviscid_interior(G, a, b, d, S, Fi);
+                        inviscid_interior(G, a, b, d, S, etaH, Fi);
                         viscous_interior(G, a, b, S, Fv);
                     } else if (per) {
                         int oa[3] = {o[0], o[1], o[2]}, ob[3] = {o[0], o[1], o[2]};
@@ -1265,13 +1324,13 @@ static int residual(orc_grid *G)
                         ob[d] = 0;
                         int a = cidx(G, oa[0], oa[1], nd == 3 ? oa[2] : 0);
                         int b = cidx(G, ob[0], ob[1], nd == 3 ? ob[2] : 0);
-                        inviscid_interior(G, a, b, d, S, Fi);
+                        inviscid_interior(G, a, b, d, S, etaH, Fi);
                         viscous_interior(G, a, b, S, Fv);
                     } else {
                         int oc[3] = {o[0], o[1], o[2]}, s;
                         if (lo < 0) { oc[d] = 0; s = -1; } else { oc[d] = n - 1; s = +1; }
                         int c = cidx(G, oc[0], oc[1], nd == 3 ? oc[2] : 0);
-                        inviscid_boundary(G, c, d, s, S, Fi);
+                        inviscid_boundary(G, c, d, s, S, etaH, Fi);
                         viscous_boundary(G, c, d, s, f, S, Fv);
                     }
                     for (int v = 0; v < nq; v++) F[v] = Fi[v] + Fv[v];
@@ -1684,7 +1743,7 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
     if (gas_init(&G->gas, mech)) { free(G); return 1; }
     G->nd = nd; G->n[0] = ni; G->n[1] = nj; G->n[2] = (nd == 3) ? nk : 1;
     for (int k = 0; k < 6; k++) G->bc[k] = bc[k];
-    G->limiter = lim; G->efix = efix;
+    G->limiter = lim; G->efix = efix; G->hcorr = 1;
     G->ncell = ni * nj * G->n[2];
     int ns = G->gas.ns;
     G->nq = ns + nd + 1 + (G->gas.ntemp == 2);
@@ -1727,6 +1786,8 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
 
 /* reacting = 0 switches the chemical and vibrational sources off */
 int orc_set_reacting(orc_grid *G, int reacting) { G->react = reacting != 0; return 0; }
+/* H-correction of the entropy fix on (1, the default) or off (0) */
+int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
 
 void orc_destroy(orc_grid *G)
 {
@@ -2004,7 +2065,7 @@ int orc_state_roe(int mech, int nd, const double *qL, const double *qR, const do
     recon_t L, R;
     recon_unpack(&G, vl, &L);
     recon_unpack(&G, vr, &R);
-    roe_flux(&G, &L, &R, S, F);
+    roe_flux(&G, &L, &R, S, 0.0, F);
     return 0;
 }
 

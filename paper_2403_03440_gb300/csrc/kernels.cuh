@@ -37,7 +37,7 @@ struct Aux {
 struct DevGrid {
   int nd, ni, nj, nk, N;
   int bc[6];
-  int limiter, react;
+  int limiter, react, hcorr;
   double efix, Tw;
   int nf[3];
   const double* S[3];
@@ -746,9 +746,11 @@ __device__ __forceinline__ double limiter(int type, double a, double b) {
   return (a * b * (a + b)) / (a * a + b * b);
 }
 
-// Roe flux (reading 17) from two reconstructed states; F = flux * |S|.
+// Roe flux (reading 17) from two reconstructed states; F = flux * |S|.  Harten's entropy fix
+// width is max(efix (|u_n| + c), 2 etaH), etaH being the face's H-correction (0 for none).
 template <class G, int ND>
-__device__ void roe(const double* L, const double* R, const double* S, double efix, double* F) {
+__device__ void roe(const double* L, const double* R, const double* S, double efix, double etaH,
+                    double* F) {
   constexpr int NS = G::NS, NQ = Aux<G, ND>::NQ;
   constexpr bool TWO = G::NTEMP == 2;
   double rl = 0.0, rr = 0.0;
@@ -787,7 +789,7 @@ __device__ void roe(const double* L, const double* R, const double* S, double ef
   const double evt = wl * evl + wr * evr;
   const double c2 = (1.0 + bt) * prt + 0.5 * bt * wl * wr * du2;
   const double ct = sqrt(c2);
-  const double delta = efix * (fabs(un) + ct);
+  const double delta = fmax(efix * (fabs(un) + ct), 2.0 * etaH);
   auto hfix = [delta](double l) {
     const double a = fabs(l);
     return a < delta ? (l * l + delta * delta) / (2.0 * delta) : a;
@@ -962,6 +964,52 @@ __device__ void viscous(const double (*gf)[ND], const double* uf, double mu, dou
 }
 
 // ---------------------------------------------------------------------------------------
+// Multidimensional H-correction of the entropy fix (Sanders, Morano and Druguet, J. Comput.
+// Phys. 145, 1998).  eta of a face = half the largest jump of u.n - c, u.n, u.n + c between the
+// cell-centre states on its two sides = (|jump of u.n| + |jump of c|) / 2; the H width of a
+// face is the largest eta over the face itself and the faces of the other directions that
+// bound its two cells.  Faces on a non-periodic boundary have eta = 0.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__device__ __forceinline__ double eta_cells(const DevGrid& g, int a, int b, const double* S) {
+  using A = Aux<G, ND>;
+  const size_t N = g.N;
+  double a2 = 0.0, dun = 0.0;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) a2 += S[d] * S[d];
+  const double area = sqrt(a2);
+#pragma unroll
+  for (int d = 0; d < ND; ++d) dun += (g.W[(A::U + d) * N + b] - g.W[(A::U + d) * N + a]) * (S[d] / area);
+  return 0.5 * (fabs(dun) + fabs(g.W[A::C * N + b] - g.W[A::C * N + a]));
+}
+
+// H width of the direction-D face with cells a (minus side) and b (plus side), either of which
+// is -1 on a non-periodic boundary; S is the face's own vector.
+template <class G, int ND, int D>
+__device__ __forceinline__ double eta_h(const DevGrid& g, int a, int b, const double* S) {
+  double eta = (a >= 0 && b >= 0) ? eta_cells<G, ND>(g, a, b, S) : 0.0;
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    const int c = m ? b : a;
+    if (c < 0) continue;
+    int ci, cj, ck;
+    cell_ijk(g, c, ci, cj, ck);
+#pragma unroll
+    for (int e = 0; e < ND; ++e) {
+      if (e == D) continue;
+#pragma unroll
+      for (int s = -1; s <= 1; s += 2) {
+        bool lw;
+        const int nb = neighbour(g, ci, cj, ck, e, s, lw);
+        if (nb < 0) continue;
+        eta = fmax(eta, eta_cells<G, ND>(g, c, nb, face_vec(g, e, ci, cj, ck, s)));
+      }
+    }
+  }
+  return eta;
+}
+
+// ---------------------------------------------------------------------------------------
 // K3: face fluxes along direction D (per face): MUSCL + Roe + central viscous.
 // ---------------------------------------------------------------------------------------
 template <class G, int ND, int D>
@@ -1013,10 +1061,11 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
         vr[v] -= 0.5 * limiter(g.limiter, dc, dp);
       }
     }
+    const double etaH = g.hcorr ? eta_h<G, ND, D>(g, a, b, S) : 0.0;
     if (!recon_ok<G, ND>(vl) || !recon_ok<G, ND>(vr)) {
-      roe<G, ND>(wa, wb, S, g.efix, Fi);
+      roe<G, ND>(wa, wb, S, g.efix, etaH, Fi);
     } else {
-      roe<G, ND>(vl, vr, S, g.efix, Fi);
+      roe<G, ND>(vl, vr, S, g.efix, etaH, Fi);
     }
     // ---- viscous (reading 18) ----
     double t[3], tl = 0.0;
@@ -1110,8 +1159,9 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
       double wi[NR], wg[NR];
       recon_load<G, ND>(g.W, N, c, wi);
       recon_ghost<G, ND>(g, c, p[0], p[1], p[2], D, s, wg);
-      if (s > 0) roe<G, ND>(wi, wg, S, g.efix, Fi);
-      else roe<G, ND>(wg, wi, S, g.efix, Fi);
+      const double etaH = g.hcorr ? eta_h<G, ND, D>(g, s > 0 ? c : -1, s > 0 ? -1 : c, S) : 0.0;
+      if (s > 0) roe<G, ND>(wi, wg, S, g.efix, etaH, Fi);
+      else roe<G, ND>(wg, wi, S, g.efix, etaH, Fi);
     }
   }
 #pragma unroll

@@ -52,6 +52,8 @@ CASES = {
     "sphere_cone_air11": (lambda: inputs.sphere_cone(9, 6, 8), inputs.sphere_cone_bc(),
                           inputs.MECH_AIR11, dict(T=5000.0, Tv=4000.0, p=5000.0)),
     "tiny_periodic_air5": (lambda: inputs.cylinder_ogrid(3, 2), inputs.cylinder_bc(), inputs.MECH_AIR5, {}),
+    "half_cyl_air11": (lambda: inputs.cylinder_half(25, 16), inputs.cylinder_half_bc(),
+                       inputs.MECH_AIR11, dict(T=6000.0, Tv=4500.0, p=8000.0)),
 }
 
 
@@ -101,6 +103,21 @@ def test_residual_parity(name):
         assert rel(Fg, Fo, ns=ref.ns) < TOL, f"face flux {d}"
     assert rel(Rg, Rr, ns=ref.ns) < TOL
     np.testing.assert_allclose(ng, nr, rtol=TOL, atol=0)
+
+
+@pytest.mark.parametrize("name", ["c1_ogrid_air5", "half_cyl_air11", "box3d_air5_kper"])
+def test_residual_parity_without_h_correction(name):
+    """The option that switches the H-correction of the entropy fix off acts on both sides
+    alike, and changes the face fluxes."""
+    ref, gpu, _ = make_pair(name)
+    Fon = gpu.residual()[0].copy()
+    ref.set_hcorr(False)
+    gpu.set_option("h_correction", 0)
+    Rr, nr = ref.residual()
+    Rg, ng = gpu.residual()
+    assert rel(Rg, Rr, ns=ref.ns) < TOL
+    np.testing.assert_allclose(ng, nr, rtol=TOL, atol=0)
+    assert rel(Rg, Fon, ns=ref.ns) > 1e-6
 
 
 @pytest.mark.parametrize("name", list(CASES))

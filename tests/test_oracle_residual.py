@@ -113,6 +113,72 @@ def test_mirror_symmetry(mech):
 
 
 @pytest.mark.parametrize("mech", [inputs.MECH_AIR5, inputs.MECH_AIR11])
+def test_mirror_symmetry_half_grid(mech):
+    """The windward half grid with odd ni is symmetric about the stagnation line (cell i <->
+    ni - 1 - i) and ends in outflow boundaries on both sides: a mirror-symmetric state has a
+    mirror-symmetric residual, with the H-correction of the entropy fix switched on."""
+    ni, nj = 15, 10
+    nodes = inputs.cylinder_half(ni, nj)
+    g = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), mech, limiter=1)
+    g.set_boundary(inputs.freestream(mech, T=300.0, p=500.0, mach=10.0), Tw=500.0)
+    pr = inputs.perturbed_primitive(mech, (nj, ni), seed=6, ndim=2)
+    mi = ni - 1 - np.arange(ni)
+    for k in pr:
+        if k == "u":
+            pr[k][0] = 0.5 * (pr[k][0] + pr[k][0][:, mi])
+            pr[k][1] = 0.5 * (pr[k][1] - pr[k][1][:, mi])
+        else:
+            pr[k] = 0.5 * (pr[k] + pr[k][..., mi])
+    g.set_state(oracle.prim_to_cons_field(mech, 2, pr))
+    R, _ = g.residual()
+    R = R.reshape(g.nq, nj, ni)
+    Rm = R[:, :, mi].copy()
+    Rm[g.ns + 1] *= -1
+    assert np.max(rel_err(R, Rm, axis=(1, 2))) < 1e-11
+
+
+def test_h_correction_closed_form():
+    """H-correction of the entropy fix (Sanders, Morano and Druguet 1998) on a 2 x 3 Cartesian
+    box, first order, eps = 0.  Across each i-face only the density jumps (same p, u = (0, v)
+    on both sides), so Roe's dissipation is l2 * (rho_R - rho_L) with l2 the fixed modulus of
+    the zero wave speed u_n = 0, and the mass flux is -|S| l2 (rho_R - rho_L) / 2.  With the
+    width 2 eta_H, l2 = eta_H: the largest of (|jump of u.n| + |jump of c|) / 2 over the face
+    and the j-faces bounding its two cells, boundary faces counting 0.  Without the
+    correction, l2 = 0 and the flux vanishes."""
+    mech = inputs.MECH_PERFECT
+    ni, nj = 2, 3
+    nodes = inputs.box_grid(ni, nj, lx=2.0, ly=3.0)
+    p = np.array([1000.0, 1000.0, 2000.0])                   # per row j
+    v = np.array([0.0, 300.0, -100.0])                       # per row j
+    rho = np.array([[0.010, 0.012], [0.010, 0.011], [0.020, 0.0205]])   # [j, i]
+    Rgas = 8314.462618 / 28.9647
+    pr = {"rho_s": rho[None], "u": np.zeros((2, nj, ni)), "T": p[:, None] / (rho * Rgas)}
+    pr["u"][1] = v[:, None]
+    pr["Tv"] = pr["T"]
+    c = np.sqrt(1.4 * p[:, None] / rho)                      # diatomic perfect gas, gamma 1.4
+
+    def eta_j(i, j):                                         # j-face between rows j and j+1
+        if j < 0 or j + 1 >= nj:
+            return 0.0
+        return 0.5 * (abs(v[j + 1] - v[j]) + abs(c[j + 1, i] - c[j, i]))
+
+    for hcorr in (True, False):
+        g = oracle.OracleGrid(nodes, BOX_BC, mech, limiter=0, efix=0.0)
+        g.set_hcorr(hcorr)
+        g.set_boundary(inputs.freestream(mech, T=300.0, p=1000.0, mach=0.0))
+        g.set_state(oracle.prim_to_cons_field(mech, 2, pr))
+        g.set_reacting(False)
+        g.residual()
+        F0 = g.field("F0").reshape(-1, g.nq)
+        for j in range(nj):
+            etaH = max(0.5 * abs(c[j, 1] - c[j, 0]), eta_j(0, j), eta_j(0, j - 1),
+                       eta_j(1, j), eta_j(1, j - 1))
+            want = -0.5 * 1.0 * (etaH if hcorr else 0.0) * (rho[j, 1] - rho[j, 0])
+            got = F0[1 + (ni + 1) * j, 0]
+            assert abs(got - want) <= 1e-9 * 0.5 * etaH * abs(rho[j, 1] - rho[j, 0]), (hcorr, j, got, want)
+
+
+@pytest.mark.parametrize("mech", [inputs.MECH_AIR5, inputs.MECH_AIR11])
 def test_telescoping_conservation(mech):
     """sum over cells of R equals the net outward flux through the boundary faces (the
     interior faces cancel), with the sources switched off."""
@@ -191,6 +257,7 @@ def test_species_diffusion_sums_to_zero():
     ni, nj = 6, 5
     nodes = inputs.box_grid(ni, nj, seed=2, wiggle=0.3)
     g = oracle.OracleGrid(nodes, BOX_BC, mech, limiter=1, efix=0.0)
+    g.set_hcorr(False)      # no entropy fix at all: Roe adds no dissipation at rest
     fs = inputs.freestream(mech, T=300.0, p=1000.0, mach=0.0)
     g.set_boundary(fs)
     pr = inputs.perturbed_primitive(mech, (nj, ni), seed=8, ndim=2)
