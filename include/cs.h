@@ -175,7 +175,13 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * J. Comput. Phys. 145, 1998; the paper names Roe's scheme, Sec. 3.2, but not its entropy
  * fix), which keeps the bow shock of a blunt body free of the carbuncle instability; 0 keeps
  * only the one-dimensional fix entropy_fix (|u_n| + c).
- * Errors: CS_ERR_ARG for an unknown name. */
+ * Method option: "update_limit" = f >= 0 (default 0 = off; not in the paper) scales each
+ * cell's whole increment by min(1, f rho / |d rho|) before the consistency corrections of
+ * cs_correct / cs_step, so that no iteration changes a cell's density by more than the
+ * fraction f.  The factor is 1 once increments are small, so the converged solution does not
+ * change; it only carries an impulsively started hypersonic flow through its start-up
+ * transient at large CFL.
+ * Errors: CS_ERR_ARG for an unknown name or a negative / NaN update_limit. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Residual monitors without device allocation (no counterpart in the paper: a service for

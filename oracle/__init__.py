@@ -42,6 +42,7 @@ def lib():
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_set_reacting.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_hcorr.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_update_limit.argtypes = [C.c_void_p, C.c_double]
         L.orc_set_boundary.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                        _dp, _dp, C.c_double]
         L.orc_freestream_state.argtypes = [C.c_void_p, _dp]
@@ -237,6 +238,9 @@ class OracleGrid:
 
     def set_hcorr(self, on):
         lib().orc_set_hcorr(self._h, int(bool(on)))
+
+    def set_update_limit(self, f):
+        self._check(lib().orc_set_update_limit(self._h, float(f)), "set_update_limit")
 
     def set_boundary(self, fs, Tw=500.0):
         Y = _f64(fs["Y"])

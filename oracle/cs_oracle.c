@@ -665,6 +665,7 @@ typedef struct {
     int nd, n[3], bc[6], limiter;
     double efix;
     int hcorr;                       /* H-correction of the entropy fix on/off */
+    double update_limit;             /* largest relative density change per update (0: off) */
     int ncell, nf[3];                /* faces per direction */
     int nq, nF, nsplit, nci;
     double *node[3];
@@ -1677,15 +1678,26 @@ static int lusgs_coupled(orc_grid *G, double cfl)
  * clip = 1, negative densities are set to zero (commented-out remark at the end of Sec. 2.3.3)
  * and counted.  mode 1: CS-1, mode 2: CS-2, mode 0: coupled (CI) update with the
  * eliminated (first) species = rho - sum of the others.
+ * Update limit (not in the paper; off unless set): with f = update_limit > 0, the cell's whole
+ * increment is scaled by alpha = min(1, f rho / |d rho|) before the corrections, so that no
+ * iteration changes a cell's density by more than the fraction f.  alpha = 1 once the
+ * increments are small, so the converged solution is unchanged; it only tames the start-up
+ * transient of an impulsively started hypersonic flow at large CFL.
  * ------------------------------------------------------------------------------------- */
-static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
+static int correct_update(orc_grid *G, int mode, int clip, const double *dqall)
 {
     int N = G->ncell, ns = G->gas.ns, nd = G->nd, nF = G->nF;
+    int nv = (mode == 0) ? G->nci : G->nsplit;
     G->nclip = 0;
     for (int c = 0; c < N; c++) {
         double rho = 0.0, rs[NSMAX];
         for (int s = 0; s < ns; s++) { rs[s] = G->Q[(size_t)s * N + c]; rho += rs[s]; }
-        double drho = dq[c];
+        /* this cell's increment, scaled by the update limit; indexed like the full array */
+        double alpha = 1.0, dloc[NQMAX + NSMAX];
+        if (G->update_limit > 0.0 && fabs(dqall[c]) > G->update_limit * rho)
+            alpha = G->update_limit * rho / fabs(dqall[c]);
+        for (int k = 0; k < nv; k++) dloc[k] = alpha * dqall[(size_t)k * N + c];
+        double drho = dloc[0];
         double rnew = rho + drho;
         if (!(rnew > 0.0)) {
             G->status_cell = c;
@@ -1695,13 +1707,13 @@ static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
         double out[NSMAX];
         if (mode == 1) {
             double sd = 0.0;
-            for (int s = 0; s < ns; s++) sd += dq[(size_t)(nF + s) * N + c];
+            for (int s = 0; s < ns; s++) sd += dloc[nF + s];
             for (int s = 0; s < ns; s++)
-                out[s] = rs[s] + dq[(size_t)(nF + s) * N + c] + (rs[s] / rho) * (drho - sd);
+                out[s] = rs[s] + dloc[nF + s] + (rs[s] / rho) * (drho - sd);
         } else if (mode == 2) {
             double t[NSMAX], sum = 0.0;
             for (int s = 0; s < ns; s++) {
-                t[s] = rs[s] + dq[(size_t)(nF + s) * N + c];
+                t[s] = rs[s] + dloc[nF + s];
                 if (clip && t[s] < 0.0) { t[s] = 0.0; G->nclip++; }
                 sum += t[s];
             }
@@ -1713,7 +1725,7 @@ static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
             for (int s = 0; s < ns; s++) out[s] = rnew * t[s] / sum;
         } else {
             double sum = 0.0;
-            for (int s = 1; s < ns; s++) { out[s] = rs[s] + dq[(size_t)(nF + s - 1) * N + c]; sum += out[s]; }
+            for (int s = 1; s < ns; s++) { out[s] = rs[s] + dloc[nF + s - 1]; sum += out[s]; }
             out[0] = rnew - sum;
         }
         for (int s = 0; s < ns; s++) {
@@ -1721,7 +1733,7 @@ static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
             G->Q[(size_t)s * N + c] = out[s];
         }
         for (int k = 1; k < nF; k++) {
-            double v = G->Q[(size_t)(ns + k - 1) * N + c] + dq[(size_t)k * N + c];
+            double v = G->Q[(size_t)(ns + k - 1) * N + c] + dloc[k];
             if (clip && G->gas.ntemp == 2 && k == nF - 1 && v < 0.0) { v = 0.0; G->nclip++; }
             G->Q[(size_t)(ns + k - 1) * N + c] = v;
         }
@@ -1788,6 +1800,8 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
 int orc_set_reacting(orc_grid *G, int reacting) { G->react = reacting != 0; return 0; }
 /* H-correction of the entropy fix on (1, the default) or off (0) */
 int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
+/* update limit f (see correct_update); 0 switches it off */
+int orc_set_update_limit(orc_grid *G, double f) { if (!(f >= 0.0)) return 1; G->update_limit = f; return 0; }
 
 void orc_destroy(orc_grid *G)
 {

@@ -311,6 +311,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   d.react = desc->reacting;
   d.efix = desc->entropy_fix;
   d.hcorr = 1;
+  d.ulim = 0.0;
   d.Tw = 300.0;
   for (int k = 0; k < 3; ++k) d.nf[k] = 0;
   for (int k = 0; k < nd; ++k)
@@ -734,6 +735,11 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!strcmp(name, "cluster_sweep")) {
     g->L->use_cluster = value != 0.0;
     g->L->cluster_kind = value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1);
+    return CS_OK;
+  }
+  if (!strcmp(name, "update_limit")) {
+    if (!(value >= 0.0)) return fail(g, CS_ERR_ARG, "update_limit must be >= 0");
+    g->g.ulim = value;
     return CS_OK;
   }
   if (!strcmp(name, "h_correction")) {

@@ -38,7 +38,7 @@ struct DevGrid {
   int nd, ni, nj, nk, N;
   int bc[6];
   int limiter, react, hcorr;
-  double efix, Tw;
+  double efix, Tw, ulim;
   int nf[3];
   const double* S[3];
   const double* fc[3];
@@ -2255,7 +2255,11 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
     rs[s] = g.Q[s * N + c];
     rho += rs[s];
   }
-  const double drho = dq[c];
+  // update limit (off when g.ulim = 0): scale the cell's whole increment so that its density
+  // changes by at most the fraction ulim; alpha = 1 leaves every product exact
+  double alpha = 1.0;
+  if (g.ulim > 0.0 && fabs(dq[c]) > g.ulim * rho) alpha = g.ulim * rho / fabs(dq[c]);
+  const double drho = alpha * dq[c];
   const double rnew = rho + drho;
   if (!(rnew > 0.0)) {
     set_status(g, ST_NONPHYSICAL, c);
@@ -2266,15 +2270,15 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
   if (mode == 1) {
     double sd = 0.0;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) sd += dq[(NF + s) * N + c];
+    for (int s = 0; s < NS; ++s) sd += alpha * dq[(NF + s) * N + c];
     const double irho = 1.0 / rho, rem = drho - sd;
 #pragma unroll
-    for (int s = 0; s < NS; ++s) out[s] = rs[s] + dq[(NF + s) * N + c] + rs[s] * irho * rem;
+    for (int s = 0; s < NS; ++s) out[s] = rs[s] + alpha * dq[(NF + s) * N + c] + rs[s] * irho * rem;
   } else if (mode == 2) {
     double t[NS], sum = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-      t[s] = rs[s] + dq[(NF + s) * N + c];
+      t[s] = rs[s] + alpha * dq[(NF + s) * N + c];
       if (clip && t[s] < 0.0) { t[s] = 0.0; ++nclip; }
       sum += t[s];
     }
@@ -2290,7 +2294,7 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
     double sum = 0.0;
 #pragma unroll
     for (int s = 1; s < NS; ++s) {
-      out[s] = rs[s] + dq[(NF + s - 1) * N + c];
+      out[s] = rs[s] + alpha * dq[(NF + s - 1) * N + c];
       sum += out[s];
     }
     out[0] = rnew - sum;
@@ -2303,7 +2307,7 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
   }
 #pragma unroll
   for (int q = 1; q < NF; ++q) {
-    double v = g.Q[(NS + q - 1) * N + c] + dq[q * N + c];
+    double v = g.Q[(NS + q - 1) * N + c] + alpha * dq[q * N + c];
     if (clip && G::NTEMP == 2 && q == NF - 1 && v < 0.0) { v = 0.0; ++nclip; }
     g.Q[(NS + q - 1) * N + c] = v;
   }

@@ -187,6 +187,33 @@ def test_correction_parity(mode, clip):
     assert rel(gpu.get_state(), ref.get_state(), ns=ref.ns) < 1e-14
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_correction_parity_with_update_limit(mode):
+    """The update limit scales a cell's whole increment by min(1, f rho / |d rho|) on both
+    sides; the increments here exceed f = 0.02 of the density in most cells."""
+    ref, gpu, Q = make_pair("c1_ogrid_air5", seed=5)
+    rng = np.random.default_rng(11)
+    n = ref.nci if mode == 0 else ref.nsplit
+    dQ = np.zeros((n, ref.ncell))
+    rho = Q[:ref.ns].sum(axis=0)
+    dQ[0] = 0.05 * rho * rng.uniform(-1, 1, ref.ncell)
+    dQ[1:ref.nF] = 0.01 * Q[ref.ns:] * rng.uniform(-1, 1, (ref.nF - 1, ref.ncell))
+    k = n - ref.nF
+    dQ[ref.nF:] = 0.5 * Q[:k] * rng.uniform(-1.5, 1, (k, ref.ncell))
+    Qlim = ref.get_state()
+    ref.set_update_limit(0.02)
+    gpu.set_option("update_limit", 0.02)
+    nr = ref.correct(mode, 0, dQ)      # no clipping: the new density is exactly rho + alpha d rho
+    ng = gpu.correct(mode, 0, dQ)
+    assert nr == ng
+    Qr = ref.get_state()
+    assert rel(gpu.get_state(), Qr, ns=ref.ns) < 1e-14
+    # no cell's density moved by more than 2 % (plus rounding)
+    drho = np.abs(Qr[:ref.ns].sum(axis=0) - Qlim[:ref.ns].sum(axis=0))
+    assert np.all(drho <= 0.02 * rho * (1 + 1e-12))
+    assert np.mean(drho > 0.019 * rho) > 0.3
+
+
 @pytest.mark.parametrize("scheme,corr", [(0, 1), (0, 2), (1, 0)])
 def test_multi_iteration_parity(scheme, corr):
     """20 iterations from the freestream (impulsive start, CFL ramp) on the C1 grid."""
