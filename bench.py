@@ -35,28 +35,33 @@ MECH = inputs.MECH_AIR11
 MACH, T_INF, P_INF, T_WALL = 15.0, 300.0, 500.0, 500.0
 CFL, CFL_START, RAMP = 2.0, 0.5, 100
 WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
-# FP64 floating-point operations per cell and iteration of each phase (2 x DFMA + DMUL + DADD
-# thread instructions counted by ncu on this workload, divided by the cell count; the
-# primitive phase varies with the Newton iteration count).  On GB300 every residual kernel
-# runs with its FP64 pipe 70-86 % busy, so the roofline of this path is the FP64 ALU, not HBM.
+# Floating-point operations per cell and iteration of each phase (2 x FMA + MUL + ADD thread
+# instructions counted by ncu on this workload, one launch from the 5th iteration, divided by
+# the cell count; the primitive phase varies with the Newton iteration count, i.e. with the
+# state).  On GB300 every residual kernel keeps its FP64 pipe 74-86 % busy at <15 % of DRAM
+# peak, so the roofline of this path is the FP64 ALU, not HBM; the sweeps are latency-bound
+# (one dependent hyperplane step after another).
 FP64_FLOPS_PER_CELL = {
-    "primitive": 11883.0,
-    "gradient": 402.0,
-    "flux": 2299.0,
-    "assemble": 137.0,
-    "spectral": 358.0,
+    "primitive": 13737.0,
+    "gradient": 400.0,
+    "flux": 2844.0,            # both directions
+    "assemble": 130.0,
+    "spectral": 359.0,
     "sweep_fwd": 474.0,        # both sweeps of all components (one cluster launch)
     "sweep_bwd": 0.0,
-    "correct": 82.0,
+    "correct": 109.0,
 }
+FP32_FLOPS_PER_CELL_SWEEP = 658.0     # the FP32 wavefront sweep of the mixed-precision operator
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
-    "primitive": 39.6e6, "flux": 2 * 65.8e6, "sweep_fwd": 36.7e6, "gradient": 17.4e6,
-    "spectral": 54.0e6, "assemble": 33.9e6, "correct": 24.4e6,
+    "primitive": 34.7e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 37.2e6, "gradient": 17.4e6,
+    "spectral": 54.1e6, "assemble": 33.9e6, "correct": 24.4e6,
 }
-# GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA microbenchmark measured
-# 1.20 TFLOP/s on this machine)
+DRAM_BYTES_SWEEP_FP32 = 36.6e6 + 38.2e6   # record packing + FP32 wavefront sweep
+# GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA throughput microbenchmark
+# measured 1.20 TFLOP/s on this machine).  FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 FP64_PEAK_GFLOPS = 1250.0
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 
 
 def log(*a):
@@ -270,11 +275,19 @@ def main():
     dom = max(prof, key=lambda p: prof[p][0])
     dom_ms = prof[dom][0] / args.steps
     launches = sum(v[1] for v in prof.values())
-    flops = FP64_FLOPS_PER_CELL[dom] * N
+    fp32_sweep = PRECISION == 1 and dom.startswith("sweep")
+    flops = (FP32_FLOPS_PER_CELL_SWEEP if fp32_sweep else FP64_FLOPS_PER_CELL[dom]) * N
+    peak = FP32_PEAK_GFLOPS if fp32_sweep else FP64_PEAK_GFLOPS
     achieved = flops / (dom_ms / 1e3) / 1e9
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS, "traffic": DRAM_BYTES_PER_LAUNCH.get(dom),
-            "kernel_phase": dom, "peak_kind": "nominal FP64 of the recipe (1.25 TFLOP/s)",
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+            "frac": achieved / peak,
+            "traffic": DRAM_BYTES_SWEEP_FP32 if fp32_sweep else DRAM_BYTES_PER_LAUNCH.get(dom),
+            "kernel_phase": dom,
+            "peak_kind": ("FP32 from unit counts and clock (152 x 128 x 2 x 2.07 GHz)" if fp32_sweep
+                          else "nominal FP64 of the recipe (1.25 TFLOP/s)"),
+            "note": ("the sweeps are bound by the latency of one dependent hyperplane step after "
+                     "another (2 x 638 per iteration), not by throughput" if dom.startswith("sweep")
+                     else "FP64-ALU bound (ncu: FP64 pipe 74-86 % busy, DRAM < 15 % of peak)"),
             "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof},
             "phases_fp64_frac": {p: (FP64_FLOPS_PER_CELL[p] * N / (prof[p][0] / args.steps / 1e3) / 1e9
                                      / FP64_PEAK_GFLOPS) if prof[p][0] > 0 else None for p in prof}}

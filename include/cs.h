@@ -176,11 +176,13 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * fix), which keeps the bow shock of a blunt body free of the carbuncle instability; 0 keeps
  * only the one-dimensional fix entropy_fix (|u_n| + c).
  * Method option: "update_limit" = f >= 0 (default 0 = off; not in the paper) scales each
- * cell's whole increment by min(1, f rho / |d rho|) before the consistency corrections of
- * cs_correct / cs_step, so that no iteration changes a cell's density by more than the
- * fraction f.  The factor is 1 once increments are small, so the converged solution does not
- * change; it only carries an impulsively started hypersonic flow through its start-up
- * transient at large CFL.
+ * cell's whole increment before the consistency corrections of cs_correct / cs_step by
+ * alpha = min(1, f rho / |d rho|), halved (at most 30 times) while the corrected state is
+ * non-physical or its specific translational(-rotational) thermal energy leaves a factor
+ * 1 + f of the old one, or (2T) its specific pool energy gains more than f times the old
+ * specific thermal plus pool energy.  alpha is 1 once increments are small, so the converged
+ * solution does not change; it only carries an impulsively started hypersonic flow through
+ * its start-up transient at large CFL.
  * Errors: CS_ERR_ARG for an unknown name or a negative / NaN update_limit. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 

@@ -9,7 +9,7 @@
  * benchmark may build, load or call it.
  *
  * Every function names the passage of the paper it follows.  Where the paper is silent or
- * garbled, the reading taken is stated at the function (and listed in the design doc of the repo).
+ * garbled, the reading taken is stated at the function.
  *
  * Units: SI, dimensional finite volume (Ma/Re == 1); 2D grids have unit depth.
  * Layout: cell c = i + ni*(j + nj*k); conserved state Q is struct-of-arrays [var][cell] with
@@ -640,19 +640,26 @@ static void cell_sources(const gas_t *g, int nd, prim_t *w)
     w->omega_v = 0.0;
     w->relax = 0.0;
     if (g->ntemp == 2) {
-        /* Landau-Teller exchange + species created/destroyed at the pool energy */
+        /* Landau-Teller exchange + species created/destroyed at the pool energy.
+         * relax = -d(Landau-Teller)/d(rho e_v) at fixed rho_s, momentum and rho E (the
+         * conserved-variable derivative of the source Jacobian reading): raising rho e_v
+         * raises Tv (d Tv = d(rho e_v)/(rho c_v,ve)) and, the total energy being fixed,
+         * lowers T (d T = -d(rho e_v)/(rho c_v,tr)), so both the pool's and the equilibrium
+         * energy's heat capacities enter; the temperature dependence of tau is left out. */
         relaxation_times(g, w, w->tau);
-        double lt = 0.0, rc = 0.0;
+        double lt = 0.0, rc = 0.0, rcT = 0.0;
         for (int s = 0; s < ns; s++) {
             if (w->tau[s] > 0.0) {
                 lt += w->rhos[s] * (e_vib(g, s, w->T) - e_vib(g, s, w->Tv)) / w->tau[s];
                 rc += w->rhos[s] * cv_vib(g, s, w->Tv) / w->tau[s];
+                rcT += w->rhos[s] * cv_vib(g, s, w->T) / w->tau[s];
             }
             double epool = is_heavy(g, s) ? e_vib(g, s, w->Tv) : 1.5 * g->Rs[s] * w->Tv;
             lt += w->omega[s] * epool;
         }
         w->omega_v = lt;
-        w->relax = (w->cvve > 0.0) ? rc / (w->rho * w->cvve) : 0.0;
+        w->relax = ((w->cvve > 0.0) ? rc / (w->rho * w->cvve) : 0.0) +
+                   ((w->cvtr > 0.0) ? rcT / (w->rho * w->cvtr) : 0.0);
     }
 }
 
@@ -1680,65 +1687,127 @@ static int lusgs_coupled(orc_grid *G, double cfl)
  * eliminated (first) species = rho - sum of the others.
  * Update limit (not in the paper; off unless set): with f = update_limit > 0, the cell's whole
  * increment is scaled by alpha = min(1, f rho / |d rho|) before the corrections, so that no
- * iteration changes a cell's density by more than the fraction f.  alpha = 1 once the
- * increments are small, so the converged solution is unchanged; it only tames the start-up
- * transient of an impulsively started hypersonic flow at large CFL.
+ * iteration changes a cell's density by more than the fraction f; alpha is then halved (at
+ * most 30 times) while the corrected state is non-physical or its specific thermal energies
+ * leave the band: e_tr = (rho E - |m|^2/(2 rho) [- rho e_v] - sum_s rho_s h0_s)/rho, which is
+ * proportional to the translational(-rotational) temperature, within a factor 1 + f of the
+ * old value, and (2T) the pool's e_v = rho e_v / rho gaining at most f (e_tr + e_v) of the
+ * old values.  alpha = 1 once the increments are small, so the converged solution is
+ * unchanged; it only carries an impulsively started hypersonic flow through its start-up
+ * transient at large CFL (where a cell can otherwise, e.g., dissociate more than its thermal
+ * energy can pay for, or take the energy of an arriving shock before its density).
  * ------------------------------------------------------------------------------------- */
-static int correct_update(orc_grid *G, int mode, int clip, const double *dqall)
+
+/* New conserved state qn of cell c for the increment alpha * dq with the correction of
+ * `mode`; returns 0, or 4 (message in G->err) for a non-physical result.  *ncl counts the
+ * values that were clipped. */
+static int cell_update(orc_grid *G, int mode, int clip, const double *dqall, int c,
+                       double alpha, double *qn, int *ncl)
 {
-    int N = G->ncell, ns = G->gas.ns, nd = G->nd, nF = G->nF;
+    int N = G->ncell, ns = G->gas.ns, nF = G->nF;
     int nv = (mode == 0) ? G->nci : G->nsplit;
-    G->nclip = 0;
-    for (int c = 0; c < N; c++) {
-        double rho = 0.0, rs[NSMAX];
-        for (int s = 0; s < ns; s++) { rs[s] = G->Q[(size_t)s * N + c]; rho += rs[s]; }
-        /* this cell's increment, scaled by the update limit; indexed like the full array */
-        double alpha = 1.0, dloc[NQMAX + NSMAX];
-        if (G->update_limit > 0.0 && fabs(dqall[c]) > G->update_limit * rho)
-            alpha = G->update_limit * rho / fabs(dqall[c]);
-        for (int k = 0; k < nv; k++) dloc[k] = alpha * dqall[(size_t)k * N + c];
-        double drho = dloc[0];
-        double rnew = rho + drho;
-        if (!(rnew > 0.0)) {
-            G->status_cell = c;
-            snprintf(G->err, sizeof(G->err), "non-positive density after update at cell %d", c);
+    double rho = 0.0, rs[NSMAX], dloc[NQMAX + NSMAX];
+    *ncl = 0;
+    for (int s = 0; s < ns; s++) { rs[s] = G->Q[(size_t)s * N + c]; rho += rs[s]; }
+    for (int k = 0; k < nv; k++) dloc[k] = alpha * dqall[(size_t)k * N + c];
+    double drho = dloc[0];
+    double rnew = rho + drho;
+    if (!(rnew > 0.0)) {
+        snprintf(G->err, sizeof(G->err), "non-positive density after update at cell %d", c);
+        return 4;
+    }
+    double out[NSMAX];
+    if (mode == 1) {
+        double sd = 0.0;
+        for (int s = 0; s < ns; s++) sd += dloc[nF + s];
+        for (int s = 0; s < ns; s++)
+            out[s] = rs[s] + dloc[nF + s] + (rs[s] / rho) * (drho - sd);
+    } else if (mode == 2) {
+        double t[NSMAX], sum = 0.0;
+        for (int s = 0; s < ns; s++) {
+            t[s] = rs[s] + dloc[nF + s];
+            if (clip && t[s] < 0.0) { t[s] = 0.0; (*ncl)++; }
+            sum += t[s];
+        }
+        if (!(sum > 0.0)) {
+            snprintf(G->err, sizeof(G->err), "non-positive species sum at cell %d", c);
             return 4;
         }
-        double out[NSMAX];
-        if (mode == 1) {
-            double sd = 0.0;
-            for (int s = 0; s < ns; s++) sd += dloc[nF + s];
-            for (int s = 0; s < ns; s++)
-                out[s] = rs[s] + dloc[nF + s] + (rs[s] / rho) * (drho - sd);
-        } else if (mode == 2) {
-            double t[NSMAX], sum = 0.0;
-            for (int s = 0; s < ns; s++) {
-                t[s] = rs[s] + dloc[nF + s];
-                if (clip && t[s] < 0.0) { t[s] = 0.0; G->nclip++; }
-                sum += t[s];
-            }
-            if (!(sum > 0.0)) {
-                G->status_cell = c;
-                snprintf(G->err, sizeof(G->err), "non-positive species sum at cell %d", c);
-                return 4;
-            }
-            for (int s = 0; s < ns; s++) out[s] = rnew * t[s] / sum;
-        } else {
-            double sum = 0.0;
-            for (int s = 1; s < ns; s++) { out[s] = rs[s] + dloc[nF + s - 1]; sum += out[s]; }
-            out[0] = rnew - sum;
-        }
-        for (int s = 0; s < ns; s++) {
-            if (clip && out[s] < 0.0 && mode != 2) { out[s] = 0.0; G->nclip++; }
-            G->Q[(size_t)s * N + c] = out[s];
-        }
-        for (int k = 1; k < nF; k++) {
-            double v = G->Q[(size_t)(ns + k - 1) * N + c] + dloc[k];
-            if (clip && G->gas.ntemp == 2 && k == nF - 1 && v < 0.0) { v = 0.0; G->nclip++; }
-            G->Q[(size_t)(ns + k - 1) * N + c] = v;
-        }
+        for (int s = 0; s < ns; s++) out[s] = rnew * t[s] / sum;
+    } else {
+        double sum = 0.0;
+        for (int s = 1; s < ns; s++) { out[s] = rs[s] + dloc[nF + s - 1]; sum += out[s]; }
+        out[0] = rnew - sum;
     }
-    (void)nd;
+    for (int s = 0; s < ns; s++) {
+        if (clip && out[s] < 0.0 && mode != 2) { out[s] = 0.0; (*ncl)++; }
+        qn[s] = out[s];
+    }
+    for (int k = 1; k < nF; k++) {
+        double v = G->Q[(size_t)(ns + k - 1) * N + c] + dloc[k];
+        if (clip && G->gas.ntemp == 2 && k == nF - 1 && v < 0.0) { v = 0.0; (*ncl)++; }
+        qn[ns + k - 1] = v;
+    }
+    return 0;
+}
+
+/* specific energies of a conserved state: e[0] = translational(-rotational) thermal energy per
+ * unit mass (formation energy, kinetic energy [and the pool] taken out), e[1] = pool energy per
+ * unit mass (2T; 0 for 1T) */
+static void specific_thermal(const orc_grid *G, const double *q, double *e)
+{
+    int ns = G->gas.ns, nd = G->nd;
+    double rho = 0.0, m2 = 0.0, et = q[ns + nd];
+    for (int s = 0; s < ns; s++) rho += q[s];
+    for (int d = 0; d < nd; d++) m2 += q[ns + d] * q[ns + d];
+    et -= 0.5 * m2 / rho;
+    for (int s = 0; s < ns; s++) et -= q[s] * G->gas.hf[s];
+    e[1] = 0.0;
+    if (G->gas.ntemp == 2) {
+        et -= q[ns + nd + 1];
+        e[1] = q[ns + nd + 1] / rho;
+    }
+    e[0] = et / rho;
+}
+
+/* is the updated state qn inside the update limit's band around q0? */
+static int within_limit(const orc_grid *G, const double *q0, const double *qn, double f)
+{
+    double e0[2], en[2];
+    specific_thermal(G, q0, e0);
+    if (!(e0[0] > 0.0)) return 1;               /* no band without a positive thermal energy */
+    specific_thermal(G, qn, en);
+    if (!(en[0] * (1.0 + f) >= e0[0] && en[0] <= (1.0 + f) * e0[0])) return 0;
+    if (G->gas.ntemp == 2 && !(en[1] <= e0[1] + f * (e0[0] + e0[1]))) return 0;
+    return 1;
+}
+
+static int correct_update(orc_grid *G, int mode, int clip, const double *dq)
+{
+    int N = G->ncell, ns = G->gas.ns, nq = G->nq;
+    double f = G->update_limit;
+    G->nclip = 0;
+    for (int c = 0; c < N; c++) {
+        double rho = 0.0, q0[NQMAX], qn[NQMAX];
+        for (int v = 0; v < nq; v++) q0[v] = G->Q[(size_t)v * N + c];
+        for (int s = 0; s < ns; s++) rho += q0[s];
+        double alpha = 1.0;
+        if (f > 0.0 && fabs(dq[c]) > f * rho) alpha = f * rho / fabs(dq[c]);
+        int ncl = 0;
+        int st = cell_update(G, mode, clip, dq, c, alpha, qn, &ncl);
+        if (f > 0.0) {
+            for (int it = 0; it < 30 && (st || !within_limit(G, q0, qn, f)); it++) {
+                alpha *= 0.5;
+                st = cell_update(G, mode, clip, dq, c, alpha, qn, &ncl);
+            }
+        }
+        if (st) {
+            G->status_cell = c;
+            return st;
+        }
+        for (int v = 0; v < nq; v++) G->Q[(size_t)v * N + c] = qn[v];
+        G->nclip += ncl;
+    }
     G->have_R = 0;
     return 0;
 }

@@ -611,7 +611,7 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, const doub
   const double patm = ph / kPref, nden = xs * kNa, T13 = rcbrt(w.T);
   const double iT = 1.0 / w.T, iTv = 1.0 / w.Tv, sqT = sqrt(w.T);
   const double sv = 1e-21 * (50000.0 * iT) * (50000.0 * iT);
-  double lt = 0.0, rc = 0.0;
+  double lt = 0.0, rc = 0.0, rcT = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     const SpeciesData& d = G::sp(s);
@@ -632,12 +632,16 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, const doub
       vib_em<G>(s, iTv, emTv[s], eV, cV);
       lt += w.rhos[s] * (eT - eV) * itau;
       rc += w.rhos[s] * cV * itau;
+      rcT += w.rhos[s] * cT * itau;
     }
     const double ep = (d.kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
     lt += omega[s] * ep;
   }
   omv = lt;
-  relax = (w.cvve > 0.0) ? rc / (w.rho * w.cvve) : 0.0;
+  // -d(Landau-Teller)/d(rho e_v) at fixed rho_s, momentum and rho E: Tv rises with rho e_v
+  // and T falls (the total energy being fixed); tau's temperature dependence is left out
+  relax = ((w.cvve > 0.0) ? rc / (w.rho * w.cvve) : 0.0) +
+          ((w.cvtr > 0.0) ? rcT / (w.rho * w.cvtr) : 0.0);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -746,7 +750,8 @@ __device__ __forceinline__ double limiter(int type, double a, double b) {
   return (a * b * (a + b)) / (a * a + b * b);
 }
 
-// Roe flux (reading 17) from two reconstructed states; F = flux * |S|.  Harten's entropy fix
+// Roe flux (Sec. 3.2 names Roe's scheme) from two reconstructed states, Roe average with
+// sqrt(rho) weights; F = flux * |S|.  Harten's entropy fix
 // width is max(efix (|u_n| + c), 2 etaH), etaH being the face's H-correction (0 for none).
 template <class G, int ND>
 __device__ void roe(const double* L, const double* R, const double* S, double efix, double etaH,
@@ -918,7 +923,8 @@ __global__ void __launch_bounds__(128) k_gradient(DevGrid g) {
     for (int q = 0; q < ND; ++q) g.grad[(v * 3 + q) * N + c] = gr[v][q] * iV;
 }
 
-// Viscous / diffusive flux through S from face gradients (reading 13, 18).
+// Viscous / diffusive flux through S from face gradients (Sec. 2.1 tau, q, q_v and Fick
+// diffusion; the energy flux includes -k_v grad Tv).
 template <class G, int ND>
 __device__ void viscous(const double (*gf)[ND], const double* uf, double mu, double kt, double kv,
                         double rhoD, const double* hs, const double* eve, const double* S,
@@ -1036,7 +1042,7 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
     p[D] = 0;     b = cell_of(g, p[0], p[1], p[2]);
   }
   if (a >= 0) {
-    // ---- interior face: MUSCL (reading 17) ----
+    // ---- interior face: MUSCL on (rho_s, u, p, Gam, beta, [e_v]) ----
     int ai, aj, ak, bi, bj, bk;
     cell_ijk(g, a, ai, aj, ak);
     cell_ijk(g, b, bi, bj, bk);
@@ -1067,7 +1073,7 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
     } else {
       roe<G, ND>(vl, vr, S, g.efix, etaH, Fi);
     }
-    // ---- viscous (reading 18) ----
+    // ---- viscous: mean of the cell gradients, centroid-line component replaced ----
     double t[3], tl = 0.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
@@ -1224,7 +1230,7 @@ __global__ void __launch_bounds__(256) k_assemble(DevGrid g) {
 }
 
 // final reduction of the norm partials (one block); out[0..1] = sqrt of sums; also computes
-// the stagnation heat flux of cell `stag` (reading 22).
+// the stagnation heat flux of cell `stag` (q_w = k (T_1 - Tw)/d_1 [+ k_v (Tv_1 - Tw)/d_1]).
 template <class G, int ND>
 __global__ void __launch_bounds__(256) k_norms(DevGrid g, int nblocks, int stag, double* out) {
   using A = Aux<G, ND>;
@@ -2239,33 +2245,23 @@ __global__ void __launch_bounds__(32 * kClusterWarps) k_split_cluster(DevGrid g,
 }
 
 // ---------------------------------------------------------------------------------------
-// K7: consistency corrections and update (Sec. 2.3.3; readings 10, 11).
+// K7: consistency corrections and update (Sec. 2.3.3; CS-1 weight W_s = Y_s, negative
+// densities clipped to 0 and counted).
 // mode 1: CS-1, 2: CS-2 (dQ in split layout), 0: coupled update (CI layout).
 // ---------------------------------------------------------------------------------------
+// New conserved state qn of cell c for the increment alpha * dq with the correction of `mode`
+// (rs: the cell's species densities, rho their sum); false for a non-physical result.
 template <class G, int ND>
-__global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, const double* dq) {
+__device__ __forceinline__ bool cell_update(const DevGrid& g, int mode, int clip, const double* dq,
+                                            int c, const double* rs, double rho, double alpha,
+                                            double* qn, int& nclip) {
   using A = Aux<G, ND>;
   constexpr int NS = G::NS, NF = A::NF;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.N) return;
   const size_t N = g.N;
-  double rs[NS], rho = 0.0;
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    rs[s] = g.Q[s * N + c];
-    rho += rs[s];
-  }
-  // update limit (off when g.ulim = 0): scale the cell's whole increment so that its density
-  // changes by at most the fraction ulim; alpha = 1 leaves every product exact
-  double alpha = 1.0;
-  if (g.ulim > 0.0 && fabs(dq[c]) > g.ulim * rho) alpha = g.ulim * rho / fabs(dq[c]);
+  nclip = 0;
   const double drho = alpha * dq[c];
   const double rnew = rho + drho;
-  if (!(rnew > 0.0)) {
-    set_status(g, ST_NONPHYSICAL, c);
-    return;
-  }
-  int nclip = 0;
+  if (!(rnew > 0.0)) return false;
   double out[NS];
   if (mode == 1) {
     double sd = 0.0;
@@ -2282,10 +2278,7 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
       if (clip && t[s] < 0.0) { t[s] = 0.0; ++nclip; }
       sum += t[s];
     }
-    if (!(sum > 0.0)) {
-      set_status(g, ST_NONPHYSICAL, c);
-      return;
-    }
+    if (!(sum > 0.0)) return false;
     const double f = rnew / sum;
 #pragma unroll
     for (int s = 0; s < NS; ++s) out[s] = t[s] * f;
@@ -2303,14 +2296,86 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
   for (int s = 0; s < NS; ++s) {
     double v = out[s];
     if (clip && v < 0.0 && mode != 2) { v = 0.0; ++nclip; }
-    g.Q[s * N + c] = v;
+    qn[s] = v;
   }
 #pragma unroll
   for (int q = 1; q < NF; ++q) {
     double v = g.Q[(NS + q - 1) * N + c] + alpha * dq[q * N + c];
     if (clip && G::NTEMP == 2 && q == NF - 1 && v < 0.0) { v = 0.0; ++nclip; }
-    g.Q[(NS + q - 1) * N + c] = v;
+    qn[NS + q - 1] = v;
   }
+  return true;
+}
+
+// Specific energies of a conserved state: e0 = translational(-rotational) thermal energy per
+// unit mass (formation, kinetic [and pool] energy taken out), e1 = pool energy per unit mass.
+template <class G, int ND>
+__device__ __forceinline__ void specific_thermal(const double* q, double& e0, double& e1) {
+  constexpr int NS = G::NS;
+  double rho = 0.0, m2 = 0.0, et = q[NS + ND];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) rho += q[s];
+#pragma unroll
+  for (int d = 0; d < ND; ++d) m2 += q[NS + d] * q[NS + d];
+  et -= 0.5 * m2 / rho;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) et -= q[s] * hf<G>(s);
+  e1 = 0.0;
+  if (G::NTEMP == 2) {
+    et -= q[NS + ND + 1];
+    e1 = q[NS + ND + 1] / rho;
+  }
+  e0 = et / rho;
+}
+
+// Is the updated state qn inside the update limit's band around q0 (specific thermal energy
+// within a factor 1 + f, pool energy gaining at most f of the old specific energies)?
+template <class G, int ND>
+__device__ __forceinline__ bool within_limit(const double* q0, const double* qn, double f) {
+  double a0, a1, b0, b1;
+  specific_thermal<G, ND>(q0, a0, a1);
+  if (!(a0 > 0.0)) return true;
+  specific_thermal<G, ND>(qn, b0, b1);
+  if (!(b0 * (1.0 + f) >= a0 && b0 <= (1.0 + f) * a0)) return false;
+  if (G::NTEMP == 2 && !(b1 <= a1 + f * (a0 + a1))) return false;
+  return true;
+}
+
+// K7: consistency correction (CS-1 mode 1, CS-2 mode 2, coupled mode 0) and update, with the
+// optional update limit: the cell's whole increment is scaled by alpha = min(1, ulim rho /
+// |d rho|), then alpha is halved (at most 30 times) while the corrected state is non-physical
+// or outside the band of within_limit.  alpha = 1 leaves every product exact, so with
+// ulim = 0 this is the plain update.
+template <class G, int ND>
+__global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, const double* dq) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NQ = A::NQ;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double q0[NQ], rho = 0.0;
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) q0[v] = g.Q[v * N + c];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) rho += q0[s];
+  const double f = g.ulim;
+  double alpha = 1.0;
+  if (f > 0.0 && fabs(dq[c]) > f * rho) alpha = f * rho / fabs(dq[c]);
+  double qn[NQ];
+  int nclip = 0;
+  bool ok = cell_update<G, ND>(g, mode, clip, dq, c, q0, rho, alpha, qn, nclip);
+  if (f > 0.0) {
+    for (int it = 0; it < 30 && (!ok || !within_limit<G, ND>(q0, qn, f)); ++it) {
+      alpha *= 0.5;
+      ok = cell_update<G, ND>(g, mode, clip, dq, c, q0, rho, alpha, qn, nclip);
+    }
+  }
+  if (!ok) {
+    set_status(g, ST_NONPHYSICAL, c);
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < NQ; ++v) g.Q[v * N + c] = qn[v];
   if (nclip) atomicAdd(&g.status[2], nclip);
 }
 

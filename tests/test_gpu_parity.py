@@ -189,8 +189,9 @@ def test_correction_parity(mode, clip):
 
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_correction_parity_with_update_limit(mode):
-    """The update limit scales a cell's whole increment by min(1, f rho / |d rho|) on both
-    sides; the increments here exceed f = 0.02 of the density in most cells."""
+    """The update limit scales a cell's whole increment by min(1, f rho / |d rho|), then
+    halves it while the thermal band is left, on both sides alike; the increments here exceed
+    f = 0.02 of the density in most cells."""
     ref, gpu, Q = make_pair("c1_ogrid_air5", seed=5)
     rng = np.random.default_rng(11)
     n = ref.nci if mode == 0 else ref.nsplit
@@ -208,10 +209,11 @@ def test_correction_parity_with_update_limit(mode):
     assert nr == ng
     Qr = ref.get_state()
     assert rel(gpu.get_state(), Qr, ns=ref.ns) < 1e-14
-    # no cell's density moved by more than 2 % (plus rounding)
+    # no cell's density moved by more than 2 % (plus rounding), and the limit acted in most
+    # cells (the density moved by less than the raw increment)
     drho = np.abs(Qr[:ref.ns].sum(axis=0) - Qlim[:ref.ns].sum(axis=0))
     assert np.all(drho <= 0.02 * rho * (1 + 1e-12))
-    assert np.mean(drho > 0.019 * rho) > 0.3
+    assert np.mean(drho < 0.99 * np.abs(dQ[0])) > 0.3
 
 
 @pytest.mark.parametrize("scheme,corr", [(0, 1), (0, 2), (1, 0)])

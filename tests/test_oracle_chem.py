@@ -155,3 +155,25 @@ def test_landau_teller_sign_and_zero():
     v = oracle.state_vib(mech, 2, q)
     ref = oracle.state_vib(mech, 2, oracle.state_cons(mech, 2, rhos, [0.0, 0.0], 1000.0, 900.0))
     assert abs(v["omega_v"]) < 1e-10 * abs(ref["omega_v"])
+
+
+def test_relaxation_diagonal_is_conserved_variable_derivative():
+    """At T = Tv the Landau-Teller source vanishes, and so do the terms from the temperature
+    dependence of tau; there the vibrational diagonal relax equals -d omega_v / d(rho e_v) at
+    fixed species densities, momentum and total energy (both Tv and T move), which a central
+    difference of the source gives independently.  Pure N2 at 3000 K: chemistry is frozen
+    to ~1e-17 relative, so the pool-energy term of omega_v does not enter."""
+    mech = inputs.MECH_AIR11
+    nd = 2
+    rhos = np.zeros(11)
+    rhos[0] = 0.02
+    q = oracle.state_cons(mech, nd, rhos, [300.0, 0.0], 3000.0, 3000.0)
+    v = oracle.state_vib(mech, nd, q)
+    iev = 11 + nd + 1                        # rho e_v slot of the conserved vector
+    h = 1e-6 * q[iev]
+    qp, qm = q.copy(), q.copy()
+    qp[iev] += h
+    qm[iev] -= h
+    d = (oracle.state_vib(mech, nd, qp)["omega_v"] - oracle.state_vib(mech, nd, qm)["omega_v"]) / (2 * h)
+    # (the Tv part alone is relax / (1 + c_v,ve / c_v,tr), ~26 % smaller for N2 at 3000 K)
+    assert abs(-d - v["relax"]) < 1e-6 * v["relax"], (-d, v["relax"])
