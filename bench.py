@@ -192,6 +192,89 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, local):
+    """Batched serving workload: independent half-cylinder cases of uneven size (64 x 48 to
+    512 x 384, Mach 6-20, 5 or 11 species), tuned, then stepped together through one CUDA graph
+    per iteration; value = sum of cells x iterations / device time."""
+    import numpy as np
+    import torch
+    import paper_2403_03440_gb300 as P
+    P.build()
+    torch.cuda.set_device(local)
+    cases = inputs.batch_cases(args.batch_cases, seed=0)
+    grids = []
+    for c in cases:
+        nodes = inputs.cylinder_half(c["ni"], c["nj"], dr1=5e-5 * 48 / c["ni"])
+        fs = inputs.freestream(c["mech"], T=T_INF, p=P_INF, mach=c["mach"])
+        g = P.Grid(nodes, inputs.cylinder_half_bc(), c["mech"])
+        g.set_boundary(fs, Tw=T_WALL)
+        g.init_freestream()
+        grids.append(g)
+    cells = sum(g.ncell for g in grids)
+    batch = P.Batch(grids)
+    t0 = time.perf_counter()
+    choice = batch.tune(precision=PRECISION, trials=2)
+    tune_s = time.perf_counter() - t0
+    # CS-1, each case's CFL reached by a geometric ramp from 0.5 over 500 iterations
+    opts = [dict(scheme=0, correction=1, clip=1, cfl=c["cfl"], cfl_start=0.5, ramp_iters=500,
+                 precision=PRECISION) for c in cases]
+    K = args.iters_per_graph
+    if args.steps % K or args.warmup % K:
+        raise SystemExit("--steps and --warmup must be multiples of --iters-per-graph")
+    batch.step(opts, iters=args.warmup, iters_per_graph=K)
+    stream = torch.cuda.ExternalStream(batch.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        stats = batch.step(opts, iters=args.steps, iters_per_graph=K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = cells * args.steps / (ms / 1e3) / 1e6
+    # end to end through the public API with host buffers: every case's state uploaded from
+    # pinned memory, one batched iteration, every state downloaded
+    hq = [torch.empty((g.nq, g.ncell), dtype=torch.float64, pin_memory=True).numpy() for g in grids]
+    for g, q in zip(grids, hq):
+        g.get_state(q)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for g, q in zip(grids, hq):
+            g.set_state(q)
+        batch.step(opts, iters=K, iters_per_graph=K)
+        for g, q in zip(grids, hq):
+            g.get_state(q)
+    e2e_s = time.perf_counter() - t0
+    nbytes = int(sum(q.nbytes for q in hq))
+    e2e = cells * K * args.e2e_steps / e2e_s / 1e6
+    # kernels per case and iteration: cfl, primitive, gradient, 2 fluxes, assemble + norms,
+    # spectral, sweep (records + wavefront kernel, or one cluster kernel), correction
+    per_iter = sum(9 + (2 if kind == 2 else 1) for kind, _ in choice)
+    if rank == 0:
+        line = {
+            "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if PRECISION == 0 else "f64 residual/update, f32 operator",
+            "data": "synthetic",
+            "config": {"workload": f"batch-{len(cases)}-half-cylinders-64x48-to-512x384-mach6-20-"
+                                   f"air5-or-air11-CS1-{'fp64' if PRECISION == 0 else 'mixed'}",
+                       "cases": len(cases), "cells": cells, "iters_per_graph": K,
+                       "cfl": "ramp from 0.5 over 500 iterations to each case's CFL (5-200)",
+                       "l2": "inputs (all cases' state and work arrays) far larger than L2",
+                       "tune_seconds": tune_s,
+                       "tuned": {f"{kind}:{C}": sum(1 for x in choice if x == (kind, C))
+                                 for kind, C in set(choice)},
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e, "unit": "Mcell-iter/s", "h2d_bytes_per_step": nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": per_iter * args.steps,
+            "cases_failed": sum(1 for st in stats if st["status_cell"] != -1),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -201,6 +284,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "batch"])
+    ap.add_argument("--batch-cases", type=int, default=64)
+    ap.add_argument("--iters-per-graph", type=int, default=1)
     args = ap.parse_args()
     global PRECISION, WORKLOAD
     if args.precision == "mixed":
@@ -214,6 +300,9 @@ def main():
         return
     if args.warmup < 3:
         raise SystemExit("warmup must be >= 3")
+    if args.workload == "batch":
+        run_batch(args, rank, world, local)
+        return
 
     import torch
     import paper_2403_03440_gb300 as P

@@ -169,7 +169,9 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * split sweeps as one thread-block-cluster launch, choosing per precision between 2 (cluster
  * kernel over hyperplane-ordered cell records, faster in FP32) and 1 (cluster kernel reading
  * the cell arrays directly, faster in FP64); 0 runs one launch per hyperplane.  All give the
- * same arithmetic up to rounding.
+ * same arithmetic up to rounding.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
+ * component of the 2D cluster sweeps (0, the default: the largest that fits; a C that does not
+ * fit the grid or the device falls back to one launch per hyperplane); cs_batch_tune sets it.
  * Method option: "h_correction" = 1 (default) widens the entropy fix of every face's Roe flux
  * to at least twice the face's multidimensional H-correction (Sanders, Morano and Druguet,
  * J. Comput. Phys. 145, 1998; the paper names Roe's scheme, Sec. 3.2, but not its entropy
@@ -206,6 +208,40 @@ cs_status cs_residual_norms_static(const double *R_dev, const double *V_dev, int
                                    double norms_host[2]);
 
 const char *cs_last_error(cs_grid g);
+
+/* ---- Batches of independent cases (no counterpart in the paper: many cases of uneven size
+ * stepped together on one GPU) ----
+ * A batch refers to grids the caller created and set up (cs_set_boundary done); it does not
+ * own them, and they must outlive it.  cs_batch_step captures iters_per_graph iterations of
+ * every case (each with its own cs_step_opts; the CFL ramp of each case is evaluated on the
+ * device from the case's iteration count) into one CUDA graph, each case on a stream of the
+ * batch, and replays the graph iters / iters_per_graph times; the cases run concurrently.  The
+ * graph is kept and reused while the options and iters_per_graph stay the same.  Work the
+ * caller queued on a grid's own stream completes before the batch runs, and the batch's work
+ * has completed when a batch call returns.  Results are those of cs_step with the same options
+ * (up to the rounding of the device-evaluated CFL ramp).
+ * Errors: CS_ERR_ARG (null pointers, ncases < 1, a grid without boundary conditions, invalid
+ * options, iters not a multiple of iters_per_graph), CS_ERR_CUDA (stream capture, graph
+ * instantiation or launch failed), CS_ERR_OOM; after the run, the first case that ended in a
+ * non-physical state or failed temperature solve gives CS_ERR_NONPHYSICAL / CS_ERR_NEWTON,
+ * the per-case status being in stats[c].status_cell (-1: fine) and iters_done (0: failed). */
+typedef struct cs_batch_s *cs_batch;
+cs_status cs_batch_create(int ncases, const cs_grid *grids, cs_batch *out);
+cs_status cs_batch_destroy(cs_batch b);
+/* Autotuner: for every 2D case of the batch, time trials applications of the split sweep
+ * operator (on the operator inputs of the current state; the state is not changed) for each
+ * cluster kernel (1: direct loads, 2: hyperplane-ordered records) and each cluster size C in
+ * {1, 2, 4, 8, 16} that fits the grid and the device, and keep the fastest (a smaller C wins
+ * unless the larger one is more than 3 % faster).  choice_out (host [2 * ncases], nullable)
+ * receives (kind, C) per case, (0, 0) where no cluster sweep applies (3D or periodic j). */
+cs_status cs_batch_tune(cs_batch b, int precision, int trials, int *choice_out);
+cs_status cs_batch_step(cs_batch b, const cs_step_opts *opts, int iters, int iters_per_graph,
+                        cs_step_stats *stats);
+/* The batch's own stream (cudaStream_t): every graph launch of cs_batch_step is issued on it,
+ * so CUDA events recorded on it before and after a cs_batch_step call bracket the batch's
+ * device work.  The stream stays owned by the batch. */
+cs_status cs_batch_stream(cs_batch b, void **stream_out);
+const char *cs_batch_last_error(cs_batch b);
 
 #ifdef __cplusplus
 }

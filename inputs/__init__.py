@@ -257,3 +257,18 @@ def perturbed_primitive(mech, cell_shape, seed, T=1500.0, Tv=None, p=2000.0,
     for d in range(ndim):
         u[d] = speed * (0.8 if d == 0 else 0.2) * (1.0 + fields[ns + 3 + d])
     return dict(rho_s=Yc * rho[None], u=u, T=Tc, Tv=Tvc)
+
+
+def batch_cases(n=64, seed=0):
+    """Seeded list of independent 2D half-cylinder cases of uneven size for batched runs:
+    grid (64 s) x (48 s) with s uniform in 1..8, Mach uniform in [6, 20], CFL log-uniform in
+    [5, 200], 5-species 1T or 11-species 2T air with probability 1/2 each."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        s = int(rng.integers(1, 9))
+        mach = float(rng.uniform(6.0, 20.0))
+        cfl = float(math.exp(rng.uniform(math.log(5.0), math.log(200.0))))
+        mech = MECH_AIR5 if rng.random() < 0.5 else MECH_AIR11
+        out.append(dict(ni=64 * s, nj=48 * s, mach=mach, cfl=cfl, mech=mech))
+    return out

@@ -98,7 +98,8 @@ EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary
            "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
            "cs_gas_info", "cs_profile", "cs_set_option", "cs_residual_norms_static",
-           "cs_last_error"]
+           "cs_last_error", "cs_batch_create", "cs_batch_destroy", "cs_batch_tune",
+           "cs_batch_step", "cs_batch_stream", "cs_batch_last_error"]
 
 _lib = None
 
@@ -129,9 +130,14 @@ def lib():
     L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
     L.cs_set_option.argtypes = [vp, C.c_char_p, C.c_double]
     L.cs_last_error.argtypes = [vp]
-    L.cs_last_error.restype = C.c_char_p
+    L.cs_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
+    L.cs_batch_destroy.argtypes = [vp]
+    L.cs_batch_tune.argtypes = [vp, C.c_int, C.c_int, ip]
+    L.cs_batch_step.argtypes = [vp, C.POINTER(cs_step_opts), C.c_int, C.c_int, C.POINTER(cs_step_stats)]
+    L.cs_batch_stream.argtypes = [vp, C.POINTER(vp)]
+    L.cs_batch_last_error.argtypes = [vp]
     for name in EXPORTS:
-        getattr(L, name).restype = C.c_int if name != "cs_last_error" else C.c_char_p
+        getattr(L, name).restype = C.c_char_p if name.endswith("last_error") else C.c_int
     _lib = L
     return L
 
@@ -291,3 +297,58 @@ class Grid:
         n = C.c_int(0)
         self._check(lib().cs_get_field(self._h, name.encode(), _ptr(out), C.byref(n)), "cs_get_field")
         return out[:n.value].copy()
+
+
+class Batch:
+    """Independent grids stepped together: K iterations of every case captured into one CUDA
+    graph and replayed (cs_batch_* of the C ABI).  The grids must outlive the batch."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g._h for g in self.grids])
+        h = C.c_void_p()
+        st = lib().cs_batch_create(len(self.grids), arr, C.byref(h))
+        if st:
+            raise CSError(st, "cs_batch_create")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().cs_batch_destroy(self._h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st:
+            raise CSError(st, f"{what}: {lib().cs_batch_last_error(self._h).decode()}")
+
+    def stream(self):
+        """Address of the batch's cudaStream_t (for CUDA events around step())."""
+        h = C.c_void_p()
+        self._check(lib().cs_batch_stream(self._h, C.byref(h)), "cs_batch_stream")
+        return h.value
+
+    def tune(self, precision=0, trials=3):
+        """Time the split sweep per case over cluster kernels and sizes; returns [(kind, C)]."""
+        out = (C.c_int * (2 * len(self.grids)))()
+        self._check(lib().cs_batch_tune(self._h, int(precision), int(trials), out), "cs_batch_tune")
+        return [(out[2 * c], out[2 * c + 1]) for c in range(len(self.grids))]
+
+    def step(self, opts, iters, iters_per_graph=1):
+        """opts: one dict of cs_step options per case (keys as Grid.step, without iters)."""
+        n = len(self.grids)
+        arr = (cs_step_opts * n)()
+        for c, o in enumerate(opts):
+            arr[c].scheme = o.get("scheme", 0)
+            arr[c].correction = o.get("correction", 1)
+            arr[c].clip = o.get("clip", 1)
+            arr[c].cfl = o.get("cfl", 10.0)
+            arr[c].cfl_start = o.get("cfl_start", 1.0)
+            arr[c].ramp_iters = o.get("ramp_iters", 0)
+            arr[c].precision = o.get("precision", 0)
+            arr[c].iters = iters
+        stats = (cs_step_stats * n)()
+        st = lib().cs_batch_step(self._h, arr, int(iters), int(iters_per_graph), stats)
+        out = [dict(iters_done=s.iters_done, r_species=s.r_species, r_energy=s.r_energy,
+                    q_stag=s.q_stag, nclip=s.nclip, status_cell=s.status_cell) for s in stats]
+        self._check(st, "cs_batch_step")
+        return out

@@ -29,7 +29,8 @@ CASES = {
 SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1)}
 
 
-def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1):
+def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1,
+        update_limit=0.0):
     c = CASES[case]
     # The windward half only: a full O-grid holds the cylinder's near wake, which is unsteady
     # at these Reynolds numbers and keeps the residual from converging.
@@ -38,6 +39,8 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
     g = P.Grid(nodes, inputs.cylinder_half_bc(), c["mech"], limiter=limiter)
     g.set_boundary(fs, Tw=500.0)
     g.init_freestream()
+    if update_limit > 0:
+        g.set_option("update_limit", update_limit)
     sch, corr = SCHEMES[scheme]
     kw = dict(scheme=sch, correction=corr, clip=clip, cfl=cfl, cfl_start=cfl_start,
               ramp_iters=ramp, precision=precision)
@@ -64,6 +67,7 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
     dt = time.perf_counter() - t0
     best = min(max(h[1], h[2]) for h in hist)
     return dict(case=case, scheme=scheme, precision="mixed" if precision else "fp64", cfl=cfl,
+                cfl_start=cfl_start, ramp=ramp, update_limit=update_limit,
                 limiter=limiter, tol=tol, status=status, iterations=done, seconds=dt,
                 ms_per_iter=1e3 * dt / max(done - 1, 1), min_drop=best,
                 q_stag_final=hist[-1][3], cells=c["ni"] * c["nj"],
@@ -82,10 +86,11 @@ def main():
     ap.add_argument("--chunk", type=int, default=100)
     ap.add_argument("--limiter", type=int, default=1)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--update-limit", type=float, default=0.0)
     a = ap.parse_args()
     P.build()
     out = run(a.case, a.scheme, a.cfl, a.cfl_start, a.ramp, a.tol, a.max_iters, a.chunk,
-              a.limiter, 1 if a.precision == "mixed" else 0)
+              a.limiter, 1 if a.precision == "mixed" else 0, update_limit=a.update_limit)
     print(json.dumps(out))
 
 

@@ -157,6 +157,7 @@ struct cs_grid_s {
   double* norms = nullptr;    // device [3]
   int* stag_dev = nullptr;
   double* params = nullptr;   // device [4]
+  int* iter_dev = nullptr;    // device iteration counter of the CFL ramp in captured iterations
   double* h_pin = nullptr;    // pinned host scratch [64]
   int* h_status = nullptr;    // pinned [4]
   int stag = -1;
@@ -385,6 +386,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   ALLOC(g->norms, 4);
   ALLOC(g->stag_dev, 1);
   ALLOC(g->params, 4);
+  ALLOC(g->iter_dev, 1);
 #undef ALLOC
   d.DLU = nullptr;
   d.piv = nullptr;
@@ -614,60 +616,97 @@ extern "C" cs_status cs_correct(cs_grid g, int mode, int clip, const double* dQ,
   return CS_OK;
 }
 
-extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* stats) {
-  if (!g || !o) return CS_ERR_ARG;
-  if (!g->have_bc) return fail(g, CS_ERR_STATE, "cs_step before cs_set_boundary");
+// CFL of the current iteration computed on the device (the geometric ramp of cs_step from a
+// device iteration counter), so that a captured iteration replays with the right CFL.
+__global__ void k_cfl(double* params, int* iter, double cfl, double cfl_start, int ramp) {
+  const int it = *iter;
+  double c = cfl;
+  if (ramp > 0 && it < ramp && cfl_start > 0.0) c = cfl_start * pow(cfl / cfl_start, (double)it / (double)ramp);
+  params[0] = c;
+  *iter = it + 1;
+}
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+static cs_status check_opts(const cs_step_opts* o) {
+  if (!o) return CS_ERR_ARG;
   if (o->scheme != CS_SCHEME_SPLIT && o->scheme != CS_SCHEME_COUPLED) return CS_ERR_ARG;
   if (o->scheme == CS_SCHEME_SPLIT && o->correction != 1 && o->correction != 2) return CS_ERR_ARG;
   if ((o->precision != CS_FP64 && o->precision != CS_MIXED) || o->iters < 0) return CS_ERR_ARG;
+  if (!(o->cfl > 0.0)) return CS_ERR_ARG;
+  return CS_OK;
+}
+
+// Enqueue one pseudo-time iteration on g->stream (no host synchronisation).  device_cfl: the
+// CFL comes from k_cfl and the device iteration counter and no profiling events are recorded
+// (stream capture); otherwise the CFL of iteration g->iter is copied from pinned memory slot
+// `slot`.  *nf / *nb receive the forward / backward sweep launch counts.
+static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, bool device_cfl,
+                                   int* nf_out, int* nb_out) {
   const bool mixed = o->precision == CS_MIXED;
-  cs_status st = CS_OK;
+  CUDA_TRY(g, cudaMemsetAsync(&g->g.status[2], 0, sizeof(int), g->stream));
+  if (device_cfl) {
+    k_cfl<<<1, 1, 0, g->stream>>>(g->params, g->iter_dev, o->cfl, o->cfl_start, o->ramp_iters);
+  } else {
+    double cfl = o->cfl;
+    if (o->ramp_iters > 0 && g->iter < o->ramp_iters && o->cfl_start > 0.0)
+      cfl = o->cfl_start * pow(o->cfl / o->cfl_start, (double)g->iter / (double)o->ramp_iters);
+    g->h_pin[41 + slot] = cfl;
+    CUDA_TRY(g, cudaMemcpyAsync(g->params, g->h_pin + 41 + slot, sizeof(double),
+                                cudaMemcpyHostToDevice, g->stream));
+  }
+  const bool rec = !device_cfl;
+  const DevGrid& d = g->g;
+  if (rec) prof_record(g, slot, 0);
+  g->L->primitive(d, g->stream);
+  if (rec) prof_record(g, slot, 1);
+  g->L->gradient(d, g->stream);
+  if (rec) prof_record(g, slot, 2);
+  g->L->flux(d, g->stream);
+  if (rec) prof_record(g, slot, 3);
+  g->L->assemble(d, g->stream, g->stag, g->norms);
+  if (rec) prof_record(g, slot, 4);
+  g->L->spectral(d, g->stream);
+  int nf, nb;
+  if (o->scheme == CS_SCHEME_SPLIT) {
+    if (rec) prof_record(g, slot, 5);
+    // the cluster path runs both sweeps in one launch (timed as phase 5)
+    nf = g->L->use_cluster ? g->L->sweep_split_cluster(d, g->stream, mixed) : 0;
+    nb = 0;
+    if (!nf) nf = g->L->sweep_split_dir(d, g->stream, true, mixed);
+    if (rec) prof_record(g, slot, 6);
+    if (!g->L->use_cluster || !g->L->sweep_split_cluster_ok) nb = g->L->sweep_split_dir(d, g->stream, false, mixed);
+    if (rec) prof_record(g, slot, 7);
+    g->L->correct(d, g->stream, o->correction, o->clip, d.dQ);
+  } else {
+    g->L->ci_block(d, g->stream);
+    if (rec) prof_record(g, slot, 5);
+    nf = g->L->sweep_coupled_dir(d, g->stream, true);
+    if (rec) prof_record(g, slot, 6);
+    nb = g->L->sweep_coupled_dir(d, g->stream, false);
+    if (rec) prof_record(g, slot, 7);
+    g->L->correct(d, g->stream, 0, o->clip, d.dQc);
+  }
+  if (rec) prof_record(g, slot, 8);
+  CUDA_TRY(g, cudaGetLastError());
+  *nf_out = nf;
+  *nb_out = nb;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* stats) {
+  if (!g || !o) return CS_ERR_ARG;
+  if (!g->have_bc) return fail(g, CS_ERR_STATE, "cs_step before cs_set_boundary");
+  cs_status st = check_opts(o);
+  if (st) return st;
   if (o->scheme == CS_SCHEME_COUPLED && (st = ensure_ci(g))) return fail(g, st, "allocation");
   if ((st = begin(g))) return st;
   int done = 0;
   for (int it = 0; it < o->iters; ++it) {
-    double cfl = o->cfl;
-    if (o->ramp_iters > 0 && g->iter < o->ramp_iters && o->cfl_start > 0.0)
-      cfl = o->cfl_start * pow(o->cfl / o->cfl_start, (double)g->iter / (double)o->ramp_iters);
     const int slot = it & 7;
-    CUDA_TRY(g, cudaMemsetAsync(&g->g.status[2], 0, sizeof(int), g->stream));
-    g->h_pin[41 + slot] = cfl;
-    CUDA_TRY(g, cudaMemcpyAsync(g->params, g->h_pin + 41 + slot, sizeof(double),
-                                cudaMemcpyHostToDevice, g->stream));
-    const DevGrid& d = g->g;
-    prof_record(g, slot, 0);
-    g->L->primitive(d, g->stream);
-    prof_record(g, slot, 1);
-    g->L->gradient(d, g->stream);
-    prof_record(g, slot, 2);
-    g->L->flux(d, g->stream);
-    prof_record(g, slot, 3);
-    g->L->assemble(d, g->stream, g->stag, g->norms);
-    prof_record(g, slot, 4);
-    g->L->spectral(d, g->stream);
     int nf, nb;
-    if (o->scheme == CS_SCHEME_SPLIT) {
-      prof_record(g, slot, 5);
-      // the cluster path runs both sweeps in one launch (timed as phase 5)
-      nf = g->L->use_cluster ? g->L->sweep_split_cluster(d, g->stream, mixed) : 0;
-      nb = 0;
-      if (!nf) nf = g->L->sweep_split_dir(d, g->stream, true, mixed);
-      prof_record(g, slot, 6);
-      if (!g->L->use_cluster || !g->L->sweep_split_cluster_ok) nb = g->L->sweep_split_dir(d, g->stream, false, mixed);
-      prof_record(g, slot, 7);
-      g->L->correct(d, g->stream, o->correction, o->clip, d.dQ);
-    } else {
-      g->L->ci_block(d, g->stream);
-      prof_record(g, slot, 5);
-      nf = g->L->sweep_coupled_dir(d, g->stream, true);
-      prof_record(g, slot, 6);
-      nb = g->L->sweep_coupled_dir(d, g->stream, false);
-      prof_record(g, slot, 7);
-      g->L->correct(d, g->stream, 0, o->clip, d.dQc);
-    }
-    prof_record(g, slot, 8);
+    if ((st = enqueue_iteration(g, o, slot, false, &nf, &nb))) return st;
     if (g->prof) {
-      const long per[CS_NPHASE] = {1, 1, (long)d.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
+      const long per[CS_NPHASE] = {1, 1, (long)g->g.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
       for (int p = 0; p < CS_NPHASE; ++p) g->prof_launches[p] += per[p];
       g->ev_used = slot + 1;
     }
@@ -737,6 +776,16 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     g->L->cluster_kind = value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1);
     return CS_OK;
   }
+  if (!strcmp(name, "cluster_size")) {
+    const int C = (int)value;
+    if ((double)C != value || (C != 0 && C != 1 && C != 2 && C != 4 && C != 8 && C != 16))
+      return fail(g, CS_ERR_ARG, "cluster_size must be 0, 1, 2, 4, 8 or 16");
+    // the probes set the kernels' non-portable cluster attribute where it is needed
+    for (int kind : {1, 2})
+      for (bool mixed : {false, true}) g->L->cluster_sizes(g->g, kind, mixed);
+    g->L->force_C = C;
+    return CS_OK;
+  }
   if (!strcmp(name, "update_limit")) {
     if (!(value >= 0.0)) return fail(g, CS_ERR_ARG, "update_limit must be >= 0");
     g->g.ulim = value;
@@ -750,3 +799,257 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
 }
 
 extern "C" const char* cs_last_error(cs_grid g) { return g ? g->err : "null grid"; }
+
+// ---------------------------------------------------------------------------------------
+// Batches of independent cases (many grids stepped together): K iterations of every case are
+// captured once into one CUDA graph, each case on its own stream between a fork and a join
+// event, and the graph is replayed; one graph launch then issues K iterations of all cases,
+// which run concurrently on the GPU.  Per-case CFL ramps are evaluated on the device.  The
+// tuner times each case's split sweep over the cluster sizes and the two cluster kernels.
+// ---------------------------------------------------------------------------------------
+struct cs_batch_s {
+  std::vector<cs_grid> grids;
+  std::vector<cudaStream_t> streams;   // one per case (library-owned, non-blocking)
+  std::vector<cudaEvent_t> ready, join;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cs_step_opts> key;       // options the graph was captured with
+  int key_k = 0;
+  char err[512] = {0};
+};
+
+static cs_status bfail(cs_batch b, cs_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(b->err, sizeof b->err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+#define BCUDA_TRY(b, call)                                                                  \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return bfail(b, CS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static void batch_release(cs_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->ready) cudaEventDestroy(e);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->origin) cudaStreamDestroy(b->origin);
+}
+
+extern "C" cs_status cs_batch_create(int ncases, const cs_grid* grids, cs_batch* out) {
+  if (!out || !grids || ncases < 1) return CS_ERR_ARG;
+  *out = nullptr;
+  for (int c = 0; c < ncases; ++c)
+    if (!grids[c] || !grids[c]->have_bc) return CS_ERR_ARG;
+  std::unique_ptr<cs_batch_s> b(new cs_batch_s);
+  b->grids.assign(grids, grids + ncases);
+  auto cleanup = [&](cs_status st) {
+    batch_release(b.get());
+    b->streams.clear(); b->ready.clear(); b->join.clear();
+    b->fork = nullptr; b->origin = nullptr;
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(CS_ERR_CUDA);
+  for (int c = 0; c < ncases; ++c) {
+    cudaStream_t s;
+    cudaEvent_t e1, e2;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return cleanup(CS_ERR_CUDA);
+    b->streams.push_back(s);
+    if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return cleanup(CS_ERR_CUDA);
+    b->ready.push_back(e1);
+    if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) return cleanup(CS_ERR_CUDA);
+    b->join.push_back(e2);
+  }
+  *out = b.release();
+  return CS_OK;
+}
+
+extern "C" cs_status cs_batch_destroy(cs_batch b) {
+  if (!b) return CS_ERR_ARG;
+  cudaStreamSynchronize(b->origin);
+  batch_release(b);
+  delete b;
+  return CS_OK;
+}
+
+// run fn with every grid's stream replaced by its batch stream (restored afterwards)
+template <class F>
+static cs_status with_batch_streams(cs_batch b, F fn) {
+  const int n = (int)b->grids.size();
+  std::vector<cudaStream_t> saved(n);
+  for (int c = 0; c < n; ++c) {
+    // work the caller queued on the grid's own stream comes first
+    BCUDA_TRY(b, cudaStreamSynchronize(b->grids[c]->stream));
+    saved[c] = b->grids[c]->stream;
+    b->grids[c]->stream = b->streams[c];
+  }
+  const cs_status st = fn();
+  for (int c = 0; c < n; ++c) {
+    cudaStreamSynchronize(b->streams[c]);
+    b->grids[c]->stream = saved[c];
+  }
+  return st;
+}
+
+extern "C" cs_status cs_batch_tune(cs_batch b, int precision, int trials, int* choice_out) {
+  if (!b || (precision != CS_FP64 && precision != CS_MIXED) || trials < 1) return CS_ERR_ARG;
+  const bool mixed = precision == CS_MIXED;
+  return with_batch_streams(b, [&]() -> cs_status {
+    cudaEvent_t e0, e1;
+    BCUDA_TRY(b, cudaEventCreate(&e0));
+    BCUDA_TRY(b, cudaEventCreate(&e1));
+    cs_status result = CS_OK;
+    for (size_t c = 0; c < b->grids.size() && !result; ++c) {
+      cs_grid g = b->grids[c];
+      Launcher* L = g->L.get();
+      const DevGrid& d = g->g;
+      // operator inputs of the current state (no update: the state does not change)
+      g->h_pin[40] = 1.0;
+      if (cudaMemcpyAsync(g->params, g->h_pin + 40, sizeof(double), cudaMemcpyHostToDevice, g->stream) != cudaSuccess ||
+          begin(g)) { result = bfail(b, CS_ERR_CUDA, "case %zu: setup", c); break; }
+      L->residual(d, g->stream, g->stag, g->norms);
+      L->spectral(d, g->stream);
+      float best = 1e30f;
+      int best_kind = 0, best_C = 0;
+      const int keep_kind = L->cluster_kind, keep_C = L->force_C;
+      for (int kind : {1, 2}) {
+        const int mask = L->cluster_sizes(d, kind, mixed);
+        for (int C : {1, 2, 4, 8, 16}) {
+          if (!(mask & (1 << C))) continue;
+          L->cluster_kind = kind;
+          L->force_C = C;
+          L->sweep_split_cluster(d, g->stream, mixed);      // warm
+          cudaEventRecord(e0, g->stream);
+          for (int t = 0; t < trials; ++t) L->sweep_split_cluster(d, g->stream, mixed);
+          cudaEventRecord(e1, g->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) { result = bfail(b, CS_ERR_CUDA, "case %zu: timing", c); break; }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          // prefer fewer CTAs unless the larger cluster is > 3 % faster
+          if (ms < 0.97f * best || (ms < best && C < best_C)) { best = ms; best_kind = kind; best_C = C; }
+        }
+        if (result) break;
+      }
+      if (result) break;
+      if (best_C) {
+        L->cluster_kind = best_kind;
+        L->force_C = best_C;
+      } else {
+        L->cluster_kind = keep_kind;
+        L->force_C = keep_C;
+      }
+      if (choice_out) {
+        choice_out[2 * c] = best_kind;
+        choice_out[2 * c + 1] = best_C;
+      }
+      if (finish(g, "cs_batch_tune")) result = bfail(b, CS_ERR_CUDA, "case %zu: %s", c, g->err);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (b->exec) {   // the captured graph used the old choices
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+      b->key.clear();
+    }
+    return result;
+  });
+}
+
+static bool same_opts(const cs_step_opts& a, const cs_step_opts& b) {
+  return a.scheme == b.scheme && a.correction == b.correction && a.clip == b.clip && a.cfl == b.cfl &&
+         a.cfl_start == b.cfl_start && a.ramp_iters == b.ramp_iters && a.precision == b.precision;
+}
+
+extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int iters, int iters_per_graph,
+                                   cs_step_stats* stats) {
+  if (!b || !opts || iters < 0 || iters_per_graph < 1 || iters % iters_per_graph) return CS_ERR_ARG;
+  const int n = (int)b->grids.size();
+  for (int c = 0; c < n; ++c)
+    if (check_opts(&opts[c])) return bfail(b, CS_ERR_ARG, "case %d: invalid options", c);
+  if (iters == 0) return CS_OK;
+  return with_batch_streams(b, [&]() -> cs_status {
+    for (int c = 0; c < n; ++c) {
+      cs_grid g = b->grids[c];
+      if (opts[c].scheme == CS_SCHEME_COUPLED && ensure_ci(g)) return bfail(b, CS_ERR_OOM, "case %d: allocation", c);
+      g->L->prepare(g->g, opts[c].precision == CS_MIXED);
+    }
+    bool recapture = !b->exec || b->key_k != iters_per_graph || (int)b->key.size() != n;
+    for (int c = 0; c < n && !recapture; ++c) recapture = !same_opts(b->key[c], opts[c]);
+    if (recapture) {
+      if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+      BCUDA_TRY(b, cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+      cs_status st = CS_OK;
+      if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) st = CS_ERR_CUDA;
+      for (int c = 0; c < n && !st; ++c)
+        if (cudaStreamWaitEvent(b->streams[c], b->fork, 0) != cudaSuccess) st = CS_ERR_CUDA;
+      for (int c = 0; c < n && !st; ++c) {
+        for (int k = 0; k < iters_per_graph && !st; ++k) {
+          int nf, nb;
+          st = enqueue_iteration(b->grids[c], &opts[c], 0, true, &nf, &nb);
+          if (st) bfail(b, st, "case %d: capture: %s", c, b->grids[c]->err);
+        }
+        if (!st && (cudaEventRecord(b->join[c], b->streams[c]) != cudaSuccess ||
+                    cudaStreamWaitEvent(b->origin, b->join[c], 0) != cudaSuccess))
+          st = CS_ERR_CUDA;
+      }
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+      if (st || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st ? st : bfail(b, CS_ERR_CUDA, "stream capture: %s", cudaGetErrorString(ee));
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&b->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) { b->exec = nullptr; return bfail(b, CS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei)); }
+      b->key.assign(opts, opts + n);
+      b->key_k = iters_per_graph;
+    }
+    // per-case setup on the case streams: status cleared, ramp counter = iterations done
+    for (int c = 0; c < n; ++c) {
+      cs_grid g = b->grids[c];
+      if (begin(g)) return bfail(b, CS_ERR_CUDA, "case %d: %s", c, g->err);
+      k_set_int<<<1, 1, 0, g->stream>>>(g->iter_dev, g->iter);
+      BCUDA_TRY(b, cudaEventRecord(b->ready[c], g->stream));
+      BCUDA_TRY(b, cudaStreamWaitEvent(b->origin, b->ready[c], 0));
+    }
+    for (int r = 0; r < iters / iters_per_graph; ++r) BCUDA_TRY(b, cudaGraphLaunch(b->exec, b->origin));
+    BCUDA_TRY(b, cudaStreamSynchronize(b->origin));
+    cs_status worst = CS_OK;
+    for (int c = 0; c < n; ++c) {
+      cs_grid g = b->grids[c];
+      BCUDA_TRY(b, cudaMemcpyAsync(g->h_pin + 32, g->norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+      const cs_status st = finish(g, "cs_batch_step");
+      g->iter += iters;
+      g->have_R = 0;
+      if (stats) {
+        stats[c].iters_done = st ? 0 : iters;
+        stats[c].r_species = g->h_pin[32];
+        stats[c].r_energy = g->h_pin[33];
+        stats[c].q_stag = g->h_pin[34];
+        stats[c].nclip = g->h_status[2];
+        stats[c].status_cell = st ? g->h_status[1] : -1;
+      }
+      if (st && !worst) {
+        worst = st;
+        bfail(b, st, "case %d: %s", c, g->err);
+      }
+    }
+    return worst;
+  });
+}
+
+extern "C" cs_status cs_batch_stream(cs_batch b, void** stream_out) {
+  if (!b || !stream_out) return CS_ERR_ARG;
+  *stream_out = (void*)b->origin;
+  return CS_OK;
+}
+
+extern "C" const char* cs_batch_last_error(cs_batch b) { return b ? b->err : "null batch"; }

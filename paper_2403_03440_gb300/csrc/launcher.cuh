@@ -35,7 +35,14 @@ struct Launcher {
   virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed = false) = 0;
   bool use_cluster = true;
   int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records
+  int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
+  // bit C of the result is set when the cluster sweep of `kind` (1 direct, 2 wavefront
+  // records) can run with C CTAs per component on this grid and device
+  virtual int cluster_sizes(const DevGrid& g, int kind, bool mixed) = 0;
+  // run the cluster-size probes of the current choice (host-side calls that must not happen
+  // inside a stream capture)
+  virtual void prepare(const DevGrid& g, bool mixed) = 0;
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
@@ -153,36 +160,42 @@ struct LauncherT : Launcher {
     }
   }
 
-  // Cluster size for the cluster sweep (0: not available for this grid / device).
+  // Can `kern` run as clusters of C CTAs (32 x warps threads each) with `rows` rows per CTA?
+  template <class K>
+  bool cluster_fits(K kern, int C, int warps) {
+    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
+    cfg.blockDim = dim3(32 * warps);
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) return true;
+    cudaGetLastError();
+    return false;
+  }
+
+  // Cluster size for the direct-load cluster sweep (0: not available for this grid / device).
   template <class T>
   int cluster_size(const DevGrid& g, int& probed) {
     if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    if (force_C > 0) return (g.nj + force_C - 1) / force_C <= kClusterRows ? force_C : 0;
     if (probed >= 0) return probed;
     probed = 0;
-    auto kern = k_split_cluster<G, T>;
     for (int C : {16, 8, 4, 2}) {
-      const int R = (g.nj + C - 1) / C;
-      if (R > kClusterRows) continue;
-      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
-      cfg.blockDim = dim3(32 * kClusterWarps);
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = C;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
+      if ((g.nj + C - 1) / C > kClusterRows) continue;
+      if (cluster_fits(k_split_cluster<G, T>, C, kClusterWarps)) {
         probed = C;
         break;
       }
-      cudaGetLastError();
     }
     return probed;
   }
@@ -205,34 +218,45 @@ struct LauncherT : Launcher {
   template <class T>
   int wave_cluster_size(const DevGrid& g, int& probed) {
     if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    if (force_C > 0) return (g.nj + force_C - 1) / force_C <= kWaveRows ? force_C : 0;
     if (probed >= 0) return probed;
     probed = 0;
-    auto kern = k_split_wave<G, T>;
     for (int C : {16, 8, 4, 2, 1}) {
-      const int R = (g.nj + C - 1) / C;
-      if (R > kWaveRows) continue;
-      if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      cudaLaunchConfig_t cfg = {};
-      cudaLaunchAttribute at[1];
-      cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
-      cfg.blockDim = dim3(32);
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = C;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) == cudaSuccess && n >= 1) {
+      if ((g.nj + C - 1) / C > kWaveRows) continue;
+      if (cluster_fits(k_split_wave<G, T>, C, 1)) {
         probed = C;
         break;
       }
-      cudaGetLastError();
     }
     return probed;
+  }
+
+  int cluster_sizes(const DevGrid& g, int kind, bool mixed) override {
+    if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    int mask = 0;
+    for (int C : {1, 2, 4, 8, 16}) {
+      bool ok;
+      if (kind == 2) {
+        ok = (g.nj + C - 1) / C <= kWaveRows && g.wrec &&
+             (mixed ? cluster_fits(k_split_wave<G, float>, C, 1) : cluster_fits(k_split_wave<G, double>, C, 1));
+      } else {
+        ok = C >= 2 && (g.nj + C - 1) / C <= kClusterRows &&
+             (mixed ? cluster_fits(k_split_cluster<G, float>, C, kClusterWarps)
+                    : cluster_fits(k_split_cluster<G, double>, C, kClusterWarps));
+      }
+      if (ok) mask |= 1 << C;
+    }
+    return mask;
+  }
+
+  void prepare(const DevGrid& g, bool mixed) override {
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
+    if (kind == 2) {
+      if (mixed) wave_cluster_size<float>(g, wprobed32_);
+      else wave_cluster_size<double>(g, wprobed64_);
+    }
+    if (mixed) cluster_size<float>(g, probed32_);
+    else cluster_size<double>(g, probed64_);
   }
 
   template <class T>

@@ -13,6 +13,7 @@ import pytest
 import inputs
 import oracle
 import paper_2403_03440_gb300 as P
+from _helpers import rel
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
@@ -25,19 +26,6 @@ def _device():
     P.build()
     P.lib()
     yield
-
-
-def rel(a, b, ns=0):
-    """Per-variable error of a vs b ([nvar][n]); species rows (first ns) share one scale."""
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
-    if a.ndim == 1:
-        a, b = a[None], b[None]
-    scale = np.abs(b).max(axis=1)
-    if ns:
-        scale[:ns] = np.max(scale[:ns])
-    scale = np.maximum(scale, 1e-300)
-    return float(np.max(np.abs(a - b).max(axis=1) / scale))
 
 
 CASES = {
