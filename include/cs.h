@@ -237,6 +237,52 @@ cs_status cs_batch_destroy(cs_batch b);
 cs_status cs_batch_tune(cs_batch b, int precision, int trials, int *choice_out);
 cs_status cs_batch_step(cs_batch b, const cs_step_opts *opts, int iters, int iters_per_graph,
                         cs_step_stats *stats);
+/* ---- Chemistry surrogate network (no counterpart in the paper: it stands in for the
+ * Arrhenius source and Jacobian-diagonal evaluation of Sec. 2.1 / Sec. 2.3.2 inside the
+ * implicit operator only; the residual keeps the exact chemistry) ----
+ * A 14-128-128-128-22 multilayer perceptron with SiLU hidden activations.  Parameters are one
+ * FP32 vector of CS_MLP_NPARAM values in the order W1 [128][14], b1 [128], W2 [128][128], b2,
+ * W3 [128][128], b3, W4 [22][128], b4 [22] (W row-major [out][in]); matrix products run on
+ * the tensor cores with bfloat16 weights, inputs and activations and FP32 accumulation.
+ * Inputs X are FP32 [n][14] and targets / outputs FP32 [n][22], device pointers, 1 <= n <=
+ * max_batch.  Loss = mean over rows and outputs of (y - t)^2; training is Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) on the FP32 master parameters.
+ * Errors: CS_ERR_ARG, CS_ERR_OOM, CS_ERR_CUDA, CS_ERR_TIMEOUT (a tensor-core completion wait
+ * ran out; the network is then unusable). */
+#define CS_MLP_IN 14
+#define CS_MLP_HIDDEN 128
+#define CS_MLP_OUT 22
+#define CS_MLP_NPARAM 37782
+typedef struct cs_mlp_s *cs_mlp;
+cs_status cs_mlp_create(int max_batch, const float *params_host, cs_mlp *out);
+cs_status cs_mlp_destroy(cs_mlp m);
+cs_status cs_mlp_get_params(cs_mlp m, float *params_host);
+cs_status cs_mlp_forward(cs_mlp m, const float *X_dev, int n, float *Y_dev);
+/* loss and gradient (host [CS_MLP_NPARAM], nullable) of one batch, no update */
+cs_status cs_mlp_grad(cs_mlp m, const float *X_dev, const float *T_dev, int n, float *grad_host,
+                      double *loss_out);
+/* one Adam step on one batch; loss_out (nullable) receives the loss before the step */
+cs_status cs_mlp_train_step(cs_mlp m, const float *X_dev, const float *T_dev, int n, float lr,
+                            double *loss_out);
+const char *cs_mlp_last_error(cs_mlp m);
+
+/* Solver coupling.  cs_surrogate_sample writes, for every cell of g, the raw features
+ * [log10 rho, T / 1e4, Tv / 1e4, Y_1 .. Y_11] (X_dev, FP32 [N][14]) and the raw targets
+ * [asinh(omega_s), asinh(d omega_s / d rho_s)] (T_dev, FP32 [N][22]; SI units, the derivative
+ * at fixed other conserved variables as in the operator; zero beyond the model's species) of
+ * the last primitive evaluation (after cs_residual or cs_step).
+ * cs_surrogate_attach makes every later iteration of g take the species Jacobian diagonal of
+ * the split operator from the network instead of the exact chemistry (whose Jacobian is then
+ * not evaluated; the residual keeps the exact source): inputs are standardised as
+ * (raw - mean) / std with norm_host = [mean[14], std[14], target mean[22], target std[22]],
+ * outputs de-standardised and passed through sinh.  The network must hold at least N rows
+ * (max_batch) and must not serve two grids that run at the same time.  cs_surrogate_detach
+ * returns to the exact chemistry.  Errors: CS_ERR_ARG (null, too small a network, a std <= 0),
+ * CS_ERR_OOM. */
+cs_status cs_surrogate_sample(cs_grid g, float *X_dev, float *T_dev);
+cs_status cs_surrogate_attach(cs_grid g, cs_mlp m, const double *norm_host);
+cs_status cs_surrogate_detach(cs_grid g);
+
 /* The batch's own stream (cudaStream_t): every graph launch of cs_batch_step is issued on it,
  * so CUDA events recorded on it before and after a cs_batch_step call bracket the batch's
  * device work.  The stream stays owned by the batch. */

@@ -272,3 +272,16 @@ def batch_cases(n=64, seed=0):
         mech = MECH_AIR5 if rng.random() < 0.5 else MECH_AIR11
         out.append(dict(ni=64 * s, nj=48 * s, mach=mach, cfl=cfl, mech=mech))
     return out
+
+
+def mlp_init(seed=0):
+    """Seeded initial parameters of the 14-128-128-128-22 surrogate network as one float32
+    vector (W1, b1, W2, b2, W3, b3, W4, b4; W row-major [out][in]): weights uniform in
+    +-1/sqrt(fan_in), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for nout, nin in ((128, 14), (128, 128), (128, 128), (22, 128)):
+        a = 1.0 / math.sqrt(nin)
+        parts.append(rng.uniform(-a, a, nout * nin))
+        parts.append(np.zeros(nout))
+    return np.concatenate(parts).astype(np.float32)

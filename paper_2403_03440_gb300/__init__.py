@@ -17,7 +17,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libcs_gb300.so")
 SOURCES = ["launch_air11_2d.cu", "launch_air11_3d.cu", "launch_air5_2d.cu", "launch_air5_3d.cu",
-           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu"]
+           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 
@@ -99,7 +99,10 @@ EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
            "cs_gas_info", "cs_profile", "cs_set_option", "cs_residual_norms_static",
            "cs_last_error", "cs_batch_create", "cs_batch_destroy", "cs_batch_tune",
-           "cs_batch_step", "cs_batch_stream", "cs_batch_last_error"]
+           "cs_batch_step", "cs_batch_stream", "cs_batch_last_error", "cs_mlp_create",
+           "cs_mlp_destroy", "cs_mlp_get_params", "cs_mlp_forward", "cs_mlp_grad",
+           "cs_mlp_train_step", "cs_mlp_last_error", "cs_surrogate_sample",
+           "cs_surrogate_attach", "cs_surrogate_detach"]
 
 _lib = None
 
@@ -136,6 +139,17 @@ def lib():
     L.cs_batch_step.argtypes = [vp, C.POINTER(cs_step_opts), C.c_int, C.c_int, C.POINTER(cs_step_stats)]
     L.cs_batch_stream.argtypes = [vp, C.POINTER(vp)]
     L.cs_batch_last_error.argtypes = [vp]
+    fp = C.POINTER(C.c_float)
+    L.cs_mlp_create.argtypes = [C.c_int, fp, C.POINTER(vp)]
+    L.cs_mlp_destroy.argtypes = [vp]
+    L.cs_mlp_get_params.argtypes = [vp, fp]
+    L.cs_mlp_forward.argtypes = [vp, vp, C.c_int, vp]
+    L.cs_mlp_grad.argtypes = [vp, vp, vp, C.c_int, fp, dp]
+    L.cs_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, dp]
+    L.cs_mlp_last_error.argtypes = [vp]
+    L.cs_surrogate_sample.argtypes = [vp, vp, vp]
+    L.cs_surrogate_attach.argtypes = [vp, vp, dp]
+    L.cs_surrogate_detach.argtypes = [vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_char_p if name.endswith("last_error") else C.c_int
     _lib = L
@@ -277,6 +291,20 @@ class Grid:
         return dict(iters_done=s.iters_done, r_species=s.r_species, r_energy=s.r_energy,
                     q_stag=s.q_stag, nclip=s.nclip)
 
+    def surrogate_sample(self, X, T):
+        """Raw features / targets of every cell into device float32 tensors [N][14], [N][22]."""
+        self._check(lib().cs_surrogate_sample(self._h, X.data_ptr(), T.data_ptr()), "cs_surrogate_sample")
+
+    def attach_surrogate(self, net, norm):
+        nrm = np.ascontiguousarray(norm, dtype=np.float64)
+        assert nrm.size == 72
+        self._check(lib().cs_surrogate_attach(self._h, net._h, _ptr(nrm)), "cs_surrogate_attach")
+        self._surrogate = net      # keep the network alive while attached
+
+    def detach_surrogate(self):
+        self._check(lib().cs_surrogate_detach(self._h), "cs_surrogate_detach")
+        self._surrogate = None
+
     PHASES = ["primitive", "gradient", "flux", "assemble", "spectral", "sweep_fwd",
               "sweep_bwd", "correct"]
 
@@ -352,3 +380,53 @@ class Batch:
                     q_stag=s.q_stag, nclip=s.nclip, status_cell=s.status_cell) for s in stats]
         self._check(st, "cs_batch_step")
         return out
+
+
+MLP_NPARAM = 37782
+
+
+class MLP:
+    """The chemistry surrogate network (cs_mlp_* of the C ABI).  Inputs and targets are device
+    tensors (torch float32, contiguous), passed by address."""
+
+    def __init__(self, params, max_batch):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == MLP_NPARAM
+        h = C.c_void_p()
+        st = lib().cs_mlp_create(int(max_batch), p.ctypes.data_as(C.POINTER(C.c_float)), C.byref(h))
+        if st:
+            raise CSError(st, "cs_mlp_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().cs_mlp_destroy(self._h)
+            self._h = None
+
+    def _check(self, st, what):
+        if st:
+            raise CSError(st, f"{what}: {lib().cs_mlp_last_error(self._h).decode()}")
+
+    def params(self):
+        out = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(lib().cs_mlp_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))),
+                    "cs_mlp_get_params")
+        return out
+
+    def forward(self, X, Y):
+        """X: device float32 [n][14]; Y: device float32 [n][22] (written)."""
+        self._check(lib().cs_mlp_forward(self._h, X.data_ptr(), X.shape[0], Y.data_ptr()), "cs_mlp_forward")
+
+    def grad(self, X, T):
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        loss = C.c_double()
+        self._check(lib().cs_mlp_grad(self._h, X.data_ptr(), T.data_ptr(), X.shape[0],
+                                      g.ctypes.data_as(C.POINTER(C.c_float)), C.byref(loss)), "cs_mlp_grad")
+        return loss.value, g
+
+    def train_step(self, X, T, lr):
+        loss = C.c_double()
+        self._check(lib().cs_mlp_train_step(self._h, X.data_ptr(), T.data_ptr(), X.shape[0],
+                                            float(lr), C.byref(loss)), "cs_mlp_train_step")
+        return loss.value

@@ -11,6 +11,10 @@
 
 using namespace cs;
 
+// the chemistry surrogate network (mlp.cu)
+int mlp_max_batch(cs_mlp m);
+void mlp_forward_on(cs_mlp m, const float* X, int n, float* Y, cudaStream_t st);
+
 // phases timed by cs_profile: primitive, gradient, flux, assemble, spectral (+CI blocks),
 // forward sweep, backward sweep, correction
 #define CS_NPHASE 8
@@ -158,6 +162,9 @@ struct cs_grid_s {
   int* stag_dev = nullptr;
   double* params = nullptr;   // device [4]
   int* iter_dev = nullptr;    // device iteration counter of the CFL ramp in captured iterations
+  cs_mlp surr = nullptr;      // attached surrogate network (species Jacobian diagonal)
+  float *sx = nullptr, *sy = nullptr;   // its inputs [N][14] and outputs [N][22]
+  double* snorm = nullptr;    // standardisation [14 + 14 + 22 + 22]
   double* h_pin = nullptr;    // pinned host scratch [64]
   int* h_status = nullptr;    // pinned [4]
   int stag = -1;
@@ -313,6 +320,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   d.efix = desc->entropy_fix;
   d.hcorr = 1;
   d.ulim = 0.0;
+  d.nojac = 0;
   d.Tw = 300.0;
   for (int k = 0; k < 3; ++k) d.nf[k] = 0;
   for (int k = 0; k < nd; ++k)
@@ -515,7 +523,18 @@ extern "C" cs_status cs_get_state(cs_grid g, double* Q_out) {
 }
 
 // enqueue the residual (no synchronisation)
-static void enqueue_residual(cs_grid g) { g->L->residual(g->g, g->stream, g->stag, g->norms); }
+// the species Jacobian diagonal of the operator from the attached network (after primitives)
+static void enqueue_surrogate(cs_grid g) {
+  if (!g->surr) return;
+  g->L->surr_features(g->g, g->stream, g->sx, g->snorm);
+  mlp_forward_on(g->surr, g->sx, g->g.N, g->sy, g->stream);
+  g->L->surr_decode(g->g, g->stream, g->sy, g->snorm);
+}
+
+static void enqueue_residual(cs_grid g) {
+  g->L->residual(g->g, g->stream, g->stag, g->norms);
+  enqueue_surrogate(g);
+}
 
 extern "C" cs_status cs_residual(cs_grid g, double* R_out, double norms_host[3]) {
   if (!g) return CS_ERR_ARG;
@@ -658,6 +677,9 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
   const DevGrid& d = g->g;
   if (rec) prof_record(g, slot, 0);
   g->L->primitive(d, g->stream);
+  // the species Jacobian diagonal of the operator from the network, when one is attached (the
+  // exact source stays in the residual)
+  enqueue_surrogate(g);
   if (rec) prof_record(g, slot, 1);
   g->L->gradient(d, g->stream);
   if (rec) prof_record(g, slot, 2);
@@ -815,6 +837,7 @@ struct cs_batch_s {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<cs_step_opts> key;       // options the graph was captured with
+  std::vector<cs_mlp> key_surr;        // and the networks attached then
   int key_k = 0;
   char err[512] = {0};
 };
@@ -981,7 +1004,8 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
       g->L->prepare(g->g, opts[c].precision == CS_MIXED);
     }
     bool recapture = !b->exec || b->key_k != iters_per_graph || (int)b->key.size() != n;
-    for (int c = 0; c < n && !recapture; ++c) recapture = !same_opts(b->key[c], opts[c]);
+    for (int c = 0; c < n && !recapture; ++c)
+      recapture = !same_opts(b->key[c], opts[c]) || b->key_surr[c] != b->grids[c]->surr;
     if (recapture) {
       if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
       BCUDA_TRY(b, cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
@@ -1010,6 +1034,8 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
       cudaGraphDestroy(graph);
       if (ei != cudaSuccess) { b->exec = nullptr; return bfail(b, CS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ei)); }
       b->key.assign(opts, opts + n);
+      b->key_surr.clear();
+      for (int c = 0; c < n; ++c) b->key_surr.push_back(b->grids[c]->surr);
       b->key_k = iters_per_graph;
     }
     // per-case setup on the case streams: status cleared, ramp counter = iterations done
@@ -1053,3 +1079,40 @@ extern "C" cs_status cs_batch_stream(cs_batch b, void** stream_out) {
 }
 
 extern "C" const char* cs_batch_last_error(cs_batch b) { return b ? b->err : "null batch"; }
+
+// ---------------------------------------------------------------------------------------
+// Chemistry surrogate coupling
+// ---------------------------------------------------------------------------------------
+extern "C" cs_status cs_surrogate_sample(cs_grid g, float* X_dev, float* T_dev) {
+  if (!g || !X_dev || !T_dev) return CS_ERR_ARG;
+  cs_status st = begin(g);
+  if (st) return st;
+  g->L->surr_sample(g->g, g->stream, X_dev, T_dev);
+  return finish(g, "cs_surrogate_sample");
+}
+
+extern "C" cs_status cs_surrogate_attach(cs_grid g, cs_mlp m, const double* norm_host) {
+  if (!g || !m || !norm_host) return CS_ERR_ARG;
+  if (mlp_max_batch(m) < g->g.N) return fail(g, CS_ERR_ARG, "network batch %d < %d cells", mlp_max_batch(m), g->g.N);
+  for (int k = 0; k < 14; ++k)
+    if (!(norm_host[14 + k] > 0.0)) return fail(g, CS_ERR_ARG, "input std %d must be > 0", k);
+  for (int k = 0; k < 22; ++k)
+    if (!(norm_host[2 * 14 + 22 + k] > 0.0)) return fail(g, CS_ERR_ARG, "target std %d must be > 0", k);
+  cudaError_t e = cudaSuccess;
+  if (!g->sx) e = dalloc(g, &g->sx, (size_t)14 * g->g.N);
+  if (e == cudaSuccess && !g->sy) e = dalloc(g, &g->sy, (size_t)22 * g->g.N);
+  if (e == cudaSuccess && !g->snorm) e = dalloc(g, &g->snorm, 2 * (14 + 22));
+  if (e != cudaSuccess) return fail(g, CS_ERR_OOM, "surrogate buffers");
+  CUDA_TRY(g, cudaMemcpyAsync(g->snorm, norm_host, sizeof(double) * 2 * (14 + 22), cudaMemcpyHostToDevice, g->stream));
+  CUDA_TRY(g, cudaStreamSynchronize(g->stream));
+  g->surr = m;
+  g->g.nojac = 1;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_surrogate_detach(cs_grid g) {
+  if (!g) return CS_ERR_ARG;
+  g->surr = nullptr;
+  g->g.nojac = 0;
+  return CS_OK;
+}

@@ -37,7 +37,7 @@ struct Aux {
 struct DevGrid {
   int nd, ni, nj, nk, N;
   int bc[6];
-  int limiter, react, hcorr;
+  int limiter, react, hcorr, nojac;
   double efix, Tw, ulim;
   int nf[3];
   const double* S[3];
@@ -440,8 +440,9 @@ __device__ __forceinline__ double dprod_b(const double* X, int q) {
   return v;
 }
 
-// contribution of reaction RI to species S (nothing when S does not change in RI)
-template <class G, bool FULL, int RI, int S>
+// contribution of reaction RI to species S (nothing when S does not change in RI); JAC =
+// false: the source only, no derivatives
+template <class G, bool FULL, bool JAC, int RI, int S>
 __device__ __forceinline__ void species_term(ChemCtx<G, FULL>& c, const RxTerms& t) {
   constexpr int nu = rx_nu(RI, S);
   if constexpr (nu != 0) {
@@ -450,6 +451,7 @@ __device__ __forceinline__ void species_term(ChemCtx<G, FULL>& c, const RxTerms&
     const ReactionData& d = c_reactions[RI];
     const double Ms = G::sp(S).M;
     c.omega[S] += Ms * nu * t.net;
+    if constexpr (!JAC) return;
     c.wT[S] += Ms * nu * t.dRT;
     c.wTv[S] += Ms * nu * t.dRV;
     if (FULL) {
@@ -467,14 +469,14 @@ __device__ __forceinline__ void species_term(ChemCtx<G, FULL>& c, const RxTerms&
     }
   }
 }
-template <class G, bool FULL, int RI, int... S>
+template <class G, bool FULL, bool JAC, int RI, int... S>
 __device__ __forceinline__ void species_terms(ChemCtx<G, FULL>& c, const RxTerms& t,
                                               std::integer_sequence<int, S...>) {
-  (species_term<G, FULL, RI, S>(c, t), ...);
+  (species_term<G, FULL, JAC, RI, S>(c, t), ...);
 }
 
 // One reaction, unrolled at compile time (species indices are constants).
-template <class G, bool FULL, int RI>
+template <class G, bool FULL, bool JAC, int RI>
 __device__ __forceinline__ void reaction(ChemCtx<G, FULL>& c) {
   constexpr RxShape x = rx_shape(RI);
   constexpr int NS = G::NS;
@@ -508,6 +510,11 @@ __device__ __forceinline__ void reaction(ChemCtx<G, FULL>& c) {
   if (x.np > 1) Pb *= c.X[x.p1];
   if (x.np > 2) Pb *= c.X[x.p2];
   const double Rf = kf * Pf * M, Rb = kb * Pb * M;
+  if constexpr (!JAC) {
+    species_terms<G, FULL, JAC, RI>(c, RxTerms{kf, kb, M, Pf, Pb, Rf - Rb, 0.0, 0.0},
+                                    std::make_integer_sequence<int, NS>{});
+    return;
+  }
   const double dlf = (d.n + d.theta * iTf) * iTf;
   const double dlb = (d.n + d.theta * iTb - (sh - dn)) * iTb;
   constexpr bool fA = x.tf == TK_A, bA = x.tb == TK_A;
@@ -518,19 +525,20 @@ __device__ __forceinline__ void reaction(ChemCtx<G, FULL>& c) {
   const double dRT = Rf * dlf * fT - Rb * dlb * bT;
   const double dRV = Rf * dlf * fV - Rb * dlb * bVv;
   const double net = Rf - Rb;
-  species_terms<G, FULL, RI>(c, RxTerms{kf, kb, M, Pf, Pb, net, dRT, dRV},
-                             std::make_integer_sequence<int, NS>{});
+  species_terms<G, FULL, JAC, RI>(c, RxTerms{kf, kb, M, Pf, Pb, net, dRT, dRV},
+                                  std::make_integer_sequence<int, NS>{});
 }
 
-template <class G, bool FULL, int... RI>
+template <class G, bool FULL, bool JAC, int... RI>
 __device__ __forceinline__ void all_reactions(ChemCtx<G, FULL>& c, std::integer_sequence<int, RI...>) {
-  (reaction<G, FULL, RI>(c), ...);
+  (reaction<G, FULL, JAC, RI>(c), ...);
 }
 
 // omega[s]; the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s (or the full fixed-T
-// Jacobian J[s*NS+r] when FULL) and the temperature derivatives wT[s], wTv[s].
+// Jacobian J[s*NS+r] when FULL) and the temperature derivatives wT[s], wTv[s] (all zero when
+// JAC is false: the source alone).
 // emT/emTv: exp(-theta_v/T) and exp(-theta_v/Tv) of every species (vib_exp).
-template <class G, bool FULL>
+template <class G, bool FULL, bool JAC = true>
 __device__ __forceinline__ void chemistry(const double* rhos, double T, double Tv, const double* emT,
                                           const double* emTv, double* omega, double* jd,
                                           double* J, double* wT, double* wTv) {
@@ -563,7 +571,7 @@ __device__ __forceinline__ void chemistry(const double* rhos, double T, double T
     if (G::NTEMP == 2) gibbs<G>(s, c.iTv, c.lnTv, emTv[s], c.gV[s], c.hV[s]);
     else { c.gV[s] = c.gT[s]; c.hV[s] = c.hT[s]; }
   }
-  all_reactions<G, FULL>(c, std::make_integer_sequence<int, G::NR>{});
+  all_reactions<G, FULL, JAC>(c, std::make_integer_sequence<int, G::NR>{});
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     omega[s] = c.omega[s];
@@ -671,15 +679,22 @@ __global__ void __launch_bounds__(128) k_primitive(DevGrid g) {
     vib_exp<G>(iT, emT);
     if (G::NTEMP == 2) vib_exp<G>(1.0 / w.Tv, emTv);
     else for (int s = 0; s < G::NS; ++s) emTv[s] = emT[s];
-    chemistry<G, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
+    if (g.nojac) {
+      // the species Jacobian diagonal comes from the surrogate network: source only
+      chemistry<G, false, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
+    } else {
+      chemistry<G, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
+    }
+    if (!g.nojac) {
 #pragma unroll
-    for (int s = 0; s < G::NS; ++s) {
-      double ev = 0.0, cvv;
-      if (G::NTEMP == 1) vib_em<G>(s, iT, emT[s], ev, cvv);
-      else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
-      double dT, dTv;
-      dT_drho<G, ND>(w, s, ev, dT, dTv);
-      jd[s] += wT[s] * dT + wTv[s] * dTv;
+      for (int s = 0; s < G::NS; ++s) {
+        double ev = 0.0, cvv;
+        if (G::NTEMP == 1) vib_em<G>(s, iT, emT[s], ev, cvv);
+        else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+        double dT, dTv;
+        dT_drho<G, ND>(w, s, ev, dT, dTv);
+        jd[s] += wT[s] * dT + wTv[s] * dTv;
+      }
     }
     if (G::NTEMP == 2) vib_source<G, ND>(w, om, emT, emTv, omv, relax);
   } else {
@@ -2618,6 +2633,75 @@ __global__ void __launch_bounds__(256) k_fill(DevGrid g, const double* fsQ) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.N) return;
   for (int v = 0; v < Aux<G, ND>::NQ; ++v) g.Q[(size_t)v * g.N + c] = fsQ[v];
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Chemistry surrogate coupling.  Raw features of a cell: log10 rho, T / 1e4, Tv / 1e4 and the
+// mass fractions Y_1..Y_11 (zero beyond the model's species); raw targets: asinh(omega_s) and
+// asinh(d omega_s / d rho_s) (SI units; zero beyond the model's species).  The network works
+// on standardised values, x = (f - mean) / std; norm = [mean_f[14], std_f[14], mean_t[22],
+// std_t[22]].
+// ---------------------------------------------------------------------------------------
+constexpr int kSurrIn = 14, kSurrOut = 22, kSurrNS = 11;
+
+template <class G, int ND>
+__device__ __forceinline__ void surr_raw_features(const DevGrid& g, int c, float* f) {
+  using A = Aux<G, ND>;
+  const size_t N = g.N;
+  f[0] = (float)log10(g.W[A::RHO * N + c]);
+  f[1] = (float)(g.W[A::T * N + c] * 1e-4);
+  f[2] = (float)(g.W[A::TV * N + c] * 1e-4);
+#pragma unroll
+  for (int s = 0; s < kSurrNS; ++s) f[3 + s] = s < G::NS ? (float)g.W[(A::Y + s) * N + c] : 0.f;
+}
+
+// raw features [N][14] and raw targets [N][22] of every cell (from the auxiliary fields of the
+// last primitive evaluation, exact chemistry)
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_surr_sample(DevGrid g, float* X, float* T) {
+  using A = Aux<G, ND>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  float f[kSurrIn];
+  surr_raw_features<G, ND>(g, c, f);
+#pragma unroll
+  for (int k = 0; k < kSurrIn; ++k) X[(size_t)c * kSurrIn + k] = f[k];
+#pragma unroll
+  for (int s = 0; s < kSurrNS; ++s) {
+    T[(size_t)c * kSurrOut + s] = s < G::NS ? (float)asinh(g.W[(A::OM + s) * N + c]) : 0.f;
+    T[(size_t)c * kSurrOut + kSurrNS + s] = s < G::NS ? (float)asinh(g.W[(A::DOM + s) * N + c]) : 0.f;
+  }
+}
+
+// standardised network inputs [N][14]
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_surr_features(DevGrid g, float* X, const double* norm) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  float f[kSurrIn];
+  surr_raw_features<G, ND>(g, c, f);
+#pragma unroll
+  for (int k = 0; k < kSurrIn; ++k)
+    X[(size_t)c * kSurrIn + k] = (float)((f[k] - norm[k]) / norm[kSurrIn + k]);
+}
+
+// network outputs [N][22] -> the species Jacobian diagonal d omega_s / d rho_s of the operator
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_surr_decode(DevGrid g, const float* Y, const double* norm) {
+  using A = Aux<G, ND>;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  const double* mt = norm + 2 * kSurrIn;
+  const double* st = mt + kSurrOut;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    const int o = kSurrNS + s;
+    const double t = (double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o];
+    g.W[(A::DOM + s) * N + c] = sinh(t);
+  }
 }
 
 }  // namespace cs

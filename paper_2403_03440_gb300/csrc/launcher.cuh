@@ -48,6 +48,10 @@ struct Launcher {
   void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
   virtual int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;
   virtual void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) = 0;
+  // chemistry surrogate coupling (raw samples; standardised inputs; decoded diagonal)
+  virtual void surr_sample(const DevGrid& g, cudaStream_t st, float* X, float* T) = 0;
+  virtual void surr_features(const DevGrid& g, cudaStream_t st, float* X, const double* norm) = 0;
+  virtual void surr_decode(const DevGrid& g, cudaStream_t st, const float* Y, const double* norm) = 0;
   // offset (in units of N) and count of a named auxiliary field, or -1
   virtual int aux_field(const char* name, int* count) const = 0;
   static int blocks(long n, int t) { return (int)((n + t - 1) / t); }
@@ -348,6 +352,16 @@ struct LauncherT : Launcher {
       ++launches;
     }
     return launches;
+  }
+
+  void surr_sample(const DevGrid& g, cudaStream_t st, float* X, float* T) override {
+    k_surr_sample<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g, X, T);
+  }
+  void surr_features(const DevGrid& g, cudaStream_t st, float* X, const double* norm) override {
+    k_surr_features<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g, X, norm);
+  }
+  void surr_decode(const DevGrid& g, cudaStream_t st, const float* Y, const double* norm) override {
+    k_surr_decode<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g, Y, norm);
   }
 
   void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) override {

@@ -1,0 +1,157 @@
+"""Training and use of the chemistry surrogate network (the species Jacobian diagonal of the
+implicit operator, learned from states the solver generates; the residual keeps the exact
+chemistry).
+
+    python -m paper_2403_03440_gb300.surrogate demo --case c1m
+prints one JSON line: the same case run to the same residual drop with the exact diagonal
+and with the network's, iterations, device time, stagnation heat flux, the primitive-phase
+time per iteration of both and the training record.
+
+All arithmetic runs in the library's kernels (cs_surrogate_sample, cs_mlp_train_step, ...);
+the host only draws the sample permutation and computes the standardisation constants.
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+import paper_2403_03440_gb300 as P  # noqa: E402
+
+CASES = {
+    # 11-species 2T air, Mach 15, over the windward half of the cylinder
+    "c1m": dict(ni=48, nj=32, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5, limiter=2,
+                cfl=2.0, cfl_start=0.5, ramp=100),
+    "c2": dict(ni=384, nj=256, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5 / 8, limiter=2,
+               cfl=2.0, cfl_start=0.5, ramp=100),
+}
+
+
+def make_grid(c):
+    nodes = inputs.cylinder_half(c["ni"], c["nj"], dr1=c["dr1"])
+    fs = inputs.freestream(c["mech"], T=300.0, p=500.0, mach=c["mach"])
+    g = P.Grid(nodes, inputs.cylinder_half_bc(), c["mech"], limiter=c["limiter"])
+    g.set_boundary(fs, Tw=500.0)
+    g.init_freestream()
+    return g
+
+
+def step_opts(c, precision=0):
+    return dict(scheme=0, correction=1, clip=1, cfl=c["cfl"], cfl_start=c["cfl_start"],
+                ramp_iters=c["ramp"], precision=precision)
+
+
+def collect(c, iters, every, precision=0):
+    """Run the case from the freestream and sample every cell every `every` iterations."""
+    import torch
+    g = make_grid(c)
+    N = g.ncell
+    Xd = torch.empty((N, 14), dtype=torch.float32, device="cuda")
+    Td = torch.empty((N, 22), dtype=torch.float32, device="cuda")
+    Xs, Ts = [], []
+    done = 0
+    while done < iters:
+        g.step(iters=every, **step_opts(c, precision))
+        done += every
+        g.surrogate_sample(Xd, Td)
+        Xs.append(Xd.cpu().numpy().copy())
+        Ts.append(Td.cpu().numpy().copy())
+    return np.concatenate(Xs), np.concatenate(Ts)
+
+
+def standardisation(X, T):
+    """[mean_x, std_x, mean_t, std_t] (std 1 where a column is constant)."""
+    mx, sx = X.mean(0, dtype=np.float64), X.std(0, dtype=np.float64)
+    mt, st = T.mean(0, dtype=np.float64), T.std(0, dtype=np.float64)
+    sx[sx < 1e-12] = 1.0
+    st[st < 1e-12] = 1.0
+    return np.concatenate([mx, sx, mt, st])
+
+
+def train(X, T, norm, epochs=4, batch=4096, lr=2e-3, seed=0, max_batch=None):
+    import torch
+    n = X.shape[0]
+    Xn = ((X - norm[:14]) / norm[14:28]).astype(np.float32)
+    Tn = ((T - norm[28:50]) / norm[50:72]).astype(np.float32)
+    net = P.MLP(inputs.mlp_init(seed), max_batch=max(batch, max_batch or 0))
+    rng = np.random.default_rng(seed)
+    record = []
+    for ep in range(epochs):
+        perm = rng.permutation(n)
+        Xe = torch.from_numpy(Xn[perm]).cuda()
+        Te = torch.from_numpy(Tn[perm]).cuda()
+        losses = []
+        for k in range(0, n - batch + 1, batch):
+            losses.append(net.train_step(Xe[k:k + batch], Te[k:k + batch], lr * (0.5 ** ep)))
+        record.append(float(np.mean(losses)))
+    return net, record
+
+
+def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0):
+    import torch
+    g = make_grid(c)
+    if net is not None:
+        g.attach_surrogate(net, norm)
+    kw = step_opts(c, precision)
+    first = g.step(iters=1, **kw)
+    r0 = (first["r_species"], first["r_energy"])
+    g.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    done, status, st = 1, "max_iters", first
+    while done < max_iters:
+        st = g.step(iters=chunk, **kw)
+        done += st["iters_done"]
+        if st["r_species"] / r0[0] <= tol and st["r_energy"] / r0[1] <= tol:
+            status = "converged"
+            break
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    prof = g.profile(False)
+    return dict(status=status, iterations=done, seconds=dt, q_stag=st["q_stag"],
+                drop=max(st["r_species"] / r0[0], st["r_energy"] / r0[1]),
+                primitive_ms_per_iter=prof["primitive"][0] / max(done - 1, 1),
+                ms_per_iter=1e3 * dt / max(done - 1, 1))
+
+
+def demo(case, tol, max_iters, samples_iters, every, epochs, precision):
+    c = CASES[case]
+    t0 = time.perf_counter()
+    X, T = collect(c, samples_iters, every, precision)
+    norm = standardisation(X, T)
+    net, record = train(X, T, norm, epochs=epochs, max_batch=c["ni"] * c["nj"])
+    t_train = time.perf_counter() - t0
+    exact = run_to(c, tol, max_iters, 500, precision=precision)
+    surr = run_to(c, tol, max_iters, 500, net=net, norm=norm, precision=precision)
+    return dict(case=case, tol=tol, samples=int(X.shape[0]), epochs=epochs, train_loss=record,
+                collect_and_train_seconds=t_train, exact=exact, surrogate=surr,
+                q_rel_diff=abs(surr["q_stag"] - exact["q_stag"]) / abs(exact["q_stag"]),
+                time_ratio=surr["seconds"] / exact["seconds"])
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("cmd", choices=["demo"])
+    ap.add_argument("--case", default="c1m", choices=list(CASES))
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--max-iters", type=int, default=100000)
+    ap.add_argument("--samples-iters", type=int, default=4000)
+    ap.add_argument("--every", type=int, default=20)
+    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    a = ap.parse_args()
+    P.build()
+    out = demo(a.case, a.tol, a.max_iters, a.samples_iters, a.every, a.epochs,
+               1 if a.precision == "mixed" else 0)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

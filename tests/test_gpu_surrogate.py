@@ -1,0 +1,88 @@
+"""Coupling of the chemistry surrogate network to the solver: the raw samples it learns from
+against the oracle's fields, the residual untouched by it (exact chemistry), and the operator
+diagonal equal to the decoded network output (checked with the network's oracle)."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+import paper_2403_03440_gb300 as P
+from oracle import mlp
+from _helpers import rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    P.build()
+    P.lib()
+    yield
+
+
+def pair(seed=1):
+    mech = inputs.MECH_AIR11
+    nodes = inputs.cylinder_half(25, 16)
+    fs = inputs.freestream(mech, T=300.0, p=500.0, mach=15.0)
+    ref = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), mech)
+    ref.set_boundary(fs, Tw=500.0)
+    g = P.Grid(nodes, inputs.cylinder_half_bc(), mech)
+    g.set_boundary(fs, Tw=500.0)
+    pr = inputs.perturbed_primitive(mech, (16, 25), seed=seed, ndim=2, T=6000.0, Tv=4500.0, p=8000.0)
+    Q = oracle.prim_to_cons_field(mech, 2, pr)
+    ref.set_state(Q)
+    g.set_state(Q)
+    return ref, g
+
+
+def test_samples_match_oracle_fields():
+    import torch
+    ref, g = pair()
+    ref.residual()
+    g.residual(want_R=False)
+    N = g.ncell
+    X = torch.empty((N, 14), dtype=torch.float32, device="cuda")
+    T = torch.empty((N, 22), dtype=torch.float32, device="cuda")
+    g.surrogate_sample(X, T)
+    X, T = X.cpu().numpy(), T.cpu().numpy()
+    rho = ref.field("rho")[:N]
+    Y = ref.get_state()[:11] / rho
+    want_x = np.concatenate([np.log10(rho)[:, None], ref.field("T")[:N, None] * 1e-4,
+                             ref.field("Tv")[:N, None] * 1e-4, Y.T], axis=1)
+    assert np.max(np.abs(X - want_x) / np.maximum(np.abs(want_x), 1e-3)) < 1e-5
+    om = ref.field("omega").reshape(11, -1)[:, :N].T
+    dom = ref.field("dom").reshape(11, -1)[:, :N].T
+    want_t = np.concatenate([np.arcsinh(om), np.arcsinh(dom)], axis=1)
+    assert np.max(np.abs(T - want_t)) < 1e-4 * np.max(np.abs(want_t))
+
+
+def test_attached_network_sets_diagonal_not_residual():
+    import torch
+    ref, g = pair(2)
+    R0, n0 = g.residual()
+    p = inputs.mlp_init(7)
+    net = P.MLP(p, max_batch=g.ncell)
+    rng = np.random.default_rng(0)
+    norm = np.concatenate([rng.normal(size=14), rng.uniform(0.5, 2, 14),
+                           rng.normal(size=22), rng.uniform(0.5, 2, 22)])
+    g.attach_surrogate(net, norm)
+    R1, n1 = g.residual()
+    # the residual keeps the exact chemistry
+    assert rel(R1, R0, ns=g.ns) < 1e-13
+    N = g.ncell
+    X = torch.empty((N, 14), dtype=torch.float32, device="cuda")
+    T = torch.empty((N, 22), dtype=torch.float32, device="cuda")
+    g.surrogate_sample(X, T)          # raw features (targets now hold the decoded diagonal)
+    raw = X.cpu().numpy()
+    xn = ((raw - norm[:14]) / norm[14:28]).astype(np.float32)
+    y = mlp.forward(p, xn)[0].astype(np.float64)
+    d_want = np.sinh(y[:, 11:] * norm[50 + 11:72] + norm[28 + 11:50])
+    d_got = g.field("dom").reshape(11, -1)[:, :N].T
+    err = np.abs(d_got - d_want) / (np.abs(d_want) + 1e-3 * np.max(np.abs(d_want)))
+    assert np.median(err) < 2e-2 and np.max(err) < 0.3
+    g.detach_surrogate()
+    g.residual(want_R=False)
+    ref.residual()
+    assert rel(g.field("dom").reshape(11, -1), ref.field("dom").reshape(11, -1)) < 1e-10
