@@ -124,10 +124,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+C3 = False      # --workload c3: the 3D sphere-cone instead of the half cylinder
+C3_DIMS = (192, 128, 96)
+C3_MACH = 20.0
+
+
 def make_case(P):
+    if C3:
+        nodes = inputs.sphere_cone(*C3_DIMS)
+        fs = inputs.freestream(MECH, T=T_INF, p=P_INF, mach=C3_MACH)
+        return nodes, fs
     nodes = inputs.cylinder_half(NI, NJ, dr1=5e-5 / 8)
     fs = inputs.freestream(MECH, T=T_INF, p=P_INF, mach=MACH)
     return nodes, fs
+
+
+def case_bc():
+    return inputs.sphere_cone_bc() if C3 else inputs.cylinder_half_bc()
+
+
+def case_cells():
+    return C3_DIMS[0] * C3_DIMS[1] * C3_DIMS[2] if C3 else NI * NJ
 
 
 PRECISION = 0   # 0: FP64 operator, 1: FP32 operator (mixed); set by --precision
@@ -144,7 +161,7 @@ def oracle_rate(iters, seconds_cap=30.0):
     import oracle
     oracle.build()
     nodes, fs = make_case(None)
-    g = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), MECH)
+    g = oracle.OracleGrid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
     done, t0 = 0, time.perf_counter()
@@ -156,7 +173,7 @@ def oracle_rate(iters, seconds_cap=30.0):
         if time.perf_counter() - t0 > seconds_cap:
             break
     dt = time.perf_counter() - t0
-    return NI * NJ * done / dt / 1e6, done, dt
+    return case_cells() * done / dt / 1e6, done, dt
 
 
 def run_reference(args, rank):
@@ -167,7 +184,7 @@ def run_reference(args, rank):
     import oracle
     oracle.build()
     nodes, fs = make_case(None)
-    g = oracle.OracleGrid(nodes, inputs.cylinder_half_bc(), MECH)
+    g = oracle.OracleGrid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.set_state(g.freestream_state())
     kw = step_kwargs(1)
@@ -178,13 +195,13 @@ def run_reference(args, rank):
     for _ in range(args.steps):
         g.step(**kw)
     dt = time.perf_counter() - t0
-    v = NI * NJ * args.steps / dt / 1e6
+    v = case_cells() * args.steps / dt / 1e6
     line = {
         "impl": "reference", "metric": "Mcell-iter/s", "value": v, "unit": "Mcell-iter/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": NI * NJ, "cfl": CFL},
+        "config": {"workload": WORKLOAD, "cells": case_cells(), "cfl": CFL},
         "cpu_baseline": {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} iterations of the full grid from the freestream"},
         "e2e": {"value": v, "unit": "Mcell-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -284,11 +301,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "batch"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
     args = ap.parse_args()
-    global PRECISION, WORKLOAD
+    global PRECISION, WORKLOAD, C3
+    if args.workload == "c3":
+        C3 = True
+        WORKLOAD = "sphere-cone-192x128x96-air11-2T-mach20-CS1-fp64"
+        args.no_cpu_baseline = True      # one oracle iteration of 2.4 M cells takes minutes
     if args.precision == "mixed":
         PRECISION = 1
         WORKLOAD = WORKLOAD.replace("fp64", "mixed-fp32-operator")
@@ -314,7 +335,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     nodes, fs = make_case(P)
-    g = P.Grid(nodes, inputs.cylinder_half_bc(), MECH)
+    g = P.Grid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
     g.init_freestream()
     N = g.ncell

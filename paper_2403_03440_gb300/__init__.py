@@ -148,7 +148,7 @@ def lib():
     L.cs_mlp_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_float, dp]
     L.cs_mlp_last_error.argtypes = [vp]
     L.cs_surrogate_sample.argtypes = [vp, vp, vp]
-    L.cs_surrogate_attach.argtypes = [vp, vp, dp]
+    L.cs_surrogate_attach.argtypes = [vp, vp, vp]
     L.cs_surrogate_detach.argtypes = [vp]
     for name in EXPORTS:
         getattr(L, name).restype = C.c_char_p if name.endswith("last_error") else C.c_int

@@ -794,8 +794,10 @@ extern "C" cs_status cs_get_field(cs_grid g, const char* name, double* out, int*
 extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!g || !name) return CS_ERR_ARG;
   if (!strcmp(name, "cluster_sweep")) {
+    // 0 per hyperplane, 1 direct-load cluster kernel, 2 record cluster kernel, 3 default (by
+    // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2)
     g->L->use_cluster = value != 0.0;
-    g->L->cluster_kind = value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1);
+    g->L->cluster_kind = value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;
   }
   if (!strcmp(name, "cluster_size")) {

@@ -1632,9 +1632,10 @@ __device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::N
     for (int q = 0; q <= H; ++q) {
       const int i = (fwd ? q : H - q) - j;
       flow_step_load<G, T>(g, q + 1, j, row, fwd, nxt);     // prefetch the next step
-      if (q > 0) cluster_wait();
+      // contributions of this row's own earlier results (the i-neighbour, the periodic
+      // neighbour) need no other CTA: computed while the cluster barrier is pending
+      T acc[NF];
       if (cur.act) {
-        T acc[NF];
 #pragma unroll
         for (int v = 0; v < NF; ++v) acc[v] = fwd ? cur.base[v] : T(0);
         if (fwd) {
@@ -1644,6 +1645,9 @@ __device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::N
           if (per && i == 0) flow_contrib<G, T>(firstS, firstL, cur.Sw, firstx, -1, acc);
           if (i < ni - 1) flow_contrib<G, T>(prevS, prevL, cur.Si, prevx, +1, acc);
         }
+      }
+      if (q > 0) cluster_wait();
+      if (cur.act) {
         if (cur.hasj) {
           const T* src;
           const int par = (q - 1) & 1;
@@ -1885,7 +1889,7 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Copy the records of rows [j0-1, j0+R] of hyperplane h (those that exist) into a ring slot of
-// (R+2) records; slot row index = j - (j0 - 1).  Whole warp; the caller commits the group.
+// (R+2) records; slot row index = j - (j0 - 1).  Whole CTA; the caller commits the group.
 template <class T>
 __device__ __forceinline__ void wave_fetch(const T* src, int rec, const int* woff, int h, int H,
                                            int ni, int nj, int j0, int R, T* slot) {
@@ -1896,7 +1900,7 @@ __device__ __forceinline__ void wave_fetch(const T* src, int rec, const int* wof
       const T* from = src + ((size_t)woff[h] + (lo - jlo)) * rec;
       T* to = slot + (size_t)(lo - (j0 - 1)) * rec;
       const int pieces = (hi - lo + 1) * rec * (int)sizeof(T) / 16;
-      for (int k = threadIdx.x; k < pieces; k += 32)
+      for (int k = threadIdx.x; k < pieces; k += blockDim.x)
         cp_async16(reinterpret_cast<char*>(to) + 16 * k, reinterpret_cast<const char*>(from) + 16 * k);
     }
   }
@@ -1971,20 +1975,21 @@ __device__ __forceinline__ void wave_contrib(const CellState<G, 2, T>& w, T lam,
     out[v] = side < 0 ? T(0.5) * (ax[v] + lam * x[v]) : T(-0.5) * (ax[v] - lam * x[v]);
 }
 
-template <class G, class T>
+template <class G, class T, int ROWS = kWaveRows>
 struct WaveSmemF {
-  T ring[kWaveSlots][kWaveRows + 2][kRecF];
-  T base[kWaveSlots][kWaveRows + 2][8];
-  T x[2][kWaveRows][Aux<G, 2>::NF];
+  T ring[kWaveSlots][ROWS + 2][kRecF];
+  T base[kWaveSlots][ROWS + 2][8];
+  T x[2][ROWS][Aux<G, 2>::NF];
   T mbox[2][Aux<G, 2>::NF];
 };
 
-template <class G, class T>
-__device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
+// BLK: one CTA holds every row (R = nj threads) and __syncthreads replaces the cluster barrier
+template <class G, class T, int ROWS = kWaveRows, bool BLK = false>
+__device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF;
   const size_t N = g.N;
-  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
+  const unsigned rank = BLK ? 0u : cluster_ctarank(), C = BLK ? 1u : cluster_nctarank();
   const int t = threadIdx.x;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
   const int j0 = rank * R, j = j0 + t;
@@ -2002,9 +2007,15 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
       if (!fwd) wave_fetch<T>(base, 8, g.woff, hof(q), H, ni, nj, j0, R, &sm.base[q % kWaveSlots][0][0]);
       cp_async_commit();
     }
-    T acc[NF], Mj[NF][NF], carry[NF], wrapc[NF], x[NF];
+    // FP32: the j-neighbour's coupling is built as a matrix before the barrier (cheap in
+    // FP32, shortens the dependent chain after it); FP64: the neighbour's state is kept and its
+    // Jacobian-vector product applied after the barrier (fewer FP64 operations per step, the
+    // FP64 pipe being the narrow resource)
+    constexpr bool kJvpJ = sizeof(T) == 8;
+    T acc[NF], Mj[kJvpJ ? 1 : NF][NF], carry[NF], wrapc[NF], x[NF];
     T iD = 0, iDev = 0, lam0 = 0, Sn[2] = {0, 0}, Sw[2] = {0, 0};
-    CellState<G, 2, T> ws;
+    T jlam = 0, Sjv[2] = {0, 0};
+    CellState<G, 2, T> ws, wjn;
     bool act = false, hasj = false;
     int cidx = 0, wcur = 0;
 #pragma unroll
@@ -2012,7 +2023,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
     // per-step set-up from the records (step q); also used for the first step
     auto setup = [&](int q) {
       cp_async_wait<kWaveD - 1>();
-      __syncwarp();
+      if (BLK) __syncthreads(); else __syncwarp();
       const int h = hof(q), i = h - j;
       act = row && q <= H && i >= 0 && i < ni;
       const int jj = j - hs;
@@ -2039,15 +2050,22 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
       }
       if (hasj) {
         const T* nb = sm.ring[(q + kWaveSlots - 1) % kWaveSlots][fwd ? t : t + 2];
-        CellState<G, 2, T> wn;
-        rec_state<G, T>(nb, wn);
-        wave_matrix<G, T>(wn, nb[RF_L1], me + (fwd ? RF_SJM : RF_SJP), fwd ? -1 : +1, Mj);
+        if constexpr (kJvpJ) {
+          rec_state<G, T>(nb, wjn);
+          jlam = nb[RF_L1];
+          Sjv[0] = me[fwd ? RF_SJM : RF_SJP];
+          Sjv[1] = me[(fwd ? RF_SJM : RF_SJP) + 1];
+        } else {
+          CellState<G, 2, T> wn;
+          rec_state<G, T>(nb, wn);
+          wave_matrix<G, T>(wn, nb[RF_L1], me + (fwd ? RF_SJM : RF_SJP), fwd ? -1 : +1, Mj);
+        }
       }
     };
     setup(0);
     for (int q = 0; q <= H; ++q) {
       const int h = hof(q), i = h - j;
-      if (q > 0) cluster_wait();
+      if (!BLK && q > 0) cluster_wait();
       if (act) {
         if (hasj) {
           const bool remote = fwd ? t == 0 : t == R - 1;
@@ -2055,10 +2073,14 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
           T xn[NF];
 #pragma unroll
           for (int v = 0; v < NF; ++v) xn[v] = src[v];
+          if constexpr (kJvpJ) {
+            flow_contrib<G, T>(wjn, jlam, Sjv, xn, fwd ? -1 : +1, acc);
+          } else {
 #pragma unroll
-          for (int r = 0; r < NF; ++r)
+            for (int r = 0; r < NF; ++r)
 #pragma unroll
-            for (int c = 0; c < NF; ++c) acc[r] += Mj[r][c] * xn[c];
+              for (int c = 0; c < NF; ++c) acc[r] += Mj[r][c] * xn[c];
+          }
         }
         const T* bse = sm.base[q % kWaveSlots][t + 1];
 #pragma unroll
@@ -2074,7 +2096,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
           for (int v = 0; v < NF; ++v) dst[v] = x[v];
         }
       }
-      cluster_arrive();
+      if (!BLK) cluster_arrive();
       if (act) {
         double* out = fwd ? g.dQs : g.dQ;
 #pragma unroll
@@ -2101,18 +2123,18 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T>& sm) {
       cp_async_commit();        // one group per step, possibly empty
       setup(q + 1);
     }
-    cluster_wait();
+    if (!BLK) cluster_wait();
     cp_async_wait<0>();
-    __syncwarp();
+    if (BLK) __syncthreads(); else __syncwarp();
   }
 }
 
 
-template <class G, class T>
+template <class G, class T, int ROWS = kWaveRows>
 struct WaveSmemS {
-  T ring[kWaveSlots][kWaveRows + 2][kRecS];
-  T base[kWaveSlots][kWaveRows + 2][kSpeciesGroup];
-  T x[2][kWaveRows][kSpeciesGroup];
+  T ring[kWaveSlots][ROWS + 2][kRecS];
+  T base[kWaveSlots][ROWS + 2][kSpeciesGroup];
+  T x[2][ROWS][kSpeciesGroup];
   T mbox[2][kSpeciesGroup];
 };
 
@@ -2124,12 +2146,12 @@ __device__ __forceinline__ T wave_coef(const T* u, T lam, const T* S, int side) 
   return side < 0 ? T(0.5) * (U + lam) : T(-0.5) * (U - lam);
 }
 
-template <class G, class T>
-__device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& sm) {
+template <class G, class T, int ROWS = kWaveRows, bool BLK = false>
+__device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, ROWS>& sm) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF, SG = kSpeciesGroup, NS = G::NS;
   const size_t N = g.N;
-  const unsigned rank = cluster_ctarank(), C = cluster_nctarank();
+  const unsigned rank = BLK ? 0u : cluster_ctarank(), C = BLK ? 1u : cluster_nctarank();
   const int t = threadIdx.x;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
   const int j0 = rank * R, j = j0 + t;
@@ -2156,7 +2178,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& 
     for (int k = 0; k < SG; ++k) { carry[k] = 0; wrapc[k] = 0; x[k] = 0; iD[k] = 0; acc[k] = 0; }
     auto setup = [&](int q) {
       cp_async_wait<kWaveD - 1>();
-      __syncwarp();
+      if (BLK) __syncthreads(); else __syncwarp();
       const int h = hof(q), i = h - j;
       act = row && q <= H && i >= 0 && i < ni;
       const int jj = j - hs;
@@ -2184,7 +2206,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& 
     setup(0);
     for (int q = 0; q <= H; ++q) {
       const int h = hof(q), i = h - j;
-      if (q > 0) cluster_wait();
+      if (!BLK && q > 0) cluster_wait();
       if (act) {
         if (hasj) {
           const bool remote = fwd ? t == 0 : t == R - 1;
@@ -2204,7 +2226,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& 
           for (int k = 0; k < SG; ++k) dst[k] = x[k];
         }
       }
-      cluster_arrive();
+      if (!BLK) cluster_arrive();
       if (act) {
         double* out = fwd ? g.dQs : g.dQ;
 #pragma unroll
@@ -2231,9 +2253,9 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T>& 
       cp_async_commit();
       setup(q + 1);
     }
-    cluster_wait();
+    if (!BLK) cluster_wait();
     cp_async_wait<0>();
-    __syncwarp();
+    if (BLK) __syncthreads(); else __syncwarp();
   }
 }
 
@@ -2248,6 +2270,28 @@ __global__ void __launch_bounds__(32) k_split_wave(DevGrid g, int R) {
 
 template <class G>
 constexpr int species_clusters() { return (G::NS + kSpeciesGroup - 1) / kSpeciesGroup; }
+
+// K6d: 2D split sweeps in FP32 with one CTA per component (the flow block, then one per group
+// of 4 species) holding every row of the grid: same records and arithmetic as K6c, with
+// __syncthreads between hyperplanes instead of a cluster barrier (FP32 throughput lets one SM
+// carry all rows; cheaper synchronisation than 16 CTAs).  nj <= kBlockRows.
+constexpr int kBlockRows = 384;
+template <class G>
+constexpr size_t block_smem_bytes() {
+  return sizeof(WaveSmemF<G, float, kBlockRows>) > sizeof(WaveSmemS<G, float, kBlockRows>)
+             ? sizeof(WaveSmemF<G, float, kBlockRows>)
+             : sizeof(WaveSmemS<G, float, kBlockRows>);
+}
+template <class G>
+__global__ void __launch_bounds__(kBlockRows) k_split_block(DevGrid g) {
+  extern __shared__ __align__(16) char bsm[];
+  const int comp = blockIdx.x;
+  if (comp == 0)
+    wave_flow<G, float, kBlockRows, true>(g, g.nj, *reinterpret_cast<WaveSmemF<G, float, kBlockRows>*>(bsm));
+  else
+    wave_species<G, float, kBlockRows, true>(g, g.nj, comp - 1,
+                                             *reinterpret_cast<WaveSmemS<G, float, kBlockRows>*>(bsm));
+}
 
 template <class G, class T>
 __global__ void __launch_bounds__(32 * kClusterWarps) k_split_cluster(DevGrid g, int R) {

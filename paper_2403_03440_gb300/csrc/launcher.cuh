@@ -210,7 +210,11 @@ struct LauncherT : Launcher {
     // measured on GB300: the wavefront-record kernel is the faster one in FP32, the
     // direct-load kernel in FP64 (fewer dependent FP64 operations per step)
     const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
-    if (kind == 2 && g.wrec) {
+    if (kind == 3 && mixed && g.wrec) {
+      const int n = sweep_block(g, st);
+      if (n) return n;
+    }
+    if ((kind == 2 || kind == 3) && g.wrec) {
       const int n = mixed ? sweep_wave_t<float>(g, st, wprobed32_) : sweep_wave_t<double>(g, st, wprobed64_);
       if (n) return n;
     }
@@ -255,12 +259,35 @@ struct LauncherT : Launcher {
 
   void prepare(const DevGrid& g, bool mixed) override {
     const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
+    if (kind == 3 && mixed) block_ok(g);
     if (kind == 2) {
       if (mixed) wave_cluster_size<float>(g, wprobed32_);
       else wave_cluster_size<double>(g, wprobed64_);
     }
     if (mixed) cluster_size<float>(g, probed32_);
     else cluster_size<double>(g, probed64_);
+  }
+
+  // FP32 block kernel: one CTA per component with every row (0 when it does not apply)
+  bool block_ok(const DevGrid& g) {
+    if (ND != 2 || g.bc[2] == BC_PERIODIC || g.nj > kBlockRows) return false;
+    if (block_probed_ < 0) {
+      block_probed_ = cudaFuncSetAttribute(k_split_block<G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)block_smem_bytes<G>()) == cudaSuccess ? 1 : 0;
+      cudaGetLastError();
+    }
+    return block_probed_ == 1;
+  }
+  int block_probed_ = -1;
+  int sweep_block(const DevGrid& g, cudaStream_t st) {
+    sweep_split_cluster_ok = false;
+    if (!block_ok(g)) return 0;
+    k_pack_wave<G, float><<<blocks(g.N, 128), 128, 0, st>>>(g);
+    const int threads = ((g.nj + 31) / 32) * 32;
+    k_split_block<G><<<1 + species_clusters<G>(), threads, block_smem_bytes<G>(), st>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return 0;
+    sweep_split_cluster_ok = true;
+    return 2;
   }
 
   template <class T>

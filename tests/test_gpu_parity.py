@@ -331,6 +331,39 @@ def test_cluster_sweep_equals_hyperplane_sweep(name):
     assert rel(a[:ref.nF], ref.lusgs_split(8.0)[:ref.nF]) < TOL
 
 
+@pytest.mark.parametrize("nodes_fn,bc,mech", [
+    (lambda: inputs.cylinder_half(40, 100), inputs.cylinder_half_bc(), inputs.MECH_AIR5),
+    (lambda: inputs.cylinder_half(25, 16), inputs.cylinder_half_bc(), inputs.MECH_AIR11),
+    (lambda: inputs.cylinder_ogrid(24, 16), inputs.cylinder_bc(), inputs.MECH_AIR11),
+])
+def test_block_sweep_equals_cluster_sweep_fp32(nodes_fn, bc, mech):
+    """FP32 operator: the one-CTA-per-component sweep (every row in one CTA, __syncthreads
+    between hyperplanes) performs the record cluster kernel's arithmetic; 100 rows span 4
+    warps.  Both agree with the FP64 oracle to FP32 rounding."""
+    nodes = nodes_fn()
+    fs = inputs.freestream(mech, T=300.0, p=500.0, mach=10.0)
+    ref = oracle.OracleGrid(nodes, bc, mech)
+    ref.set_boundary(fs, Tw=500.0)
+    gpu = P.Grid(nodes, bc, mech)
+    gpu.set_boundary(fs, Tw=500.0)
+    pr = inputs.perturbed_primitive(mech, (ref.nj, ref.ni), seed=9, ndim=2)
+    Q = oracle.prim_to_cons_field(mech, 2, pr)
+    ref.set_state(Q)
+    out = {}
+    for mode in (4, 2):
+        gpu.set_option("cluster_sweep", mode)
+        gpu.set_state(Q)
+        gpu.residual(want_R=False)
+        out[mode] = gpu.lusgs_split(8.0, precision=1)
+    gpu.set_option("cluster_sweep", 3)
+    assert rel(out[4][:ref.nF], out[2][:ref.nF]) < 1e-6
+    assert rel(out[4][ref.nF:], out[2][ref.nF:], ns=ref.ns) < 1e-6
+    ref.residual()
+    d = ref.lusgs_split(8.0)
+    assert rel(out[4][:ref.nF], d[:ref.nF]) < 1e-4
+    assert rel(out[4][ref.nF:], d[ref.nF:], ns=ref.ns) < 1e-4
+
+
 @pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "box3d_air5_kper"])
 def test_mixed_precision_split_operator(name):
     """Mixed precision: the split sweeps compute in FP32 from FP64 radii, diagonals and
