@@ -64,6 +64,24 @@ FP64_PEAK_GFLOPS = 1250.0
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 
 
+def job_time_ms(local_ms, dist=None, device="cpu"):
+    """Time of the whole job: the slowest rank's timed-region time (max over ranks, then a
+    barrier so that no rank starts the next phase early).  Replicas only: this is the one
+    collective of a multi-GPU run, outside the timed region."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world, cells, steps, total_ms):
+    """Whole-job throughput in Mcell-iter/s: every rank's cells x iterations over the job time."""
+    return world * cells * steps / (total_ms / 1e3) / 1e6
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -150,9 +168,12 @@ def case_cells():
 PRECISION = 0   # 0: FP64 operator, 1: FP32 operator (mixed); set by --precision
 
 
+SCHEME = (0, 1)   # (scheme, correction): CS-1 split by default; --scheme cs2 / ci
+
+
 def step_kwargs(iters):
-    return dict(scheme=0, correction=1, clip=1, cfl=CFL, cfl_start=CFL_START, ramp_iters=RAMP,
-                iters=iters, precision=PRECISION)
+    return dict(scheme=SCHEME[0], correction=SCHEME[1], clip=1, cfl=CFL, cfl_start=CFL_START,
+                ramp_iters=RAMP, iters=iters, precision=PRECISION)
 
 
 def oracle_rate(iters, seconds_cap=30.0):
@@ -302,10 +323,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch"])
+    ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
     args = ap.parse_args()
-    global PRECISION, WORKLOAD, C3
+    global PRECISION, WORKLOAD, C3, SCHEME
+    SCHEME = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1)}[args.scheme]
     if args.workload == "c3":
         C3 = True
         WORKLOAD = "sphere-cone-192x128x96-air11-2T-mach20-CS1-fp64"
@@ -313,6 +336,8 @@ def main():
     if args.precision == "mixed":
         PRECISION = 1
         WORKLOAD = WORKLOAD.replace("fp64", "mixed-fp32-operator")
+    if args.scheme != "cs1":
+        WORKLOAD = WORKLOAD.replace("CS1", args.scheme.upper())
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -360,13 +385,8 @@ def main():
         torch.cuda.synchronize()
     prof = g.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = world * N * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = job_time_ms(sum(step_ms), dist, "cuda")
+    value = job_value(world, N, args.steps, total_ms)
 
     # ---- end to end through the C ABI with host buffers ----
     Qh = torch.empty((g.nq, N), dtype=torch.float64, pin_memory=True).numpy()
@@ -415,7 +435,8 @@ def main():
             "dtype": "f64" if PRECISION == 0 else "f64 residual/update, f32 operator",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "species": 11, "temperatures": 2,
-                       "scheme": "CS-1 split LU-SGS", "cfl": CFL,
+                       "scheme": {"cs1": "CS-1 split LU-SGS", "cs2": "CS-2 split LU-SGS",
+                                  "ci": "coupled (CI) LU-SGS"}[args.scheme], "cfl": CFL,
                        "l2": "flushed before every timed iteration (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),

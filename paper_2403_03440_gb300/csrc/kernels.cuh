@@ -1837,7 +1837,7 @@ __global__ void __launch_bounds__(128) k_pack_wave(DevGrid g) {
   if (c >= g.N) return;
   const size_t N = g.N;
   const int ni = g.ni, i = c % ni, j = c / ni, h = i + j;
-  const size_t w = (size_t)g.woff[h] + (j - wave_jlo(h, ni));
+  const size_t w = (size_t)__ldg(&g.woff[h]) + (j - wave_jlo(h, ni));
   const double* W = g.W;
   const double* Si0 = g.S[0] + 3 * (size_t)face_of(g, 0, i, j, 0);
   const double* Si1 = g.S[0] + 3 * (size_t)face_of(g, 0, i + 1, j, 0);
@@ -1989,6 +1989,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF;
   const size_t N = g.N;
+  constexpr int D = BLK ? 2 : kWaveD;   // prefetch distance (see k_split_block)
   const unsigned rank = BLK ? 0u : cluster_ctarank(), C = BLK ? 1u : cluster_nctarank();
   const int t = threadIdx.x;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
@@ -2002,7 +2003,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
     const int hs = fwd ? 1 : -1;      // hyperplane step
     auto hof = [&](int q) { return fwd ? q : H - q; };
     if (!fwd) __threadfence();   // forward results in `base` are read back through cp.async
-    for (int q = 0; q < kWaveD; ++q) {
+    for (int q = 0; q < D; ++q) {
       wave_fetch<T>(rec, kRecF, g.woff, hof(q), H, ni, nj, j0, R, &sm.ring[q % kWaveSlots][0][0]);
       if (!fwd) wave_fetch<T>(base, 8, g.woff, hof(q), H, ni, nj, j0, R, &sm.base[q % kWaveSlots][0][0]);
       cp_async_commit();
@@ -2022,7 +2023,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
     for (int v = 0; v < NF; ++v) { carry[v] = 0; wrapc[v] = 0; x[v] = 0; }
     // per-step set-up from the records (step q); also used for the first step
     auto setup = [&](int q) {
-      cp_async_wait<kWaveD - 1>();
+      cp_async_wait<D - 1>();
       if (BLK) __syncthreads(); else __syncwarp();
       const int h = hof(q), i = h - j;
       act = row && q <= H && i >= 0 && i < ni;
@@ -2039,7 +2040,7 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
       iD = me[RF_ID];
       iDev = me[RF_IDEV];
       cidx = i + ni * j;
-      wcur = g.woff[h] + (j - wave_jlo(h, ni));
+      wcur = __ldg(&g.woff[h]) + (j - wave_jlo(h, ni));
       const bool prev_exists = fwd ? i > 0 : i < ni - 1;
       const bool wrap = per && (fwd ? i == ni - 1 : i == 0);
 #pragma unroll
@@ -2113,12 +2114,12 @@ __device__ void wave_flow(const DevGrid& g, int R, WaveSmemF<G, T, ROWS>& sm) {
         if (per && i == (fwd ? 0 : ni - 1)) wave_contrib<G, T>(ws, lam0, Sw, fwd ? +1 : -1, x, wrapc);
       }
       // prefetch step q + D, then prepare step q + 1
-      if (q + kWaveD <= H) {
-        wave_fetch<T>(rec, kRecF, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
-                      &sm.ring[(q + kWaveD) % kWaveSlots][0][0]);
+      if (q + D <= H) {
+        wave_fetch<T>(rec, kRecF, g.woff, hof(q + D), H, ni, nj, j0, R,
+                      &sm.ring[(q + D) % kWaveSlots][0][0]);
         if (!fwd)
-          wave_fetch<T>(base, 8, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
-                        &sm.base[(q + kWaveD) % kWaveSlots][0][0]);
+          wave_fetch<T>(base, 8, g.woff, hof(q + D), H, ni, nj, j0, R,
+                        &sm.base[(q + D) % kWaveSlots][0][0]);
       }
       cp_async_commit();        // one group per step, possibly empty
       setup(q + 1);
@@ -2151,6 +2152,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, R
   using A = Aux<G, 2>;
   constexpr int NF = A::NF, SG = kSpeciesGroup, NS = G::NS;
   const size_t N = g.N;
+  constexpr int D = BLK ? 2 : kWaveD;   // prefetch distance (see k_split_block)
   const unsigned rank = BLK ? 0u : cluster_ctarank(), C = BLK ? 1u : cluster_nctarank();
   const int t = threadIdx.x;
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
@@ -2166,7 +2168,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, R
     const int hs = fwd ? 1 : -1;
     auto hof = [&](int q) { return fwd ? q : H - q; };
     if (!fwd) __threadfence();
-    for (int q = 0; q < kWaveD; ++q) {
+    for (int q = 0; q < D; ++q) {
       wave_fetch<T>(rec, kRecS, g.woff, hof(q), H, ni, nj, j0, R, &sm.ring[q % kWaveSlots][0][0]);
       if (!fwd) wave_fetch<T>(base, SG, g.woff, hof(q), H, ni, nj, j0, R, &sm.base[q % kWaveSlots][0][0]);
       cp_async_commit();
@@ -2177,7 +2179,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, R
 #pragma unroll
     for (int k = 0; k < SG; ++k) { carry[k] = 0; wrapc[k] = 0; x[k] = 0; iD[k] = 0; acc[k] = 0; }
     auto setup = [&](int q) {
-      cp_async_wait<kWaveD - 1>();
+      cp_async_wait<D - 1>();
       if (BLK) __syncthreads(); else __syncwarp();
       const int h = hof(q), i = h - j;
       act = row && q <= H && i >= 0 && i < ni;
@@ -2186,7 +2188,7 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, R
       if (!act) return;
       const T* me = sm.ring[q % kWaveSlots][t + 1];
       cidx = i + ni * j;
-      wcur = g.woff[h] + (j - wave_jlo(h, ni));
+      wcur = __ldg(&g.woff[h]) + (j - wave_jlo(h, ni));
       const bool prev_exists = fwd ? i > 0 : i < ni - 1;
       const bool wrap = per && (fwd ? i == ni - 1 : i == 0);
 #pragma unroll
@@ -2243,12 +2245,12 @@ __device__ void wave_species(const DevGrid& g, int R, int grp, WaveSmemS<G, T, R
 #pragma unroll
           for (int k = 0; k < SG; ++k) wrapc[k] = kw * x[k];
       }
-      if (q + kWaveD <= H) {
-        wave_fetch<T>(rec, kRecS, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
-                      &sm.ring[(q + kWaveD) % kWaveSlots][0][0]);
+      if (q + D <= H) {
+        wave_fetch<T>(rec, kRecS, g.woff, hof(q + D), H, ni, nj, j0, R,
+                      &sm.ring[(q + D) % kWaveSlots][0][0]);
         if (!fwd)
-          wave_fetch<T>(base, SG, g.woff, hof(q + kWaveD), H, ni, nj, j0, R,
-                        &sm.base[(q + kWaveD) % kWaveSlots][0][0]);
+          wave_fetch<T>(base, SG, g.woff, hof(q + D), H, ni, nj, j0, R,
+                        &sm.base[(q + D) % kWaveSlots][0][0]);
       }
       cp_async_commit();
       setup(q + 1);
@@ -2274,7 +2276,9 @@ constexpr int species_clusters() { return (G::NS + kSpeciesGroup - 1) / kSpecies
 // K6d: 2D split sweeps in FP32 with one CTA per component (the flow block, then one per group
 // of 4 species) holding every row of the grid: same records and arithmetic as K6c, with
 // __syncthreads between hyperplanes instead of a cluster barrier (FP32 throughput lets one SM
-// carry all rows; cheaper synchronisation than 16 CTAs).  nj <= kBlockRows.
+// carry all rows).  nj <= kBlockRows.  With several warps the prefetch distance is 2 (4 ring
+// slots): the slot that the fetch at the end of step q overwrites was last read in the setup of
+// step q - 1, which every warp has left at the block barrier of the setup of step q.
 constexpr int kBlockRows = 384;
 template <class G>
 constexpr size_t block_smem_bytes() {
@@ -2726,9 +2730,11 @@ __global__ void __launch_bounds__(128) k_surr_features(DevGrid g, float* X, cons
   if (c >= g.N) return;
   float f[kSurrIn];
   surr_raw_features<G, ND>(g, c, f);
+  // standardised, and held to the range the training data spans (|x| <= 8) so that a state
+  // unlike any the network saw cannot drive it far outside
 #pragma unroll
   for (int k = 0; k < kSurrIn; ++k)
-    X[(size_t)c * kSurrIn + k] = (float)((f[k] - norm[k]) / norm[kSurrIn + k]);
+    X[(size_t)c * kSurrIn + k] = (float)fmin(fmax((f[k] - norm[k]) / norm[kSurrIn + k], -8.0), 8.0);
 }
 
 // network outputs [N][22] -> the species Jacobian diagonal d omega_s / d rho_s of the operator
@@ -2743,7 +2749,9 @@ __global__ void __launch_bounds__(128) k_surr_decode(DevGrid g, const float* Y, 
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
     const int o = kSurrNS + s;
-    const double t = (double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o];
+    // de-standardised and kept finite (a non-finite network output maps to the bound, which
+    // only adds to the operator's diagonal)
+    const double t = fmin(fmax((double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o], -700.0), 700.0);
     g.W[(A::DOM + s) * N + c] = sinh(t);
   }
 }

