@@ -287,7 +287,7 @@ def run_batch(args, rank, world, local):
     e2e = cells * K * args.e2e_steps / e2e_s / 1e6
     # kernels per case and iteration: cfl, primitive, gradient, 2 fluxes, assemble + norms,
     # spectral, sweep (records + wavefront kernel, or one cluster kernel), correction
-    per_iter = sum(9 + (2 if kind == 2 else 1) for kind, _ in choice)
+    per_iter = sum(9 + (2 if kind in (2, 3) else 1) for kind, _ in choice)
     if rank == 0:
         line = {
             "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,

@@ -166,12 +166,12 @@ cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
- * split sweeps as one thread-block-cluster launch, choosing per precision between 2 (cluster
- * kernel over hyperplane-ordered cell records, faster in FP32) and 1 (cluster kernel reading
- * the cell arrays directly, faster in FP64); 0 runs one launch per hyperplane; 4 runs the
- * FP32 operator's sweeps with one CTA per component holding every row (nj <= 384;
- * __syncthreads between hyperplanes; FP64 and larger grids fall back to 2).  All give the
- * same arithmetic up to rounding.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
+ * split sweeps in one launch, choosing per precision: for the FP32 operator 4 where it applies,
+ * else 2; for FP64, 1.  1 is a thread-block-cluster kernel reading the cell arrays directly,
+ * 2 a cluster kernel over hyperplane-ordered cell records, 4 the FP32 operator's sweeps with
+ * one CTA per component holding every row (nj <= 384; __syncthreads between hyperplanes;
+ * FP64 and larger grids fall back to 2); 0 runs one launch per hyperplane.  All give the same
+ * arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
  * component of the 2D cluster sweeps (0, the default: the largest that fits; a C that does not
  * fit the grid or the device falls back to one launch per hyperplane); cs_batch_tune sets it.
  * Method option: "h_correction" = 1 (default) widens the entropy fix of every face's Roe flux

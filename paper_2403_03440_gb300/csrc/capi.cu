@@ -677,9 +677,6 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
   const DevGrid& d = g->g;
   if (rec) prof_record(g, slot, 0);
   g->L->primitive(d, g->stream);
-  // the species Jacobian diagonal of the operator from the network, when one is attached (the
-  // exact source stays in the residual)
-  enqueue_surrogate(g);
   if (rec) prof_record(g, slot, 1);
   g->L->gradient(d, g->stream);
   if (rec) prof_record(g, slot, 2);
@@ -687,6 +684,9 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
   if (rec) prof_record(g, slot, 3);
   g->L->assemble(d, g->stream, g->stag, g->norms);
   if (rec) prof_record(g, slot, 4);
+  // the species Jacobian diagonal of the operator from the network, when one is attached (the
+  // exact source stays in the residual); timed with the spectral phase
+  enqueue_surrogate(g);
   g->L->spectral(d, g->stream);
   int nf, nb;
   if (o->scheme == CS_SCHEME_SPLIT) {
@@ -944,8 +944,9 @@ extern "C" cs_status cs_batch_tune(cs_batch b, int precision, int trials, int* c
       float best = 1e30f;
       int best_kind = 0, best_C = 0;
       const int keep_kind = L->cluster_kind, keep_C = L->force_C;
-      for (int kind : {1, 2}) {
-        const int mask = L->cluster_sizes(d, kind, mixed);
+      for (int kind : {1, 2, 3}) {
+        // kind 3 (one CTA per component, FP32 only) has no cluster size: timed once as C = 1
+        const int mask = kind == 3 ? (mixed && L->block_available(d) ? 2 : 0) : L->cluster_sizes(d, kind, mixed);
         for (int C : {1, 2, 4, 8, 16}) {
           if (!(mask & (1 << C))) continue;
           L->cluster_kind = kind;

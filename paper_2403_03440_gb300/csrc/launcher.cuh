@@ -40,6 +40,8 @@ struct Launcher {
   // bit C of the result is set when the cluster sweep of `kind` (1 direct, 2 wavefront
   // records) can run with C CTAs per component on this grid and device
   virtual int cluster_sizes(const DevGrid& g, int kind, bool mixed) = 0;
+  // does the FP32 one-CTA-per-component sweep apply to this grid?
+  virtual bool block_available(const DevGrid& g) = 0;
   // run the cluster-size probes of the current choice (host-side calls that must not happen
   // inside a stream capture)
   virtual void prepare(const DevGrid& g, bool mixed) = 0;
@@ -207,9 +209,9 @@ struct LauncherT : Launcher {
 
   // one launch: both sweeps of the flow block and of every species (returns launches)
   int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed) override {
-    // measured on GB300: the wavefront-record kernel is the faster one in FP32, the
-    // direct-load kernel in FP64 (fewer dependent FP64 operations per step)
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
+    // measured on GB300: in FP32 the one-CTA-per-component kernel (where nj fits) and then
+    // the wavefront-record kernel, in FP64 the direct-load kernel
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 1);
     if (kind == 3 && mixed && g.wrec) {
       const int n = sweep_block(g, st);
       if (n) return n;
@@ -258,9 +260,9 @@ struct LauncherT : Launcher {
   }
 
   void prepare(const DevGrid& g, bool mixed) override {
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 2 : 1);
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 1);
     if (kind == 3 && mixed) block_ok(g);
-    if (kind == 2) {
+    if (kind == 2 || kind == 3) {
       if (mixed) wave_cluster_size<float>(g, wprobed32_);
       else wave_cluster_size<double>(g, wprobed64_);
     }
@@ -279,6 +281,7 @@ struct LauncherT : Launcher {
     return block_probed_ == 1;
   }
   int block_probed_ = -1;
+  bool block_available(const DevGrid& g) override { return block_ok(g); }
   int sweep_block(const DevGrid& g, cudaStream_t st) {
     sweep_split_cluster_ok = false;
     if (!block_ok(g)) return 0;

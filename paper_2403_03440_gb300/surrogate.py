@@ -79,7 +79,7 @@ def standardisation(X, T):
     return np.concatenate([mx, sx, mt, st])
 
 
-def train(X, T, norm, epochs=4, batch=4096, lr=2e-3, seed=0, max_batch=None):
+def train(X, T, norm, epochs=40, batch=4096, lr=2e-3, seed=0, max_batch=None):
     import torch
     n = X.shape[0]
     Xn = ((X - norm[:14]) / norm[14:28]).astype(np.float32)
@@ -93,7 +93,7 @@ def train(X, T, norm, epochs=4, batch=4096, lr=2e-3, seed=0, max_batch=None):
         Te = torch.from_numpy(Tn[perm]).cuda()
         losses = []
         for k in range(0, n - batch + 1, batch):
-            losses.append(net.train_step(Xe[k:k + batch], Te[k:k + batch], lr * (0.5 ** ep)))
+            losses.append(net.train_step(Xe[k:k + batch], Te[k:k + batch], lr * (0.9 ** ep)))
         record.append(float(np.mean(losses)))
     return net, record
 
@@ -152,7 +152,7 @@ def main():
     ap.add_argument("--max-iters", type=int, default=100000)
     ap.add_argument("--samples-iters", type=int, default=4000)
     ap.add_argument("--every", type=int, default=20)
-    ap.add_argument("--epochs", type=int, default=4)
+    ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     a = ap.parse_args()
     P.build()

@@ -59,7 +59,7 @@ def test_batch_equals_case_by_case_steps():
         alone = make_grid(k)
         kind, C = choice[k]
         if C:
-            alone.set_option("cluster_sweep", kind)
+            alone.set_option("cluster_sweep", {1: 1, 2: 2, 3: 4}[kind])
             alone.set_option("cluster_size", C)
         o = dict(opts[k])
         s = alone.step(iters=18, **o)
@@ -81,6 +81,8 @@ def test_batch_tune_choices():
         for k, (kind, C) in enumerate(choice):
             if k == 3:                        # 3D: no cluster sweep
                 assert (kind, C) == (0, 0)
+            elif kind == 3:                   # FP32 one-CTA-per-component kernel
+                assert prec == 1 and C == 1
             else:
                 assert kind in (1, 2) and C in (1, 2, 4, 8, 16)
                 assert (grids[k].nj + C - 1) // C <= 32
