@@ -2749,9 +2749,11 @@ __global__ void __launch_bounds__(128) k_surr_decode(DevGrid g, const float* Y, 
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
     const int o = kSurrNS + s;
-    // de-standardised and kept finite (a non-finite network output maps to the bound, which
-    // only adds to the operator's diagonal)
-    const double t = fmin(fmax((double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o], -700.0), 700.0);
+    // de-standardised and held to the span of the training targets (mean +- 8 standard
+    // deviations of asinh(d omega / d rho)); a non-finite output maps to the lower bound, which
+    // only adds to the operator's diagonal
+    const double t = fmin(fmax((double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o], mt[o] - 8.0 * st[o]),
+                          mt[o] + 8.0 * st[o]);
     g.W[(A::DOM + s) * N + c] = sinh(t);
   }
 }

@@ -210,6 +210,161 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const bf16* __restrict__ A, i
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
 }
 
+// Layer sizes (the flat FP32 parameter layout is described with the elementwise kernels below).
+constexpr int LNH = CS_MLP_HIDDEN, LKIN = 16, LNOUTP = 32;
+
+// Fused inference: the whole network on 128-row tiles of a persistent grid.  Each CTA stages
+// the bfloat16 weights into shared memory once (canonical K-major layout, 76 KB), then per
+// tile: inputs -> bf16 tile, and for each layer one tcgen05.mma group into tensor memory,
+// tcgen05.ld, bias (+ SiLU), bf16 back into shared memory as the next layer's A operand; the
+// last layer's FP32 outputs go to Y [n][22].  No activation leaves the SM.
+constexpr int kFuseSmemW = (LNH * LKIN + 2 * LNH * LNH + LNOUTP * LNH) * 2;   // 77824 B
+constexpr int kFuseSmemA = kTileM * LNH * 2;                                   // 32768 B
+constexpr int kFuseSmemX = kTileM * LKIN * 2;                                  // 4096 B
+constexpr int kFuseSmemBytes = kFuseSmemW + kFuseSmemA + kFuseSmemX + 64;
+
+// stage rows [0, rows) x [0, K) of a row-major bf16 matrix into the canonical K-major layout
+__device__ __forceinline__ void stage_kmajor(const bf16* src, int rows, int K, unsigned char* dst) {
+  const int c8n = K / 8;
+  for (int v = threadIdx.x; v < rows * c8n; v += blockDim.x) {
+    const int r = v / c8n, c8 = v - r * c8n;
+    const uint4 x = *reinterpret_cast<const uint4*>(src + (size_t)r * K + c8 * 8);
+    *reinterpret_cast<uint4*>(dst + (c8 * (rows / 8) + (r >> 3)) * 128 + (r & 7) * 16) = x;
+  }
+}
+
+// one layer: D[128 x N] = A[128 x K] W[N x K]^T into tensor memory; returns false on timeout
+__device__ __forceinline__ bool fused_layer(uint32_t tmem, uint32_t a0, uint32_t w0, int N, int K,
+                                            uint32_t bar, uint32_t& phase) {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t idesc = instr_desc(kTileM, N);
+    for (int j = 0; j < K / 16; ++j) {
+      const uint64_t ad = smem_desc(a0 + 2 * j * (kTileM / 8) * 128, (kTileM / 8) * 128, 128);
+      const uint64_t bd = smem_desc(w0 + 2 * j * (N / 8) * 128, (N / 8) * 128, 128);
+      const uint32_t acc = j > 0 ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+          ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 ::"r"(bar) : "memory");
+  }
+  const bool ok = wait_parity(bar, phase);
+  phase ^= 1;
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  return !__syncthreads_or(!ok);
+}
+
+// hidden-layer epilogue: row r = thread, N = 128 columns: bias + SiLU -> bf16 into the A tile
+__device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float* __restrict__ bias,
+                                                      unsigned char* A) {
+  const int warp = threadIdx.x >> 5, r = threadIdx.x;
+  for (int c0 = 0; c0 < LNH; c0 += 32) {
+    float v[32];
+    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+    for (int g8 = 0; g8 < 4; ++g8) {
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int n0 = c0 + g8 * 8 + 2 * h;
+        const float z0 = v[g8 * 8 + 2 * h] + bias[n0], z1 = v[g8 * 8 + 2 * h + 1] + bias[n0 + 1];
+        const bf16 b0 = __float2bfloat16_rn(z0 / (1.f + __expf(-z0)));
+        const bf16 b1 = __float2bfloat16_rn(z1 / (1.f + __expf(-z1)));
+        w[h] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+      }
+      const int c8 = (c0 >> 3) + g8;
+      *reinterpret_cast<uint4*>(A + (c8 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mlp_infer(const float* __restrict__ X, int n,
+                                                        const bf16* __restrict__ W1, const bf16* __restrict__ W2,
+                                                        const bf16* __restrict__ W3, const bf16* __restrict__ W4,
+                                                        const float* __restrict__ b1, const float* __restrict__ b2,
+                                                        const float* __restrict__ b3, const float* __restrict__ b4,
+                                                        float* __restrict__ Y, int* err) {
+  extern __shared__ __align__(128) unsigned char fsm[];
+  unsigned char* sW1 = fsm;
+  unsigned char* sW2 = sW1 + LNH * LKIN * 2;
+  unsigned char* sW3 = sW2 + LNH * LNH * 2;
+  unsigned char* sW4 = sW3 + LNH * LNH * 2;
+  unsigned char* sA = fsm + kFuseSmemW;
+  unsigned char* sX = sA + kFuseSmemA;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sX + kFuseSmemX);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t barA = smem_u32(bar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                 ::"r"(smem_u32(tslot)), "r"(128u) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barA) : "memory");
+  stage_kmajor(W1, LNH, LKIN, sW1);
+  stage_kmajor(W2, LNH, LNH, sW2);
+  stage_kmajor(W3, LNH, LNH, sW3);
+  stage_kmajor(W4, LNOUTP, LNH, sW4);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const uint32_t sAu = smem_u32(sA), sXu = smem_u32(sX);
+  uint32_t phase = 0;
+  bool failed = false;
+  const int ntiles = (n + kTileM - 1) / kTileM;
+  for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int row0 = tile * kTileM;
+    // inputs: thread r owns row r; 14 features + 2 zero columns as bf16, canonical layout
+    {
+      const int r = tid, gr = row0 + r;
+      uint32_t w[8];
+#pragma unroll
+      for (int h = 0; h < 8; ++h) {
+        const int k0 = 2 * h, k1 = 2 * h + 1;
+        const float x0 = (gr < n && k0 < 14) ? X[(size_t)gr * 14 + k0] : 0.f;
+        const float x1 = (gr < n && k1 < 14) ? X[(size_t)gr * 14 + k1] : 0.f;
+        w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
+      }
+      *reinterpret_cast<uint4*>(sX + (0 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+      *reinterpret_cast<uint4*>(sX + (1 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
+          make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    if (!fused_layer(tmem, sXu, smem_u32(sW1), LNH, LKIN, barA, phase)) { failed = true; break; }
+    fused_hidden_epilogue(tmem, b1, sA);
+    if (!fused_layer(tmem, sAu, smem_u32(sW2), LNH, LNH, barA, phase)) { failed = true; break; }
+    fused_hidden_epilogue(tmem, b2, sA);
+    if (!fused_layer(tmem, sAu, smem_u32(sW3), LNH, LNH, barA, phase)) { failed = true; break; }
+    fused_hidden_epilogue(tmem, b3, sA);
+    if (!fused_layer(tmem, sAu, smem_u32(sW4), LNOUTP, LNH, barA, phase)) { failed = true; break; }
+    {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+      const int gr = row0 + tid;
+      if (gr < n)
+#pragma unroll
+        for (int o = 0; o < 22; ++o) Y[(size_t)gr * 22 + o] = v[o] + b4[o];
+    }
+    // the next tile's first MMA overwrites the accumulators: every warp has read them
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+  }
+  if (failed && tid == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128u) : "memory");
+}
+
 // ---------------------------------------------------------------------------------------
 // Elementwise kernels of the network
 // ---------------------------------------------------------------------------------------
@@ -421,7 +576,8 @@ static cudaError_t gemm_attrs() {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_gemm<EPI_STORE>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) ||
       (e = cudaFuncSetAttribute(k_gemm<EPI_SILU>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) ||
-      (e = cudaFuncSetAttribute(k_gemm<EPI_ATOMIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)))
+      (e = cudaFuncSetAttribute(k_gemm<EPI_ATOMIC>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) ||
+      (e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuseSmemBytes)))
     return e;
   g_attr_done = true;
   return cudaSuccess;
@@ -448,6 +604,20 @@ static void forward(cs_mlp m, int npad, bool save) {
   gemm<EPI_STORE>(m, m->H3, NH, w.W4, NH, npad, NOUTP, NH, w.b4, m->Y, NOUTP);
 }
 
+static int g_num_sms = 0;
+static void infer(cs_mlp m, const float* X, int n, float* Y, cudaStream_t st) {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms < 1) g_num_sms = 1;
+  }
+  const int ntiles = (n + kTileM - 1) / kTileM;
+  const int grid = ntiles < 2 * g_num_sms ? ntiles : 2 * g_num_sms;
+  const Weights& w = m->w;
+  k_mlp_infer<<<grid, kThreads, kFuseSmemBytes, st>>>(X, n, w.W1, w.W2, w.W3, w.W4, w.b1, w.b2,
+                                                      w.b3, w.b4, Y, m->err);
+}
 static cs_status check_err(cs_mlp m, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return mfail(m, CS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -559,12 +729,9 @@ extern "C" cs_status cs_mlp_get_params(cs_mlp m, float* params_host) {
 
 extern "C" cs_status cs_mlp_forward(cs_mlp m, const float* X_dev, int n, float* Y_dev) {
   if (!m || !Y_dev) return CS_ERR_ARG;
-  int npad;
-  cs_status s = pack(m, X_dev, n, &npad, false);
-  if (s) return s;
+  if (!X_dev || n < 1 || n > m->max_batch) return mfail(m, CS_ERR_ARG, "batch of %d rows (1..%d)", n, m->max_batch);
   cudaMemsetAsync(m->err, 0, sizeof(int), m->st);
-  forward(m, npad, false);
-  k_unpack_output<<<blocks((long)n * NOUT, 256), 256, 0, m->st>>>(m->Y, n, Y_dev);
+  infer(m, X_dev, n, Y_dev, m->st);
   return check_err(m, "cs_mlp_forward");
 }
 
@@ -596,7 +763,9 @@ extern "C" cs_status cs_mlp_train_step(cs_mlp m, const float* X_dev, const float
   k_adam<<<blocks(NPARAM, 256), 256, 0, m->st>>>(m->p, m->grad, m->m, m->v, lr, bc1, bc2);
   k_cast_params<<<blocks(NH * NH, 256), 256, 0, m->st>>>(m->p, m->w);
   if (loss_out) *loss_out = *m->h_loss / ((double)n * NOUT);
-  if (cudaGetLastError() != cudaSuccess) return mfail(m, CS_ERR_CUDA, "adam");
+  // the updated weights are complete when the call returns (another stream may use them next)
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(m->st) != cudaSuccess)
+    return mfail(m, CS_ERR_CUDA, "adam");
   return CS_OK;
 }
 
@@ -606,15 +775,7 @@ extern "C" const char* cs_mlp_last_error(cs_mlp m) { return m ? m->msg : "null n
 // standardised FP32 inputs X into Y [n][22], enqueued on stream st without synchronisation.
 // A network must not serve two streams at once (its activation buffers are shared).
 int mlp_max_batch(cs_mlp m) { return m ? m->max_batch : 0; }
-void mlp_forward_on(cs_mlp m, const float* X, int n, float* Y, cudaStream_t st) {
-  const cudaStream_t keep = m->st;
-  m->st = st;
-  const int npad = ((n + kTileM - 1) / kTileM) * kTileM;
-  k_pack_input<<<blocks((long)npad * KIN, 256), 256, 0, st>>>(X, n, npad, m->X, nullptr);
-  forward(m, npad, false);
-  k_unpack_output<<<blocks((long)n * NOUT, 256), 256, 0, st>>>(m->Y, n, Y);
-  m->st = keep;
-}
+void mlp_forward_on(cs_mlp m, const float* X, int n, float* Y, cudaStream_t st) { infer(m, X, n, Y, st); }
 int mlp_error(cs_mlp m) {
   int e = 0;
   cudaMemcpy(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost);

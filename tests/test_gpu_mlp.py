@@ -37,12 +37,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("n", [1, 128, 200, 1000])
+# inference runs the fused persistent kernel: 40100 rows are 314 tiles, more than the grid's
+# CTAs, so CTAs loop over tiles and the last tile is ragged
+@pytest.mark.parametrize("n", [1, 128, 200, 1000, 40100])
 def test_forward_matches_oracle(n):
     import torch
     p = inputs.mlp_init(2)
     X, _ = data(n, 1)
-    net = P.MLP(p, max_batch=1024)
+    net = P.MLP(p, max_batch=max(n, 1024))
     Y = torch.empty((n, mlp.NOUT), dtype=torch.float32, device="cuda")
     net.forward(dev(X), Y)
     Yo = mlp.forward(p, X)[0]
@@ -84,6 +86,21 @@ def test_training_follows_oracle_and_reduces_loss():
     for _ in range(300):
         losses.append(net.train_step(Xd, Td, 3e-3))
     assert losses[-1] < 0.1 * losses[0]
+
+
+def test_forward_after_training_uses_updated_weights():
+    """Inference right after train_step sees the new bfloat16 weights (the step is complete
+    when it returns), and agrees with the oracle evaluated at the returned parameters."""
+    import torch
+    X, T = data(384, 5)
+    net = P.MLP(inputs.mlp_init(6), max_batch=384)
+    Xd, Td = dev(X), dev(T)
+    for _ in range(20):
+        net.train_step(Xd, Td, 3e-3)
+    Y = torch.empty((384, mlp.NOUT), dtype=torch.float32, device="cuda")
+    net.forward(Xd, Y)
+    Yo = mlp.forward(net.params(), X)[0]
+    assert rel_l2(Y.cpu().numpy(), Yo) < 5e-3
 
 
 def test_rejects_bad_batch():
