@@ -43,6 +43,8 @@ def lib():
         L.orc_set_reacting.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_hcorr.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_update_limit.argtypes = [C.c_void_p, C.c_double]
+        L.orc_set_dual.argtypes = [C.c_void_p, C.c_double, C.c_double]
+        L.orc_dual_advance.argtypes = [C.c_void_p]
         L.orc_set_boundary.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                        _dp, _dp, C.c_double]
         L.orc_freestream_state.argtypes = [C.c_void_p, _dp]
@@ -241,6 +243,14 @@ class OracleGrid:
 
     def set_update_limit(self, f):
         self._check(lib().orc_set_update_limit(self._h, float(f)), "set_update_limit")
+
+    def set_dual(self, dt, theta=0.0):
+        """Dual time stepping with physical step dt (0: steady) and coefficient theta."""
+        self._check(lib().orc_set_dual(self._h, float(dt), float(theta)), "set_dual")
+
+    def dual_advance(self):
+        """Begin a physical time step from the current state (Q^{n-1} <- Q^n <- Q)."""
+        self._check(lib().orc_dual_advance(self._h), "dual_advance")
 
     def set_boundary(self, fs, Tw=500.0):
         Y = _f64(fs["Y"])

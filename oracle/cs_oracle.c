@@ -692,8 +692,28 @@ typedef struct {
     int stag_cell, have_R, iter;
     int status_cell, nclip;
     int react;                       /* 0: sources off (non-reactive runs) */
+    /* dual time stepping (Sec. 2.3, Eq. dualimplicit): physical step dt (0: steady), theta,
+     * stored physical levels Q^n, Q^{n-1} and how many of them exist (0, 1, 2) */
+    double dual_dt, dual_theta;
+    double *Qn, *Qnm1;
+    int dual_levels;
     char err[256];
 } orc_grid;
+
+/* Physical-time coefficients of the dual time-stepping residual (Sec. 2.3): the unsteady term
+ * V [(1+theta)(Q^m - Q^n) - theta (Q^n - Q^{n-1})] / dt is added to R, and (1+theta) V / dt to
+ * every diagonal.  Reading: theta multiplies a level difference that exists only from the
+ * second physical step on, so the first step after the start takes theta = 0 (implicit
+ * Euler).  Returns 0 when dual time stepping is off or no physical step has begun. */
+static int dual_coeffs(const orc_grid *G, double *a, double *b)
+{
+    *a = *b = 0.0;
+    if (!(G->dual_dt > 0.0) || G->dual_levels < 1) return 0;
+    double th = G->dual_levels >= 2 ? G->dual_theta : 0.0;
+    *a = (1.0 + th) / G->dual_dt;
+    *b = th / G->dual_dt;
+    return 1;
+}
 
 static int fidx(const orc_grid *G, int d, int i, int j, int k)
 {
@@ -1358,6 +1378,12 @@ static int residual(orc_grid *G)
         const prim_t *w = &G->w[c];
         for (int s = 0; s < ns; s++) r[s] -= G->V[c] * w->omega[s];
         if (G->gas.ntemp == 2) r[ns + nd + 1] -= G->V[c] * w->omega_v;
+        double da, db;
+        if (dual_coeffs(G, &da, &db))
+            for (int v = 0; v < nq; v++) {
+                size_t x = (size_t)v * G->ncell + c;
+                r[v] += G->V[c] * (da * (G->Q[x] - G->Qn[x]) - db * (G->Qn[x] - G->Qnm1[x]));
+            }
         for (int v = 0; v < nq; v++) G->R[(size_t)v * G->ncell + c] = r[v];
         /* residual monitors (Sec. 3.2; reading: L2 over cells of R/V) */
         for (int s = 0; s < ns; s++) rs += (r[s] / G->V[c]) * (r[s] / G->V[c]);
@@ -1419,6 +1445,8 @@ static void spectral(orc_grid *G, double cfl)
             sCI += G->lamCI[3 * c + d];
         }
         double Vdt = sumdt / cfl;                  /* V / dtau */
+        double da, db;
+        if (dual_coeffs(G, &da, &db)) Vdt += da * G->V[c];   /* + (1+theta) V / dt */
         G->DF[c] = Vdt + sF;
         G->DFev[c] = Vdt + sF + G->V[c] * w->relax;
         for (int s = 0; s < ns; s++)
@@ -1872,6 +1900,36 @@ int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
 /* update limit f (see correct_update); 0 switches it off */
 int orc_set_update_limit(orc_grid *G, double f) { if (!(f >= 0.0)) return 1; G->update_limit = f; return 0; }
 
+/* dual time stepping: physical step dt (0 switches it off) and theta >= 0; the stored levels
+ * are discarded (the next orc_dual_advance starts from the current state) */
+int orc_set_dual(orc_grid *G, double dt, double theta)
+{
+    if (!(dt >= 0.0) || !(theta >= 0.0)) return 1;
+    size_t n = (size_t)G->nq * G->ncell;
+    if (dt > 0.0 && !G->Qn) {
+        G->Qn = calloc(n, sizeof(double));
+        G->Qnm1 = calloc(n, sizeof(double));
+        if (!G->Qn || !G->Qnm1) return 1;
+    }
+    G->dual_dt = dt;
+    G->dual_theta = theta;
+    G->dual_levels = 0;
+    G->have_R = 0;
+    return 0;
+}
+
+/* begin a physical time step from the current state: Q^{n-1} <- Q^n, Q^n <- Q */
+int orc_dual_advance(orc_grid *G)
+{
+    if (!(G->dual_dt > 0.0) || !G->Qn) return 1;
+    size_t n = (size_t)G->nq * G->ncell;
+    memcpy(G->Qnm1, G->Qn, n * sizeof(double));
+    memcpy(G->Qn, G->Q, n * sizeof(double));
+    if (G->dual_levels < 2) G->dual_levels++;
+    G->have_R = 0;
+    return 0;
+}
+
 void orc_destroy(orc_grid *G)
 {
     if (!G) return;
@@ -1879,6 +1937,7 @@ void orc_destroy(orc_grid *G)
     free(G->V); free(G->xc); free(G->Q); free(G->R); free(G->dQs); free(G->dQ); free(G->dQci_s);
     free(G->dQci); free(G->w); free(G->grad); free(G->lamF); free(G->lamC); free(G->lamCI);
     free(G->DF); free(G->DFev); free(G->Ds); free(G->DLU); free(G->piv);
+    free(G->Qn); free(G->Qnm1);
     free(G);
 }
 
