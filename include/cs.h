@@ -190,6 +190,25 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * Errors: CS_ERR_ARG for an unknown name or a negative / NaN update_limit. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
+/* Dual time stepping for unsteady flow (Sec. 2.3, the dual-time form of the implicit scheme).
+ * With a physical step dt > 0 every residual (cs_residual, cs_step, batches) becomes
+ *   R + V [(1+theta)(Q - Q^n) - theta (Q^n - Q^{n-1})] / dt
+ * (its monitors too: the pseudo-time iterations converge it to zero) and (1+theta) V / dt is
+ * added to every diagonal of both operators, where Q^n and Q^{n-1} are the last two physical
+ * time levels.  theta = 0 is the implicit Euler step, theta = 1/2 the second-order three-level
+ * backward difference (theta = 2, which the paper names for second order, is first order by
+ * Taylor expansion).  cs_set_dual allocates the two levels on first use (2 x nq x ncell
+ * doubles, library-owned), discards any stored levels and leaves the scheme steady until
+ * cs_dual_advance begins the first physical step; dt = 0 switches dual time stepping off.
+ * cs_dual_advance begins a physical step from the current state (Q^{n-1} <- Q^n, Q^n <- Q,
+ * enqueued on the grid's stream); the first step after cs_set_dual uses theta = 0 (no
+ * Q^{n-1} exists yet), the following ones theta.  A user loop: cs_set_dual once, then per
+ * physical step cs_dual_advance and cs_step until the inner residual has dropped.
+ * Errors: CS_ERR_ARG for a negative or non-finite dt or theta; CS_ERR_OOM if the levels cannot
+ * be allocated; cs_dual_advance: CS_ERR_STATE while dual time stepping is off. */
+cs_status cs_set_dual(cs_grid g, double dt, double theta);
+cs_status cs_dual_advance(cs_grid g);
+
 /* Residual monitors without device allocation (no counterpart in the paper: a service for
  * callers that cannot allocate device memory, e.g. an application whose memory pool already
  * holds the device, or monitoring code that must not let cudaMalloc / cudaFree synchronise the
@@ -269,7 +288,8 @@ cs_status cs_mlp_train_step(cs_mlp m, const float *X_dev, const float *T_dev, in
 const char *cs_mlp_last_error(cs_mlp m);
 
 /* Solver coupling.  cs_surrogate_sample writes, for every cell of g, the raw features
- * [log10 rho, T / 1e4, Tv / 1e4, Y_1 .. Y_11] (X_dev, FP32 [N][14]) and the raw targets
+ * [log10 rho, log10 T, log10 Tv, log10(Y_1 + 1e-10) .. log10(Y_11 + 1e-10)] (X_dev, FP32
+ * [N][14]; -10 beyond the model's species) and the raw targets
  * [asinh(omega_s), asinh(d omega_s / d rho_s)] (T_dev, FP32 [N][22]; SI units, the derivative
  * at fixed other conserved variables as in the operator; zero beyond the model's species) of
  * the last primitive evaluation (after cs_residual or cs_step).

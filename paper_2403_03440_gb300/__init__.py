@@ -97,7 +97,8 @@ class cs_step_stats(C.Structure):
 EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary",
            "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
-           "cs_gas_info", "cs_profile", "cs_set_option", "cs_residual_norms_static",
+           "cs_gas_info", "cs_profile", "cs_set_option", "cs_set_dual", "cs_dual_advance",
+           "cs_residual_norms_static",
            "cs_last_error", "cs_batch_create", "cs_batch_destroy", "cs_batch_tune",
            "cs_batch_step", "cs_batch_stream", "cs_batch_last_error", "cs_mlp_create",
            "cs_mlp_destroy", "cs_mlp_get_params", "cs_mlp_forward", "cs_mlp_grad",
@@ -132,6 +133,8 @@ def lib():
     L.cs_gas_info.argtypes = [C.c_int, dp, dp, ip]
     L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
     L.cs_set_option.argtypes = [vp, C.c_char_p, C.c_double]
+    L.cs_set_dual.argtypes = [vp, C.c_double, C.c_double]
+    L.cs_dual_advance.argtypes = [vp]
     L.cs_last_error.argtypes = [vp]
     L.cs_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
     L.cs_batch_destroy.argtypes = [vp]
@@ -310,6 +313,14 @@ class Grid:
 
     def set_option(self, name, value):
         self._check(lib().cs_set_option(self._h, name.encode(), float(value)), "cs_set_option")
+
+    def set_dual(self, dt, theta=0.0):
+        """Dual time stepping with physical step dt (0: steady) and coefficient theta."""
+        self._check(lib().cs_set_dual(self._h, float(dt), float(theta)), "cs_set_dual")
+
+    def dual_advance(self):
+        """Begin a physical time step from the current state (Q^{n-1} <- Q^n <- Q)."""
+        self._check(lib().cs_dual_advance(self._h), "cs_dual_advance")
 
     def profile(self, enable):
         """Return {phase: (ms, launches)} accumulated since the last call; (re)arm timing."""

@@ -1,5 +1,6 @@
 // C ABI of the library (include/cs.h): grid objects, device memory, geometry kernels and the
 // host-side sequencing of the iteration (Sec. 2.2-2.3 of arXiv:2403.03440).
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -166,6 +167,8 @@ struct cs_grid_s {
   float *sx = nullptr, *sy = nullptr;   // its inputs [N][14] and outputs [N][22]
   double* snorm = nullptr;    // standardisation [14 + 14 + 22 + 22]
   double* h_pin = nullptr;    // pinned host scratch [64]
+  double dual_dt = 0.0, dual_theta = 0.0;   // dual time stepping (dt 0: steady)
+  int dual_levels = 0;        // physical levels stored (0, 1, 2)
   int* h_status = nullptr;    // pinned [4]
   int stag = -1;
   int have_R = 0, have_bc = 0, iter = 0;
@@ -822,6 +825,55 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   return fail(g, CS_ERR_ARG, "unknown option %s", name);
 }
 
+// Dual time stepping (Sec. 2.3): the coefficients (1+theta)/dt and theta/dt live in device
+// memory (params[1], params[2]) so that captured iterations read the current values; theta
+// takes effect from the second physical step on (the first has no Q^{n-1}).
+__global__ void k_set_dual(double* params, double a, double b) {
+  params[1] = a;
+  params[2] = b;
+}
+
+static cs_status upload_dual(cs_grid g) {
+  double a = 0.0, b = 0.0;
+  if (g->dual_dt > 0.0 && g->dual_levels >= 1) {
+    const double th = g->dual_levels >= 2 ? g->dual_theta : 0.0;
+    a = (1.0 + th) / g->dual_dt;
+    b = th / g->dual_dt;
+  }
+  k_set_dual<<<1, 1, 0, g->stream>>>(g->params, a, b);
+  CUDA_TRY(g, cudaGetLastError());
+  g->have_R = 0;
+  return CS_OK;
+}
+
+extern "C" cs_status cs_set_dual(cs_grid g, double dt, double theta) {
+  if (!g) return CS_ERR_ARG;
+  if (!(dt >= 0.0) || !(theta >= 0.0) || !std::isfinite(dt) || !std::isfinite(theta))
+    return fail(g, CS_ERR_ARG, "dual time step %g and theta %g must be finite and >= 0", dt, theta);
+  if (dt > 0.0 && !g->g.Qn) {
+    const size_t n = (size_t)g->L->nq * g->g.N;
+    double *a = nullptr, *b = nullptr;
+    if (dalloc(g, &a, n) != cudaSuccess || dalloc(g, &b, n) != cudaSuccess)
+      return fail(g, CS_ERR_OOM, "dual time levels");
+    g->g.Qn = a;
+    g->g.Qnm1 = b;
+  }
+  g->dual_dt = dt;
+  g->dual_theta = theta;
+  g->dual_levels = 0;
+  return upload_dual(g);
+}
+
+extern "C" cs_status cs_dual_advance(cs_grid g) {
+  if (!g) return CS_ERR_ARG;
+  if (!(g->dual_dt > 0.0) || !g->g.Qn) return fail(g, CS_ERR_STATE, "dual time stepping is off");
+  const size_t bytes = (size_t)g->L->nq * g->g.N * sizeof(double);
+  CUDA_TRY(g, cudaMemcpyAsync(const_cast<double*>(g->g.Qnm1), g->g.Qn, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  CUDA_TRY(g, cudaMemcpyAsync(const_cast<double*>(g->g.Qn), g->g.Q, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  if (g->dual_levels < 2) ++g->dual_levels;
+  return upload_dual(g);
+}
+
 extern "C" const char* cs_last_error(cs_grid g) { return g ? g->err : "null grid"; }
 
 // ---------------------------------------------------------------------------------------
@@ -840,6 +892,7 @@ struct cs_batch_s {
   cudaGraphExec_t exec = nullptr;
   std::vector<cs_step_opts> key;       // options the graph was captured with
   std::vector<cs_mlp> key_surr;        // and the networks attached then
+  std::vector<const double*> key_dual; // and the dual-time level buffers then
   int key_k = 0;
   char err[512] = {0};
 };
@@ -1008,7 +1061,8 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
     }
     bool recapture = !b->exec || b->key_k != iters_per_graph || (int)b->key.size() != n;
     for (int c = 0; c < n && !recapture; ++c)
-      recapture = !same_opts(b->key[c], opts[c]) || b->key_surr[c] != b->grids[c]->surr;
+      recapture = !same_opts(b->key[c], opts[c]) || b->key_surr[c] != b->grids[c]->surr ||
+                  b->key_dual[c] != b->grids[c]->g.Qn;
     if (recapture) {
       if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
       BCUDA_TRY(b, cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
@@ -1039,6 +1093,8 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
       b->key.assign(opts, opts + n);
       b->key_surr.clear();
       for (int c = 0; c < n; ++c) b->key_surr.push_back(b->grids[c]->surr);
+      b->key_dual.clear();
+      for (int c = 0; c < n; ++c) b->key_dual.push_back(b->grids[c]->g.Qn);
       b->key_k = iters_per_graph;
     }
     // per-case setup on the case streams: status cleared, ramp counter = iterations done

@@ -72,7 +72,9 @@ struct DevGrid {
   void* wrecs;            // species-group records [groups][N][kRecS]
   void* wbase;            // forward results in hyperplane order: flow [N][8], species [groups][N][4]
   int* status;            // [0] code, [1] cell, [2] clip count
-  const double* params;   // [0] cfl
+  const double* params;   // [0] cfl, [1] (1+theta)/dt, [2] theta/dt (dual time; 0: steady)
+  const double* Qn;       // dual time stepping: physical levels Q^n, Q^{n-1} [nq][N] (or null)
+  const double* Qnm1;
 };
 
 __device__ __forceinline__ void set_status(const DevGrid& g, int code, int cell) {
@@ -1219,6 +1221,16 @@ __global__ void __launch_bounds__(256) k_assemble(DevGrid g) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) r[s] -= V * g.W[(A::OM + s) * N + c];
     if (G::NTEMP == 2) r[NQ - 1] -= V * g.W[A::OMV * N + c];
+    // dual time stepping (Sec. 2.3): + V [(1+theta)(Q - Q^n) - theta (Q^n - Q^{n-1})] / dt
+    const double da = g.params[1];
+    if (da > 0.0) {
+      const double db = g.params[2];
+#pragma unroll
+      for (int v = 0; v < NQ; ++v) {
+        const double qn = g.Qn[v * N + c];
+        r[v] += V * (da * (g.Q[v * N + c] - qn) - db * (qn - g.Qnm1[v * N + c]));
+      }
+    }
 #pragma unroll
     for (int v = 0; v < NQ; ++v) g.R[v * N + c] = r[v];
     const double iV = 1.0 / V;
@@ -1338,7 +1350,8 @@ __global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
     sC += lC;
     sCI += lCI;
   }
-  const double Vdt = sumdt / g.params[0];
+  // V / dtau, plus (1+theta) V / dt under dual time stepping (every diagonal carries it)
+  const double Vdt = sumdt / g.params[0] + g.params[1] * V;
   g.Vdt[c] = Vdt;
   const double DF = Vdt + sF, DFev = Vdt + sF + V * W[A::RELAX * N + c];
   g.DF[c] = DF;
@@ -2697,11 +2710,14 @@ template <class G, int ND>
 __device__ __forceinline__ void surr_raw_features(const DevGrid& g, int c, float* f) {
   using A = Aux<G, ND>;
   const size_t N = g.N;
+  // logarithms throughout: the rates are Arrhenius in T and mass-action in the densities, and
+  // trace species span many decades (1e-10 floors the mass fractions)
   f[0] = (float)log10(g.W[A::RHO * N + c]);
-  f[1] = (float)(g.W[A::T * N + c] * 1e-4);
-  f[2] = (float)(g.W[A::TV * N + c] * 1e-4);
+  f[1] = (float)log10(g.W[A::T * N + c]);
+  f[2] = (float)log10(g.W[A::TV * N + c]);
 #pragma unroll
-  for (int s = 0; s < kSurrNS; ++s) f[3 + s] = s < G::NS ? (float)g.W[(A::Y + s) * N + c] : 0.f;
+  for (int s = 0; s < kSurrNS; ++s)
+    f[3 + s] = s < G::NS ? (float)log10(fmax(g.W[(A::Y + s) * N + c], 0.0) + 1e-10) : -10.f;
 }
 
 // raw features [N][14] and raw targets [N][22] of every cell (from the auxiliary fields of the

@@ -49,8 +49,9 @@ def test_samples_match_oracle_fields():
     X, T = X.cpu().numpy(), T.cpu().numpy()
     rho = ref.field("rho")[:N]
     Y = ref.get_state()[:11] / rho
-    want_x = np.concatenate([np.log10(rho)[:, None], ref.field("T")[:N, None] * 1e-4,
-                             ref.field("Tv")[:N, None] * 1e-4, Y.T], axis=1)
+    want_x = np.concatenate([np.log10(rho)[:, None], np.log10(ref.field("T")[:N, None]),
+                             np.log10(ref.field("Tv")[:N, None]),
+                             np.log10(np.maximum(Y.T, 0.0) + 1e-10)], axis=1)
     assert np.max(np.abs(X - want_x) / np.maximum(np.abs(want_x), 1e-3)) < 1e-5
     om = ref.field("omega").reshape(11, -1)[:, :N].T
     dom = ref.field("dom").reshape(11, -1)[:, :N].T
