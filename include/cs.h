@@ -290,14 +290,16 @@ const char *cs_mlp_last_error(cs_mlp m);
 /* Solver coupling.  cs_surrogate_sample writes, for every cell of g, the raw features
  * [log10 rho, log10 T, log10 Tv, log10(Y_1 + 1e-10) .. log10(Y_11 + 1e-10)] (X_dev, FP32
  * [N][14]; -10 beyond the model's species) and the raw targets
- * [asinh(omega_s), asinh(d omega_s / d rho_s)] (T_dev, FP32 [N][22]; SI units, the derivative
- * at fixed other conserved variables as in the operator; zero beyond the model's species) of
- * the last primitive evaluation (after cs_residual or cs_step).
+ * [asinh(omega_s), asinh(max(0, -d omega_s / d rho_s))] (T_dev, FP32 [N][22]; SI units, the
+ * derivative at fixed other conserved variables as in the operator, of which the operator uses
+ * only this stiffness part; zero beyond the model's species) of the last primitive evaluation
+ * (after cs_residual or cs_step).
  * cs_surrogate_attach makes every later iteration of g take the species Jacobian diagonal of
  * the split operator from the network instead of the exact chemistry (whose Jacobian is then
  * not evaluated; the residual keeps the exact source): inputs are standardised as
  * (raw - mean) / std with norm_host = [mean[14], std[14], target mean[22], target std[22]],
- * outputs de-standardised and passed through sinh.  The network must hold at least N rows
+ * outputs de-standardised, held to [max(0, mean - 8 std), mean + 8 std] and passed through
+ * sinh to give d omega_s / d rho_s = -sinh(t).  The network must hold at least N rows
  * (max_batch) and must not serve two grids that run at the same time.  cs_surrogate_detach
  * returns to the exact chemistry.  Errors: CS_ERR_ARG (null, too small a network, a std <= 0),
  * CS_ERR_OOM. */

@@ -285,3 +285,29 @@ def mlp_init(seed=0):
         parts.append(rng.uniform(-a, a, nout * nin))
         parts.append(np.zeros(nout))
     return np.concatenate(parts).astype(np.float32)
+
+
+def species_box(ns, seed=0, n=(10, 10, 10), size=(1.0, 1.0, 1.0)):
+    """Uniform non-reacting flow of ns species in a Cartesian box, far field on every side
+    (the species-count scaling test of Sec. 3.1).  Species s has molar mass M[s] (kg/kmol,
+    log-uniform in [2, 100]) and dof[s] translational-rotational degrees of freedom (3 or 5,
+    equally likely); mass fractions Y are a seeded Dirichlet(1) draw.  The flow: T = 300 K,
+    p = 1e4 Pa, velocity (600, 300, 150) m/s, so that it crosses every face family."""
+    rng = np.random.default_rng(seed)
+    M = np.exp(rng.uniform(math.log(2.0), math.log(100.0), ns))
+    dof = np.where(rng.uniform(size=ns) < 0.5, 3.0, 5.0)
+    Y = rng.dirichlet(np.ones(ns))
+    return dict(ns=ns, M=M, dof=dof, Y=Y, T=300.0, p=1.0e4, u=np.array([600.0, 300.0, 150.0]),
+                n=tuple(n), size=tuple(size))
+
+
+def species_box_rhs(ns, ncell, seed=0):
+    """Seeded right-hand side [ns + 4][ncell] (rho_1..rho_ns, m_x, m_y, m_z, rho E) for the
+    implicit operator of the species box: uniform in [-1, 1] times 1e-4 (species), 1e-1
+    (momentum) and 1e2 (energy) per unit volume scale."""
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(-1.0, 1.0, (ns + 4, ncell))
+    r[:ns] *= 1e-4
+    r[ns:ns + 3] *= 1e-1
+    r[ns + 3] *= 1e2
+    return r

@@ -2735,7 +2735,9 @@ __global__ void __launch_bounds__(128) k_surr_sample(DevGrid g, float* X, float*
 #pragma unroll
   for (int s = 0; s < kSurrNS; ++s) {
     T[(size_t)c * kSurrOut + s] = s < G::NS ? (float)asinh(g.W[(A::OM + s) * N + c]) : 0.f;
-    T[(size_t)c * kSurrOut + kSurrNS + s] = s < G::NS ? (float)asinh(g.W[(A::DOM + s) * N + c]) : 0.f;
+    // the part of d omega_s / d rho_s the operator uses: its stiffness max(0, -d omega / d rho)
+    T[(size_t)c * kSurrOut + kSurrNS + s] =
+        s < G::NS ? (float)asinh(fmax(0.0, -g.W[(A::DOM + s) * N + c])) : 0.f;
   }
 }
 
@@ -2765,12 +2767,13 @@ __global__ void __launch_bounds__(128) k_surr_decode(DevGrid g, const float* Y, 
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
     const int o = kSurrNS + s;
-    // de-standardised and held to the span of the training targets (mean +- 8 standard
-    // deviations of asinh(d omega / d rho)); a non-finite output maps to the lower bound, which
-    // only adds to the operator's diagonal
-    const double t = fmin(fmax((double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o], mt[o] - 8.0 * st[o]),
-                          mt[o] + 8.0 * st[o]);
-    g.W[(A::DOM + s) * N + c] = sinh(t);
+    // de-standardised stiffness asinh(max(0, -d omega / d rho)), held to the span of the
+    // training targets (mean +- 8 standard deviations, and >= 0); a non-finite output maps to
+    // the upper bound, which only adds to the operator's diagonal
+    const double y = (double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o];
+    const double hi = mt[o] + 8.0 * st[o];
+    const double t = y == y ? fmin(fmax(y, fmax(0.0, mt[o] - 8.0 * st[o])), hi) : hi;
+    g.W[(A::DOM + s) * N + c] = -sinh(t);
   }
 }
 

@@ -214,14 +214,22 @@ __global__ void __launch_bounds__(kThreads) k_gemm(const bf16* __restrict__ A, i
 constexpr int LNH = CS_MLP_HIDDEN, LKIN = 16, LNOUTP = 32;
 
 // Fused inference: the whole network on 128-row tiles of a persistent grid.  Each CTA stages
-// the bfloat16 weights into shared memory once (canonical K-major layout, 76 KB), then per
-// tile: inputs -> bf16 tile, and for each layer one tcgen05.mma group into tensor memory,
-// tcgen05.ld, bias (+ SiLU), bf16 back into shared memory as the next layer's A operand; the
-// last layer's FP32 outputs go to Y [n][22].  No activation leaves the SM.
+// the bfloat16 weights and the biases into shared memory once (canonical K-major layout,
+// 76 KB + 1.6 KB), then per tile: inputs -> bf16 tile, and for each layer one tcgen05.mma group
+// into tensor memory, tcgen05.ld, bias (+ SiLU), bf16 back into shared memory as the next
+// layer's A operand; the last layer's FP32 outputs go to Y [n][22].  No activation leaves the
+// SM.  8 warps: warp w reads tensor-memory lanes 32 (w % 4) .. +31 (the rows it may access)
+// and columns 64 (w / 4) .. +63 of the accumulator.  The input tile lives in the first 4 KB of
+// the activation tile: layer 1's MMA has completed (mbarrier) before its epilogue overwrites
+// it, and the next tile's inputs are written after layer 4's MMA has completed.  Two CTAs fit
+// on an SM (shared memory), so one CTA's MMAs overlap the other's epilogue.
+constexpr int kFuseThreads = 256;
 constexpr int kFuseSmemW = (LNH * LKIN + 2 * LNH * LNH + LNOUTP * LNH) * 2;   // 77824 B
 constexpr int kFuseSmemA = kTileM * LNH * 2;                                   // 32768 B
-constexpr int kFuseSmemX = kTileM * LKIN * 2;                                  // 4096 B
-constexpr int kFuseSmemBytes = kFuseSmemW + kFuseSmemA + kFuseSmemX + 64;
+constexpr int kFuseSmemB = (3 * LNH + LNOUTP) * 4;                             // 1664 B
+constexpr int kFuseSmemBytes = kFuseSmemW + kFuseSmemA + kFuseSmemB + 64;
+static_assert(kTileM * LKIN * 2 <= kFuseSmemA, "input tile inside the activation tile");
+static_assert(2 * (kFuseSmemBytes + 1024) <= 228 * 1024, "two CTAs per SM");
 
 // stage rows [0, rows) x [0, K) of a row-major bf16 matrix into the canonical K-major layout
 __device__ __forceinline__ void stage_kmajor(const bf16* src, int rows, int K, unsigned char* dst) {
@@ -260,23 +268,27 @@ __device__ __forceinline__ bool fused_layer(uint32_t tmem, uint32_t a0, uint32_t
   return !__syncthreads_or(!ok);
 }
 
-// hidden-layer epilogue: row r = thread, N = 128 columns: bias + SiLU -> bf16 into the A tile
-__device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float* __restrict__ bias,
-                                                      unsigned char* A) {
-  const int warp = threadIdx.x >> 5, r = threadIdx.x;
-  for (int c0 = 0; c0 < LNH; c0 += 32) {
+// hidden-layer epilogue of this warp's 32 rows x 64 columns: bias + SiLU -> bf16 into the A tile
+__device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float* bias, unsigned char* A) {
+  const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
+  const int r = 32 * q + (threadIdx.x & 31);
+#pragma unroll
+  for (int cc = 0; cc < 2; ++cc) {
+    const int c0 = 64 * h + 32 * cc;
     float v[32];
-    tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
 #pragma unroll
     for (int g8 = 0; g8 < 4; ++g8) {
       uint32_t w[4];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int n0 = c0 + g8 * 8 + 2 * h;
-        const float z0 = v[g8 * 8 + 2 * h] + bias[n0], z1 = v[g8 * 8 + 2 * h + 1] + bias[n0 + 1];
-        const bf16 b0 = __float2bfloat16_rn(z0 / (1.f + __expf(-z0)));
-        const bf16 b1 = __float2bfloat16_rn(z1 / (1.f + __expf(-z1)));
-        w[h] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+      for (int e = 0; e < 4; ++e) {
+        const int n0 = c0 + g8 * 8 + 2 * e;
+        const float z0 = v[g8 * 8 + 2 * e] + bias[n0], z1 = v[g8 * 8 + 2 * e + 1] + bias[n0 + 1];
+        // silu(z) = z / (1 + e^-z); the approximate division returns 0 once e^-z exceeds
+        // 2^126, the function's limit there
+        const bf16 o0 = __float2bfloat16_rn(__fdividef(z0, 1.f + __expf(-z0)));
+        const bf16 o1 = __float2bfloat16_rn(__fdividef(z1, 1.f + __expf(-z1)));
+        w[e] = (uint32_t)__bfloat16_as_ushort(o0) | ((uint32_t)__bfloat16_as_ushort(o1) << 16);
       }
       const int c8 = (c0 >> 3) + g8;
       *reinterpret_cast<uint4*>(A + (c8 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
@@ -285,20 +297,21 @@ __device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_mlp_infer(const float* __restrict__ X, int n,
-                                                        const bf16* __restrict__ W1, const bf16* __restrict__ W2,
-                                                        const bf16* __restrict__ W3, const bf16* __restrict__ W4,
-                                                        const float* __restrict__ b1, const float* __restrict__ b2,
-                                                        const float* __restrict__ b3, const float* __restrict__ b4,
-                                                        float* __restrict__ Y, int* err) {
+__global__ void __launch_bounds__(kFuseThreads) k_mlp_infer(const float* __restrict__ X, int n,
+                                                            const bf16* __restrict__ W1, const bf16* __restrict__ W2,
+                                                            const bf16* __restrict__ W3, const bf16* __restrict__ W4,
+                                                            const float* __restrict__ b1, const float* __restrict__ b2,
+                                                            const float* __restrict__ b3, const float* __restrict__ b4,
+                                                            float* __restrict__ Y, int* err) {
   extern __shared__ __align__(128) unsigned char fsm[];
   unsigned char* sW1 = fsm;
   unsigned char* sW2 = sW1 + LNH * LKIN * 2;
   unsigned char* sW3 = sW2 + LNH * LNH * 2;
   unsigned char* sW4 = sW3 + LNH * LNH * 2;
   unsigned char* sA = fsm + kFuseSmemW;
-  unsigned char* sX = sA + kFuseSmemA;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sX + kFuseSmemX);
+  unsigned char* sX = sA;                     // the input tile aliases the activation tile
+  float* sB = reinterpret_cast<float*>(sA + kFuseSmemA);   // b1 | b2 | b3 | b4 (padded to 32)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sA + kFuseSmemA + kFuseSmemB);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
   const int tid = threadIdx.x, warp = tid >> 5;
   const uint32_t barA = smem_u32(bar);
@@ -312,6 +325,10 @@ __global__ void __launch_bounds__(kThreads) k_mlp_infer(const float* __restrict_
   stage_kmajor(W2, LNH, LNH, sW2);
   stage_kmajor(W3, LNH, LNH, sW3);
   stage_kmajor(W4, LNOUTP, LNH, sW4);
+  for (int k = tid; k < 3 * LNH + LNOUTP; k += kFuseThreads) {
+    const int l = k / LNH, o = k - l * LNH;
+    sB[k] = l == 0 ? b1[o] : (l == 1 ? b2[o] : (l == 2 ? b3[o] : (o < 22 ? b4[o] : 0.f)));
+  }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -322,37 +339,36 @@ __global__ void __launch_bounds__(kThreads) k_mlp_infer(const float* __restrict_
   const int ntiles = (n + kTileM - 1) / kTileM;
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int row0 = tile * kTileM;
-    // inputs: thread r owns row r; 14 features + 2 zero columns as bf16, canonical layout
+    // inputs: thread (row r, half h) converts features 8h .. 8h+7 of row r (14 features and 2
+    // zero columns) to bf16, one 16-byte core-matrix row of the canonical layout
     {
-      const int r = tid, gr = row0 + r;
-      uint32_t w[8];
+      const int r = tid & (kTileM - 1), h = tid >> 7, gr = row0 + r;
+      uint32_t w[4];
 #pragma unroll
-      for (int h = 0; h < 8; ++h) {
-        const int k0 = 2 * h, k1 = 2 * h + 1;
+      for (int e = 0; e < 4; ++e) {
+        const int k0 = 8 * h + 2 * e, k1 = k0 + 1;
         const float x0 = (gr < n && k0 < 14) ? X[(size_t)gr * 14 + k0] : 0.f;
         const float x1 = (gr < n && k1 < 14) ? X[(size_t)gr * 14 + k1] : 0.f;
-        w[h] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
+        w[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
       }
-      *reinterpret_cast<uint4*>(sX + (0 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
+      *reinterpret_cast<uint4*>(sX + (h * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
           make_uint4(w[0], w[1], w[2], w[3]);
-      *reinterpret_cast<uint4*>(sX + (1 * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
-          make_uint4(w[4], w[5], w[6], w[7]);
     }
     if (!fused_layer(tmem, sXu, smem_u32(sW1), LNH, LKIN, barA, phase)) { failed = true; break; }
-    fused_hidden_epilogue(tmem, b1, sA);
+    fused_hidden_epilogue(tmem, sB, sA);
     if (!fused_layer(tmem, sAu, smem_u32(sW2), LNH, LNH, barA, phase)) { failed = true; break; }
-    fused_hidden_epilogue(tmem, b2, sA);
+    fused_hidden_epilogue(tmem, sB + LNH, sA);
     if (!fused_layer(tmem, sAu, smem_u32(sW3), LNH, LNH, barA, phase)) { failed = true; break; }
-    fused_hidden_epilogue(tmem, b3, sA);
+    fused_hidden_epilogue(tmem, sB + 2 * LNH, sA);
     if (!fused_layer(tmem, sAu, smem_u32(sW4), LNOUTP, LNH, barA, phase)) { failed = true; break; }
-    {
+    if (warp < 4) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
       const int gr = row0 + tid;
       if (gr < n)
 #pragma unroll
-        for (int o = 0; o < 22; ++o) Y[(size_t)gr * 22 + o] = v[o] + b4[o];
+        for (int o = 0; o < 22; ++o) Y[(size_t)gr * 22 + o] = v[o] + sB[3 * LNH + o];
     }
     // the next tile's first MMA overwrites the accumulators: every warp has read them
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -615,7 +631,7 @@ static void infer(cs_mlp m, const float* X, int n, float* Y, cudaStream_t st) {
   const int ntiles = (n + kTileM - 1) / kTileM;
   const int grid = ntiles < 2 * g_num_sms ? ntiles : 2 * g_num_sms;
   const Weights& w = m->w;
-  k_mlp_infer<<<grid, kThreads, kFuseSmemBytes, st>>>(X, n, w.W1, w.W2, w.W3, w.W4, w.b1, w.b2,
+  k_mlp_infer<<<grid, kFuseThreads, kFuseSmemBytes, st>>>(X, n, w.W1, w.W2, w.W3, w.W4, w.b1, w.b2,
                                                       w.b3, w.b4, Y, m->err);
 }
 static cs_status check_err(cs_mlp m, const char* what) {

@@ -118,22 +118,22 @@ def predict(net, X, norm):
 
 
 def calibrate(net, norm, val, q=0.95):
-    """Shift the decoded diagonal towards more damping by the q-quantile of the network's
-    under-prediction on held-out samples, per species: where the exact d omega_s / d rho_s is
-    a large negative number (the stiff cells, asinh < -1), the amount by which the prediction
-    falls short of it in asinh space.  An under-predicted diagonal lets a stiff species
-    increment overshoot; an over-predicted one only slows that species' convergence.
-    Returns the shifted standardisation vector and the shifts."""
+    """Shift the decoded stiffness towards more damping by the q-quantile of the network's
+    under-prediction on held-out samples, per species: where the exact stiffness
+    max(0, -d omega_s / d rho_s) is large (asinh > 1), the amount by which the prediction falls
+    short of it in asinh space.  An under-predicted diagonal lets a stiff species increment
+    overshoot; an over-predicted one only slows that species' convergence.  Returns the
+    shifted standardisation vector and the shifts."""
     Xv, Tv = val
     t = Tv[:, 11:].astype(np.float64)
     y = predict(net, Xv, norm)[:, 11:]
     shift = np.zeros(11)
     for s in range(11):
-        stiff = t[:, s] < -1.0
+        stiff = t[:, s] > 1.0
         if stiff.sum() >= 20:
-            shift[s] = max(0.0, float(np.quantile(y[stiff, s] - t[stiff, s], q)))
+            shift[s] = max(0.0, float(np.quantile(t[stiff, s] - y[stiff, s], q)))
     out = norm.copy()
-    out[28 + 11:50] -= shift
+    out[28 + 11:50] += shift
     return out, shift
 
 

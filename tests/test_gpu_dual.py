@@ -27,30 +27,34 @@ def _device():
 MECH = inputs.MECH_AIR11
 
 
-def half_cylinder_pair(seed=2):
+def half_cylinder_pair(mech):
+    """Impulsive start of a Mach 10 flow over the half cylinder (a moving, strongly unsteady
+    start-up), oracle and CUDA path from the same freestream state."""
     nodes = inputs.cylinder_half(25, 16)
     bc = inputs.cylinder_half_bc()
-    fs = inputs.freestream(MECH, T=300.0, p=500.0, mach=10.0)
-    ref = oracle.OracleGrid(nodes, bc, MECH)
+    fs = inputs.freestream(mech, T=300.0, p=500.0, mach=10.0)
+    ref = oracle.OracleGrid(nodes, bc, mech)
     ref.set_boundary(fs, Tw=500.0)
-    gpu = P.Grid(nodes, bc, MECH)
+    gpu = P.Grid(nodes, bc, mech)
     gpu.set_boundary(fs, Tw=500.0)
-    pr = inputs.perturbed_primitive(MECH, (ref.nj, ref.ni), seed=seed, ndim=2, T=6000.0,
-                                    Tv=4500.0, p=8000.0)
-    Q = oracle.prim_to_cons_field(MECH, 2, pr)
+    Q = ref.freestream_state()
     ref.set_state(Q)
     gpu.set_state(Q)
     return ref, gpu
 
 
-@pytest.mark.parametrize("scheme,corr,theta", [(0, 1, 0.5), (0, 2, 0.0), (1, 1, 0.5)])
-def test_physical_steps_match_oracle(scheme, corr, theta):
-    """Three physical steps of 4 inner iterations each (the third with theta active)."""
-    ref, gpu = half_cylinder_pair()
-    dt = 2e-6
+@pytest.mark.parametrize("mech,scheme,corr,theta", [(MECH, 0, 1, 0.5), (inputs.MECH_AIR5, 0, 2, 0.0),
+                                                    (inputs.MECH_AIR5, 1, 1, 0.5)])
+def test_physical_steps_match_oracle(mech, scheme, corr, theta):
+    """Three physical steps of 4 inner iterations each (the later ones with theta active).
+    dt = 1 us is below the pseudo time step of the outer cells and above that of the wall
+    cells, so both terms of the diagonal matter."""
+    ref, gpu = half_cylinder_pair(mech)
+    dt = 1e-6
     ref.set_dual(dt, theta)
     gpu.set_dual(dt, theta)
-    kw = dict(scheme=scheme, correction=corr, clip=1, cfl=5.0, cfl_start=1.0, ramp_iters=8,
+    cfl = 2.0 if mech == MECH else 5.0
+    kw = dict(scheme=scheme, correction=corr, clip=1, cfl=cfl, cfl_start=0.5, ramp_iters=8,
               iters=4)
     for _ in range(3):
         ref.dual_advance()
@@ -93,7 +97,14 @@ def test_reactor_converged_steps_match_oracle(precision):
         ref.step(**kw)
         gpu.step(precision=precision, **kw)
     tol = 1e-10 if precision == 0 else 1e-8
-    assert rel(gpu.get_state(), ref.get_state(), ns=ref.ns) < tol
+    a, b = gpu.get_state(), ref.get_state()
+    # the flow moves along x: the y momentum is zero up to rounding noise on both sides, so
+    # the momentum rows share the momentum magnitude as their scale
+    ns = ref.ns
+    scale = np.abs(b).max(axis=1)
+    scale[:ns] = scale[:ns].max()
+    scale[ns:ns + 2] = np.abs(b[ns:ns + 2]).max()
+    assert np.max(np.abs(a - b).max(axis=1) / scale) < tol
 
 
 def test_dual_in_a_batch_equals_stepping_alone():

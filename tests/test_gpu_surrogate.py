@@ -55,7 +55,7 @@ def test_samples_match_oracle_fields():
     assert np.max(np.abs(X - want_x) / np.maximum(np.abs(want_x), 1e-3)) < 1e-5
     om = ref.field("omega").reshape(11, -1)[:, :N].T
     dom = ref.field("dom").reshape(11, -1)[:, :N].T
-    want_t = np.concatenate([np.arcsinh(om), np.arcsinh(dom)], axis=1)
+    want_t = np.concatenate([np.arcsinh(om), np.arcsinh(np.maximum(0.0, -dom))], axis=1)
     assert np.max(np.abs(T - want_t)) < 1e-4 * np.max(np.abs(want_t))
 
 
@@ -80,7 +80,9 @@ def test_attached_network_sets_diagonal_not_residual():
     raw = X.cpu().numpy()
     xn = ((raw - norm[:14]) / norm[14:28]).astype(np.float32)
     y = mlp.forward(p, xn)[0].astype(np.float64)
-    d_want = np.sinh(y[:, 11:] * norm[50 + 11:72] + norm[28 + 11:50])
+    mt, st = norm[28 + 11:50], norm[50 + 11:72]
+    t = np.clip(y[:, 11:] * st + mt, np.maximum(0.0, mt - 8 * st), mt + 8 * st)
+    d_want = -np.sinh(t)
     d_got = g.field("dom").reshape(11, -1)[:, :N].T
     err = np.abs(d_got - d_want) / (np.abs(d_want) + 1e-3 * np.max(np.abs(d_want)))
     assert np.median(err) < 2e-2 and np.max(err) < 0.3
