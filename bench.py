@@ -313,6 +313,81 @@ def run_batch(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def measured_hbm_peak():
+    """(GB/s, description): the measured copy bandwidth of the GB300s, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured copy bandwidth (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s (of fallback)"
+
+
+def run_species(args, rank, world, local):
+    """Species-count scaling test (Sec. 3.1): one implicit step of the split (CS) and coupled
+    (CI) operators for a uniform non-reacting flow of ns species in a 10 x 10 x 10 box, ns from
+    16 to 4096 (CI up to 1024: its dense per-cell factors would need 134 GB at 4096).  Device
+    time per step, L2 flushed (256 MiB write) before every timed step.  value = CS time per
+    step at the largest ns; the table gives both operators, their growth against ns = 16 and
+    the speed-up (t_CI - t_CS) / t_CI the paper reports."""
+    import numpy as np
+    import torch
+    import paper_2403_03440_gb300 as P
+    P.build()
+    torch.cuda.set_device(local)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cfl = 10.0
+    table = []
+    with ClockSampler(local) as clk:
+        for ns in args.species:
+            case = inputs.species_box(ns, seed=0)
+            box = P.SpeciesBox(case)
+            rhs = torch.from_numpy(inputs.species_box_rhs(ns, box.ncell, seed=1)).cuda()
+            row = {"ns": ns}
+            for scheme, key in ((0, "cs_ms"), (1, "ci_ms")):
+                if scheme == 1 and ns > args.ci_max_species:
+                    row[key] = None
+                    continue
+                reps = args.steps if (scheme == 0 or ns <= 256) else max(3, args.steps // 10)
+                for _ in range(args.warmup if (scheme == 0 or ns <= 256) else 1):
+                    box.step(scheme, cfl, rhs)
+                row[key] = box.time(scheme, cfl, rhs, reps, flush=flush)
+            table.append(row)
+            del box
+            torch.cuda.empty_cache()
+    base = table[0]
+    for row in table:
+        row["cs_growth"] = row["cs_ms"] / base["cs_ms"]
+        if row["ci_ms"] is not None and base["ci_ms"]:
+            row["ci_growth"] = row["ci_ms"] / base["ci_ms"]
+            row["speedup_pct"] = 100.0 * (row["ci_ms"] - row["cs_ms"]) / row["ci_ms"]
+    last = table[-1]
+    # algorithmic HBM bytes of the CS step per species-cell: rhs read, forward increment
+    # written and read back, increment written (4 x 8 B); per cell the 5-unknown flow block
+    N = 1000
+    bytes_cs = N * (32 * last["ns"] + 5 * 8 * 8)
+    achieved = bytes_cs / (last["cs_ms"] / 1e3) / 1e9
+    peak = measured_hbm_peak()
+    if rank == 0:
+        line = {
+            "metric": "implicit step time (CS)", "value": last["cs_ms"], "unit": "ms",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": last["cs_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"species-box-10x10x10-nonreacting-ns{args.species[0]}-{args.species[-1]}",
+                       "cfl": cfl, "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": "single GPU"},
+            "table": table,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak[0], "unit": "GB/s",
+                         "frac": achieved / peak[0], "traffic": None, "peak_kind": peak[1],
+                         "note": "CS step at the largest ns; latency-bound (2 x 28 dependent "
+                                 "hyperplanes), bytes are the algorithmic ones"},
+            "clocks": clk.summary(),
+            "gpu_launches": 3 * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,7 +397,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch", "species"])
+    ap.add_argument("--species", type=lambda t: [int(x) for x in t.split(",")],
+                    default=[16, 64, 256, 1024, 4096])
+    ap.add_argument("--ci-max-species", type=int, default=1024)
     ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
@@ -348,6 +426,9 @@ def main():
         raise SystemExit("warmup must be >= 3")
     if args.workload == "batch":
         run_batch(args, rank, world, local)
+        return
+    if args.workload == "species":
+        run_species(args, rank, world, local)
         return
 
     import torch

@@ -313,6 +313,41 @@ cs_status cs_surrogate_detach(cs_grid g);
 cs_status cs_batch_stream(cs_batch b, void **stream_out);
 const char *cs_batch_last_error(cs_batch b);
 
+/* ---------------------------------------------------------------------------------------
+ * Species-count scaling test (Sec. 3.1): one implicit step of the split (CS) or coupled (CI)
+ * operator for a uniform, non-reacting flow of ns species in a Cartesian box, any ns.
+ * Species s is calorically perfect: molar mass M_host[s] (kg/kmol), dof_host[s] translational-
+ * rotational degrees of freedom (c_v,s = dof/2 R_u/M_s), mass fraction Y_host[s]; the flow
+ * has temperature T (K), pressure p (Pa) and velocity u_host[3] (m/s); the box has
+ * ni x nj x nk cells over size_host[3] (m), far field on every side (boundary neighbours add
+ * nothing to the sweeps).  Radii are inviscid (the flow is uniform): lambda_F = |u.S| + c|S|,
+ * lambda_C = |u.S|, V/dtau = sum lambda_F / cfl.
+ * cs_species_box_step: rhs_dev = device [ns + 4][ncell] in the conserved layout (rho_1 ..
+ * rho_ns, m_x, m_y, m_z, rho E); dQ_dev = device, split: [5 + ns][ncell] (rho, m, rho E,
+ * rho_1 .. rho_ns), coupled: [4 + ns][ncell] (rho, m, rho E, rho_2 .. rho_ns).  The coupled
+ * operator assembles and LU-factorises a dense (ns+4)^2 diagonal block per cell (library-owned,
+ * allocated on first use; refused with CS_ERR_ARG above 32 GiB).  Synchronises the box's stream.
+ * cs_species_box_time: the same step `reps` times on the box's stream, each bracketed by CUDA
+ * events and preceded (outside the events) by a write of flush_bytes to flush_dev (a device
+ * buffer larger than L2, or null with flush_bytes 0); ms_out receives the mean device time per
+ * step.  It does not check the coupled factorisation: run cs_species_box_step first.
+ * cs_species_box_state copies the box's conserved state into Q_dev ([ns + 4][ncell]).
+ * Errors: CS_ERR_ARG (sizes, ns outside 1..65536, non-positive T, p, M, dof, negative Y, host
+ * pointers where device ones are required), CS_ERR_OOM, CS_ERR_CUDA, CS_ERR_NONPHYSICAL (a
+ * singular coupled block). */
+typedef struct cs_species_box_s *cs_species_box;
+cs_status cs_species_box_create(int ns, int ni, int nj, int nk, const double *size_host,
+                                const double *M_host, const double *dof_host, const double *Y_host,
+                                double T, double p, const double *u_host, cs_species_box *out);
+cs_status cs_species_box_destroy(cs_species_box b);
+cs_status cs_species_box_state(cs_species_box b, double *Q_dev);
+cs_status cs_species_box_step(cs_species_box b, int scheme, double cfl, const double *rhs_dev,
+                              double *dQ_dev);
+cs_status cs_species_box_time(cs_species_box b, int scheme, double cfl, const double *rhs_dev,
+                              double *dQ_dev, int reps, void *flush_dev, size_t flush_bytes,
+                              double *ms_out);
+const char *cs_species_box_last_error(cs_species_box b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,7 +17,8 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libcs_gb300.so")
 SOURCES = ["launch_air11_2d.cu", "launch_air11_3d.cu", "launch_air5_2d.cu", "launch_air5_3d.cu",
-           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu", "mlp.cu"]
+           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu", "mlp.cu",
+           "species_box.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC"]
 
@@ -103,7 +104,9 @@ EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary
            "cs_batch_step", "cs_batch_stream", "cs_batch_last_error", "cs_mlp_create",
            "cs_mlp_destroy", "cs_mlp_get_params", "cs_mlp_forward", "cs_mlp_grad",
            "cs_mlp_train_step", "cs_mlp_last_error", "cs_surrogate_sample",
-           "cs_surrogate_attach", "cs_surrogate_detach"]
+           "cs_surrogate_attach", "cs_surrogate_detach", "cs_species_box_create", "cs_species_box_destroy",
+           "cs_species_box_state", "cs_species_box_step", "cs_species_box_time",
+           "cs_species_box_last_error"]
 
 _lib = None
 
@@ -134,6 +137,15 @@ def lib():
     L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
     L.cs_set_option.argtypes = [vp, C.c_char_p, C.c_double]
     L.cs_set_dual.argtypes = [vp, C.c_double, C.c_double]
+    dp = C.POINTER(C.c_double)
+    L.cs_species_box_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp,
+                                        C.c_double, C.c_double, dp, C.POINTER(vp)]
+    L.cs_species_box_destroy.argtypes = [vp]
+    L.cs_species_box_state.argtypes = [vp, vp]
+    L.cs_species_box_step.argtypes = [vp, C.c_int, C.c_double, vp, vp]
+    L.cs_species_box_time.argtypes = [vp, C.c_int, C.c_double, vp, vp, C.c_int, vp, C.c_size_t, dp]
+    L.cs_species_box_last_error.argtypes = [vp]
+    L.cs_species_box_last_error.restype = C.c_char_p
     L.cs_dual_advance.argtypes = [vp]
     L.cs_last_error.argtypes = [vp]
     L.cs_batch_create.argtypes = [C.c_int, C.POINTER(vp), C.POINTER(vp)]
@@ -441,3 +453,70 @@ class MLP:
         self._check(lib().cs_mlp_train_step(self._h, X.data_ptr(), T.data_ptr(), X.shape[0],
                                             float(lr), C.byref(loss)), "cs_mlp_train_step")
         return loss.value
+
+
+class SpeciesBox:
+    """Uniform non-reacting flow of ns species in a box: one implicit step of the split or
+    coupled operator (cs_species_box_* of the C ABI; the species-count scaling test)."""
+
+    def __init__(self, case):
+        ns = int(case["ns"])
+        self.ns = ns
+        self.n = tuple(int(x) for x in case["n"])
+        self.ncell = self.n[0] * self.n[1] * self.n[2]
+
+        def arr(a, k):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            assert a.shape == (k,)
+            return a
+        self._keep = [arr(case["size"], 3), arr(case["M"], ns), arr(case["dof"], ns),
+                      arr(case["Y"], ns), arr(case["u"], 3)]
+        size, M, dof, Y, u = self._keep
+        P = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))  # noqa: E731
+        h = C.c_void_p()
+        st = lib().cs_species_box_create(ns, *self.n, P(size), P(M), P(dof), P(Y),
+                                         float(case["T"]), float(case["p"]), P(u), C.byref(h))
+        if st:
+            raise CSError(st, "cs_species_box_create")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None:
+            try:
+                lib().cs_species_box_destroy(self._h)
+            except Exception:
+                pass
+            self._h = None
+
+    def _check(self, st, what):
+        if st:
+            raise CSError(st, f"{what}: {lib().cs_species_box_last_error(self._h).decode()}")
+
+    def state(self):
+        import torch
+        Q = torch.empty((self.ns + 4, self.ncell), dtype=torch.float64, device="cuda")
+        self._check(lib().cs_species_box_state(self._h, Q.data_ptr()), "cs_species_box_state")
+        return Q
+
+    def step(self, scheme, cfl, rhs, out=None):
+        """rhs: device float64 [ns + 4][ncell]; returns the device increments."""
+        import torch
+        n = self.ns + 5 if scheme == 0 else self.ns + 4
+        if out is None:
+            out = torch.empty((n, self.ncell), dtype=torch.float64, device="cuda")
+        self._check(lib().cs_species_box_step(self._h, scheme, float(cfl), rhs.data_ptr(),
+                                              out.data_ptr()), "cs_species_box_step")
+        return out
+
+    def time(self, scheme, cfl, rhs, reps, flush=None):
+        """Mean device ms of `reps` steps; flush: a device tensor written before each step."""
+        import torch
+        n = self.ns + 5 if scheme == 0 else self.ns + 4
+        out = torch.empty((n, self.ncell), dtype=torch.float64, device="cuda")
+        ms = C.c_double()
+        fp = flush.data_ptr() if flush is not None else None
+        fb = flush.numel() * flush.element_size() if flush is not None else 0
+        self._check(lib().cs_species_box_time(self._h, scheme, float(cfl), rhs.data_ptr(),
+                                              out.data_ptr(), int(reps), fp, fb, C.byref(ms)),
+                    "cs_species_box_time")
+        return ms.value
