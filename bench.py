@@ -42,22 +42,22 @@ WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # peak, so the roofline of this path is the FP64 ALU, not HBM; the sweeps are latency-bound
 # (one dependent hyperplane step after another).
 FP64_FLOPS_PER_CELL = {
-    "primitive": 13737.0,
+    "primitive": 13818.0,
     "gradient": 400.0,
     "flux": 2844.0,            # both directions
     "assemble": 130.0,
-    "spectral": 359.0,
+    "spectral": 361.0,
     "sweep_fwd": 474.0,        # both sweeps of all components (one cluster launch)
     "sweep_bwd": 0.0,
     "correct": 109.0,
 }
-FP32_FLOPS_PER_CELL_SWEEP = 658.0     # the FP32 wavefront sweep of the mixed-precision operator
+FP32_FLOPS_PER_CELL_SWEEP = 652.0     # the FP32 one-CTA-per-component sweep of the mixed operator
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
-    "primitive": 34.7e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 37.2e6, "gradient": 17.4e6,
+    "primitive": 34.0e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 37.2e6, "gradient": 17.4e6,
     "spectral": 54.1e6, "assemble": 33.9e6, "correct": 24.4e6,
 }
-DRAM_BYTES_SWEEP_FP32 = 36.6e6 + 38.2e6   # record packing + FP32 wavefront sweep
+DRAM_BYTES_SWEEP_FP32 = 36.6e6 + 38.3e6   # record packing + FP32 sweep
 # GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA throughput microbenchmark
 # measured 1.20 TFLOP/s on this machine).  FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
 FP64_PEAK_GFLOPS = 1250.0

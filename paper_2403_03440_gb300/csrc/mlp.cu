@@ -268,6 +268,12 @@ __device__ __forceinline__ bool fused_layer(uint32_t tmem, uint32_t a0, uint32_t
   return !__syncthreads_or(!ok);
 }
 
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // hidden-layer epilogue of this warp's 32 rows x 64 columns: bias + SiLU -> bf16 into the A tile
 __device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float* bias, unsigned char* A) {
   const int warp = threadIdx.x >> 5, q = warp & 3, h = warp >> 2;
@@ -284,10 +290,11 @@ __device__ __forceinline__ void fused_hidden_epilogue(uint32_t tmem, const float
       for (int e = 0; e < 4; ++e) {
         const int n0 = c0 + g8 * 8 + 2 * e;
         const float z0 = v[g8 * 8 + 2 * e] + bias[n0], z1 = v[g8 * 8 + 2 * e + 1] + bias[n0 + 1];
-        // silu(z) = z / (1 + e^-z); the approximate division returns 0 once e^-z exceeds
-        // 2^126, the function's limit there
-        const bf16 o0 = __float2bfloat16_rn(__fdividef(z0, 1.f + __expf(-z0)));
-        const bf16 o1 = __float2bfloat16_rn(__fdividef(z1, 1.f + __expf(-z1)));
+        // silu(z) = z sigma(z) = (z/2)(1 + tanh(z/2)): one special-function op per value
+        // (tanh.approx, relative error ~2^-11, below the bfloat16 rounding that follows)
+        const float h0 = 0.5f * z0, h1 = 0.5f * z1;
+        const bf16 o0 = __float2bfloat16_rn(fmaf(h0, tanh_approx(h0), h0));
+        const bf16 o1 = __float2bfloat16_rn(fmaf(h1, tanh_approx(h1), h1));
         w[e] = (uint32_t)__bfloat16_as_ushort(o0) | ((uint32_t)__bfloat16_as_ushort(o1) << 16);
       }
       const int c8 = (c0 >> 3) + g8;
@@ -337,24 +344,32 @@ __global__ void __launch_bounds__(kFuseThreads) k_mlp_infer(const float* __restr
   uint32_t phase = 0;
   bool failed = false;
   const int ntiles = (n + kTileM - 1) / kTileM;
+  // inputs: thread (row r, half h) converts features 8h .. 8h+7 of row r (14 features and 2
+  // zero columns) to bf16, one 16-byte core-matrix row of the canonical layout.  The next
+  // tile's features are loaded into registers while the current tile's layers run.
+  const int xr = tid & (kTileM - 1), xh = tid >> 7;
+  float xin[8];
+  auto load_x = [&](int tile) {
+    const int gr = tile * kTileM + xr;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = 8 * xh + e;
+      xin[e] = (tile < ntiles && gr < n && k < 14) ? X[(size_t)gr * 14 + k] : 0.f;
+    }
+  };
+  load_x(blockIdx.x);
   for (int tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int row0 = tile * kTileM;
-    // inputs: thread (row r, half h) converts features 8h .. 8h+7 of row r (14 features and 2
-    // zero columns) to bf16, one 16-byte core-matrix row of the canonical layout
     {
-      const int r = tid & (kTileM - 1), h = tid >> 7, gr = row0 + r;
       uint32_t w[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int k0 = 8 * h + 2 * e, k1 = k0 + 1;
-        const float x0 = (gr < n && k0 < 14) ? X[(size_t)gr * 14 + k0] : 0.f;
-        const float x1 = (gr < n && k1 < 14) ? X[(size_t)gr * 14 + k1] : 0.f;
-        w[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x0)) |
-               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(x1)) << 16);
-      }
-      *reinterpret_cast<uint4*>(sX + (h * (kTileM / 8) + (r >> 3)) * 128 + (r & 7) * 16) =
+      for (int e = 0; e < 4; ++e)
+        w[e] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(xin[2 * e])) |
+               ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(xin[2 * e + 1])) << 16);
+      *reinterpret_cast<uint4*>(sX + (xh * (kTileM / 8) + (xr >> 3)) * 128 + (xr & 7) * 16) =
           make_uint4(w[0], w[1], w[2], w[3]);
     }
+    load_x(tile + gridDim.x);
     if (!fused_layer(tmem, sXu, smem_u32(sW1), LNH, LKIN, barA, phase)) { failed = true; break; }
     fused_hidden_epilogue(tmem, sB, sA);
     if (!fused_layer(tmem, sAu, smem_u32(sW2), LNH, LNH, barA, phase)) { failed = true; break; }

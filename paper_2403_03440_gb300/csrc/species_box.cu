@@ -38,6 +38,7 @@ constexpr int kSweepThreads = 256;
 constexpr int kGroup = 32;            // species per warp row of a species CTA
 constexpr int kCiThreads = 256;
 constexpr double kMaxFactorBytes = 32.0 * (1ull << 30);   // largest CI factor storage allowed
+constexpr size_t kStageBytes = 200 * 1024;   // shared memory for the staged CS sweep (<= 227 KB)
 
 struct Box {
   int ns, ni, nj, nk, N, H;          // H hyperplanes
@@ -158,13 +159,13 @@ __global__ void k_rhs_flow(Box b, const double* rhs, double* rf) {
 }
 
 // frozen-composition flow flux Jacobian of cell nb's state through S, applied to x (5)
-__device__ __forceinline__ void jvp_flow(const Box& b, int nb, const double* S, const double* x,
-                                         double* y) {
+// (a: the auxiliary records, rEv: rho E of every cell; in shared memory when staged)
+__device__ __forceinline__ void jvp_flow(const Box& b, const double* a, const double* rEv, int nb,
+                                         const double* S, const double* x, double* y) {
   const size_t N = b.N;
-  const double* a = b.aux;
   const double rho = a[A_RHO * N + nb], p = a[A_P * N + nb], gm1 = a[A_GM1 * N + nb];
   const double u[3] = {a[A_U * N + nb], a[(A_U + 1) * N + nb], a[(A_U + 2) * N + nb]};
-  const double rE = b.Q[(b.ns + 3) * N + nb];
+  const double rE = rEv[nb];
   const double U = u[0] * S[0] + u[1] * S[1] + u[2] * S[2];
   const double k = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double Sm = S[0] * x[1] + S[1] * x[2] + S[2] * x[3];
@@ -176,11 +177,23 @@ __device__ __forceinline__ void jvp_flow(const Box& b, int nb, const double* S, 
 }
 
 // CS: CTA 0 sweeps the flow block, CTA g >= 1 the species [kGroup (g-1), kGroup g).  xs is the
-// species scratch in [cell][species] layout (coalesced across a warp's species).
+// species scratch in [cell][species] layout (coalesced across a warp's species).  When the
+// launch provides (kAux + 1) N doubles of dynamic shared memory, every CTA first copies the
+// auxiliary records and rho E of all cells there, so that the 2 H dependent hyperplane steps
+// read neighbours from shared memory instead of L2/DRAM.
 __global__ void __launch_bounds__(kSweepThreads) k_cs_sweeps(Box b, const double* rhs, const double* rf,
-                                                             double* xF, double* xs, double* dQ) {
+                                                             double* xF, double* xs, double* dQ, int staged) {
+  extern __shared__ double sh_aux[];
   const size_t N = b.N;
   const double* a = b.aux;
+  const double* rEv = b.Q + (size_t)(b.ns + 3) * N;
+  if (staged) {
+    for (size_t e = threadIdx.x; e < (size_t)kAux * N; e += blockDim.x) sh_aux[e] = b.aux[e];
+    for (size_t e = threadIdx.x; e < N; e += blockDim.x) sh_aux[(size_t)kAux * N + e] = rEv[e];
+    __syncthreads();
+    a = sh_aux;
+    rEv = sh_aux + (size_t)kAux * N;
+  }
   if (blockIdx.x == 0) {
     for (int pass = 0; pass < 2; ++pass) {
       const bool fwd = pass == 0;
@@ -196,7 +209,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_cs_sweeps(Box b, const double
             if (nb < 0) continue;
             double xn[5], ax[5];
             for (int v = 0; v < 5; ++v) xn[v] = fwd ? xF[v * N + nb] : dQ[v * N + nb];
-            jvp_flow(b, nb, b.S[d], xn, ax);
+            jvp_flow(b, a, rEv, nb, b.S[d], xn, ax);
             const double l = a[(A_LF + d) * N + nb];
             for (int v = 0; v < 5; ++v) acc[v] += fwd ? 0.5 * (ax[v] + l * xn[v]) : -0.5 * (ax[v] - l * xn[v]);
           }
@@ -437,6 +450,7 @@ struct cs_species_box_s {
   double* LU = nullptr;      // CI factors [N][n][n] (allocated on first use)
   int* piv = nullptr;
   int* err = nullptr;
+  bool stage_attr = false;   // the staged CS sweep's shared-memory attribute is set
   std::vector<int> hp_off;
   char msg[256] = {0};
 };
@@ -560,7 +574,13 @@ static cs_status enqueue_step(cs_species_box b, int scheme, double cfl, const do
     k_rhs_flow<<<warps_grid, 256, 0, b->st>>>(x, rhs, b->rf);
     const int G = x.ns < kGroup ? x.ns : kGroup;
     const int groups = (x.ns + G - 1) / G;
-    k_cs_sweeps<<<1 + groups, kSweepThreads, 0, b->st>>>(x, rhs, b->rf, b->xF, b->xs, dQ);
+    const size_t smem = (size_t)(kAux + 1) * N * sizeof(double);
+    const int staged = smem <= kStageBytes ? 1 : 0;
+    if (staged && !b->stage_attr &&
+        cudaFuncSetAttribute(k_cs_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes) == cudaSuccess)
+      b->stage_attr = true;
+    const int use = staged && b->stage_attr;
+    k_cs_sweeps<<<1 + groups, kSweepThreads, use ? smem : 0, b->st>>>(x, rhs, b->rf, b->xF, b->xs, dQ, use);
   } else {
     const int n = x.ns + 4;
     if ((double)N * n * n * sizeof(double) > kMaxFactorBytes)
