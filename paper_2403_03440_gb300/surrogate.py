@@ -49,29 +49,36 @@ def step_opts(c, precision=0):
                 ramp_iters=c["ramp"], precision=precision)
 
 
-def collect(c, iters, every, precision=0, dense=None):
-    """Run the case from the freestream and sample every cell: every iteration during the
+def collect(c, iters, every, precision=0, dense=None, frac=1.0, seed=0):
+    """Run the case from the freestream and sample its cells: every iteration during the
     start-up transient (the first `dense` iterations, by default the CFL ramp), whose states
-    are the stiffest and the least like the converged flow, then every `every` iterations."""
+    are the stiffest and the least like the converged flow, then every `every` iterations.
+    frac < 1 keeps a seeded random fraction of the cells of each snapshot (large grids)."""
     import torch
     g = make_grid(c)
     N = g.ncell
     dense = c["ramp"] if dense is None else dense
+    rng = np.random.default_rng(seed)
     Xd = torch.empty((N, 14), dtype=torch.float32, device="cuda")
     Td = torch.empty((N, 22), dtype=torch.float32, device="cuda")
     Xs, Ts = [], []
+
+    def keep():
+        g.surrogate_sample(Xd, Td)
+        X, T = Xd.cpu().numpy(), Td.cpu().numpy()
+        if frac < 1.0:
+            sel = rng.random(N) < frac
+            X, T = X[sel], T[sel]
+        Xs.append(X.copy())
+        Ts.append(T.copy())
     done = 0
     g.residual(want_R=False)           # the freestream start is part of every run
-    g.surrogate_sample(Xd, Td)
-    Xs.append(Xd.cpu().numpy().copy())
-    Ts.append(Td.cpu().numpy().copy())
+    keep()
     while done < iters:
         k = 1 if done < dense else every
         g.step(iters=k, **step_opts(c, precision))
         done += k
-        g.surrogate_sample(Xd, Td)
-        Xs.append(Xd.cpu().numpy().copy())
-        Ts.append(Td.cpu().numpy().copy())
+        keep()
     return np.concatenate(Xs), np.concatenate(Ts)
 
 
@@ -138,44 +145,70 @@ def calibrate(net, norm, val, q=0.95):
     return out, shift
 
 
-def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0):
+def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=True):
+    """Run the case from the freestream until both residual monitors drop by `tol`.  With a
+    network attached and `fallback`, a chunk of iterations that ends in a non-physical state
+    is redone from its starting state with the exact chemistry diagonal (the exact chemistry
+    stays in the residual, so the network can always be dropped), then the network resumes;
+    `fallback_chunks` counts these."""
     import torch
     g = make_grid(c)
     if net is not None:
         g.attach_surrogate(net, norm)
     kw = step_opts(c, precision)
-    first = g.step(iters=1, **kw)
-    r0 = (first["r_species"], first["r_energy"])
+    fallbacks = 0
+
+    def advance(k):
+        nonlocal fallbacks
+        Q0 = g.get_state()
+        try:
+            return g.step(iters=k, **kw)
+        except P.CSError:
+            if net is None or not fallback:
+                raise
+        fallbacks += 1
+        g.set_state(Q0)
+        g.detach_surrogate()
+        try:
+            return g.step(iters=k, **kw)
+        finally:
+            g.attach_surrogate(net, norm)
+
     g.profile(True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    done, status, st = 1, "max_iters", first
-    while done < max_iters:
-        try:
-            st = g.step(iters=chunk, **kw)
-        except P.CSError as e:
-            status = f"error: {e}"
-            break
-        done += st["iters_done"]
-        if st["r_species"] / r0[0] <= tol and st["r_energy"] / r0[1] <= tol:
-            status = "converged"
-            break
+    status, done = "max_iters", 0
+    try:
+        first = advance(1)
+        r0 = (first["r_species"], first["r_energy"])
+        done, st = 1, first
+        while done < max_iters:
+            st = advance(chunk)
+            done += st["iters_done"]
+            if st["r_species"] / r0[0] <= tol and st["r_energy"] / r0[1] <= tol:
+                status = "converged"
+                break
+    except P.CSError as e:
+        status = f"error: {e}"
+        st = dict(q_stag=float("nan"), r_species=float("nan"), r_energy=float("nan"))
+        r0 = (1.0, 1.0)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     prof = g.profile(False)
     return dict(status=status, iterations=done, seconds=dt, q_stag=st["q_stag"],
                 drop=max(st["r_species"] / r0[0], st["r_energy"] / r0[1]),
-                primitive_ms_per_iter=prof["primitive"][0] / max(done - 1, 1),
-                ms_per_iter=1e3 * dt / max(done - 1, 1))
+                fallback_chunks=fallbacks,
+                primitive_ms_per_iter=prof["primitive"][0] / max(done, 1),
+                ms_per_iter=1e3 * dt / max(done, 1))
 
 
-def demo(case, tol, max_iters, samples_iters, every, epochs):
+def demo(case, tol, max_iters, samples_iters, every, epochs, frac=1.0):
     """The case run to the same residual drop three ways: the plain FP64 operator with the
     exact chemistry diagonal, the FP32 operator with the exact diagonal, and the FP32 operator
     with the network's diagonal (the residual, update and corrections FP64 in all three)."""
     c = CASES[case]
     t0 = time.perf_counter()
-    X, T = collect(c, samples_iters, every, 0)
+    X, T = collect(c, samples_iters, every, 0, frac=frac)
     norm = standardisation(X, T)
     net, record, val = train(X, T, norm, epochs=epochs, max_batch=c["ni"] * c["nj"])
     norm_used, shift = calibrate(net, norm, val)
@@ -202,9 +235,10 @@ def main():
     ap.add_argument("--samples-iters", type=int, default=4000)
     ap.add_argument("--every", type=int, default=20)
     ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--sample-frac", type=float, default=1.0)
     a = ap.parse_args()
     P.build()
-    out = demo(a.case, a.tol, a.max_iters, a.samples_iters, a.every, a.epochs)
+    out = demo(a.case, a.tol, a.max_iters, a.samples_iters, a.every, a.epochs, a.sample_frac)
     print(json.dumps(out))
 
 

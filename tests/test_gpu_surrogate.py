@@ -94,20 +94,22 @@ def test_attached_network_sets_diagonal_not_residual():
 
 def test_trained_network_gain():
     """What the trained network gains: the half-cylinder case (11-species 2T air, Mach 15) run
-    to a 1e-5 residual drop with the exact species diagonal and with the network's, trained by
-    the library's kernels on the solver's own states.  Both converge to the same stagnation
-    heat flux (the residual keeps the exact chemistry), in about as many iterations, and the
-    network's primitive phase is cheaper (its Jacobian chain is not evaluated)."""
+    to a 1e-6 residual drop with the exact species diagonal and with the network's, trained by
+    the library's kernels on the solver's own states (3000 iterations sampled, 40 epochs, the
+    held-out calibration).  Both converge to the same stagnation heat flux (the residual keeps
+    the exact chemistry) in about as many iterations, the network's primitive phase is cheaper
+    (its Jacobian chain is not evaluated), and the exact-diagonal fallback is rarely needed."""
     from paper_2403_03440_gb300 import surrogate as S
     c = S.CASES["c1m"]
-    X, T = S.collect(c, 1500, 10, 0)
+    X, T = S.collect(c, 3000, 10, 0)
     norm = S.standardisation(X, T)
-    net, record, val = S.train(X, T, norm, epochs=15, max_batch=c["ni"] * c["nj"])
+    net, record, val = S.train(X, T, norm, epochs=40, max_batch=c["ni"] * c["nj"])
     assert record[-1] < 0.2 * record[0]
     norm_used, shift = S.calibrate(net, norm, val)
-    exact = S.run_to(c, 1e-5, 20000, 500)
-    surr = S.run_to(c, 1e-5, 20000, 500, net=net, norm=norm_used)
+    exact = S.run_to(c, 1e-6, 20000, 500)
+    surr = S.run_to(c, 1e-6, 20000, 500, net=net, norm=norm_used)
     assert exact["status"] == "converged" and surr["status"] == "converged", (exact, surr)
+    assert surr["fallback_chunks"] <= 2, surr
     assert abs(surr["q_stag"] - exact["q_stag"]) < 1e-4 * abs(exact["q_stag"])
     assert surr["iterations"] <= 1.2 * exact["iterations"]
     assert surr["primitive_ms_per_iter"] < exact["primitive_ms_per_iter"]
