@@ -388,6 +388,59 @@ def run_species(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def measured_bf16_peak():
+    """(TFLOP/s, description): the measured cuBLAS bf16 burst rate, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured cuBLAS bf16 burst (of measured)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s (of fallback)"
+
+
+def run_mlp(args, rank, world, local):
+    """Surrogate network inference (the fused tcgen05 kernel) on as many rows as the 384 x 256
+    grid has cells: inputs resident on the device, L2 flushed before every timed call."""
+    import torch
+    import paper_2403_03440_gb300 as P
+    P.build()
+    torch.cuda.set_device(local)
+    rows = NI * NJ
+    net = P.MLP(inputs.mlp_init(0), max_batch=rows)
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    X = torch.randn((rows, 14), generator=gen, dtype=torch.float32).cuda()
+    Y = torch.empty((rows, 22), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        net.forward(X, Y)
+    torch.cuda.synchronize()
+    total = 0.0
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            net.forward(X, Y)
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+    ms = total / args.steps
+    flop = 2.0 * rows * (14 * 128 + 2 * 128 * 128 + 128 * 22)
+    peak = measured_bf16_peak()
+    tf = flop / (ms / 1e3) / 1e12
+    if rank == 0:
+        print(json.dumps({
+            "metric": "surrogate inference rows/s", "value": rows / (ms / 1e3), "unit": "rows/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 x bf16 -> f32", "data": "synthetic",
+            "config": {"workload": f"mlp-14-128-128-128-22-silu-{rows}-rows", "rows": rows,
+                       "l2": "flushed before every timed call (256 MiB write)"},
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak[0], "unit": "TFLOP/s",
+                         "frac": tf / peak[0], "traffic": None, "peak_kind": peak[1],
+                         "note": "CUDA events around cs_mlp_forward (includes its error-flag memset and status read)"},
+            "clocks": clk.summary(), "gpu_launches": args.steps}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,7 +450,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch", "species"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "batch", "species", "mlp"])
     ap.add_argument("--species", type=lambda t: [int(x) for x in t.split(",")],
                     default=[16, 64, 256, 1024, 4096])
     ap.add_argument("--ci-max-species", type=int, default=1024)
@@ -429,6 +482,9 @@ def main():
         return
     if args.workload == "species":
         run_species(args, rank, world, local)
+        return
+    if args.workload == "mlp":
+        run_mlp(args, rank, world, local)
         return
 
     import torch

@@ -35,10 +35,9 @@ namespace csbox {
 
 constexpr double kRu = 8314.462618;   // J/(kmol K)
 constexpr int kSweepThreads = 256;
-constexpr int kGroup = 32;            // species per warp row of a species CTA
+constexpr int kGroup = 8;             // species per CTA of the split sweep
 constexpr int kCiThreads = 256;
 constexpr double kMaxFactorBytes = 32.0 * (1ull << 30);   // largest CI factor storage allowed
-constexpr size_t kStageBytes = 200 * 1024;   // shared memory for the staged CS sweep (<= 227 KB)
 
 struct Box {
   int ns, ni, nj, nk, N, H;          // H hyperplanes
@@ -51,9 +50,11 @@ struct Box {
   const int* hp_off;                 // [H + 1]
   const int* hp_cell;                // [N] cells in hyperplane order
 };
-// per-cell auxiliary record
+// per-cell auxiliary record: primitives, radii, diagonals and their reciprocals, and the
+// species sweep's neighbour coefficients 1/2 (U_d + lambda_C,d), 1/2 (U_d - lambda_C,d)
+// (computed once per cell, not once per species)
 enum { A_RHO = 0, A_U = 1, A_P = 4, A_C = 5, A_GM1 = 6, A_T = 7, A_LF = 8, A_LC = 11, A_DF = 14,
-       A_DS = 15, kAux = 16 };
+       A_DS = 15, A_IRHO = 16, A_IDF = 17, A_IDS = 18, A_KF = 19, A_KB = 22, kAux = 25 };
 
 __device__ __forceinline__ void cell_ijk(const Box& b, int c, int& i, int& j, int& k) {
   i = c % b.ni;
@@ -136,12 +137,17 @@ __global__ void k_aux(Box b, double cfl) {
     const double lC = fabs(U);
     a[(A_LF + d) * N + c] = lF;
     a[(A_LC + d) * N + c] = lC;
+    a[(A_KF + d) * N + c] = 0.5 * (U + lC);
+    a[(A_KB + d) * N + c] = 0.5 * (U - lC);
     sF += lF;
     sC += lC;
   }
   const double Vdt = sF / cfl;
   a[A_DF * N + c] = Vdt + sF;
   a[A_DS * N + c] = Vdt + sC;
+  a[A_IRHO * N + c] = 1.0 / rho;
+  a[A_IDF * N + c] = 1.0 / (Vdt + sF);
+  a[A_IDS * N + c] = 1.0 / (Vdt + sC);
 }
 
 // flow-block right-hand side (sum_s rhs_s, rhs_m, rhs_E) [5][N] (one warp per cell)
@@ -169,7 +175,7 @@ __device__ __forceinline__ void jvp_flow(const Box& b, const double* a, const do
   const double U = u[0] * S[0] + u[1] * S[1] + u[2] * S[2];
   const double k = 0.5 * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
   const double Sm = S[0] * x[1] + S[1] * x[2] + S[2] * x[3];
-  const double dU = (Sm - U * x[0]) / rho;
+  const double dU = (Sm - U * x[0]) * a[A_IRHO * N + nb];
   const double dp = gm1 * (k * x[0] - (u[0] * x[1] + u[1] * x[2] + u[2] * x[3]) + x[4]);
   y[0] = Sm;
   for (int q = 0; q < 3; ++q) y[1 + q] = x[1 + q] * U + rho * u[q] * dU + S[q] * dp;
@@ -177,23 +183,14 @@ __device__ __forceinline__ void jvp_flow(const Box& b, const double* a, const do
 }
 
 // CS: CTA 0 sweeps the flow block, CTA g >= 1 the species [kGroup (g-1), kGroup g).  xs is the
-// species scratch in [cell][species] layout (coalesced across a warp's species).  When the
-// launch provides (kAux + 1) N doubles of dynamic shared memory, every CTA first copies the
-// auxiliary records and rho E of all cells there, so that the 2 H dependent hyperplane steps
-// read neighbours from shared memory instead of L2/DRAM.
+// species scratch in [cell][species] layout (contiguous across a CTA's species of a cell).
+// A species update is three multiply-adds with the neighbours' precomputed coefficients and
+// one multiply by the cell's reciprocal diagonal.
 __global__ void __launch_bounds__(kSweepThreads) k_cs_sweeps(Box b, const double* rhs, const double* rf,
-                                                             double* xF, double* xs, double* dQ, int staged) {
-  extern __shared__ double sh_aux[];
+                                                             double* xF, double* xs, double* dQ) {
   const size_t N = b.N;
   const double* a = b.aux;
   const double* rEv = b.Q + (size_t)(b.ns + 3) * N;
-  if (staged) {
-    for (size_t e = threadIdx.x; e < (size_t)kAux * N; e += blockDim.x) sh_aux[e] = b.aux[e];
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) sh_aux[(size_t)kAux * N + e] = rEv[e];
-    __syncthreads();
-    a = sh_aux;
-    rEv = sh_aux + (size_t)kAux * N;
-  }
   if (blockIdx.x == 0) {
     for (int pass = 0; pass < 2; ++pass) {
       const bool fwd = pass == 0;
@@ -213,7 +210,7 @@ __global__ void __launch_bounds__(kSweepThreads) k_cs_sweeps(Box b, const double
             const double l = a[(A_LF + d) * N + nb];
             for (int v = 0; v < 5; ++v) acc[v] += fwd ? 0.5 * (ax[v] + l * xn[v]) : -0.5 * (ax[v] - l * xn[v]);
           }
-          const double iD = 1.0 / a[A_DF * N + c];
+          const double iD = a[A_IDF * N + c];
           for (int v = 0; v < 5; ++v) {
             if (fwd) xF[v * N + c] = acc[v] * iD;
             else dQ[v * N + c] = xF[v * N + c] + acc[v] * iD;
@@ -241,13 +238,10 @@ __global__ void __launch_bounds__(kSweepThreads) k_cs_sweeps(Box b, const double
           for (int d = 0; d < 3; ++d) {
             const int nb = neighbour(b, c, d, fwd ? -1 : 1);
             if (nb < 0) continue;
-            const double* S = b.S[d];
-            const double U = a[A_U * N + nb] * S[0] + a[(A_U + 1) * N + nb] * S[1] + a[(A_U + 2) * N + nb] * S[2];
-            const double l = a[(A_LC + d) * N + nb];
-            const double xn = fwd ? xs[(size_t)nb * ns + s] : dQ[(size_t)(5 + s) * N + nb];
-            acc += fwd ? 0.5 * (U * xn + l * xn) : -0.5 * (U * xn - l * xn);
+            if (fwd) acc += a[(A_KF + d) * N + nb] * xs[(size_t)nb * ns + s];
+            else acc -= a[(A_KB + d) * N + nb] * dQ[(size_t)(5 + s) * N + nb];
           }
-          const double iD = 1.0 / a[A_DS * N + c];
+          const double iD = a[A_IDS * N + c];
           if (fwd) xs[(size_t)c * ns + s] = acc * iD;
           else dQ[(size_t)(5 + s) * N + c] = xs[(size_t)c * ns + s] + acc * iD;
         }
@@ -450,7 +444,6 @@ struct cs_species_box_s {
   double* LU = nullptr;      // CI factors [N][n][n] (allocated on first use)
   int* piv = nullptr;
   int* err = nullptr;
-  bool stage_attr = false;   // the staged CS sweep's shared-memory attribute is set
   std::vector<int> hp_off;
   char msg[256] = {0};
 };
@@ -574,13 +567,7 @@ static cs_status enqueue_step(cs_species_box b, int scheme, double cfl, const do
     k_rhs_flow<<<warps_grid, 256, 0, b->st>>>(x, rhs, b->rf);
     const int G = x.ns < kGroup ? x.ns : kGroup;
     const int groups = (x.ns + G - 1) / G;
-    const size_t smem = (size_t)(kAux + 1) * N * sizeof(double);
-    const int staged = smem <= kStageBytes ? 1 : 0;
-    if (staged && !b->stage_attr &&
-        cudaFuncSetAttribute(k_cs_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes) == cudaSuccess)
-      b->stage_attr = true;
-    const int use = staged && b->stage_attr;
-    k_cs_sweeps<<<1 + groups, kSweepThreads, use ? smem : 0, b->st>>>(x, rhs, b->rf, b->xF, b->xs, dQ, use);
+    k_cs_sweeps<<<1 + groups, kSweepThreads, 0, b->st>>>(x, rhs, b->rf, b->xF, b->xs, dQ);
   } else {
     const int n = x.ns + 4;
     if ((double)N * n * n * sizeof(double) > kMaxFactorBytes)

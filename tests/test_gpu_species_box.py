@@ -41,7 +41,6 @@ def run_pair(ns, n, scheme, seed=0, cfl=5.0):
     return box, gbox, got, want
 
 
-# (12, 12, 12): too many cells for the split sweep's shared-memory staging (global reads)
 @pytest.mark.parametrize("ns,n", [(1, (4, 3, 3)), (5, (7, 5, 3)), (33, (5, 4, 3)), (16, (6, 1, 4)),
                                   (3, (12, 12, 12))])
 @pytest.mark.parametrize("scheme", [0, 1])
