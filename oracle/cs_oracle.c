@@ -686,6 +686,8 @@ typedef struct {
     double *grad;                    /* [cell][NGMAX][3] */
     double *Fface[3];                /* [dir][face][nq] */
     double *lamF, *lamC, *lamCI;     /* hat-lambda per cell and direction [cell*3] */
+    double *lamCIv;                  /* 2 lambda_vis of the coupled operator [cell*3] */
+    int ci_split;                    /* coupled operator: 0 spectral splitting, 1 eigenvalue */
     double *DF, *DFev, *Ds;          /* diagonals */
     double *DLU; int *piv;           /* CI diagonal blocks, LU factors */
     double norms[2], qstag;
@@ -1407,6 +1409,8 @@ static int residual(orc_grid *G)
  * 2 lambda_vis; V/dtau = sum_d (lambda_inv,d + lambda_vis,d) / CFL (flow radius, both
  * schemes); the source's radius lambda_S enters through the diagonal, not through dtau.
  * ------------------------------------------------------------------------------------- */
+static void absjac_ci(const orc_grid *G, const prim_t *w, const double *S, const double *dc, double *out);
+
 static void spectral(orc_grid *G, double cfl)
 {
     int nd = G->nd, ns = G->gas.ns;
@@ -1423,11 +1427,12 @@ static void spectral(orc_grid *G, double cfl)
         }
         nuF /= w->rho;
         nuCI = fmax(nuF, nuC);
-        double sumdt = 0.0, sF = 0.0, sC = 0.0, sCI = 0.0;
+        double sumdt = 0.0, sF = 0.0, sC = 0.0, sCI = 0.0, sCIv = 0.0;
+        double Sbar[3][3] = {{0}};
         for (int d = 0; d < nd; d++) {
             const double *Sm = &G->S[d][3 * face_of(G, o, d, -1)];
             const double *Sp = &G->S[d][3 * face_of(G, o, d, +1)];
-            double Sb[3], a2 = 0.0, U = 0.0;
+            double *Sb = Sbar[d], a2 = 0.0, U = 0.0;
             for (int q = 0; q < nd; q++) {
                 Sb[q] = 0.5 * (Sm[q] + Sp[q]);
                 a2 += Sb[q] * Sb[q];
@@ -1439,6 +1444,8 @@ static void spectral(orc_grid *G, double cfl)
             G->lamF[3 * c + d] = liF + 2.0 * lvF;
             G->lamC[3 * c + d] = liC + 2.0 * lvC;
             G->lamCI[3 * c + d] = liF + 2.0 * lvCI;
+            G->lamCIv[3 * c + d] = 2.0 * lvCI;
+            sCIv += 2.0 * lvCI;
             sumdt += liF + lvF;
             sF += G->lamF[3 * c + d];
             sC += G->lamC[3 * c + d];
@@ -1456,7 +1463,19 @@ static void spectral(orc_grid *G, double cfl)
             int n = G->nci, nF = G->nF;
             double *A = &G->DLU[(size_t)c * n * n];
             for (int k = 0; k < n * n; k++) A[k] = 0.0;
-            for (int k = 0; k < n; k++) A[k * n + k] = Vdt + sCI;
+            if (!G->ci_split) {
+                for (int k = 0; k < n; k++) A[k * n + k] = Vdt + sCI;
+            } else {
+                /* eigenvalue splitting: (V/dtau + sum 2 lambda_vis) I + sum_d |A_c(S_d)| */
+                for (int k = 0; k < n; k++) A[k * n + k] = Vdt + sCIv;
+                for (int d = 0; d < nd; d++)
+                    for (int col = 0; col < n; col++) {
+                        double e[NQMAX] = {0}, a[NQMAX];
+                        e[col] = 1.0;
+                        absjac_ci(G, w, Sbar[d], e, a);
+                        for (int r = 0; r < n; r++) A[r * n + col] += a[r];
+                    }
+            }
             if (G->gas.ntemp == 2) A[(nF - 1) * n + (nF - 1)] += G->V[c] * w->relax;
             int nq = G->nq;
             double Jq[NSMAX * NQMAX], om[NSMAX];
@@ -1570,6 +1589,59 @@ static void jvp_ci(const orc_grid *G, const prim_t *w, const double *S, const do
     for (int s = 1; s < ns; s++) out[nF + s - 1] = o[s];
 }
 
+/* |A(S)| dq at the state w (full layout) for the eigenvalue splitting A+- = (A +- |A|)/2 of
+ * Sec. 2.3, |A| = R |Lambda| R^-1.  A has the eigenvalue U_n (all waves but the two acoustic
+ * ones) and U_n +- c, with right eigenvectors (Y_s, u +- c n, H +- U_n c, e_v) per unit
+ * normal n and projections alpha+- = (dp +- rho c dU_n) / (2 c^2) (dp the linearised
+ * pressure of jvp_full, dU_n = (n.dm - U_n d rho)/rho), so that
+ *   |A| dq = |S| (|U_n| dq + (|U_n+c| - |U_n|) alpha+ r+ + (|U_n-c| - |U_n|) alpha- r-),
+ * the same wave decomposition as the Roe dissipation, at one state. */
+static void absjac_full(const orc_grid *G, const prim_t *w, const double *S, const double *dq, double *out)
+{
+    int ns = G->gas.ns, nd = G->nd, two = G->gas.ntemp == 2;
+    double area = 0.0;
+    for (int q = 0; q < nd; q++) area += S[q] * S[q];
+    area = sqrt(area);
+    double n[3] = {0, 0, 0};
+    for (int q = 0; q < nd; q++) n[q] = S[q] / area;
+    double drho = 0.0, dp = 0.0, Un = 0.0, ndm = 0.0;
+    for (int s = 0; s < ns; s++) { drho += dq[s]; dp += w->prs[s] * dq[s]; }
+    for (int q = 0; q < nd; q++) {
+        Un += w->u[q] * n[q];
+        ndm += n[q] * dq[ns + q];
+        dp -= w->beta * w->u[q] * dq[ns + q];
+    }
+    dp += w->beta * dq[ns + nd];
+    if (two) dp += w->prev * dq[ns + nd + 1];
+    double dUn = (ndm - Un * drho) / w->rho;
+    double c = w->c, c2 = c * c;
+    double ap = (dp + w->rho * c * dUn) / (2.0 * c2), am = (dp - w->rho * c * dUn) / (2.0 * c2);
+    double l0 = fabs(Un), lp = fabs(Un + c) - l0, lm = fabs(Un - c) - l0;
+    double H = (w->rhoE + w->p) / w->rho;
+    for (int s = 0; s < ns; s++) out[s] = area * (l0 * dq[s] + (lp * ap + lm * am) * w->Y[s]);
+    for (int q = 0; q < nd; q++)
+        out[ns + q] = area * (l0 * dq[ns + q] + lp * ap * (w->u[q] + c * n[q]) + lm * am * (w->u[q] - c * n[q]));
+    out[ns + nd] = area * (l0 * dq[ns + nd] + lp * ap * (H + Un * c) + lm * am * (H - Un * c));
+    if (two) out[ns + nd + 1] = area * (l0 * dq[ns + nd + 1] + (lp * ap + lm * am) * w->rhoev / w->rho);
+}
+
+/* |A(S)| in the coupled variables (the similarity transform of jvp_ci) */
+static void absjac_ci(const orc_grid *G, const prim_t *w, const double *S, const double *dc, double *out)
+{
+    int ns = G->gas.ns, nF = G->nF;
+    double dq[NQMAX], o[NQMAX];
+    double first = dc[0];
+    for (int s = 1; s < ns; s++) { dq[s] = dc[nF + s - 1]; first -= dc[nF + s - 1]; }
+    dq[0] = first;
+    for (int k = 1; k < nF; k++) dq[ns + k - 1] = dc[k];
+    absjac_full(G, w, S, dq, o);
+    double orho = 0.0;
+    for (int s = 0; s < ns; s++) orho += o[s];
+    out[0] = orho;
+    for (int k = 1; k < nF; k++) out[k] = o[ns + k - 1];
+    for (int s = 1; s < ns; s++) out[nF + s - 1] = o[s];
+}
+
 /* ---------------------------------------------------------------------------------------
  * LU-SGS sweeps (Sec. 2.2: (D+L) dQ* = RHS forward, (D+U) dQ = D dQ* backward, with the
  * spectral splitting A^+- = (A +- lambda I)/2 and the point equation Eq. (ijkiterate)).
@@ -1600,6 +1672,29 @@ static void gather(const orc_grid *G, int c, int lower, int nv, const double *x,
             for (int v = 0; v < nv; v++) {
                 if (s < 0) acc[v] += 0.5 * (ax[v] + l * xn[v]);
                 else acc[v] -= 0.5 * (ax[v] - l * xn[v]);
+            }
+        }
+}
+
+/* coupled operator with the eigenvalue splitting: the neighbour couples with
+ * -(A_nb(S_f) + |A_nb(S_f)| + 2 lambda_vis)/2 (minus side) or +(A_nb - |A_nb| - 2 lambda_vis)/2 */
+static void gather_ci_eigen(const orc_grid *G, int c, int lower, const double *x, double *acc)
+{
+    int o[3], n = G->nci, N = G->ncell;
+    cell_coords(G, c, o);
+    for (int d = 0; d < G->nd; d++)
+        for (int s = -1; s <= 1; s += 2) {
+            int hl, nb = neighbour(G, o, d, s, &hl);
+            if (nb < 0 || hl != lower) continue;
+            const double *Sf = &G->S[d][3 * face_of(G, o, d, s)];
+            double xn[NQMAX], ax[NQMAX], bx[NQMAX];
+            for (int v = 0; v < n; v++) xn[v] = x[(size_t)v * N + nb];
+            jvp_ci(G, &G->w[nb], Sf, xn, ax);
+            absjac_ci(G, &G->w[nb], Sf, xn, bx);
+            double l = G->lamCIv[3 * nb + d];
+            for (int v = 0; v < n; v++) {
+                if (s < 0) acc[v] += 0.5 * (ax[v] + bx[v] + l * xn[v]);
+                else acc[v] -= 0.5 * (ax[v] - bx[v] - l * xn[v]);
             }
         }
 }
@@ -1692,14 +1787,16 @@ static int lusgs_coupled(orc_grid *G, double cfl)
         acc[0] = -rr;
         for (int k = 1; k < nF; k++) acc[k] = -G->R[(size_t)(ns + k - 1) * N + c];
         for (int s = 1; s < ns; s++) acc[nF + s - 1] = -G->R[(size_t)s * N + c];
-        gather(G, c, 1, n, x, N, jvp_ci, G->lamCI, acc);
+        if (G->ci_split) gather_ci_eigen(G, c, 1, x, acc);
+        else gather(G, c, 1, n, x, N, jvp_ci, G->lamCI, acc);
         lu_solve(&G->DLU[(size_t)c * n * n], &G->piv[(size_t)c * n], n, acc);
         for (int k = 0; k < n; k++) x[(size_t)k * N + c] = acc[k];
     }
     for (int c = N - 1; c >= 0; c--) {
         double acc[NQMAX];
         for (int k = 0; k < n; k++) acc[k] = 0.0;
-        gather(G, c, 0, n, y, N, jvp_ci, G->lamCI, acc);
+        if (G->ci_split) gather_ci_eigen(G, c, 0, y, acc);
+        else gather(G, c, 0, n, y, N, jvp_ci, G->lamCI, acc);
         lu_solve(&G->DLU[(size_t)c * n * n], &G->piv[(size_t)c * n], n, acc);
         for (int k = 0; k < n; k++) y[(size_t)k * N + c] = x[(size_t)k * N + c] + acc[k];
     }
@@ -1881,6 +1978,7 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
     G->lamF = calloc(N * 3, sizeof(double));
     G->lamC = calloc(N * 3, sizeof(double));
     G->lamCI = calloc(N * 3, sizeof(double));
+    G->lamCIv = calloc(N * 3, sizeof(double));
     G->DF = calloc(N, sizeof(double));
     G->DFev = calloc(N, sizeof(double));
     G->Ds = calloc(N * ns, sizeof(double));
@@ -1899,6 +1997,15 @@ int orc_set_reacting(orc_grid *G, int reacting) { G->react = reacting != 0; retu
 int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
 /* update limit f (see correct_update); 0 switches it off */
 int orc_set_update_limit(orc_grid *G, double f) { if (!(f >= 0.0)) return 1; G->update_limit = f; return 0; }
+
+/* flux-Jacobian splitting of the coupled operator: 0 spectral (the paper's choice), 1 the
+ * eigenvalue splitting A+- = (A +- |A|)/2 */
+int orc_set_ci_splitting(orc_grid *G, int mode)
+{
+    if (mode != 0 && mode != 1) return 1;
+    G->ci_split = mode;
+    return 0;
+}
 
 /* dual time stepping: physical step dt (0 switches it off) and theta >= 0; the stored levels
  * are discarded (the next orc_dual_advance starts from the current state) */
@@ -1935,7 +2042,7 @@ void orc_destroy(orc_grid *G)
     if (!G) return;
     for (int d = 0; d < G->nd; d++) { free(G->node[d]); free(G->S[d]); free(G->fc[d]); free(G->Fface[d]); }
     free(G->V); free(G->xc); free(G->Q); free(G->R); free(G->dQs); free(G->dQ); free(G->dQci_s);
-    free(G->dQci); free(G->w); free(G->grad); free(G->lamF); free(G->lamC); free(G->lamCI);
+    free(G->dQci); free(G->w); free(G->grad); free(G->lamF); free(G->lamC); free(G->lamCI); free(G->lamCIv);
     free(G->DF); free(G->DFev); free(G->Ds); free(G->DLU); free(G->piv);
     free(G->Qn); free(G->Qnm1);
     free(G);
@@ -2081,6 +2188,7 @@ int orc_field(const orc_grid *G, const char *name, double *out)
     if (!strcmp(name, "lamF")) { memcpy(out, G->lamF, sizeof(double) * N * 3); return N * 3; }
     if (!strcmp(name, "lamC")) { memcpy(out, G->lamC, sizeof(double) * N * 3); return N * 3; }
     if (!strcmp(name, "lamCI")) { memcpy(out, G->lamCI, sizeof(double) * N * 3); return N * 3; }
+    if (!strcmp(name, "lamCIv")) { memcpy(out, G->lamCIv, sizeof(double) * N * 3); return N * 3; }
     if (!strcmp(name, "DF")) { memcpy(out, G->DF, sizeof(double) * N); return N; }
     if (!strcmp(name, "DFev")) { memcpy(out, G->DFev, sizeof(double) * N); return N; }
     if (!strcmp(name, "Ds")) { memcpy(out, G->Ds, sizeof(double) * N * ns); return N * ns; }
@@ -2123,17 +2231,18 @@ int orc_coupling_block(orc_grid *G, int c, int d, int side, int scheme, double *
     if (nb < 0) return 1;
     const double *Sf = &G->S[d][3 * face_of(G, o, d, side)];
     int nv = scheme == 0 ? G->nF : scheme == 1 ? G->gas.ns : G->nci;
-    const double *lam = scheme == 0 ? G->lamF : scheme == 1 ? G->lamC : G->lamCI;
+    const double *lam = scheme == 0 ? G->lamF : scheme == 1 ? G->lamC : scheme == 2 ? G->lamCI : G->lamCIv;
     double l = lam[3 * nb + d];
     for (int col = 0; col < nv; col++) {
-        double e[NQMAX] = {0}, a[NQMAX];
+        double e[NQMAX] = {0}, a[NQMAX], b[NQMAX] = {0};
         e[col] = 1.0;
         if (scheme == 0) jvp_flow(G, &G->w[nb], Sf, e, a);
-        else if (scheme == 2) jvp_ci(G, &G->w[nb], Sf, e, a);
+        else if (scheme >= 2) jvp_ci(G, &G->w[nb], Sf, e, a);
         else { double U = face_U(G, &G->w[nb], Sf); for (int r = 0; r < nv; r++) a[r] = (r == col) ? U : 0.0; }
+        if (scheme == 3) absjac_ci(G, &G->w[nb], Sf, e, b);     /* eigenvalue splitting */
         for (int r = 0; r < nv; r++) {
-            double coef = (side < 0) ? -0.5 * (a[r] + (r == col ? l : 0.0)) : 0.5 * (a[r] - (r == col ? l : 0.0));
-            out[r * nv + col] = coef;
+            double dis = b[r] + (r == col ? l : 0.0);
+            out[r * nv + col] = (side < 0) ? -0.5 * (a[r] + dis) : 0.5 * (a[r] - dis);
         }
     }
     return 0;
@@ -2224,7 +2333,9 @@ int orc_state_jvp(int mech, int nd, const double *q, const double *S, int which,
     if (st) return st;
     if (which == 0) jvp_full(&G, &w, S, dq, out);
     else if (which == 1) jvp_flow(&G, &w, S, dq, out);
-    else jvp_ci(&G, &w, S, dq, out);
+    else if (which == 2) jvp_ci(&G, &w, S, dq, out);
+    else if (which == 3) absjac_full(&G, &w, S, dq, out);
+    else absjac_ci(&G, &w, S, dq, out);
     return 0;
 }
 
