@@ -454,12 +454,12 @@ def main():
     ap.add_argument("--species", type=lambda t: [int(x) for x in t.split(",")],
                     default=[16, 64, 256, 1024, 4096])
     ap.add_argument("--ci-max-species", type=int, default=1024)
-    ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci"])
+    ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci", "ci_eig"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
     args = ap.parse_args()
     global PRECISION, WORKLOAD, C3, SCHEME
-    SCHEME = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1)}[args.scheme]
+    SCHEME = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}[args.scheme]
     if args.workload == "c3":
         C3 = True
         WORKLOAD = "sphere-cone-192x128x96-air11-2T-mach20-CS1-fp64"
@@ -499,6 +499,8 @@ def main():
     nodes, fs = make_case(P)
     g = P.Grid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
+    if args.scheme == "ci_eig":
+        g.set_option("ci_splitting", 1)
     g.init_freestream()
     N = g.ncell
     for _ in range(args.warmup):
@@ -573,7 +575,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "cells": N, "species": 11, "temperatures": 2,
                        "scheme": {"cs1": "CS-1 split LU-SGS", "cs2": "CS-2 split LU-SGS",
-                                  "ci": "coupled (CI) LU-SGS"}[args.scheme], "cfl": CFL,
+                                  "ci": "coupled (CI) LU-SGS",
+                                  "ci_eig": "coupled (CI) LU-SGS, eigenvalue splitting"}[args.scheme], "cfl": CFL,
                        "l2": "flushed before every timed iteration (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),

@@ -187,7 +187,15 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * specific thermal plus pool energy.  alpha is 1 once increments are small, so the converged
  * solution does not change; it only carries an impulsively started hypersonic flow through
  * its start-up transient at large CFL.
- * Errors: CS_ERR_ARG for an unknown name or a negative / NaN update_limit. */
+ * Method option: "ci_splitting" = 0 (default) splits the coupled operator's flux Jacobian
+ * spectrally, A+- = (A +- lambda I)/2 (the paper's choice, Sec. 2.3); 1 uses the eigenvalue
+ * splitting A+- = (A +- |A|)/2 with |A| = R |Lambda| R^-1 (the acoustic waves U_n +- c and
+ * U_n for the rest), the viscous radius staying a scalar: the diagonal block becomes
+ * (V/dtau + sum 2 lambda_vis) I + sum_d |A(S_d)| - V dS/dQ and the neighbours couple with
+ * -(A + |A| + 2 lambda_vis)/2 and (A - |A| - 2 lambda_vis)/2.  The split operator is not
+ * affected.
+ * Errors: CS_ERR_ARG for an unknown name, a negative / NaN update_limit or a ci_splitting
+ * other than 0 or 1. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Dual time stepping for unsteady flow (Sec. 2.3, the dual-time form of the implicit scheme).

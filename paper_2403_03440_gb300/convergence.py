@@ -26,7 +26,9 @@ CASES = {
     # 2D Mach 15 cylinder, 384 x 256 cells over the windward half, 11-species two-temperature air
     "c2": dict(ni=384, nj=256, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5 / 8),
 }
-SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1)}
+# ci_eig: the coupled operator with the eigenvalue splitting A+- = (A +- |A|)/2 instead of the
+# spectral one (option ci_splitting = 1)
+SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}
 
 
 def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1,
@@ -41,6 +43,8 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
     g.init_freestream()
     if update_limit > 0:
         g.set_option("update_limit", update_limit)
+    if scheme == "ci_eig":
+        g.set_option("ci_splitting", 1)
     sch, corr = SCHEMES[scheme]
     kw = dict(scheme=sch, correction=corr, clip=clip, cfl=cfl, cfl_start=cfl_start,
               ramp_iters=ramp, precision=precision)

@@ -822,6 +822,11 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     g->g.hcorr = value != 0.0;
     return CS_OK;
   }
+  if (!strcmp(name, "ci_splitting")) {
+    if (value != 0.0 && value != 1.0) return fail(g, CS_ERR_ARG, "ci_splitting must be 0 or 1");
+    g->g.cisplit = (int)value;
+    return CS_OK;
+  }
   return fail(g, CS_ERR_ARG, "unknown option %s", name);
 }
 
@@ -893,6 +898,7 @@ struct cs_batch_s {
   std::vector<cs_step_opts> key;       // options the graph was captured with
   std::vector<cs_mlp> key_surr;        // and the networks attached then
   std::vector<const double*> key_dual; // and the dual-time level buffers then
+  std::vector<int> key_split;          // and the coupled operator's splitting then
   int key_k = 0;
   char err[512] = {0};
 };
@@ -1062,7 +1068,7 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
     bool recapture = !b->exec || b->key_k != iters_per_graph || (int)b->key.size() != n;
     for (int c = 0; c < n && !recapture; ++c)
       recapture = !same_opts(b->key[c], opts[c]) || b->key_surr[c] != b->grids[c]->surr ||
-                  b->key_dual[c] != b->grids[c]->g.Qn;
+                  b->key_dual[c] != b->grids[c]->g.Qn || b->key_split[c] != b->grids[c]->g.cisplit;
     if (recapture) {
       if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
       BCUDA_TRY(b, cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
@@ -1095,6 +1101,8 @@ extern "C" cs_status cs_batch_step(cs_batch b, const cs_step_opts* opts, int ite
       for (int c = 0; c < n; ++c) b->key_surr.push_back(b->grids[c]->surr);
       b->key_dual.clear();
       for (int c = 0; c < n; ++c) b->key_dual.push_back(b->grids[c]->g.Qn);
+      b->key_split.clear();
+      for (int c = 0; c < n; ++c) b->key_split.push_back(b->grids[c]->g.cisplit);
       b->key_k = iters_per_graph;
     }
     // per-case setup on the case streams: status cleared, ramp counter = iterations done

@@ -38,6 +38,7 @@ struct DevGrid {
   int nd, ni, nj, nk, N;
   int bc[6];
   int limiter, react, hcorr, nojac;
+  int cisplit;            // coupled operator: 0 spectral splitting, 1 eigenvalue splitting
   double efix, Tw, ulim;
   int nf[3];
   const double* S[3];
@@ -1344,11 +1345,11 @@ __global__ void __launch_bounds__(128) k_spectral(DevGrid g) {
     const double lF = liF + 2.0 * lvF, lC = liC + 2.0 * lvC, lCI = liF + 2.0 * lvCI;
     g.lamF[d * N + c] = lF;
     g.lamC[d * N + c] = lC;
-    g.lamCI[d * N + c] = lCI;
+    g.lamCI[d * N + c] = g.cisplit ? 2.0 * lvCI : lCI;   // eigenvalue splitting: viscous part only
     sumdt += liF + lvF;
     sF += lF;
     sC += lC;
-    sCI += lCI;
+    sCI += g.cisplit ? 2.0 * lvCI : lCI;
   }
   // V / dtau, plus (1+theta) V / dt under dual time stepping (every diagonal carries it)
   const double Vdt = sumdt / g.params[0] + g.params[1] * V;
@@ -2455,6 +2456,51 @@ __global__ void __launch_bounds__(256) k_correct(DevGrid g, int mode, int clip, 
   if (nclip) atomicAdd(&g.status[2], nclip);
 }
 
+// |A(S)| x in CI variables for the eigenvalue splitting A+- = (A +- |A|)/2 (Sec. 2.3): the
+// acoustic waves U_n +- c carry alpha+- = (dp +- rho c dU_n) / (2 c^2) along (Y_s, u +- c n,
+// H +- U_n c, e_v); every other wave moves with U_n:
+//   |A| dq = |S| (|U_n| dq + (|U_n + c| - |U_n|) alpha+ r+ + (|U_n - c| - |U_n|) alpha- r-).
+template <class G, int ND>
+__device__ __forceinline__ void absjac_ci(const DevGrid& g, int nb, const double* S, const double* x,
+                                          double* y) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS, NF = A::NF;
+  const size_t N = g.N;
+  const double* W = g.W;
+  const double rho = W[A::RHO * N + nb], beta = W[A::BETA * N + nb], c = W[A::C * N + nb];
+  double a2 = 0.0;
+  for (int d = 0; d < ND; ++d) a2 += S[d] * S[d];
+  const double area = sqrt(a2), ia = 1.0 / area;
+  double u[ND], n[ND], Un = 0.0, ndm = 0.0, dp = 0.0;
+  double first = x[0];
+  for (int s = 1; s < NS; ++s) {
+    dp += W[(A::PRS + s) * N + nb] * x[NF + s - 1];
+    first -= x[NF + s - 1];
+  }
+  dp += W[(A::PRS + 0) * N + nb] * first;
+  for (int d = 0; d < ND; ++d) {
+    u[d] = W[(A::U + d) * N + nb];
+    n[d] = S[d] * ia;
+    Un += u[d] * n[d];
+    ndm += n[d] * x[1 + d];
+    dp -= beta * u[d] * x[1 + d];
+  }
+  dp += beta * x[ND + 1];
+  if (G::NTEMP == 2) dp += W[A::PREV * N + nb] * x[NF - 1];
+  const double dUn = (ndm - Un * x[0]) / rho;
+  const double i2c2 = 0.5 / (c * c);
+  const double ap = (dp + rho * c * dUn) * i2c2, am = (dp - rho * c * dUn) * i2c2;
+  const double l0 = fabs(Un), lp = fabs(Un + c) - l0, lm = fabs(Un - c) - l0;
+  const double H = W[A::H * N + nb];
+  const double wsum = lp * ap + lm * am;          // coefficient of the (Y_s, e_v) parts
+  y[0] = area * (l0 * x[0] + wsum);               // sum of the species rows (sum_s Y_s = 1)
+  for (int d = 0; d < ND; ++d)
+    y[1 + d] = area * (l0 * x[1 + d] + lp * ap * (u[d] + c * n[d]) + lm * am * (u[d] - c * n[d]));
+  y[ND + 1] = area * (l0 * x[ND + 1] + lp * ap * (H + Un * c) + lm * am * (H - Un * c));
+  if (G::NTEMP == 2) y[NF - 1] = area * (l0 * x[NF - 1] + wsum * W[A::EV * N + nb]);
+  for (int s = 1; s < NS; ++s) y[NF + s - 1] = area * (l0 * x[NF + s - 1] + wsum * W[(A::Y + s) * N + nb]);
+}
+
 // ---------------------------------------------------------------------------------------
 // Coupled (CI) operator: dense diagonal blocks (V/dtau + sum lambda) I - V dS/dQ_CI with one
 // species eliminated through the total density (Sec. 2.2, Sec. 2.3.3; the eliminated species
@@ -2473,6 +2519,23 @@ __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
   for (int e = 0; e < NC; ++e) M[e * NC + e] = diag;
   const double V = g.V[c];
   if (G::NTEMP == 2) M[(NF - 1) * NC + NF - 1] += V * g.W[A::RELAX * N + c];
+  if (g.cisplit) {
+    // eigenvalue splitting: + sum_d |A_c(S_d)|, S_d the mean of the cell's two d-faces
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    for (int d = 0; d < ND; ++d) {
+      const double* Sm = face_vec(g, d, i, j, k, -1);
+      const double* Sp = face_vec(g, d, i, j, k, +1);
+      double Sb[ND];
+      for (int q = 0; q < ND; ++q) Sb[q] = 0.5 * (Sm[q] + Sp[q]);
+      for (int col = 0; col < NC; ++col) {
+        double e[NC], a[NC];
+        for (int q = 0; q < NC; ++q) e[q] = q == col ? 1.0 : 0.0;
+        absjac_ci<G, ND>(g, c, Sb, e, a);
+        for (int r = 0; r < NC; ++r) M[r * NC + col] += a[r];
+      }
+    }
+  }
   if (g.react && G::NR > 0) {
     double q[NQ];
     for (int v = 0; v < NQ; ++v) q[v] = g.Q[v * N + c];
@@ -2629,7 +2692,14 @@ __global__ void __launch_bounds__(64) k_sweep_coupled(DevGrid g, int h, int off,
       double xn[NC], ax[NC];
       for (int q = 0; q < NC; ++q) xn[q] = X[q * N + nb];
       jvp_ci<G, ND>(g, nb, Sf, xn, ax);
+      // spectral splitting: lamCI = the coupled radius; eigenvalue splitting: lamCI = 2
+      // lambda_vis and |A_nb(S_f)| x is added
       const double l = g.lamCI[d * N + nb];
+      if (g.cisplit) {
+        double bx[NC];
+        absjac_ci<G, ND>(g, nb, Sf, xn, bx);
+        for (int q = 0; q < NC; ++q) ax[q] += (s < 0 ? bx[q] : -bx[q]);
+      }
       for (int q = 0; q < NC; ++q) {
         if (s < 0) acc[q] += 0.5 * (ax[q] + l * xn[q]);
         else acc[q] -= 0.5 * (ax[q] - l * xn[q]);

@@ -144,6 +144,55 @@ def test_coupled_operator_parity(name):
         assert rel(dg[ref.nF:], dr[ref.nF:], ns=ref.nci - ref.nF) < tol
 
 
+@pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "box3d_air5_kper", "sphere_cone_air11"])
+@pytest.mark.parametrize("reacting", [False, True])
+def test_coupled_operator_parity_eigenvalue_splitting(name, reacting):
+    """The coupled operator with the eigenvalue splitting A+- = (A +- |A|)/2: dense diagonal
+    blocks with sum_d |A(S_d)|, |A| x in the sweeps; the non-reacting blocks at the FP64
+    tolerance, the reacting ones at the conditioning bound of the spectral case."""
+    ref, gpu, _ = make_pair(name, seed=6, reacting=reacting)
+    ref.set_ci_splitting(1)
+    gpu.set_option("ci_splitting", 1)
+    ref.residual()
+    gpu.residual(want_R=False)
+    dr = ref.lusgs_coupled(4.0)
+    dg = gpu.lusgs_coupled(4.0)
+    assert rel(gpu.field("lamCI").reshape(ref.nd, -1), ref.field("lamCIv").reshape(-1, 3)[:, :ref.nd].T) < TOL
+    tol = TOL * 10 if not reacting else (1e-8 if ref.ns < 11 else 1e-6)
+    assert rel(dg[:ref.nF], dr[:ref.nF]) < tol
+    assert rel(dg[ref.nF:], dr[ref.nF:], ns=ref.nci - ref.nF) < tol
+    # and it is a different operator from the spectral one
+    gpu.set_option("ci_splitting", 0)
+    gpu.residual(want_R=False)
+    ds = gpu.lusgs_coupled(4.0)
+    assert rel(ds[:ref.nF], dr[:ref.nF]) > 1e-4
+
+
+def test_eigenvalue_splitting_multi_iteration_parity():
+    """20 coupled iterations with the eigenvalue splitting from the freestream (C1 grid; CFL
+    ramped from 0.5 to 5: at CFL 10 this operator, with less diagonal weight than the
+    spectral one, loses the impulsive start on both sides)."""
+    nodes_fn, bc, mech, _ = CASES["c1_ogrid_air5"]
+    nodes = nodes_fn()
+    fs = inputs.freestream(mech, T=300.0, p=500.0, mach=10.0)
+    ref = oracle.OracleGrid(nodes, bc, mech)
+    ref.set_boundary(fs, Tw=500.0)
+    ref.set_ci_splitting(1)
+    gpu = P.Grid(nodes, bc, mech)
+    gpu.set_boundary(fs, Tw=500.0)
+    gpu.set_option("ci_splitting", 1)
+    Q0 = ref.freestream_state()
+    ref.set_state(Q0)
+    gpu.set_state(Q0)
+    kw = dict(scheme=1, correction=1, clip=1, cfl=5.0, cfl_start=0.5, ramp_iters=50, iters=20)
+    sr = ref.step(**kw)
+    sg = gpu.step(**kw)
+    assert sr["iters_done"] == sg["iters_done"] == 20
+    assert rel(gpu.get_state(), ref.get_state(), ns=ref.ns) < 1e-9
+    with pytest.raises(P.CSError):
+        gpu.set_option("ci_splitting", 2)
+
+
 @pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "sphere_cone_air11"])
 def test_coupled_operator_parity_nonreacting(name):
     """Without the source Jacobian the coupled blocks are well conditioned: exact sweep
