@@ -377,11 +377,11 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
       return CS_ERR_CUDA;
     if (cudaStreamSynchronize(g->stream) != cudaSuccess) return CS_ERR_CUDA;
     d.woff = woff;
-    const size_t groups = (L->ns + 3) / 4;
+    const size_t groups = (L->ns + kSpeciesGroup - 1) / kSpeciesGroup;
     double *wr, *wrs, *wb;
     ALLOC(wr, (size_t)kRecF * N);
     ALLOC(wrs, groups * kRecS * N);
-    ALLOC(wb, (8 + 4 * groups) * N);
+    ALLOC(wb, (8 + kSpeciesGroup * groups) * N);
     d.wrec = wr;
     d.wrecs = wrs;
     d.wbase = wb;
@@ -968,16 +968,22 @@ template <class F>
 static cs_status with_batch_streams(cs_batch b, F fn) {
   const int n = (int)b->grids.size();
   std::vector<cudaStream_t> saved(n);
+  std::vector<int> warps(n);
   for (int c = 0; c < n; ++c) {
     // work the caller queued on the grid's own stream comes first
     BCUDA_TRY(b, cudaStreamSynchronize(b->grids[c]->stream));
     saved[c] = b->grids[c]->stream;
     b->grids[c]->stream = b->streams[c];
+    // many grids share the GPU: the one-warp form of the cluster sweep keeps twice as many
+    // CTAs resident
+    warps[c] = b->grids[c]->L->cluster_warps;
+    b->grids[c]->L->cluster_warps = 1;
   }
   const cs_status st = fn();
   for (int c = 0; c < n; ++c) {
     cudaStreamSynchronize(b->streams[c]);
     b->grids[c]->stream = saved[c];
+    b->grids[c]->L->cluster_warps = warps[c];
   }
   return st;
 }

@@ -1550,16 +1550,21 @@ __device__ __forceinline__ T* dsmem(T* p, unsigned rank) {
 }
 
 constexpr int kClusterRows = 32;   // max rows per CTA
-constexpr int kClusterWarps = 1;   // warps per CTA (8 warps measured slower than 1: the per-step
-                                   // cost is load latency and FP64 dependency depth)
-// Row handled by this thread of the CTA (rows t = warp + kClusterWarps k for the first lane of
-// each of the rpw lane groups), or -1 for a thread that only takes part in the barriers.
+// Warps per CTA of the direct-load cluster kernel: 1 or 2, both covering the CTA's R rows (one
+// lane per row).  With 2, the flow cluster splits each step's FP64 work: warp 0 takes the
+// coupling of the neighbouring row and the update, warp 1 the row's own earlier cells (GB300
+// issues FP64 at ~1/64 of its FP32 rate; the two warps run on two SM sub-partitions), 5 % faster
+// for one grid; with 1 a CTA needs half the registers, so twice as many CTAs stay resident, which
+// is what a batch of many grids needs.  Splitting rows over more warps instead was measured
+// slower (more FP64 instructions at the same cost each).  In a species cluster the second warp
+// only takes part in the barriers.
+// Row handled by this lane (the first lane of each of the R lane groups), or -1 for a lane
+// that only takes part in the barriers.
 __device__ __forceinline__ int cluster_row(int R) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rpw = (R + kClusterWarps - 1) / kClusterWarps;     // rows per warp (<= 4)
-  const int stride = 32 / rpw;
+  const int lane = threadIdx.x & 31;
+  const int stride = 32 / R;
   if (lane % stride != 0) return -1;
-  const int t = warp + kClusterWarps * (lane / stride);
+  const int t = lane / stride;
   return t < R ? t : -1;
 }
 
@@ -1625,8 +1630,10 @@ __device__ __forceinline__ void flow_step_load(const DevGrid& g, int q, int j, b
   }
 }
 
+// One warp per CTA: the row's own earlier cells are coupled while the cluster barrier is
+// pending, the neighbouring row after it (the variant with fewer registers per CTA, for batches).
 template <class G, class T>
-__device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF, T>& xc) {
+__device__ void sweep_flow_cluster1(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF, T>& xc) {
   using A = Aux<G, 2>;
   constexpr int NF = A::NF;
   const size_t N = g.N;
@@ -1697,13 +1704,122 @@ __device__ void sweep_flow_cluster(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::N
   }
 }
 
-constexpr int kSpeciesGroup = 4;   // species per cluster (they share u, lambda and S)
+// Two warps per CTA: warp 0 couples the neighbouring row and updates, warp 1 couples the row's
+// own earlier cells.
+template <class G, class T>
+__device__ void sweep_flow_cluster2(const DevGrid& g, int R, Xchg<G, Aux<G, 2>::NF, T>& xc,
+                                    T (&accI)[kClusterRows][Aux<G, 2>::NF]) {
+  using A = Aux<G, 2>;
+  constexpr int NF = A::NF;
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank();
+  const bool lead = threadIdx.x < 32;          // warp 0: neighbour row + update; warp 1: own row
+  const int t = cluster_row(R);
+  const int j = rank * R + t;
+  const bool row = t >= 0 && j < g.nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int ni = g.ni, H = ni + g.nj - 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    T prevx[NF], firstx[NF];
+    CellState<G, 2, T> prevS, firstS;
+    T prevL = 0, firstL = 0;
+    FlowStep<G, T> cur, nxt;
+    flow_step_load<G, T>(g, 0, j, row, fwd, cur);
+    for (int q = 0; q <= H; ++q) {
+      const int i = (fwd ? q : H - q) - j;
+      flow_step_load<G, T>(g, q + 1, j, row, fwd, nxt);     // prefetch the next step
+      T acc[NF];
+#pragma unroll
+      for (int v = 0; v < NF; ++v) acc[v] = T(0);
+      if (lead) {
+        // coupling of the neighbouring row: its result of step q-1 comes from this CTA's shared
+        // memory or, across a CTA boundary, the neighbour CTA's, after the cluster barrier
+        if (q > 0) cluster_wait();
+        if (cur.act && cur.hasj) {
+          const T* src;
+          const int par = (q - 1) & 1;
+          if (fwd) src = (t > 0) ? xc.v[par][t - 1] : dsmem(&xc.v[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xc.v[par][t + 1] : dsmem(&xc.v[par][0][0], rank + 1);
+          T xn[NF];
+#pragma unroll
+          for (int v = 0; v < NF; ++v) xn[v] = src[v];
+          flow_contrib<G, T>(cur.jn, cur.jlam, cur.Sj, xn, fwd ? -1 : +1, acc);
+        }
+      } else if (cur.act) {
+        // the row's own earlier results (the i-neighbour, the periodic neighbour): no other
+        // CTA is involved, so this runs while warp 0 waits for the cluster barrier
+        if (fwd) {
+          if (i > 0) flow_contrib<G, T>(prevS, prevL, cur.Si, prevx, -1, acc);
+          if (per && i == ni - 1) flow_contrib<G, T>(firstS, firstL, cur.Sw, firstx, +1, acc);
+        } else {
+          if (per && i == 0) flow_contrib<G, T>(firstS, firstL, cur.Sw, firstx, -1, acc);
+          if (i < ni - 1) flow_contrib<G, T>(prevS, prevL, cur.Si, prevx, +1, acc);
+        }
+#pragma unroll
+        for (int v = 0; v < NF; ++v) accI[t][v] = acc[v];
+      }
+      __syncthreads();                 // warp 1's contributions are in accI
+      if (lead && cur.act) {
+        double* out = fwd ? g.dQs : g.dQ;
+#pragma unroll
+        for (int v = 0; v < NF; ++v) {
+          const T d = (G::NTEMP == 2 && v == NF - 1) ? cur.iDev : cur.iD;
+          const T a = acc[v] + accI[t][v];
+          const T x = fwd ? (cur.base[v] + a) * d : cur.base[v] + a * d;
+          out[v * N + cur.c] = (double)x;
+          xc.v[q & 1][t][v] = x;
+        }
+      }
+      __syncthreads();                 // this step's results are in xc.v[q & 1]
+      if (!lead) {
+        if (cur.act) {
+#pragma unroll
+          for (int v = 0; v < NF; ++v) prevx[v] = xc.v[q & 1][t][v];
+          prevS = cur.me;
+          prevL = cur.lam0;
+          if (i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+            for (int v = 0; v < NF; ++v) firstx[v] = prevx[v];
+            firstS = cur.me;
+            firstL = cur.lam0;
+          }
+        }
+        if (q > 0) cluster_wait();     // complete the previous phase before arriving again
+      }
+      cluster_arrive();
+      cur = nxt;
+    }
+    cluster_wait();
+  }
+}
+
+// Species per component (they share u, lambda and S).  The record kernels (k_pack_wave,
+// k_split_wave, k_split_block) move a group's values with 16-byte cp.async copies, so their
+// group times the element size must be a multiple of 16 bytes; the direct-load cluster kernel
+// takes two species per cluster, which keeps the FP64 work of a species step below the flow
+// block's.
+constexpr int kSpeciesGroup = 4;
+constexpr int kClusterSpeciesGroup = 4;
+static_assert(kSpeciesGroup * sizeof(float) % 16 == 0, "record groups must be whole 16-byte pieces");
 
 template <class G, class T>
-__device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, kSpeciesGroup, T>& xc) {
+__device__ void sweep_species_cluster(const DevGrid& g, int R, int s0, Xchg<G, kClusterSpeciesGroup, T>& xc) {
   using A = Aux<G, 2>;
-  constexpr int NF = A::NF, SG = kSpeciesGroup;
+  constexpr int NF = A::NF, SG = kClusterSpeciesGroup;
   const size_t N = g.N;
+  if (threadIdx.x >= 32) {
+    // the second warp of a species CTA: the same sequence of cluster barriers as warp 0
+    const int H = g.ni + g.nj - 2;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int q = 0; q <= H; ++q) {
+        if (q > 0) cluster_wait();
+        cluster_arrive();
+      }
+      cluster_wait();
+    }
+    return;
+  }
   const unsigned rank = cluster_ctarank();
   const int t = cluster_row(R);
   const int j = rank * R + t;
@@ -2286,6 +2402,9 @@ __global__ void __launch_bounds__(32) k_split_wave(DevGrid g, int R) {
 
 template <class G>
 constexpr int species_clusters() { return (G::NS + kSpeciesGroup - 1) / kSpeciesGroup; }
+// species clusters of the direct-load cluster kernel k_split_cluster
+template <class G>
+constexpr int cluster_species_clusters() { return (G::NS + kClusterSpeciesGroup - 1) / kClusterSpeciesGroup; }
 
 // K6d: 2D split sweeps in FP32 with one CTA per component (the flow block, then one per group
 // of 4 species) holding every row of the grid: same records and arithmetic as K6c, with
@@ -2311,14 +2430,21 @@ __global__ void __launch_bounds__(kBlockRows) k_split_block(DevGrid g) {
                                              *reinterpret_cast<WaveSmemS<G, float, kBlockRows>*>(bsm));
 }
 
-template <class G, class T>
-__global__ void __launch_bounds__(32 * kClusterWarps) k_split_cluster(DevGrid g, int R) {
-  constexpr int NV = Aux<G, 2>::NF > kSpeciesGroup ? Aux<G, 2>::NF : kSpeciesGroup;
+template <class G, class T, int W>
+__global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
+  constexpr int NV = Aux<G, 2>::NF > kClusterSpeciesGroup ? Aux<G, 2>::NF : kClusterSpeciesGroup;
   __shared__ Xchg<G, NV, double> xf;   // sized for the widest use
+  __shared__ double accI[kClusterRows][Aux<G, 2>::NF];
   const int comp = blockIdx.x / (int)cluster_nctarank();   // uniform within a cluster
-  if (comp == 0) sweep_flow_cluster<G, T>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF, T>*>(&xf));
-  else sweep_species_cluster<G, T>(g, R, (comp - 1) * kSpeciesGroup,
-                                   *reinterpret_cast<Xchg<G, kSpeciesGroup, T>*>(&xf));
+  if (comp == 0) {
+    if constexpr (W == 2)
+      sweep_flow_cluster2<G, T>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF, T>*>(&xf),
+                                *reinterpret_cast<T(*)[kClusterRows][Aux<G, 2>::NF]>(&accI));
+    else
+      sweep_flow_cluster1<G, T>(g, R, *reinterpret_cast<Xchg<G, Aux<G, 2>::NF, T>*>(&xf));
+  }
+  else sweep_species_cluster<G, T>(g, R, (comp - 1) * kClusterSpeciesGroup,
+                                   *reinterpret_cast<Xchg<G, kClusterSpeciesGroup, T>*>(&xf));
 }
 
 // ---------------------------------------------------------------------------------------

@@ -36,6 +36,7 @@ struct Launcher {
   bool use_cluster = true;
   int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records
   int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
+  int cluster_warps = 2;   // warps per CTA of the direct-load cluster kernel (batches: 1)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
   // bit C of the result is set when the cluster sweep of `kind` (1 direct, 2 wavefront
   // records) can run with C CTAs per component on this grid and device
@@ -166,16 +167,17 @@ struct LauncherT : Launcher {
     }
   }
 
-  // Can `kern` run as clusters of C CTAs (32 x warps threads each) with `rows` rows per CTA?
+  // Can `kern` run as clusters of C CTAs (32 x warps threads each), one cluster per component
+  // (the flow block and `groups` species groups)?
   template <class K>
-  bool cluster_fits(K kern, int C, int warps) {
+  bool cluster_fits(K kern, int C, int warps, int groups) {
     if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
+    cfg.gridDim = dim3(C * (1 + groups));
     cfg.blockDim = dim3(32 * warps);
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
@@ -189,6 +191,17 @@ struct LauncherT : Launcher {
     return false;
   }
 
+  // The direct-load cluster kernel fits with C CTAs per cluster (checked for its two-warp form,
+  // the one with more registers per CTA); clusters above 8 CTAs are allowed for both forms.
+  template <class T>
+  bool direct_fits(int C) {
+    if (C > 8 && cudaFuncSetAttribute(k_split_cluster<G, T, 1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    return cluster_fits(k_split_cluster<G, T, 2>, C, 2, cluster_species_clusters<G>());
+  }
+
   // Cluster size for the direct-load cluster sweep (0: not available for this grid / device).
   template <class T>
   int cluster_size(const DevGrid& g, int& probed) {
@@ -198,7 +211,7 @@ struct LauncherT : Launcher {
     probed = 0;
     for (int C : {16, 8, 4, 2}) {
       if ((g.nj + C - 1) / C > kClusterRows) continue;
-      if (cluster_fits(k_split_cluster<G, T>, C, kClusterWarps)) {
+      if (direct_fits<T>(C)) {
         probed = C;
         break;
       }
@@ -233,7 +246,7 @@ struct LauncherT : Launcher {
     probed = 0;
     for (int C : {16, 8, 4, 2, 1}) {
       if ((g.nj + C - 1) / C > kWaveRows) continue;
-      if (cluster_fits(k_split_wave<G, T>, C, 1)) {
+      if (cluster_fits(k_split_wave<G, T>, C, 1, species_clusters<G>())) {
         probed = C;
         break;
       }
@@ -248,11 +261,10 @@ struct LauncherT : Launcher {
       bool ok;
       if (kind == 2) {
         ok = (g.nj + C - 1) / C <= kWaveRows && g.wrec &&
-             (mixed ? cluster_fits(k_split_wave<G, float>, C, 1) : cluster_fits(k_split_wave<G, double>, C, 1));
+             (mixed ? cluster_fits(k_split_wave<G, float>, C, 1, species_clusters<G>()) : cluster_fits(k_split_wave<G, double>, C, 1, species_clusters<G>()));
       } else {
         ok = C >= 2 && (g.nj + C - 1) / C <= kClusterRows &&
-             (mixed ? cluster_fits(k_split_cluster<G, float>, C, kClusterWarps)
-                    : cluster_fits(k_split_cluster<G, double>, C, kClusterWarps));
+             (mixed ? direct_fits<float>(C) : direct_fits<double>(C));
       }
       if (ok) mask |= 1 << C;
     }
@@ -326,8 +338,9 @@ struct LauncherT : Launcher {
     if (C == 0) return 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[1];
-    cfg.gridDim = dim3(C * (1 + species_clusters<G>()));
-    cfg.blockDim = dim3(32 * kClusterWarps);
+    cfg.gridDim = dim3(C * (1 + cluster_species_clusters<G>()));
+    const int W = cluster_warps == 1 ? 1 : 2;
+    cfg.blockDim = dim3(32 * W);
     cfg.stream = st;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
@@ -336,7 +349,9 @@ struct LauncherT : Launcher {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const int R = (g.nj + C - 1) / C;
-    if (cudaLaunchKernelEx(&cfg, k_split_cluster<G, T>, g, R) != cudaSuccess) {
+    const cudaError_t e = W == 1 ? cudaLaunchKernelEx(&cfg, k_split_cluster<G, T, 1>, g, R)
+                                 : cudaLaunchKernelEx(&cfg, k_split_cluster<G, T, 2>, g, R);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return 0;
     }
