@@ -47,14 +47,14 @@ FP64_FLOPS_PER_CELL = {
     "flux": 2844.0,            # both directions
     "assemble": 130.0,
     "spectral": 361.0,
-    "sweep_fwd": 474.0,        # both sweeps of all components (one cluster launch)
+    "sweep_fwd": 504.0,        # both sweeps of all components (one cluster launch)
     "sweep_bwd": 0.0,
     "correct": 109.0,
 }
 FP32_FLOPS_PER_CELL_SWEEP = 652.0     # the FP32 one-CTA-per-component sweep of the mixed operator
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
-    "primitive": 34.0e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 37.2e6, "gradient": 17.4e6,
+    "primitive": 34.0e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 36.6e6, "gradient": 17.4e6,
     "spectral": 54.1e6, "assemble": 33.9e6, "correct": 24.4e6,
 }
 DRAM_BYTES_SWEEP_FP32 = 36.6e6 + 38.3e6   # record packing + FP32 sweep
