@@ -454,6 +454,8 @@ def main():
     ap.add_argument("--species", type=lambda t: [int(x) for x in t.split(",")],
                     default=[16, 64, 256, 1024, 4096])
     ap.add_argument("--ci-max-species", type=int, default=1024)
+    ap.add_argument("--dual-dt", type=float, default=0.0,
+                    help="physical time step of dual time stepping (0: steady pseudo-time iteration)")
     ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci", "ci_eig"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
@@ -469,6 +471,8 @@ def main():
         WORKLOAD = WORKLOAD.replace("fp64", "mixed-fp32-operator")
     if args.scheme != "cs1":
         WORKLOAD = WORKLOAD.replace("CS1", args.scheme.upper())
+    if args.dual_dt > 0:
+        WORKLOAD += f"-dual-dt{args.dual_dt:g}"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -502,6 +506,11 @@ def main():
     if args.scheme == "ci_eig":
         g.set_option("ci_splitting", 1)
     g.init_freestream()
+    if args.dual_dt > 0:
+        # dual time stepping: one physical step begun from the freestream, theta = 1/2 (the
+        # pseudo-time iterations below are its inner iterations)
+        g.set_dual(args.dual_dt, 0.5)
+        g.dual_advance()
     N = g.ncell
     for _ in range(args.warmup):
         g.step(**step_kwargs(1))
