@@ -25,6 +25,8 @@ CASES = {
     "c1": dict(ni=48, nj=32, mech=inputs.MECH_AIR5, mach=10.0, dr1=5e-5),
     # 2D Mach 15 cylinder, 384 x 256 cells over the windward half, 11-species two-temperature air
     "c2": dict(ni=384, nj=256, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5 / 8),
+    # 3D Mach 20 sphere-cone, 192 x 128 x 96 cells, 11-species two-temperature air
+    "c3": dict(ni=192, nj=128, nk=96, mech=inputs.MECH_AIR11, mach=20.0),
 }
 # ci_eig: the coupled operator with the eigenvalue splitting A+- = (A +- |A|)/2 instead of the
 # spectral one (option ci_splitting = 1)
@@ -34,11 +36,14 @@ SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}
 def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1,
         update_limit=0.0):
     c = CASES[case]
-    # The windward half only: a full O-grid holds the cylinder's near wake, which is unsteady
-    # at these Reynolds numbers and keeps the residual from converging.
-    nodes = inputs.cylinder_half(c["ni"], c["nj"], dr1=c["dr1"])
+    if "nk" in c:
+        nodes, bc = inputs.sphere_cone(c["ni"], c["nj"], c["nk"]), inputs.sphere_cone_bc()
+    else:
+        # The windward half only: a full O-grid holds the cylinder's near wake, which is
+        # unsteady at these Reynolds numbers and keeps the residual from converging.
+        nodes, bc = inputs.cylinder_half(c["ni"], c["nj"], dr1=c["dr1"]), inputs.cylinder_half_bc()
     fs = inputs.freestream(c["mech"], T=300.0, p=500.0, mach=c["mach"])
-    g = P.Grid(nodes, inputs.cylinder_half_bc(), c["mech"], limiter=limiter)
+    g = P.Grid(nodes, bc, c["mech"], limiter=limiter)
     g.set_boundary(fs, Tw=500.0)
     g.init_freestream()
     if update_limit > 0:
@@ -74,7 +79,7 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
                 cfl_start=cfl_start, ramp=ramp, update_limit=update_limit,
                 limiter=limiter, tol=tol, status=status, iterations=done, seconds=dt,
                 ms_per_iter=1e3 * dt / max(done - 1, 1), min_drop=best,
-                q_stag_final=hist[-1][3], cells=c["ni"] * c["nj"],
+                q_stag_final=hist[-1][3], cells=c["ni"] * c["nj"] * c.get("nk", 1),
                 history=hist[:: max(1, len(hist) // 50)] + [hist[-1]])
 
 
