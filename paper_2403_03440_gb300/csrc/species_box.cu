@@ -266,64 +266,127 @@ __device__ double block_sum(double v, double* sh) {
 
 // Dense diagonal block per cell, LU with partial pivoting in place, column-major (element
 // (i, j) at j n + i); piv[k] = row swapped with row k.  One CTA per cell (grid-stride).
+// Right-looking and blocked by panels of kPanel columns: (1) the panel is factorised column
+// by column (pivot search, swap of the whole row, scaling, update inside the panel); (2) the
+// panel's block row right of it is solved with the panel's unit lower triangle; (3) the
+// trailing matrix takes the rank-kPanel update L21 U12 in 64 x 64 tiles staged through shared
+// memory, each thread accumulating a 4 x 4 block in registers.  The same arithmetic as the
+// unblocked algorithm up to the order of the sums in the trailing update.
+constexpr int kPanel = 32, kTile = 64;
+
 __global__ void __launch_bounds__(kCiThreads) k_ci_factor(Box b, double* LU, int* piv, int* err) {
   __shared__ double sv[kCiThreads];
   __shared__ int si[kCiThreads];
+  __shared__ double sL[kPanel][kTile];   // L21 tile, column c of the panel x 64 rows
+  __shared__ double sU[kPanel][kTile];   // U12 tile, row c of the panel x 64 columns
   const int n = b.ns + 4;
   const size_t nn = (size_t)n * n;
+  const int tid = threadIdx.x;
   for (int c = blockIdx.x; c < b.N; c += gridDim.x) {
     double* A = LU + (size_t)c * nn;
     const double diag = b.aux[A_DF * (size_t)b.N + c];   // V/dtau + sum lambda (no source Jacobian)
-    for (size_t e = threadIdx.x; e < nn; e += blockDim.x) A[e] = (e % (n + 1) == 0) ? diag : 0.0;
+    for (size_t e = tid; e < nn; e += blockDim.x) A[e] = (e % (n + 1) == 0) ? diag : 0.0;
     __syncthreads();
-    for (int k = 0; k < n; ++k) {
-      // pivot: the largest |A(i, k)|, i >= k (first one on ties)
-      double best = -1.0;
-      int bi = k;
-      for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
-        const double v = fabs(A[(size_t)k * n + i]);
-        if (v > best) { best = v; bi = i; }
+    bool singular = false;
+    for (int k0 = 0; k0 < n && !singular; k0 += kPanel) {
+      const int kb = n - k0 < kPanel ? n - k0 : kPanel, ke = k0 + kb;
+      // (1) panel
+      for (int k = k0; k < ke; ++k) {
+        double best = -1.0;
+        int bi = k;
+        for (int i = k + tid; i < n; i += blockDim.x) {
+          const double v = fabs(A[(size_t)k * n + i]);
+          if (v > best) { best = v; bi = i; }
+        }
+        sv[tid] = best;
+        si[tid] = bi;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+          if (tid < w) {
+            const double o = sv[tid + w];
+            const int oi = si[tid + w];
+            if (o > sv[tid] || (o == sv[tid] && oi < si[tid])) { sv[tid] = o; si[tid] = oi; }
+          }
+          __syncthreads();
+        }
+        const int p = si[0];
+        const double pv = sv[0];
+        __syncthreads();
+        if (tid == 0) piv[(size_t)c * n + k] = p;
+        if (!(pv > 0.0)) {
+          if (tid == 0) atomicExch(err, c + 1);
+          singular = true;
+          break;
+        }
+        if (p != k)
+          for (int jj = tid; jj < n; jj += blockDim.x) {
+            const double t = A[(size_t)jj * n + k];
+            A[(size_t)jj * n + k] = A[(size_t)jj * n + p];
+            A[(size_t)jj * n + p] = t;
+          }
+        __syncthreads();
+        const double ip = 1.0 / A[(size_t)k * n + k];
+        for (int i = k + 1 + tid; i < n; i += blockDim.x) A[(size_t)k * n + i] *= ip;
+        __syncthreads();
+        const int mr = n - k - 1, mc = ke - k - 1;       // rows below, panel columns right of k
+        for (long e = tid; e < (long)mr * mc; e += blockDim.x) {
+          const int i = k + 1 + (int)(e % mr), jj = k + 1 + (int)(e / mr);
+          A[(size_t)jj * n + i] -= A[(size_t)k * n + i] * A[(size_t)jj * n + k];
+        }
+        __syncthreads();
       }
-      sv[threadIdx.x] = best;
-      si[threadIdx.x] = bi;
+      if (singular || ke >= n) continue;
+      // (2) U12 = L11^-1 A12, one thread per column right of the panel
+      for (int jj = ke + tid; jj < n; jj += blockDim.x) {
+        double* col = A + (size_t)jj * n;
+        for (int r = k0 + 1; r < ke; ++r) {
+          double acc = col[r];
+          for (int cc = k0; cc < r; ++cc) acc -= A[(size_t)cc * n + r] * col[cc];
+          col[r] = acc;
+        }
+      }
       __syncthreads();
-      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-          const double o = sv[threadIdx.x + w];
-          const int oi = si[threadIdx.x + w];
-          if (o > sv[threadIdx.x] || (o == sv[threadIdx.x] && oi < si[threadIdx.x])) {
-            sv[threadIdx.x] = o;
-            si[threadIdx.x] = oi;
+      // (3) A22 -= L21 U12
+      const int m = n - ke;
+      const int tiles = (m + kTile - 1) / kTile;
+      const int tx = tid % 16, ty = tid / 16;            // 4 x 4 block: rows 4 tx, columns 4 ty
+      for (int tt = 0; tt < tiles * tiles; ++tt) {
+        const int r0 = ke + (tt % tiles) * kTile, c0 = ke + (tt / tiles) * kTile;
+        for (int e = tid; e < kPanel * kTile; e += blockDim.x) {
+          const int cc = e / kTile, rr = e % kTile;
+          const bool in = cc < kb;
+          sL[cc][rr] = (in && r0 + rr < n) ? A[(size_t)(k0 + cc) * n + r0 + rr] : 0.0;
+          sU[cc][rr] = (in && c0 + rr < n) ? A[(size_t)(c0 + rr) * n + k0 + cc] : 0.0;
+        }
+        __syncthreads();
+        double acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[a][q] = 0.0;
+        for (int cc = 0; cc < kb; ++cc) {
+          double l[4], u[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) { l[a] = sL[cc][4 * tx + a]; u[a] = sU[cc][4 * ty + a]; }
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[a][q] += l[a] * u[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int jj = c0 + 4 * ty + q;
+          if (jj >= n) continue;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = r0 + 4 * tx + a;
+            if (i < n) A[(size_t)jj * n + i] -= acc[a][q];
           }
         }
         __syncthreads();
       }
-      const int p = si[0];
-      const double pv = sv[0];
-      __syncthreads();
-      if (threadIdx.x == 0) piv[(size_t)c * n + k] = p;
-      if (!(pv > 0.0)) {
-        if (threadIdx.x == 0) atomicExch(err, c + 1);
-        break;
-      }
-      if (p != k)
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-          const double t = A[(size_t)j * n + k];
-          A[(size_t)j * n + k] = A[(size_t)j * n + p];
-          A[(size_t)j * n + p] = t;
-        }
-      __syncthreads();
-      const double ip = 1.0 / A[(size_t)k * n + k];
-      for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)k * n + i] *= ip;
-      __syncthreads();
-      // trailing update A(i, j) -= A(i, k) A(k, j), i, j > k (i fastest: contiguous)
-      const int m = n - k - 1;
-      for (long e = threadIdx.x; e < (long)m * m; e += blockDim.x) {
-        const int i = k + 1 + (int)(e % m), j = k + 1 + (int)(e / m);
-        A[(size_t)j * n + i] -= A[(size_t)k * n + i] * A[(size_t)j * n + k];
-      }
-      __syncthreads();
     }
+    __syncthreads();
   }
 }
 
