@@ -400,6 +400,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   ALLOC(g->iter_dev, 1);
 #undef ALLOC
   d.DLU = nullptr;
+  d.DINV = nullptr;
   d.piv = nullptr;
   d.params = g->params;
   if (cudaMallocHost(&g->h_pin, 64 * sizeof(double)) != cudaSuccess) return CS_ERR_OOM;
@@ -434,6 +435,7 @@ extern "C" cs_status cs_grid_destroy(cs_grid g) {
   cudaStreamSynchronize(g->stream);
   for (void* p : g->allocs) cudaFree(p);
   if (g->g.DLU) cudaFree(g->g.DLU);
+  if (g->g.DINV) cudaFree(g->g.DINV);
   if (g->g.piv) cudaFree(g->g.piv);
   if (g->h_pin) cudaFreeHost(g->h_pin);
   if (g->h_status) cudaFreeHost(g->h_status);
@@ -586,11 +588,17 @@ extern "C" cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double
 static cs_status ensure_ci(cs_grid g) {
   if (g->g.DLU) return CS_OK;
   const size_t nc = g->L->nci;
-  void *a = nullptr, *b = nullptr;
+  void *a = nullptr, *b = nullptr, *v = nullptr;
   if (cudaMalloc(&a, nc * nc * (size_t)g->g.N * sizeof(double)) != cudaSuccess) return CS_ERR_OOM;
   if (cudaMalloc(&b, nc * (size_t)g->g.N * sizeof(int)) != cudaSuccess) { cudaFree(a); return CS_ERR_OOM; }
+  if (cudaMalloc(&v, nc * nc * (size_t)g->g.N * sizeof(double)) != cudaSuccess) {
+    cudaFree(a);
+    cudaFree(b);
+    return CS_ERR_OOM;
+  }
   g->g.DLU = (double*)a;
   g->g.piv = (int*)b;
+  g->g.DINV = (double*)v;
   return CS_OK;
 }
 
@@ -705,9 +713,11 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
   } else {
     g->L->ci_block(d, g->stream);
     if (rec) prof_record(g, slot, 5);
-    nf = g->L->sweep_coupled_dir(d, g->stream, true);
+    // both sweeps in one cluster launch where it applies (2D), else one launch per hyperplane
+    const bool one = g->L->use_cluster && g->L->sweep_coupled_cluster(d, g->stream);
+    nf = one ? 1 : g->L->sweep_coupled_dir(d, g->stream, true);
     if (rec) prof_record(g, slot, 6);
-    nb = g->L->sweep_coupled_dir(d, g->stream, false);
+    nb = one ? 0 : g->L->sweep_coupled_dir(d, g->stream, false);
     if (rec) prof_record(g, slot, 7);
     g->L->correct(d, g->stream, 0, o->clip, d.dQc);
   }

@@ -59,6 +59,7 @@ struct DevGrid {
   double* Ds;             // [ns][N]
   double* DLU;            // [N][nci*nci]
   int* piv;               // [N][nci]
+  double* DINV;           // [N][nci*nci] inverse of the coupled diagonal block (row-major)
   double* dQs;            // [nsplit][N]
   double* dQ;
   double* dQcs;           // [nci][N]
@@ -2632,6 +2633,20 @@ __device__ __forceinline__ void absjac_ci(const DevGrid& g, int nb, const double
 // species eliminated through the total density (Sec. 2.2, Sec. 2.3.3; the eliminated species
 // is the first of the list, N2, not the electron: see jvp_ci), LU with partial pivoting.
 // ---------------------------------------------------------------------------------------
+template <int NC>
+__device__ __forceinline__ void lu_solve(const double* M, const int* piv, double* b) {
+  for (int kk = 0; kk < NC; ++kk) {
+    const int p = piv[kk];
+    if (p != kk) { const double t = b[kk]; b[kk] = b[p]; b[p] = t; }
+  }
+  for (int r = 1; r < NC; ++r)
+    for (int col = 0; col < r; ++col) b[r] -= M[r * NC + col] * b[col];
+  for (int r = NC - 1; r >= 0; --r) {
+    for (int col = r + 1; col < NC; ++col) b[r] -= M[r * NC + col] * b[col];
+    b[r] /= M[r * NC + r];
+  }
+}
+
 template <class G, int ND>
 __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
   using A = Aux<G, ND>;
@@ -2739,21 +2754,19 @@ __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
       for (int col = kk + 1; col < NC; ++col) M[r * NC + col] -= l * M[kk * NC + col];
     }
   }
+  // the explicit inverse, column by column from the factors: the cluster sweep multiplies by
+  // it (independent dot products) instead of running the two dependent substitutions per step
+  if (g.DINV) {
+    double* Dv = g.DINV + (size_t)c * NC * NC;
+    for (int col = 0; col < NC; ++col) {
+      double e[NC];
+      for (int r = 0; r < NC; ++r) e[r] = r == col ? 1.0 : 0.0;
+      lu_solve<NC>(M, g.piv + (size_t)c * NC, e);
+      for (int r = 0; r < NC; ++r) Dv[r * NC + col] = e[r];
+    }
+  }
 }
 
-template <int NC>
-__device__ __forceinline__ void lu_solve(const double* M, const int* piv, double* b) {
-  for (int kk = 0; kk < NC; ++kk) {
-    const int p = piv[kk];
-    if (p != kk) { const double t = b[kk]; b[kk] = b[p]; b[p] = t; }
-  }
-  for (int r = 1; r < NC; ++r)
-    for (int col = 0; col < r; ++col) b[r] -= M[r * NC + col] * b[col];
-  for (int r = NC - 1; r >= 0; --r) {
-    for (int col = r + 1; col < NC; ++col) b[r] -= M[r * NC + col] * b[col];
-    b[r] /= M[r * NC + r];
-  }
-}
 
 // coupled Jacobian-vector product in CI variables (rho, m, rhoE, [rho e_v], rho_2..rho_ns);
 // the first species is eliminated: rho_1st = rho - sum of the others
@@ -2834,6 +2847,119 @@ __global__ void __launch_bounds__(64) k_sweep_coupled(DevGrid g, int h, int off,
   lu_solve<NC>(g.DLU + (size_t)c * NC * NC, g.piv + (size_t)c * NC, acc);
   double* Y = FWD ? g.dQcs : g.dQc;
   for (int q = 0; q < NC; ++q) Y[q * N + c] = FWD ? acc[q] : g.dQcs[q * N + c] + acc[q];
+}
+
+// ---------------------------------------------------------------------------------------
+// Coupled (CI) sweeps of a 2D grid in one thread-block-cluster launch: the same arithmetic as
+// k_sweep_coupled, with the hyperplane loop inside the kernel (as in k_split_cluster): CTA r
+// of the cluster owns rows [r R, (r+1) R), one lane per row; the row's previous cell (and the
+// first one, for a periodic i) stay in registers, the neighbouring row's result comes from
+// shared memory or, across a CTA boundary, distributed shared memory, and one cluster barrier
+// separates consecutive hyperplanes.  Each cell applies the coupled Jacobian of its
+// neighbours matrix-free and solves with its LU factors.
+// ---------------------------------------------------------------------------------------
+// one neighbour's coupling (spectral or eigenvalue splitting), as in k_sweep_coupled
+template <class G>
+__device__ __forceinline__ void ci_contrib(const DevGrid& g, int nb, int d, const double* Sf,
+                                           const double* xn, int side, double* acc) {
+  constexpr int NC = Aux<G, 2>::NCI;
+  double ax[NC];
+  jvp_ci<G, 2>(g, nb, Sf, xn, ax);
+  if (g.cisplit) {
+    double bx[NC];
+    absjac_ci<G, 2>(g, nb, Sf, xn, bx);
+    for (int q = 0; q < NC; ++q) ax[q] += (side < 0 ? bx[q] : -bx[q]);
+  }
+  const double l = g.lamCI[d * (size_t)g.N + nb];
+  for (int q = 0; q < NC; ++q) {
+    if (side < 0) acc[q] += 0.5 * (ax[q] + l * xn[q]);
+    else acc[q] -= 0.5 * (ax[q] - l * xn[q]);
+  }
+}
+
+template <class G>
+__global__ void __launch_bounds__(32) k_ci_cluster(DevGrid g, int R) {
+  using A = Aux<G, 2>;
+  constexpr int NS = G::NS, NF = A::NF, NC = A::NCI;
+  __shared__ double xv[2][kClusterRows][NC];
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank();
+  const int t = cluster_row(R);
+  const int j = rank * R + t;
+  const bool row = t >= 0 && j < g.nj;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double prevx[NC], firstx[NC];
+    int prevc = 0, firstc = 0;
+    for (int q = 0; q <= H; ++q) {
+      const int i = (fwd ? q : H - q) - j;
+      const bool act = row && i >= 0 && i < ni;
+      double acc[NC];
+      int c = 0;
+      if (act) {
+        c = i + ni * j;
+        if (fwd) {
+          double rr = 0.0;
+          for (int s = 0; s < NS; ++s) rr += g.R[s * N + c];
+          acc[0] = -rr;
+          for (int v = 1; v < NF; ++v) acc[v] = -g.R[(NS + v - 1) * N + c];
+          for (int s = 1; s < NS; ++s) acc[NF + s - 1] = -g.R[s * N + c];
+        } else {
+          for (int v = 0; v < NC; ++v) acc[v] = 0.0;
+        }
+        // the row's own earlier cells: no other CTA involved, before the barrier
+        if (fwd) {
+          if (i > 0) ci_contrib<G>(g, prevc, 0, face_vec(g, 0, i, j, 0, -1), prevx, -1, acc);
+          if (per && i == ni - 1) ci_contrib<G>(g, firstc, 0, face_vec(g, 0, i, j, 0, +1), firstx, +1, acc);
+        } else {
+          if (per && i == 0) ci_contrib<G>(g, firstc, 0, face_vec(g, 0, i, j, 0, -1), firstx, -1, acc);
+          if (i < ni - 1) ci_contrib<G>(g, prevc, 0, face_vec(g, 0, i, j, 0, +1), prevx, +1, acc);
+        }
+      }
+      if (q > 0) cluster_wait();
+      if (act) {
+        const int jj = fwd ? j - 1 : j + 1;
+        if (jj >= 0 && jj < nj) {
+          const int par = (q - 1) & 1;
+          const double* src;
+          if (fwd) src = (t > 0) ? xv[par][t - 1] : dsmem(&xv[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xv[par][t + 1] : dsmem(&xv[par][0][0], rank + 1);
+          double xn[NC];
+          for (int v = 0; v < NC; ++v) xn[v] = src[v];
+          ci_contrib<G>(g, i + ni * jj, 1, face_vec(g, 1, i, j, 0, fwd ? -1 : +1), xn, fwd ? -1 : +1, acc);
+        }
+        {
+          const double* Dv = g.DINV + (size_t)c * NC * NC;
+          double y[NC];
+#pragma unroll
+          for (int r = 0; r < NC; ++r) {
+            double a = 0.0;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) a += Dv[r * NC + k] * acc[k];
+            y[r] = a;
+          }
+#pragma unroll
+          for (int r = 0; r < NC; ++r) acc[r] = y[r];
+        }
+        double* out = fwd ? g.dQcs : g.dQc;
+        for (int v = 0; v < NC; ++v) {
+          const double x = fwd ? acc[v] : g.dQcs[v * N + c] + acc[v];
+          out[v * N + c] = x;
+          xv[q & 1][t][v] = x;
+          prevx[v] = x;
+        }
+        prevc = c;
+        if (i == (fwd ? 0 : ni - 1)) {
+          for (int v = 0; v < NC; ++v) firstx[v] = prevx[v];
+          firstc = c;
+        }
+      }
+      cluster_arrive();
+    }
+    cluster_wait();
+  }
 }
 
 // ---------------------------------------------------------------------------------------

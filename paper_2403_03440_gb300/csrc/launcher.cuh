@@ -48,8 +48,14 @@ struct Launcher {
   virtual void prepare(const DevGrid& g, bool mixed) = 0;
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
-  void sweep_coupled(const DevGrid& g, cudaStream_t st) { sweep_coupled_dir(g, st, true); sweep_coupled_dir(g, st, false); }
+  void sweep_coupled(const DevGrid& g, cudaStream_t st) {
+    if (use_cluster && sweep_coupled_cluster(g, st)) return;
+    sweep_coupled_dir(g, st, true);
+    sweep_coupled_dir(g, st, false);
+  }
   virtual int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;
+  // both coupled sweeps of a 2D grid in one cluster launch; 0 where it does not apply
+  virtual int sweep_coupled_cluster(const DevGrid& g, cudaStream_t st) = 0;
   virtual void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) = 0;
   // chemistry surrogate coupling (raw samples; standardised inputs; decoded diagonal)
   virtual void surr_sample(const DevGrid& g, cudaStream_t st, float* X, float* T) = 0;
@@ -382,6 +388,41 @@ struct LauncherT : Launcher {
 
   void ci_block(const DevGrid& g, cudaStream_t st) override {
     k_ci_block<G, ND><<<blocks(g.N, 64), 64, 0, st>>>(g);
+  }
+
+  int ci_probed_ = -1;
+  int sweep_coupled_cluster(const DevGrid& g, cudaStream_t st) override {
+    if constexpr (ND != 2) {
+      return 0;
+    } else {
+      if (g.bc[2] == BC_PERIODIC) return 0;
+      if (ci_probed_ < 0) {
+        ci_probed_ = 0;
+        for (int C : {16, 8, 4, 2}) {
+          if ((g.nj + C - 1) / C > kClusterRows) continue;
+          if (cluster_fits(k_ci_cluster<G>, C, 1, 0)) { ci_probed_ = C; break; }
+        }
+      }
+      const int C = ci_probed_;
+      if (C == 0) return 0;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3(32);
+      cfg.stream = st;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const int R = (g.nj + C - 1) / C;
+      if (cudaLaunchKernelEx(&cfg, k_ci_cluster<G>, g, R) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return 1;
+    }
   }
 
   int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) override {
