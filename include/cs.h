@@ -132,7 +132,8 @@ cs_status cs_residual(cs_grid g, double *R_out, double norms_host[3]);
 /* Split operator (Sec. 2.3.1-2.3.2) solved by LU-SGS (Sec. 2.2) with the local time step of
  * the given CFL; uses R of the last cs_residual.  dQ_out (host or device,
  * [nsplit][ncell], nullable).  precision: CS_FP64 or CS_MIXED.  Errors: CS_ERR_STATE (no
- * residual). */
+ * residual); CS_ERR_TIMEOUT (a bounded wait of the 2D point-to-point sweep for a neighbouring
+ * CTA's increments gave up; the increments are then not valid). */
 cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double *dQ_out);
 
 /* Coupled (CI) operator: unified spectral radius, dense diagonal blocks with the source
@@ -145,7 +146,8 @@ cs_status cs_lusgs_coupled(cs_grid g, double cfl, double *dQ_out);
  * modes 1-2, coupled for mode 0.  nclip_out (nullable): clipped values. */
 cs_status cs_correct(cs_grid g, int mode, int clip, const double *dQ, int *nclip_out);
 
-/* opts->iters pseudo-time iterations: residual, operator, correction + update. */
+/* opts->iters pseudo-time iterations: residual, operator, correction + update.  Errors: those
+ * of cs_residual, cs_lusgs_split / cs_lusgs_coupled and cs_correct. */
 cs_status cs_step(cs_grid g, const cs_step_opts *opts, cs_step_stats *stats);
 
 /* Per-cell auxiliary fields for tests and monitors: name in {"T", "Tv", "p", "c", "rho",
@@ -167,11 +169,19 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
  * split sweeps in one launch, choosing per precision: for the FP32 operator 4 where it applies,
- * else 2; for FP64, 1.  1 is a thread-block-cluster kernel reading the cell arrays directly,
- * 2 a cluster kernel over hyperplane-ordered cell records, 4 the FP32 operator's sweeps with
- * one CTA per component holding every row (nj <= 384; __syncthreads between hyperplanes;
- * FP64 and larger grids fall back to 2); 0 runs one launch per hyperplane.  All give the same
- * arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
+ * else 2; for FP64, 5 where its records can be allocated, else 1.  1 is a thread-block-cluster
+ * kernel reading the cell arrays directly, 2 a cluster kernel over hyperplane-ordered cell
+ * records, 4 the FP32 operator's sweeps with one CTA per component holding every row
+ * (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall back to 2), 5 the
+ * FP64 operator's sweeps over neighbour couplings assembled beforehand (D^-1 times the split
+ * Jacobian blocks, formed in one parallel launch into library-owned records of 4 nF nP + 4
+ * doubles per cell and 2 nF nP + 2 per row j, nP = nF rounded up to even; then a cluster
+ * kernel with 8 threads per row, whose CTAs exchange the rows at their boundaries point to
+ * point (st.async into the next CTA's shared memory, one mbarrier per hyperplane; needs
+ * (ni + nj - 1) x 72 bytes of shared memory per CTA, at most 200 KiB, else 6 is used); single
+ * grids only, batches and the FP32 operator fall back to 1), 6 the same couplings with one
+ * cluster barrier per hyperplane; 0 runs one launch per hyperplane.
+ * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
  * component of the 2D cluster sweeps (0, the default: the largest that fits; a C that does not
  * fit the grid or the device falls back to one launch per hyperplane); cs_batch_tune sets it.
  * Method option: "h_correction" = 1 (default) widens the entropy fix of every face's Roe flux

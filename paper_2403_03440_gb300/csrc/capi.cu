@@ -173,6 +173,7 @@ struct cs_grid_s {
   int stag = -1;
   int have_R = 0, have_bc = 0, iter = 0;
   int last_op = -1;           // 0 split, 1 coupled
+  bool mat_refused = false;   // the coupling records of the 2D FP64 sweep could not be allocated
   char err[512] = {0};
   // per-phase CUDA-event timing of cs_step (enabled by cs_profile)
   bool prof = false;
@@ -559,6 +560,18 @@ extern "C" cs_status cs_residual(cs_grid g, double* R_out, double norms_host[3])
   return CS_OK;
 }
 
+// coupling records of the FP64 2D split sweep (K6e); without them (allocation refused) the
+// sweep falls back to the direct-load cluster kernel
+static void ensure_mat(cs_grid g) {
+  if (g->g.SMC || g->mat_refused) return;
+  const size_t n = g->L->mat_doubles(g->g);
+  if (n == 0 || dalloc(g, &g->g.SMC, n) != cudaSuccess) {
+    cudaGetLastError();
+    g->g.SMC = nullptr;
+    g->mat_refused = true;
+  }
+}
+
 static cs_status set_cfl(cs_grid g, double cfl) {
   if (!(cfl > 0.0)) return fail(g, CS_ERR_ARG, "cfl must be positive");
   g->h_pin[40] = cfl;
@@ -574,6 +587,7 @@ extern "C" cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double
   cs_status st = begin(g);
   if (st) return st;
   if ((st = set_cfl(g, cfl))) return st;
+  if (precision == CS_FP64) ensure_mat(g);
   g->L->spectral(g->g, g->stream);
   g->L->sweep_split(g->g, g->stream, precision == CS_MIXED);
   if (dQ_out)
@@ -734,6 +748,7 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
   cs_status st = check_opts(o);
   if (st) return st;
   if (o->scheme == CS_SCHEME_COUPLED && (st = ensure_ci(g))) return fail(g, st, "allocation");
+  if (o->scheme == CS_SCHEME_SPLIT && o->precision == CS_FP64) ensure_mat(g);
   if ((st = begin(g))) return st;
   int done = 0;
   for (int it = 0; it < o->iters; ++it) {
@@ -808,9 +823,11 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!g || !name) return CS_ERR_ARG;
   if (!strcmp(name, "cluster_sweep")) {
     // 0 per hyperplane, 1 direct-load cluster kernel, 2 record cluster kernel, 3 default (by
-    // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2)
+    // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2),
+    // 5 assembled couplings (FP64 operator only; the FP32 one falls back to 1), exchanged point
+    // to point between CTAs where the ring fits, 6 the same with a cluster barrier per hyperplane
     g->L->use_cluster = value != 0.0;
-    g->L->cluster_kind = value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
+    g->L->cluster_kind = value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;
   }
   if (!strcmp(name, "cluster_size")) {

@@ -68,6 +68,7 @@ struct DevGrid {
   double* Vdt;            // [N] V / dtau
   double* invD;           // [2 + ns][N]: 1/D_F, 1/D_F,ev, 1/D_s
   double* rhsF;           // [nF][N]: -(sum_s R_s, R_m, R_E, [R_ev])
+  double* SMC;            // 2D split-sweep couplings of k_sweep_mat (cell and row records) or null
   // 2D wavefront sweep: per-cell sweep records in hyperplane order (w = woff[h] + j - jlo(h))
   const int* woff;        // [H + 2]
   void* wrec;             // flow records [N][kRecF] (compute type)
@@ -2446,6 +2447,473 @@ __global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
   }
   else sweep_species_cluster<G, T>(g, R, (comp - 1) * kClusterSpeciesGroup,
                                    *reinterpret_cast<Xchg<G, kClusterSpeciesGroup, T>*>(&xf));
+}
+
+// ---------------------------------------------------------------------------------------
+// K6e: FP64 split sweeps of a 2D grid with the neighbour couplings assembled beforehand.
+// The coupling of cell c with a neighbour nb across face S is the linear map
+// x_nb -> D_c^-1 (+-1/2)(A_nb(S) x_nb +- lambda_nb x_nb) (Sec. 2.2, 2.3.1-2.3.2): it depends
+// only on the state frozen for the iteration, not on the increments.  k_sweep_mat forms it for
+// every cell and face in one fully parallel launch (the flow block as an NF x NF matrix, the
+// species as one scalar shared by every species before the species' own D_s^-1), so the sweep
+// itself is left with the dependent part alone: per cell and step a dot product of length NF
+// per flow component.  GB300 issues one warp-wide FP64 FMA per SM sub-partition only every
+// ~64 cycles, which made the matrix-free Jacobian product (tens of FP64 operations after every
+// cluster barrier, on one or two sub-partitions) the bound of K6b; here each row of a CTA has
+// kMatSlots threads, one per flow component (or species of the CTA's group), and a CTA's rows
+// cover all four sub-partitions.
+// Record of cell c (doubles): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF rows of NP
+// (NF rounded up to even, so that every row starts on 16 bytes), then the species coefficients
+// in the same order.  Per row j after the N cell records: the periodic-i wrap couplings
+// (forward: cell (ni-1, j) with (0, j); backward: (0, j) with (ni-1, j)), flow blocks then
+// species coefficients.
+// ---------------------------------------------------------------------------------------
+constexpr int kMatSlots = 8;       // threads per row of a CTA
+constexpr int kMatSpecies = kMatSlots;
+
+template <class G>
+struct MatRec {
+  static constexpr int NF = Aux<G, 2>::NF;
+  static constexpr int NP = (NF + 1) / 2 * 2;
+  static constexpr int BLK = NF * NP;
+  static constexpr int CELL = 4 * BLK + 4;
+  static constexpr int ROW = 2 * BLK + 2;
+  static_assert(NF <= kMatSlots, "one thread per flow component");
+};
+template <class G>
+constexpr int mat_species_groups() { return (G::NS + kMatSpecies - 1) / kMatSpecies; }
+
+// D_c^-1 (+-1/2)(A_nb(S) +- lambda I) of the flow block, written row-major with pitch NP
+template <class G>
+__device__ __forceinline__ void mat_block(const DevGrid& g, int nb, const double* S, double lam,
+                                          int side, double dF, double dEv, double* out) {
+  constexpr int NF = MatRec<G>::NF, NP = MatRec<G>::NP;
+  CellState<G, 2, double> w;
+  load_state<G, 2, double>(g, nb, w);
+  const double Sf[2] = {S[0], S[1]};
+#pragma unroll
+  for (int k = 0; k < NF; ++k) {
+    double e[NF], a[NF];
+#pragma unroll
+    for (int q = 0; q < NF; ++q) e[q] = q == k ? 1.0 : 0.0;
+    jvp_flow<G, 2, double>(w, Sf, e, a);
+#pragma unroll
+    for (int v = 0; v < NF; ++v) {
+      const double l = v == k ? lam : 0.0;
+      const double m = side < 0 ? 0.5 * (a[v] + l) : -0.5 * (a[v] - l);
+      out[v * NP + k] = ((G::NTEMP == 2 && v == NF - 1) ? dEv : dF) * m;
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NF; ++v)
+#pragma unroll
+    for (int k = NF; k < NP; ++k) out[v * NP + k] = 0.0;
+}
+
+// species coupling (+-1/2)(U_nb +- lambda_C,nb) before D_s^-1, U_nb = u_nb . S
+template <class G>
+__device__ __forceinline__ double mat_coef(const DevGrid& g, int nb, const double* S, double lam, int side) {
+  using A = Aux<G, 2>;
+  const size_t N = g.N;
+  const double U = g.W[A::U * N + nb] * S[0] + g.W[(A::U + 1) * N + nb] * S[1];
+  return side < 0 ? 0.5 * (U + lam) : -0.5 * (U - lam);
+}
+
+template <class G>
+__global__ void __launch_bounds__(128) k_sweep_mat(DevGrid g) {
+  using M = MatRec<G>;
+  constexpr int BLK = M::BLK;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  const int ni = g.ni, nj = g.nj, i = c % ni, j = c / ni;
+  const double dF = g.invD[c], dEv = g.invD[N + c];
+  double* rec = g.SMC + (size_t)c * M::CELL;
+  double* co = rec + 4 * BLK;
+  const double* S;
+  // a face on the grid's boundary couples nothing: its block and coefficient are zero
+  if (i == 0 || j == 0 || i == ni - 1 || j == nj - 1) {
+    for (int e = 0; e < M::CELL; ++e) rec[e] = 0.0;
+  }
+  // forward: the lower neighbours (i-1, j) and (i, j-1); backward: the upper ones
+  if (i > 0) {
+    S = g.S[0] + 3 * (size_t)face_of(g, 0, i, j, 0);
+    mat_block<G>(g, c - 1, S, g.lamF[c - 1], -1, dF, dEv, rec);
+    co[0] = mat_coef<G>(g, c - 1, S, g.lamC[c - 1], -1);
+  }
+  if (j > 0) {
+    S = g.S[1] + 3 * (size_t)face_of(g, 1, i, j, 0);
+    mat_block<G>(g, c - ni, S, g.lamF[N + c - ni], -1, dF, dEv, rec + BLK);
+    co[1] = mat_coef<G>(g, c - ni, S, g.lamC[N + c - ni], -1);
+  }
+  if (i < ni - 1) {
+    S = g.S[0] + 3 * (size_t)face_of(g, 0, i + 1, j, 0);
+    mat_block<G>(g, c + 1, S, g.lamF[c + 1], +1, dF, dEv, rec + 2 * BLK);
+    co[2] = mat_coef<G>(g, c + 1, S, g.lamC[c + 1], +1);
+  }
+  if (j < nj - 1) {
+    S = g.S[1] + 3 * (size_t)face_of(g, 1, i, j + 1, 0);
+    mat_block<G>(g, c + ni, S, g.lamF[N + c + ni], +1, dF, dEv, rec + 3 * BLK);
+    co[3] = mat_coef<G>(g, c + ni, S, g.lamC[N + c + ni], +1);
+  }
+  if (g.bc[0] == BC_PERIODIC) {
+    double* pr = g.SMC + N * M::CELL + (size_t)j * M::ROW;
+    if (i == ni - 1) {          // forward: (0, j) precedes (ni-1, j) and lies on its + side
+      const int nb = ni * j;
+      S = g.S[0] + 3 * (size_t)face_of(g, 0, ni, j, 0);
+      mat_block<G>(g, nb, S, g.lamF[nb], +1, dF, dEv, pr);
+      pr[2 * BLK] = mat_coef<G>(g, nb, S, g.lamC[nb], +1);
+    }
+    if (i == 0) {               // backward: (ni-1, j) precedes (0, j) and lies on its - side
+      const int nb = ni - 1 + ni * j;
+      S = g.S[0] + 3 * (size_t)face_of(g, 0, 0, j, 0);
+      mat_block<G>(g, nb, S, g.lamF[nb], -1, dF, dEv, pr + BLK);
+      pr[2 * BLK + 1] = mat_coef<G>(g, nb, S, g.lamC[nb], -1);
+    }
+  }
+}
+
+// inputs of one thread's cell at step q (loaded a step ahead)
+template <class G>
+struct MatStep {
+  // raw loads only (no arithmetic on them here, so that a prefetch does not wait for its own
+  // loads): the coupling rows (species: the two coefficients before D_s^-1), the diagonal
+  // inverse d and base = the right-hand side (forward) or the forward result (backward)
+  double bi[MatRec<G>::NP], bj[MatRec<G>::NP], base, d;
+  int c, i;
+  bool act;
+};
+
+template <class G>
+__device__ __forceinline__ void mat_step_load(const DevGrid& g, int q, int j, bool on, bool fwd,
+                                              bool flow, int v, int s, MatStep<G>& m) {
+  using M = MatRec<G>;
+  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
+  const int ni = g.ni, H = ni + g.nj - 2;
+  const int i = (fwd ? q : H - q) - j;
+  m.act = on && q <= H && i >= 0 && i < ni;
+  m.i = i;
+  if (!m.act) return;
+  const size_t N = g.N;
+  const int c = i + ni * j;
+  m.c = c;
+  const double* rec = g.SMC + (size_t)c * M::CELL;
+  if (flow) {
+    const double2* ri = reinterpret_cast<const double2*>(rec + (fwd ? 0 : 2 * BLK) + v * NP);
+    const double2* rj = reinterpret_cast<const double2*>(rec + (fwd ? BLK : 3 * BLK) + v * NP);
+#pragma unroll
+    for (int k = 0; k < NP / 2; ++k) {
+      const double2 a = ri[k], b = rj[k];
+      m.bi[2 * k] = a.x;
+      m.bi[2 * k + 1] = a.y;
+      m.bj[2 * k] = b.x;
+      m.bj[2 * k + 1] = b.y;
+    }
+    m.d = g.invD[((G::NTEMP == 2 && v == NF - 1) ? N : 0) + c];
+    m.base = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
+  } else {
+    m.d = g.invD[(2 + s) * N + c];
+    m.base = fwd ? -g.R[(size_t)s * N + c] : g.dQs[(size_t)(NF + s) * N + c];
+    const double* co = rec + 4 * BLK;
+    m.bi[0] = co[fwd ? 0 : 2];
+    m.bj[0] = co[fwd ? 1 : 3];
+  }
+}
+
+template <class G>
+__global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_mat(DevGrid g, int R) {
+  using M = MatRec<G>;
+  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
+  __shared__ __align__(16) double xs[2][kClusterRows][kMatSlots];
+  const size_t N = g.N;
+  const int comp = blockIdx.x / (int)cluster_nctarank();   // 0: flow block, else a species group
+  const unsigned rank = cluster_ctarank();
+  const int t = threadIdx.x / kMatSlots, v = threadIdx.x % kMatSlots;
+  const int j = rank * R + t;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const bool flow = comp == 0;
+  const int s = (comp - 1) * kMatSpecies + v;
+  const bool on = t < R && j < nj && (flow ? v < NF : s < G::NS);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double xp[NF], xf[NF], pw[NP];   // flow: the row's previous and first results, wrap block row
+    double sp = 0.0, sf = 0.0, pc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) xp[k] = xf[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pw[k] = 0.0;
+    if (on && per) {
+      const double* pr = g.SMC + N * M::CELL + (size_t)j * M::ROW;
+      if (flow) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pw[k] = pr[(fwd ? 0 : BLK) + v * NP + k];
+      } else {
+        pc = pr[2 * BLK + (fwd ? 0 : 1)];
+      }
+    }
+    double* out = fwd ? g.dQs : g.dQ;
+    const size_t orow = (size_t)(flow ? v : NF + s) * N;
+    MatStep<G> cur, nxt;
+    mat_step_load<G>(g, 0, j, on, fwd, flow, v, s, cur);
+    for (int q = 0; q <= H; ++q) {
+      mat_step_load<G>(g, q + 1, j, on, fwd, flow, v, s, nxt);     // prefetch the next step
+      // the row's own earlier cells (and the periodic wrap) need no other CTA: coupled while the
+      // cluster barrier is pending
+      double acc = 0.0;
+      if (cur.act) {
+        const int i = cur.i;
+        acc = fwd ? cur.d * cur.base : cur.base;
+        const bool hasi = fwd ? i > 0 : i < ni - 1;
+        const bool wrap = per && i == (fwd ? ni - 1 : 0);
+        if (flow) {
+          if (hasi) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += cur.bi[k] * xp[k];
+          }
+          if (wrap) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += pw[k] * xf[k];
+          }
+        } else {
+          if (hasi) acc += (cur.d * cur.bi[0]) * sp;
+          if (wrap) acc += cur.d * pc * sf;
+        }
+      }
+      if (q > 0) cluster_wait();
+      if (cur.act) {
+        // the neighbouring row's result of step q-1: this CTA's shared memory or, across a CTA
+        // boundary, the neighbour CTA's
+        if (fwd ? j > 0 : j < nj - 1) {
+          const int par = (q - 1) & 1;
+          const double* src;
+          if (fwd) src = (t > 0) ? xs[par][t - 1] : dsmem(&xs[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xs[par][t + 1] : dsmem(&xs[par][0][0], rank + 1);
+          if (flow) {
+            // two partial sums: a shorter chain of dependent FP64 operations
+            double a0 = acc, a1 = 0.0;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) {
+              if (k & 1) a1 += cur.bj[k] * src[k];
+              else a0 += cur.bj[k] * src[k];
+            }
+            acc = a0 + a1;
+          } else {
+            acc += (cur.d * cur.bj[0]) * src[v];
+          }
+        }
+        xs[q & 1][t][v] = acc;
+      }
+      __syncwarp();                    // a row's kMatSlots threads share one warp
+      cluster_arrive();
+      // after the arrive: its release then covers only the shared-memory exchange, not the
+      // global store (which the next step's release finds long completed)
+      if (cur.act) {
+        out[orow + cur.c] = acc;
+        if (flow) {
+#pragma unroll
+          for (int k = 0; k < NF; ++k) xp[k] = xs[q & 1][t][k];
+        } else {
+          sp = acc;
+        }
+        if (cur.i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+          for (int k = 0; k < NF; ++k) xf[k] = xp[k];
+          sf = sp;
+        }
+      }
+      cur = nxt;
+    }
+    cluster_wait();
+  }
+}
+
+// Point-to-point form of K6e: the rows of a CTA step together (__syncthreads between
+// hyperplanes) and only the row at a CTA boundary talks to the neighbouring CTA, by writing its
+// result straight into that CTA's shared memory (st.async) and completing a per-hyperplane
+// mbarrier there.  No cluster-wide barrier per step: a CTA waits only for the data it needs, so
+// a CTA can run ahead of the ones downstream and the cross-CTA latency is paid once per CTA
+// boundary rather than once per hyperplane.  The receiving ring holds one slot per hyperplane
+// of a pass (its mbarrier completes one phase per pass; every slot's expected byte count is
+// registered before a cluster barrier that precedes all sends of the pass).
+constexpr long kP2PSpinLimit = 1L << 22;   // bounded waits (then ST_TIMEOUT)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t cluster_map(uint32_t a, unsigned rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ bool p2p_wait(uint32_t bar, uint32_t parity) {
+  for (long it = 0; it < kP2PSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// dynamic shared memory of k_split_p2p: the ring [H + 1][kMatSlots] doubles, then H + 1 mbarriers
+__host__ __device__ inline size_t p2p_smem_bytes(int ni, int nj) {
+  return (size_t)(ni + nj - 1) * (kMatSlots * sizeof(double) + sizeof(unsigned long long));
+}
+
+template <class G>
+__global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid g, int R) {
+  using M = MatRec<G>;
+  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
+  extern __shared__ __align__(16) unsigned char p2p_dyn[];
+  __shared__ __align__(16) double xs[2][kClusterRows][kMatSlots];
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  double* ring = reinterpret_cast<double*>(p2p_dyn);
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + (size_t)(H + 1) * kMatSlots);
+  const size_t N = g.N;
+  const int comp = blockIdx.x / (int)cluster_nctarank();   // 0: flow block, else a species group
+  const unsigned rank = cluster_ctarank();
+  const int t = threadIdx.x / kMatSlots, v = threadIdx.x % kMatSlots;
+  const int j = rank * R + t;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const bool flow = comp == 0;
+  const int s = (comp - 1) * kMatSpecies + v;
+  const bool on = t < R && j < nj && (flow ? v < NF : s < G::NS);
+  // bytes one boundary row sends per hyperplane: one double per active slot
+  const int nsend = flow ? NF : (G::NS - (comp - 1) * kMatSpecies < kMatSpecies ? G::NS - (comp - 1) * kMatSpecies : kMatSpecies);
+  for (int q = threadIdx.x; q <= H; q += blockDim.x)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + q)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  __syncthreads();
+  bool timed_out = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    // this pass's expected bytes per slot: the CTA's first (forward) or last (backward) row
+    // receives its neighbouring row's result of the previous hyperplane from the next CTA
+    if (threadIdx.x < 32) {
+      const int jc = fwd ? (int)rank * R : (int)rank * R + R - 1;
+      const bool row_ok = jc < nj && (fwd ? jc > 0 : jc + 1 < nj);
+      for (int q = threadIdx.x; q <= H; q += 32) {
+        const int ic = (fwd ? q : H - q) - jc;
+        const uint32_t bytes = (row_ok && ic >= 0 && ic < ni) ? nsend * (uint32_t)sizeof(double) : 0u;
+        unsigned long long st;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
+                     : "=l"(st) : "r"(smem_u32(mbar + q)), "r"(bytes) : "memory");
+      }
+    }
+    cluster_arrive();
+    cluster_wait();
+    double xp[NF], xf[NF], pw[NP];   // flow: the row's previous and first results, wrap block row
+    double sp = 0.0, sf = 0.0, pc = 0.0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) xp[k] = xf[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pw[k] = 0.0;
+    if (on && per) {
+      const double* pr = g.SMC + N * M::CELL + (size_t)j * M::ROW;
+      if (flow) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pw[k] = pr[(fwd ? 0 : BLK) + v * NP + k];
+      } else {
+        pc = pr[2 * BLK + (fwd ? 0 : 1)];
+      }
+    }
+    double* out = fwd ? g.dQs : g.dQ;
+    const size_t orow = (size_t)(flow ? v : NF + s) * N;
+    // the row whose neighbour lives in the next CTA of this pass's direction, and the receiver
+    const bool boundary_in = fwd ? t == 0 : t == R - 1;
+    const bool boundary_out = fwd ? t == R - 1 : t == 0;
+    const unsigned peer = fwd ? rank + 1 : rank - 1;
+    const bool hasj = fwd ? j > 0 : j < nj - 1;
+    const bool sends = fwd ? j + 1 < nj : j > 0;
+    // the inputs of step q are loaded four steps ahead, into the buffer of step q mod 4 right
+    // after step q - 4 has used it: the loads have three steps to arrive
+    auto step = [&](int q, MatStep<G>& cur) {
+      // the row's own earlier cells (and the periodic wrap) need no other row: coupled before
+      // this step's synchronisation
+      double acc = 0.0;
+      if (cur.act) {
+        acc = fwd ? cur.d * cur.base : cur.base;
+        const bool hasi = fwd ? cur.i > 0 : cur.i < ni - 1;
+        const bool wrap = per && cur.i == (fwd ? ni - 1 : 0);
+        if (flow) {
+          if (hasi) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += cur.bi[k] * xp[k];
+          }
+          if (wrap) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += pw[k] * xf[k];
+          }
+        } else {
+          if (hasi) acc += (cur.d * cur.bi[0]) * sp;
+          if (wrap) acc += cur.d * pc * sf;
+        }
+      }
+      if (q > 0) __syncthreads();      // the CTA's results of step q-1 are in xs
+      if (cur.act) {
+        // the neighbouring row's result of step q-1; across a CTA boundary the neighbouring CTA
+        // wrote it into ring slot q
+        if (hasj) {
+          const double* src;
+          if (!boundary_in) {
+            src = xs[(q - 1) & 1][fwd ? t - 1 : t + 1];
+          } else {
+            if (!p2p_wait(smem_u32(mbar + q), (uint32_t)pass) && !timed_out) {
+              timed_out = true;
+              set_status(g, ST_TIMEOUT, cur.c);
+            }
+            src = ring + (size_t)q * kMatSlots;
+          }
+          if (flow) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += cur.bj[k] * src[k];
+          } else {
+            acc += (cur.d * cur.bj[0]) * src[v];
+          }
+        }
+        xs[q & 1][t][v] = acc;
+        if (boundary_out && sends) {
+          const uint32_t dst = cluster_map(smem_u32(ring + (size_t)(q + 1) * kMatSlots + v), peer);
+          const uint32_t bar = cluster_map(smem_u32(mbar + q + 1), peer);
+          asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];\n"
+                       ::"r"(dst), "l"(__double_as_longlong(acc)), "r"(bar) : "memory");
+        }
+        out[orow + cur.c] = acc;
+      }
+      __syncwarp();                    // a row's kMatSlots threads share one warp
+      if (cur.act) {
+        if (flow) {
+#pragma unroll
+          for (int k = 0; k < NF; ++k) xp[k] = xs[q & 1][t][k];
+        } else {
+          sp = xs[q & 1][t][v];
+        }
+        if (cur.i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+          for (int k = 0; k < NF; ++k) xf[k] = xp[k];
+          sf = sp;
+        }
+      }
+      mat_step_load<G>(g, q + 4, j, on, fwd, flow, v, s, cur);
+    };
+    MatStep<G> m0, m1, m2, m3;
+    mat_step_load<G>(g, 0, j, on, fwd, flow, v, s, m0);
+    mat_step_load<G>(g, 1, j, on, fwd, flow, v, s, m1);
+    mat_step_load<G>(g, 2, j, on, fwd, flow, v, s, m2);
+    mat_step_load<G>(g, 3, j, on, fwd, flow, v, s, m3);
+    for (int q = 0; q <= H; q += 4) {
+      step(q, m0);
+      if (q + 1 <= H) step(q + 1, m1);
+      if (q + 2 <= H) step(q + 2, m2);
+      if (q + 3 <= H) step(q + 3, m3);
+    }
+    __syncthreads();
+  }
+  // no CTA leaves while a neighbour may still write into its shared memory
+  cluster_arrive();
+  cluster_wait();
 }
 
 // ---------------------------------------------------------------------------------------

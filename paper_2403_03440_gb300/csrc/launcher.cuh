@@ -34,7 +34,9 @@ struct Launcher {
   }
   virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed = false) = 0;
   bool use_cluster = true;
-  int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records
+  int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records,
+                           // 3: one CTA per component (FP32), 4: assembled couplings (FP64),
+                           // point to point where it fits, 5: the same with a cluster barrier
   int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
   int cluster_warps = 2;   // warps per CTA of the direct-load cluster kernel (batches: 1)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
@@ -47,6 +49,8 @@ struct Launcher {
   // inside a stream capture)
   virtual void prepare(const DevGrid& g, bool mixed) = 0;
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
+  // doubles of DevGrid::SMC, the coupling records of the FP64 2D sweep (0: not used)
+  virtual size_t mat_doubles(const DevGrid& g) const = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) {
     if (use_cluster && sweep_coupled_cluster(g, st)) return;
@@ -176,8 +180,14 @@ struct LauncherT : Launcher {
   // Can `kern` run as clusters of C CTAs (32 x warps threads each), one cluster per component
   // (the flow block and `groups` species groups)?
   template <class K>
-  bool cluster_fits(K kern, int C, int warps, int groups) {
+  bool cluster_fits(K kern, int C, int warps, int groups, size_t dyn_smem = 0) {
     if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    // static plus dynamic shared memory above 48 KiB needs the opt-in
+    if (dyn_smem > 0 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -185,6 +195,7 @@ struct LauncherT : Launcher {
     cudaLaunchAttribute at[1];
     cfg.gridDim = dim3(C * (1 + groups));
     cfg.blockDim = dim3(32 * warps);
+    cfg.dynamicSmemBytes = dyn_smem;
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = C;
     at[0].val.clusterDim.y = 1;
@@ -229,8 +240,12 @@ struct LauncherT : Launcher {
   // one launch: both sweeps of the flow block and of every species (returns launches)
   int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed) override {
     // measured on GB300: in FP32 the one-CTA-per-component kernel (where nj fits) and then
-    // the wavefront-record kernel, in FP64 the direct-load kernel
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 1);
+    // the wavefront-record kernel, in FP64 the assembled couplings, then the direct-load kernel
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 4);
+    if ((kind == 4 || kind == 5) && !mixed) {
+      const int n = sweep_mat(g, st, kind == 4);
+      if (n) return n;
+    }
     if (kind == 3 && mixed && g.wrec) {
       const int n = sweep_block(g, st);
       if (n) return n;
@@ -278,7 +293,11 @@ struct LauncherT : Launcher {
   }
 
   void prepare(const DevGrid& g, bool mixed) override {
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 1);
+    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 4);
+    if ((kind == 4 || kind == 5) && !mixed && g.SMC) {
+      mat_cluster_size(g, false);
+      if (kind == 4) mat_cluster_size(g, true);
+    }
     if (kind == 3 && mixed) block_ok(g);
     if (kind == 2 || kind == 3) {
       if (mixed) wave_cluster_size<float>(g, wprobed32_);
@@ -363,6 +382,79 @@ struct LauncherT : Launcher {
     }
     sweep_split_cluster_ok = true;
     return 1;
+  }
+
+  // FP64 2D sweeps over assembled couplings (K6e): k_sweep_mat, then one cluster launch with
+  // kMatSlots threads per row, point to point between CTAs (k_split_p2p) where its ring fits in
+  // shared memory, else with a cluster barrier per hyperplane (k_split_mat).  Single grids only:
+  // a batch keeps the one-warp direct kernel, whose CTAs need fewer registers and no records.
+  size_t mat_doubles(const DevGrid& g) const override {
+    return ND == 2 ? (size_t)g.N * MatRec<G>::CELL + (size_t)g.nj * MatRec<G>::ROW : 0;
+  }
+  static constexpr size_t kP2PMaxSmem = 200 * 1024;
+  bool mat_fits(const DevGrid& g, int C, bool p2p) {
+    const int R = (g.nj + C - 1) / C;
+    if (R > kClusterRows) return false;
+    const int warps = (kMatSlots * R + 31) / 32;
+    if (!p2p) return cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
+    const size_t smem = p2p_smem_bytes(g.ni, g.nj);
+    return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G>, C, warps, mat_species_groups<G>(), smem);
+  }
+  int mat_cluster_size(const DevGrid& g, bool p2p) {
+    if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
+    const int m = p2p ? 1 : 0;
+    if (force_C > 0) {
+      if (mat_forced_C_[m] != force_C) {
+        mat_forced_C_[m] = force_C;
+        mat_forced_ok_[m] = mat_fits(g, force_C, p2p);
+      }
+      return mat_forced_ok_[m] ? force_C : 0;
+    }
+    if (mat_probed_[m] >= 0) return mat_probed_[m];
+    mat_probed_[m] = 0;
+    for (int C : {16, 8, 4, 2}) {
+      if (mat_fits(g, C, p2p)) {
+        mat_probed_[m] = C;
+        break;
+      }
+    }
+    return mat_probed_[m];
+  }
+  int mat_probed_[2] = {-1, -1}, mat_forced_C_[2] = {0, 0};
+  bool mat_forced_ok_[2] = {false, false};
+  int sweep_mat(const DevGrid& g, cudaStream_t st, bool allow_p2p) {
+    sweep_split_cluster_ok = false;
+    if constexpr (ND != 2) {
+      return 0;
+    } else {
+      if (cluster_warps == 1 || !g.SMC) return 0;
+      int C = allow_p2p ? mat_cluster_size(g, true) : 0;
+      const bool p2p = C > 0;
+      if (!p2p) C = mat_cluster_size(g, false);
+      if (C == 0) return 0;
+      const int R = (g.nj + C - 1) / C;
+      k_sweep_mat<G><<<blocks(g.N, 128), 128, 0, st>>>(g);
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(C * (1 + mat_species_groups<G>()));
+      cfg.blockDim = dim3((kMatSlots * R + 31) / 32 * 32);
+      cfg.dynamicSmemBytes = p2p ? p2p_smem_bytes(g.ni, g.nj) : 0;
+      cfg.stream = st;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      const cudaError_t e = p2p ? cudaLaunchKernelEx(&cfg, k_split_p2p<G>, g, R)
+                                : cudaLaunchKernelEx(&cfg, k_split_mat<G>, g, R);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      sweep_split_cluster_ok = true;
+      return 2;
+    }
   }
 
   int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed) override {

@@ -366,18 +366,39 @@ def test_cluster_sweep_equals_hyperplane_sweep(name):
     in the two kernels, so they agree to rounding)."""
     ref, gpu, Q = make_pair(name, seed=7)
     out = {}
-    for mode in (2, 1, 0):               # wavefront-record cluster, direct cluster, per hyperplane
+    # wavefront-record cluster, direct cluster, assembled couplings (point to point between
+    # CTAs; with a cluster barrier), per hyperplane
+    for mode in (2, 1, 5, 6, 0):
         gpu.set_option("cluster_sweep", mode)
         gpu.set_state(Q)
         gpu.residual(want_R=False)
         out[mode] = gpu.lusgs_split(8.0)
+    # the assembled couplings with every cluster size that holds the rows (at most 32 per CTA;
+    # C above the row count leaves CTAs without rows)
+    for mode in (5, 6):
+        for C in (2, 4, 16):
+            if -(-ref.nj // C) > 32:
+                continue
+            gpu.set_option("cluster_sweep", mode)
+            gpu.set_option("cluster_size", C)
+            gpu.set_state(Q)
+            gpu.residual(want_R=False)
+            out[(mode, C)] = gpu.lusgs_split(8.0)
+    gpu.set_option("cluster_size", 0)
     gpu.set_option("cluster_sweep", 3)
     a, b = out[2], out[0]
     for m in (1, 2):
         assert rel(out[m][:ref.nF], b[:ref.nF]) < 1e-13, m
         assert rel(out[m][ref.nF:], b[ref.nF:], ns=ref.ns) < 1e-13, m
+    # the couplings are multiplied by D^-1 before the sweep (another rounding order)
+    for m in [5, 6] + [k for k in out if isinstance(k, tuple)]:
+        assert rel(out[m][:ref.nF], b[:ref.nF]) < 1e-12, m
+        assert rel(out[m][ref.nF:], b[ref.nF:], ns=ref.ns) < 1e-12, m
     ref.residual()
-    assert rel(a[:ref.nF], ref.lusgs_split(8.0)[:ref.nF]) < TOL
+    d = ref.lusgs_split(8.0)
+    for m in (2, 5, 6):
+        assert rel(out[m][:ref.nF], d[:ref.nF]) < TOL, m
+        assert rel(out[m][ref.nF:], d[ref.nF:], ns=ref.ns) < TOL, m
 
 
 @pytest.mark.parametrize("nodes_fn,bc,mech", [
