@@ -51,13 +51,16 @@ FP64_FLOPS_PER_CELL = {
     "sweep_bwd": 0.0,
     "correct": 109.0,
 }
-FP32_FLOPS_PER_CELL_SWEEP = 652.0     # the FP32 one-CTA-per-component sweep of the mixed operator
+# the mixed operator's sweep phase: couplings formed in FP64 (k_sweep_mat, 753 FP64 flop) and
+# swept in FP32 (k_split_p2p, the FP64 form's 374 flop as FP32)
+FP64_FLOPS_PER_CELL_SWEEP_MIXED = 753.0
+FP32_FLOPS_PER_CELL_SWEEP = 374.0
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
     "primitive": 34.0e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 195.7e6 + 143.6e6, "gradient": 17.4e6,
     "spectral": 54.1e6, "assemble": 33.9e6, "correct": 24.4e6,
 }
-DRAM_BYTES_SWEEP_FP32 = 36.6e6 + 38.3e6   # record packing + FP32 sweep
+DRAM_BYTES_SWEEP_FP32 = None              # FP32 records: not captured with ncu
 CI_SWEEP_DRAM_BYTES = 367.3e6              # k_ci_cluster, both coupled sweeps of the 384 x 256 grid
 # GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA throughput microbenchmark
 # measured 1.20 TFLOP/s on this machine).  FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
@@ -570,6 +573,9 @@ def main():
             "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof},
             "phases_fp64_frac": {p: (FP64_FLOPS_PER_CELL[p] * N / (prof[p][0] / args.steps / 1e3) / 1e9
                                      / FP64_PEAK_GFLOPS) if prof[p][0] > 0 else None for p in prof}}
+    if PRECISION == 1 and prof["sweep_fwd"][0] > 0:
+        roof["phases_fp64_frac"]["sweep_fwd"] = (FP64_FLOPS_PER_CELL_SWEEP_MIXED * N / (prof["sweep_fwd"][0] / args.steps / 1e3)
+                                                 / 1e9 / FP64_PEAK_GFLOPS)
     if SCHEME[0] == 1:
         # coupled operator: the sweep and block phases run other kernels (k_ci_cluster, k_ci_block),
         # whose FP64 counts were not taken; the sweep is reported against HBM with the DRAM bytes

@@ -168,22 +168,24 @@ cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
- * split sweeps in one launch, choosing per precision: for the FP32 operator 4 where it applies,
- * else 2; for FP64, 5 where its records can be allocated, else 1.  1 is a thread-block-cluster
- * kernel reading the cell arrays directly, 2 a cluster kernel over hyperplane-ordered cell
- * records, 4 the FP32 operator's sweeps with one CTA per component holding every row
- * (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall back to 2), 5 the
- * FP64 operator's sweeps over neighbour couplings assembled beforehand (D^-1 times the split
- * Jacobian blocks, formed in one parallel launch into library-owned records of 4 nF nP + 4
- * doubles per cell and 2 nF nP + 2 per row j, nP = nF rounded up to even; then a cluster
- * kernel with 8 threads per row, whose CTAs exchange the rows at their boundaries point to
- * point (st.async into the next CTA's shared memory, one mbarrier per hyperplane; needs
- * (ni + nj - 1) x 72 bytes of shared memory per CTA, at most 200 KiB, else 6 is used); single
- * grids only, batches and the FP32 operator fall back to 1), 6 the same couplings with one
- * cluster barrier per hyperplane; 0 runs one launch per hyperplane.
- * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.  "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per
- * component of the 2D cluster sweeps (0, the default: the largest that fits; a C that does not
- * fit the grid or the device falls back to one launch per hyperplane); cs_batch_tune sets it.
+ * split sweeps in one launch, choosing per precision: 5 where its records can be allocated and
+ * its ring fits, else for the FP32 operator 4 where it applies, else 2, and for FP64 6, else 1.
+ * 1 is a thread-block-cluster kernel reading the cell arrays directly, 2 a cluster kernel over
+ * hyperplane-ordered cell records, 4 the FP32 operator's sweeps with one CTA per component
+ * holding every row (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall
+ * back to 2), 5 the sweeps over neighbour couplings assembled beforehand: D^-1 times the split
+ * Jacobian blocks, formed in FP64 by one parallel launch into library-owned records (FP64, or
+ * FP32 for the FP32 operator) of 4 nF nP + 4 elements per cell and 2 nF nP + 4 per row j, nP =
+ * nF rounded up to a whole 16-byte load; then a cluster kernel with 8 threads per row whose
+ * CTAs exchange the rows at their boundaries point to point (st.async into the next CTA's
+ * shared memory, one mbarrier per hyperplane; (ni + nj - 1) x (8 x element size + 8) bytes of
+ * shared memory per CTA, at most 200 KiB; single grids only), 6 the FP64 couplings with one
+ * cluster barrier per hyperplane (the FP32 operator falls back to 1); 0 runs one launch per
+ * hyperplane.
+ * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.
+ * "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per component of the 2D cluster
+ * sweeps (0, the default: the largest that fits; a C that does not fit the grid or the device
+ * falls back to one launch per hyperplane); cs_batch_tune sets it.
  * Method option: "h_correction" = 1 (default) widens the entropy fix of every face's Roe flux
  * to at least twice the face's multidimensional H-correction (Sanders, Morano and Druguet,
  * J. Comput. Phys. 145, 1998; the paper names Roe's scheme, Sec. 3.2, but not its entropy

@@ -560,8 +560,9 @@ extern "C" cs_status cs_residual(cs_grid g, double* R_out, double norms_host[3])
   return CS_OK;
 }
 
-// coupling records of the FP64 2D split sweep (K6e); without them (allocation refused) the
-// sweep falls back to the direct-load cluster kernel
+// coupling records of the 2D split sweep over assembled couplings (K6e; FP64 or FP32 records in
+// the same buffer); without them (allocation refused) the sweep falls back to the other cluster
+// kernels
 static void ensure_mat(cs_grid g) {
   if (g->g.SMC || g->mat_refused) return;
   const size_t n = g->L->mat_doubles(g->g);
@@ -587,7 +588,7 @@ extern "C" cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double
   cs_status st = begin(g);
   if (st) return st;
   if ((st = set_cfl(g, cfl))) return st;
-  if (precision == CS_FP64) ensure_mat(g);
+  ensure_mat(g);
   g->L->spectral(g->g, g->stream);
   g->L->sweep_split(g->g, g->stream, precision == CS_MIXED);
   if (dQ_out)
@@ -748,7 +749,7 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
   cs_status st = check_opts(o);
   if (st) return st;
   if (o->scheme == CS_SCHEME_COUPLED && (st = ensure_ci(g))) return fail(g, st, "allocation");
-  if (o->scheme == CS_SCHEME_SPLIT && o->precision == CS_FP64) ensure_mat(g);
+  if (o->scheme == CS_SCHEME_SPLIT) ensure_mat(g);
   if ((st = begin(g))) return st;
   int done = 0;
   for (int it = 0; it < o->iters; ++it) {
@@ -824,8 +825,9 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!strcmp(name, "cluster_sweep")) {
     // 0 per hyperplane, 1 direct-load cluster kernel, 2 record cluster kernel, 3 default (by
     // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2),
-    // 5 assembled couplings (FP64 operator only; the FP32 one falls back to 1), exchanged point
-    // to point between CTAs where the ring fits, 6 the same with a cluster barrier per hyperplane
+    // 5 assembled couplings exchanged point to point between CTAs where the ring fits (else
+    // FP64: 6, FP32: 1), 6 the same FP64 couplings with a cluster barrier per hyperplane (the
+    // FP32 operator falls back to 1)
     g->L->use_cluster = value != 0.0;
     g->L->cluster_kind = value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;

@@ -2462,32 +2462,46 @@ __global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
 // cluster barrier, on one or two sub-partitions) the bound of K6b; here each row of a CTA has
 // kMatSlots threads, one per flow component (or species of the CTA's group), and a CTA's rows
 // cover all four sub-partitions.
-// Record of cell c (doubles): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF rows of NP
-// (NF rounded up to even, so that every row starts on 16 bytes), then the species coefficients
-// in the same order.  Per row j after the N cell records: the periodic-i wrap couplings
+// Record of cell c (elements of the operator's type T: FP64, or FP32 for the mixed-precision
+// operator, formed in FP64 and rounded once): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF
+// rows of NP (NF rounded up to a whole 16-byte load, so that every row starts on 16 bytes),
+// then the species coefficients in the same order.  Per row j after the N cell records: the periodic-i wrap couplings
 // (forward: cell (ni-1, j) with (0, j); backward: (0, j) with (ni-1, j)), flow blocks then
 // species coefficients.
 // ---------------------------------------------------------------------------------------
 constexpr int kMatSlots = 8;       // threads per row of a CTA
 constexpr int kMatSpecies = kMatSlots;
 
-template <class G>
+template <class G, class T = double>
 struct MatRec {
   static constexpr int NF = Aux<G, 2>::NF;
-  static constexpr int NP = (NF + 1) / 2 * 2;
+  static constexpr int VEC = 16 / (int)sizeof(T);     // elements of one 16-byte load
+  static constexpr int NP = (NF + VEC - 1) / VEC * VEC;
   static constexpr int BLK = NF * NP;
   static constexpr int CELL = 4 * BLK + 4;
-  static constexpr int ROW = 2 * BLK + 2;
+  static constexpr int ROW = 2 * BLK + 4;
   static_assert(NF <= kMatSlots, "one thread per flow component");
+  static_assert(CELL % VEC == 0, "cell records start on 16 bytes");
+};
+template <class T> struct Vec16;
+template <> struct Vec16<double> {
+  using type = double2;
+  __device__ static void unpack(const double2& a, double* o) { o[0] = a.x; o[1] = a.y; }
+};
+template <> struct Vec16<float> {
+  using type = float4;
+  __device__ static void unpack(const float4& a, float* o) {
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  }
 };
 template <class G>
 constexpr int mat_species_groups() { return (G::NS + kMatSpecies - 1) / kMatSpecies; }
 
 // D_c^-1 (+-1/2)(A_nb(S) +- lambda I) of the flow block, written row-major with pitch NP
-template <class G>
+template <class G, class T>
 __device__ __forceinline__ void mat_block(const DevGrid& g, int nb, const double* S, double lam,
-                                          int side, double dF, double dEv, double* out) {
-  constexpr int NF = MatRec<G>::NF, NP = MatRec<G>::NP;
+                                          int side, double dF, double dEv, T* out) {
+  constexpr int NF = MatRec<G, T>::NF, NP = MatRec<G, T>::NP;
   CellState<G, 2, double> w;
   load_state<G, 2, double>(g, nb, w);
   const double Sf[2] = {S[0], S[1]};
@@ -2501,13 +2515,13 @@ __device__ __forceinline__ void mat_block(const DevGrid& g, int nb, const double
     for (int v = 0; v < NF; ++v) {
       const double l = v == k ? lam : 0.0;
       const double m = side < 0 ? 0.5 * (a[v] + l) : -0.5 * (a[v] - l);
-      out[v * NP + k] = ((G::NTEMP == 2 && v == NF - 1) ? dEv : dF) * m;
+      out[v * NP + k] = (T)(((G::NTEMP == 2 && v == NF - 1) ? dEv : dF) * m);
     }
   }
 #pragma unroll
   for (int v = 0; v < NF; ++v)
 #pragma unroll
-    for (int k = NF; k < NP; ++k) out[v * NP + k] = 0.0;
+    for (int k = NF; k < NP; ++k) out[v * NP + k] = T(0);
 }
 
 // species coupling (+-1/2)(U_nb +- lambda_C,nb) before D_s^-1, U_nb = u_nb . S
@@ -2519,75 +2533,77 @@ __device__ __forceinline__ double mat_coef(const DevGrid& g, int nb, const doubl
   return side < 0 ? 0.5 * (U + lam) : -0.5 * (U - lam);
 }
 
-template <class G>
+template <class G, class T>
 __global__ void __launch_bounds__(128) k_sweep_mat(DevGrid g) {
-  using M = MatRec<G>;
+  using M = MatRec<G, T>;
   constexpr int BLK = M::BLK;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.N) return;
   const size_t N = g.N;
   const int ni = g.ni, nj = g.nj, i = c % ni, j = c / ni;
   const double dF = g.invD[c], dEv = g.invD[N + c];
-  double* rec = g.SMC + (size_t)c * M::CELL;
-  double* co = rec + 4 * BLK;
+  T* rec = reinterpret_cast<T*>(g.SMC) + (size_t)c * M::CELL;
+  T* co = rec + 4 * BLK;
   const double* S;
   // a face on the grid's boundary couples nothing: its block and coefficient are zero
   if (i == 0 || j == 0 || i == ni - 1 || j == nj - 1) {
-    for (int e = 0; e < M::CELL; ++e) rec[e] = 0.0;
+    for (int e = 0; e < M::CELL; ++e) rec[e] = T(0);
   }
   // forward: the lower neighbours (i-1, j) and (i, j-1); backward: the upper ones
   if (i > 0) {
     S = g.S[0] + 3 * (size_t)face_of(g, 0, i, j, 0);
-    mat_block<G>(g, c - 1, S, g.lamF[c - 1], -1, dF, dEv, rec);
-    co[0] = mat_coef<G>(g, c - 1, S, g.lamC[c - 1], -1);
+    mat_block<G, T>(g, c - 1, S, g.lamF[c - 1], -1, dF, dEv, rec);
+    co[0] = (T)mat_coef<G>(g, c - 1, S, g.lamC[c - 1], -1);
   }
   if (j > 0) {
     S = g.S[1] + 3 * (size_t)face_of(g, 1, i, j, 0);
-    mat_block<G>(g, c - ni, S, g.lamF[N + c - ni], -1, dF, dEv, rec + BLK);
-    co[1] = mat_coef<G>(g, c - ni, S, g.lamC[N + c - ni], -1);
+    mat_block<G, T>(g, c - ni, S, g.lamF[N + c - ni], -1, dF, dEv, rec + BLK);
+    co[1] = (T)mat_coef<G>(g, c - ni, S, g.lamC[N + c - ni], -1);
   }
   if (i < ni - 1) {
     S = g.S[0] + 3 * (size_t)face_of(g, 0, i + 1, j, 0);
-    mat_block<G>(g, c + 1, S, g.lamF[c + 1], +1, dF, dEv, rec + 2 * BLK);
-    co[2] = mat_coef<G>(g, c + 1, S, g.lamC[c + 1], +1);
+    mat_block<G, T>(g, c + 1, S, g.lamF[c + 1], +1, dF, dEv, rec + 2 * BLK);
+    co[2] = (T)mat_coef<G>(g, c + 1, S, g.lamC[c + 1], +1);
   }
   if (j < nj - 1) {
     S = g.S[1] + 3 * (size_t)face_of(g, 1, i, j + 1, 0);
-    mat_block<G>(g, c + ni, S, g.lamF[N + c + ni], +1, dF, dEv, rec + 3 * BLK);
-    co[3] = mat_coef<G>(g, c + ni, S, g.lamC[N + c + ni], +1);
+    mat_block<G, T>(g, c + ni, S, g.lamF[N + c + ni], +1, dF, dEv, rec + 3 * BLK);
+    co[3] = (T)mat_coef<G>(g, c + ni, S, g.lamC[N + c + ni], +1);
   }
   if (g.bc[0] == BC_PERIODIC) {
-    double* pr = g.SMC + N * M::CELL + (size_t)j * M::ROW;
+    T* pr = reinterpret_cast<T*>(g.SMC) + N * M::CELL + (size_t)j * M::ROW;
     if (i == ni - 1) {          // forward: (0, j) precedes (ni-1, j) and lies on its + side
       const int nb = ni * j;
       S = g.S[0] + 3 * (size_t)face_of(g, 0, ni, j, 0);
-      mat_block<G>(g, nb, S, g.lamF[nb], +1, dF, dEv, pr);
-      pr[2 * BLK] = mat_coef<G>(g, nb, S, g.lamC[nb], +1);
+      mat_block<G, T>(g, nb, S, g.lamF[nb], +1, dF, dEv, pr);
+      pr[2 * BLK] = (T)mat_coef<G>(g, nb, S, g.lamC[nb], +1);
     }
     if (i == 0) {               // backward: (ni-1, j) precedes (0, j) and lies on its - side
       const int nb = ni - 1 + ni * j;
       S = g.S[0] + 3 * (size_t)face_of(g, 0, 0, j, 0);
-      mat_block<G>(g, nb, S, g.lamF[nb], -1, dF, dEv, pr + BLK);
-      pr[2 * BLK + 1] = mat_coef<G>(g, nb, S, g.lamC[nb], -1);
+      mat_block<G, T>(g, nb, S, g.lamF[nb], -1, dF, dEv, pr + BLK);
+      pr[2 * BLK + 1] = (T)mat_coef<G>(g, nb, S, g.lamC[nb], -1);
     }
   }
 }
 
 // inputs of one thread's cell at step q (loaded a step ahead)
-template <class G>
+template <class G, class T = double>
 struct MatStep {
   // raw loads only (no arithmetic on them here, so that a prefetch does not wait for its own
   // loads): the coupling rows (species: the two coefficients before D_s^-1), the diagonal
   // inverse d and base = the right-hand side (forward) or the forward result (backward)
-  double bi[MatRec<G>::NP], bj[MatRec<G>::NP], base, d;
+  T bi[MatRec<G, T>::NP], bj[MatRec<G, T>::NP], base, d;
   int c, i;
   bool act;
 };
 
-template <class G>
+template <class G, class T = double>
 __device__ __forceinline__ void mat_step_load(const DevGrid& g, int q, int j, bool on, bool fwd,
-                                              bool flow, int v, int s, MatStep<G>& m) {
-  using M = MatRec<G>;
+                                              bool flow, int v, int s, MatStep<G, T>& m) {
+  using M = MatRec<G, T>;
+  using V = typename Vec16<T>::type;
+  constexpr int VEC = M::VEC;
   constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
   const int ni = g.ni, H = ni + g.nj - 2;
   const int i = (fwd ? q : H - q) - j;
@@ -2597,24 +2613,21 @@ __device__ __forceinline__ void mat_step_load(const DevGrid& g, int q, int j, bo
   const size_t N = g.N;
   const int c = i + ni * j;
   m.c = c;
-  const double* rec = g.SMC + (size_t)c * M::CELL;
+  const T* rec = reinterpret_cast<const T*>(g.SMC) + (size_t)c * M::CELL;
   if (flow) {
-    const double2* ri = reinterpret_cast<const double2*>(rec + (fwd ? 0 : 2 * BLK) + v * NP);
-    const double2* rj = reinterpret_cast<const double2*>(rec + (fwd ? BLK : 3 * BLK) + v * NP);
+    const V* ri = reinterpret_cast<const V*>(rec + (fwd ? 0 : 2 * BLK) + v * NP);
+    const V* rj = reinterpret_cast<const V*>(rec + (fwd ? BLK : 3 * BLK) + v * NP);
 #pragma unroll
-    for (int k = 0; k < NP / 2; ++k) {
-      const double2 a = ri[k], b = rj[k];
-      m.bi[2 * k] = a.x;
-      m.bi[2 * k + 1] = a.y;
-      m.bj[2 * k] = b.x;
-      m.bj[2 * k + 1] = b.y;
+    for (int k = 0; k < NP / VEC; ++k) {
+      Vec16<T>::unpack(ri[k], m.bi + VEC * k);
+      Vec16<T>::unpack(rj[k], m.bj + VEC * k);
     }
-    m.d = g.invD[((G::NTEMP == 2 && v == NF - 1) ? N : 0) + c];
-    m.base = fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c];
+    m.d = (T)g.invD[((G::NTEMP == 2 && v == NF - 1) ? N : 0) + c];
+    m.base = (T)(fwd ? g.rhsF[v * N + c] : g.dQs[v * N + c]);
   } else {
-    m.d = g.invD[(2 + s) * N + c];
-    m.base = fwd ? -g.R[(size_t)s * N + c] : g.dQs[(size_t)(NF + s) * N + c];
-    const double* co = rec + 4 * BLK;
+    m.d = (T)g.invD[(2 + s) * N + c];
+    m.base = (T)(fwd ? -g.R[(size_t)s * N + c] : g.dQs[(size_t)(NF + s) * N + c]);
+    const T* co = rec + 4 * BLK;
     m.bi[0] = co[fwd ? 0 : 2];
     m.bj[0] = co[fwd ? 1 : 3];
   }
@@ -2757,19 +2770,29 @@ __device__ __forceinline__ bool p2p_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// dynamic shared memory of k_split_p2p: the ring [H + 1][kMatSlots] doubles, then H + 1 mbarriers
+// dynamic shared memory of k_split_p2p: the ring [H + 1][kMatSlots] of T, then H + 1 mbarriers
+template <class T>
 __host__ __device__ inline size_t p2p_smem_bytes(int ni, int nj) {
-  return (size_t)(ni + nj - 1) * (kMatSlots * sizeof(double) + sizeof(unsigned long long));
+  return (size_t)(ni + nj - 1) * (kMatSlots * sizeof(T) + sizeof(unsigned long long));
+}
+// one element into another CTA's shared memory, completing bytes on that CTA's mbarrier
+__device__ __forceinline__ void st_async(uint32_t dst, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];\n"
+               ::"r"(dst), "l"(__double_as_longlong(v)), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t dst, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];\n"
+               ::"r"(dst), "r"(__float_as_uint(v)), "r"(bar) : "memory");
 }
 
-template <class G>
+template <class G, class T>
 __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid g, int R) {
-  using M = MatRec<G>;
+  using M = MatRec<G, T>;
   constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
   extern __shared__ __align__(16) unsigned char p2p_dyn[];
-  __shared__ __align__(16) double xs[2][kClusterRows][kMatSlots];
+  __shared__ __align__(16) T xs[2][kClusterRows][kMatSlots];
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
-  double* ring = reinterpret_cast<double*>(p2p_dyn);
+  T* ring = reinterpret_cast<T*>(p2p_dyn);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + (size_t)(H + 1) * kMatSlots);
   const size_t N = g.N;
   const int comp = blockIdx.x / (int)cluster_nctarank();   // 0: flow block, else a species group
@@ -2780,7 +2803,7 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
   const bool flow = comp == 0;
   const int s = (comp - 1) * kMatSpecies + v;
   const bool on = t < R && j < nj && (flow ? v < NF : s < G::NS);
-  // bytes one boundary row sends per hyperplane: one double per active slot
+  // elements one boundary row sends per hyperplane: one per active slot
   const int nsend = flow ? NF : (G::NS - (comp - 1) * kMatSpecies < kMatSpecies ? G::NS - (comp - 1) * kMatSpecies : kMatSpecies);
   for (int q = threadIdx.x; q <= H; q += blockDim.x)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + q)) : "memory");
@@ -2796,7 +2819,7 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
       const bool row_ok = jc < nj && (fwd ? jc > 0 : jc + 1 < nj);
       for (int q = threadIdx.x; q <= H; q += 32) {
         const int ic = (fwd ? q : H - q) - jc;
-        const uint32_t bytes = (row_ok && ic >= 0 && ic < ni) ? nsend * (uint32_t)sizeof(double) : 0u;
+        const uint32_t bytes = (row_ok && ic >= 0 && ic < ni) ? nsend * (uint32_t)sizeof(T) : 0u;
         unsigned long long st;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
                      : "=l"(st) : "r"(smem_u32(mbar + q)), "r"(bytes) : "memory");
@@ -2804,14 +2827,14 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
     }
     cluster_arrive();
     cluster_wait();
-    double xp[NF], xf[NF], pw[NP];   // flow: the row's previous and first results, wrap block row
-    double sp = 0.0, sf = 0.0, pc = 0.0;
+    T xp[NF], xf[NF], pw[NP];   // flow: the row's previous and first results, wrap block row
+    T sp = 0, sf = 0, pc = 0;
 #pragma unroll
-    for (int k = 0; k < NF; ++k) xp[k] = xf[k] = 0.0;
+    for (int k = 0; k < NF; ++k) xp[k] = xf[k] = T(0);
 #pragma unroll
-    for (int k = 0; k < NP; ++k) pw[k] = 0.0;
+    for (int k = 0; k < NP; ++k) pw[k] = T(0);
     if (on && per) {
-      const double* pr = g.SMC + N * M::CELL + (size_t)j * M::ROW;
+      const T* pr = reinterpret_cast<const T*>(g.SMC) + N * M::CELL + (size_t)j * M::ROW;
       if (flow) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) pw[k] = pr[(fwd ? 0 : BLK) + v * NP + k];
@@ -2829,10 +2852,10 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
     const bool sends = fwd ? j + 1 < nj : j > 0;
     // the inputs of step q are loaded four steps ahead, into the buffer of step q mod 4 right
     // after step q - 4 has used it: the loads have three steps to arrive
-    auto step = [&](int q, MatStep<G>& cur) {
+    auto step = [&](int q, MatStep<G, T>& cur) {
       // the row's own earlier cells (and the periodic wrap) need no other row: coupled before
       // this step's synchronisation
-      double acc = 0.0;
+      T acc = 0;
       if (cur.act) {
         acc = fwd ? cur.d * cur.base : cur.base;
         const bool hasi = fwd ? cur.i > 0 : cur.i < ni - 1;
@@ -2856,7 +2879,7 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
         // the neighbouring row's result of step q-1; across a CTA boundary the neighbouring CTA
         // wrote it into ring slot q
         if (hasj) {
-          const double* src;
+          const T* src;
           if (!boundary_in) {
             src = xs[(q - 1) & 1][fwd ? t - 1 : t + 1];
           } else {
@@ -2876,11 +2899,9 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
         xs[q & 1][t][v] = acc;
         if (boundary_out && sends) {
           const uint32_t dst = cluster_map(smem_u32(ring + (size_t)(q + 1) * kMatSlots + v), peer);
-          const uint32_t bar = cluster_map(smem_u32(mbar + q + 1), peer);
-          asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];\n"
-                       ::"r"(dst), "l"(__double_as_longlong(acc)), "r"(bar) : "memory");
+          st_async(dst, acc, cluster_map(smem_u32(mbar + q + 1), peer));
         }
-        out[orow + cur.c] = acc;
+        out[orow + cur.c] = (double)acc;
       }
       __syncwarp();                    // a row's kMatSlots threads share one warp
       if (cur.act) {
@@ -2896,13 +2917,13 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
           sf = sp;
         }
       }
-      mat_step_load<G>(g, q + 4, j, on, fwd, flow, v, s, cur);
+      mat_step_load<G, T>(g, q + 4, j, on, fwd, flow, v, s, cur);
     };
-    MatStep<G> m0, m1, m2, m3;
-    mat_step_load<G>(g, 0, j, on, fwd, flow, v, s, m0);
-    mat_step_load<G>(g, 1, j, on, fwd, flow, v, s, m1);
-    mat_step_load<G>(g, 2, j, on, fwd, flow, v, s, m2);
-    mat_step_load<G>(g, 3, j, on, fwd, flow, v, s, m3);
+    MatStep<G, T> m0, m1, m2, m3;
+    mat_step_load<G, T>(g, 0, j, on, fwd, flow, v, s, m0);
+    mat_step_load<G, T>(g, 1, j, on, fwd, flow, v, s, m1);
+    mat_step_load<G, T>(g, 2, j, on, fwd, flow, v, s, m2);
+    mat_step_load<G, T>(g, 3, j, on, fwd, flow, v, s, m3);
     for (int q = 0; q <= H; q += 4) {
       step(q, m0);
       if (q + 1 <= H) step(q + 1, m1);

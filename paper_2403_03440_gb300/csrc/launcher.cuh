@@ -2,6 +2,7 @@
 // its own translation unit (launch_<model>.cu) so the three models compile in parallel.
 #pragma once
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -239,18 +240,20 @@ struct LauncherT : Launcher {
 
   // one launch: both sweeps of the flow block and of every species (returns launches)
   int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed) override {
-    // measured on GB300: in FP32 the one-CTA-per-component kernel (where nj fits) and then
-    // the wavefront-record kernel, in FP64 the assembled couplings, then the direct-load kernel
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 4);
-    if ((kind == 4 || kind == 5) && !mixed) {
-      const int n = sweep_mat(g, st, kind == 4);
+    // measured on GB300: the assembled couplings exchanged point to point (both precisions),
+    // then in FP32 the one-CTA-per-component kernel (where nj fits) and the wavefront-record
+    // kernel, in FP64 the assembled couplings with a cluster barrier and the direct-load kernel
+    const int kind = cluster_kind ? cluster_kind : 4;
+    if (kind == 4 || kind == 5) {
+      const int n = mixed ? (kind == 4 ? sweep_mat<float>(g, st, true) : 0) : sweep_mat<double>(g, st, kind == 4);
       if (n) return n;
     }
-    if (kind == 3 && mixed && g.wrec) {
+    const int alt = kind >= 4 ? (mixed ? 3 : 1) : kind;
+    if (alt == 3 && mixed && g.wrec) {
       const int n = sweep_block(g, st);
       if (n) return n;
     }
-    if ((kind == 2 || kind == 3) && g.wrec) {
+    if ((alt == 2 || alt == 3) && g.wrec) {
       const int n = mixed ? sweep_wave_t<float>(g, st, wprobed32_) : sweep_wave_t<double>(g, st, wprobed64_);
       if (n) return n;
     }
@@ -293,13 +296,18 @@ struct LauncherT : Launcher {
   }
 
   void prepare(const DevGrid& g, bool mixed) override {
-    const int kind = cluster_kind ? cluster_kind : (mixed ? 3 : 4);
-    if ((kind == 4 || kind == 5) && !mixed && g.SMC) {
-      mat_cluster_size(g, false);
-      if (kind == 4) mat_cluster_size(g, true);
+    const int kind = cluster_kind ? cluster_kind : 4;
+    if ((kind == 4 || kind == 5) && g.SMC) {
+      if (mixed) {
+        if (kind == 4) mat_cluster_size<float>(g, true);
+      } else {
+        mat_cluster_size<double>(g, false);
+        if (kind == 4) mat_cluster_size<double>(g, true);
+      }
     }
-    if (kind == 3 && mixed) block_ok(g);
-    if (kind == 2 || kind == 3) {
+    const int alt = kind >= 4 ? (mixed ? 3 : 1) : kind;
+    if (alt == 3 && mixed) block_ok(g);
+    if (alt == 2 || alt == 3) {
       if (mixed) wave_cluster_size<float>(g, wprobed32_);
       else wave_cluster_size<double>(g, wprobed64_);
     }
@@ -384,61 +392,68 @@ struct LauncherT : Launcher {
     return 1;
   }
 
-  // FP64 2D sweeps over assembled couplings (K6e): k_sweep_mat, then one cluster launch with
+  // 2D sweeps over assembled couplings (K6e): k_sweep_mat, then one cluster launch with
   // kMatSlots threads per row, point to point between CTAs (k_split_p2p) where its ring fits in
-  // shared memory, else with a cluster barrier per hyperplane (k_split_mat).  Single grids only:
-  // a batch keeps the one-warp direct kernel, whose CTAs need fewer registers and no records.
+  // shared memory, else (FP64 only) with a cluster barrier per hyperplane (k_split_mat).  T is
+  // the operator's type (FP64, or FP32 for the mixed-precision operator).  Single grids only: a
+  // batch keeps the one-warp direct kernel, whose CTAs need fewer registers and no records.
   size_t mat_doubles(const DevGrid& g) const override {
-    return ND == 2 ? (size_t)g.N * MatRec<G>::CELL + (size_t)g.nj * MatRec<G>::ROW : 0;
+    if (ND != 2) return 0;
+    const size_t d = (size_t)g.N * MatRec<G, double>::CELL + (size_t)g.nj * MatRec<G, double>::ROW;
+    const size_t f = ((size_t)g.N * MatRec<G, float>::CELL + (size_t)g.nj * MatRec<G, float>::ROW + 1) / 2;
+    return d > f ? d : f;
   }
   static constexpr size_t kP2PMaxSmem = 200 * 1024;
+  template <class T>
   bool mat_fits(const DevGrid& g, int C, bool p2p) {
     const int R = (g.nj + C - 1) / C;
     if (R > kClusterRows) return false;
     const int warps = (kMatSlots * R + 31) / 32;
-    if (!p2p) return cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
-    const size_t smem = p2p_smem_bytes(g.ni, g.nj);
-    return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G>, C, warps, mat_species_groups<G>(), smem);
+    if (!p2p) return std::is_same<T, double>::value && cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
+    const size_t smem = p2p_smem_bytes<T>(g.ni, g.nj);
+    return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G, T>, C, warps, mat_species_groups<G>(), smem);
   }
+  template <class T>
   int mat_cluster_size(const DevGrid& g, bool p2p) {
     if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
-    const int m = p2p ? 1 : 0;
+    const int m = (p2p ? 1 : 0) + (std::is_same<T, float>::value ? 2 : 0);
     if (force_C > 0) {
       if (mat_forced_C_[m] != force_C) {
         mat_forced_C_[m] = force_C;
-        mat_forced_ok_[m] = mat_fits(g, force_C, p2p);
+        mat_forced_ok_[m] = mat_fits<T>(g, force_C, p2p);
       }
       return mat_forced_ok_[m] ? force_C : 0;
     }
     if (mat_probed_[m] >= 0) return mat_probed_[m];
     mat_probed_[m] = 0;
     for (int C : {16, 8, 4, 2}) {
-      if (mat_fits(g, C, p2p)) {
+      if (mat_fits<T>(g, C, p2p)) {
         mat_probed_[m] = C;
         break;
       }
     }
     return mat_probed_[m];
   }
-  int mat_probed_[2] = {-1, -1}, mat_forced_C_[2] = {0, 0};
-  bool mat_forced_ok_[2] = {false, false};
+  int mat_probed_[4] = {-1, -1, -1, -1}, mat_forced_C_[4] = {0, 0, 0, 0};
+  bool mat_forced_ok_[4] = {false, false, false, false};
+  template <class T>
   int sweep_mat(const DevGrid& g, cudaStream_t st, bool allow_p2p) {
     sweep_split_cluster_ok = false;
     if constexpr (ND != 2) {
       return 0;
     } else {
       if (cluster_warps == 1 || !g.SMC) return 0;
-      int C = allow_p2p ? mat_cluster_size(g, true) : 0;
+      int C = allow_p2p ? mat_cluster_size<T>(g, true) : 0;
       const bool p2p = C > 0;
-      if (!p2p) C = mat_cluster_size(g, false);
+      if (!p2p) C = std::is_same<T, double>::value ? mat_cluster_size<T>(g, false) : 0;
       if (C == 0) return 0;
       const int R = (g.nj + C - 1) / C;
-      k_sweep_mat<G><<<blocks(g.N, 128), 128, 0, st>>>(g);
+      k_sweep_mat<G, T><<<blocks(g.N, 128), 128, 0, st>>>(g);
       cudaLaunchConfig_t cfg = {};
       cudaLaunchAttribute at[1];
       cfg.gridDim = dim3(C * (1 + mat_species_groups<G>()));
       cfg.blockDim = dim3((kMatSlots * R + 31) / 32 * 32);
-      cfg.dynamicSmemBytes = p2p ? p2p_smem_bytes(g.ni, g.nj) : 0;
+      cfg.dynamicSmemBytes = p2p ? p2p_smem_bytes<T>(g.ni, g.nj) : 0;
       cfg.stream = st;
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = C;
@@ -446,7 +461,7 @@ struct LauncherT : Launcher {
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      const cudaError_t e = p2p ? cudaLaunchKernelEx(&cfg, k_split_p2p<G>, g, R)
+      const cudaError_t e = p2p ? cudaLaunchKernelEx(&cfg, k_split_p2p<G, T>, g, R)
                                 : cudaLaunchKernelEx(&cfg, k_split_mat<G>, g, R);
       if (e != cudaSuccess) {
         cudaGetLastError();

@@ -409,7 +409,8 @@ def test_cluster_sweep_equals_hyperplane_sweep(name):
 def test_block_sweep_equals_cluster_sweep_fp32(nodes_fn, bc, mech):
     """FP32 operator: the one-CTA-per-component sweep (every row in one CTA, __syncthreads
     between hyperplanes) performs the record cluster kernel's arithmetic; 100 rows span 4
-    warps.  Both agree with the FP64 oracle to FP32 rounding."""
+    warps.  Both, and the sweep over FP32 couplings assembled in FP64 (point-to-point cluster
+    exchange), agree with the FP64 oracle to FP32 rounding."""
     nodes = nodes_fn()
     fs = inputs.freestream(mech, T=300.0, p=500.0, mach=10.0)
     ref = oracle.OracleGrid(nodes, bc, mech)
@@ -420,7 +421,8 @@ def test_block_sweep_equals_cluster_sweep_fp32(nodes_fn, bc, mech):
     Q = oracle.prim_to_cons_field(mech, 2, pr)
     ref.set_state(Q)
     out = {}
-    for mode in (4, 2):
+    # one CTA per component, wavefront records, assembled couplings point to point (FP32 records)
+    for mode in (4, 2, 5):
         gpu.set_option("cluster_sweep", mode)
         gpu.set_state(Q)
         gpu.residual(want_R=False)
@@ -430,8 +432,9 @@ def test_block_sweep_equals_cluster_sweep_fp32(nodes_fn, bc, mech):
     assert rel(out[4][ref.nF:], out[2][ref.nF:], ns=ref.ns) < 1e-6
     ref.residual()
     d = ref.lusgs_split(8.0)
-    assert rel(out[4][:ref.nF], d[:ref.nF]) < 1e-4
-    assert rel(out[4][ref.nF:], d[ref.nF:], ns=ref.ns) < 1e-4
+    for m in (4, 5):
+        assert rel(out[m][:ref.nF], d[:ref.nF]) < 1e-4, m
+        assert rel(out[m][ref.nF:], d[ref.nF:], ns=ref.ns) < 1e-4, m
 
 
 @pytest.mark.parametrize("name", ["c1_ogrid_air5", "ogrid_air11", "box3d_air5_kper"])
