@@ -402,6 +402,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
 #undef ALLOC
   d.DLU = nullptr;
   d.DINV = nullptr;
+  d.CIM = nullptr;
   d.piv = nullptr;
   d.params = g->params;
   if (cudaMallocHost(&g->h_pin, 64 * sizeof(double)) != cudaSuccess) return CS_ERR_OOM;
@@ -437,6 +438,7 @@ extern "C" cs_status cs_grid_destroy(cs_grid g) {
   for (void* p : g->allocs) cudaFree(p);
   if (g->g.DLU) cudaFree(g->g.DLU);
   if (g->g.DINV) cudaFree(g->g.DINV);
+  if (g->g.CIM) cudaFree(g->g.CIM);
   if (g->g.piv) cudaFree(g->g.piv);
   if (g->h_pin) cudaFreeHost(g->h_pin);
   if (g->h_status) cudaFreeHost(g->h_status);
@@ -614,6 +616,12 @@ static cs_status ensure_ci(cs_grid g) {
   g->g.DLU = (double*)a;
   g->g.piv = (int*)b;
   g->g.DINV = (double*)v;
+  // 2D: the neighbour blocks of the assembled coupled sweep (without them, the one-lane-per-row
+  // cluster sweep runs)
+  const size_t nm = g->L->ci_mat_doubles(g->g);
+  void* m = nullptr;
+  if (nm > 0 && cudaMalloc(&m, nm * sizeof(double)) == cudaSuccess) g->g.CIM = (double*)m;
+  else cudaGetLastError();
   return CS_OK;
 }
 
@@ -729,8 +737,9 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
     g->L->ci_block(d, g->stream);
     if (rec) prof_record(g, slot, 5);
     // both sweeps in one cluster launch where it applies (2D), else one launch per hyperplane
-    const bool one = g->L->use_cluster && g->L->sweep_coupled_cluster(d, g->stream);
-    nf = one ? 1 : g->L->sweep_coupled_dir(d, g->stream, true);
+    const int nc = g->L->use_cluster ? g->L->sweep_coupled_cluster(d, g->stream) : 0;
+    const bool one = nc > 0;
+    nf = one ? nc : g->L->sweep_coupled_dir(d, g->stream, true);
     if (rec) prof_record(g, slot, 6);
     nb = one ? 0 : g->L->sweep_coupled_dir(d, g->stream, false);
     if (rec) prof_record(g, slot, 7);

@@ -60,6 +60,7 @@ struct DevGrid {
   double* DLU;            // [N][nci*nci]
   int* piv;               // [N][nci]
   double* DINV;           // [N][nci*nci] inverse of the coupled diagonal block (row-major)
+  double* CIM;            // 2D coupled neighbour blocks of k_ci_mat (cell and row records) or null
   double* dQs;            // [nsplit][N]
   double* dQ;
   double* dQcs;           // [nci][N]
@@ -3446,6 +3447,207 @@ __global__ void __launch_bounds__(32) k_ci_cluster(DevGrid g, int R) {
         }
       }
       cluster_arrive();
+    }
+    cluster_wait();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Coupled (CI) sweeps of a 2D grid over assembled neighbour blocks.  k_ci_mat forms, for every
+// cell, the coupling blocks of its four neighbours in CI variables,
+// (+-1/2)(A_nb(S) [+- |A_nb(S)|] +- lambda_nb I), column by column from jvp_ci / absjac_ci (the
+// products k_ci_cluster applies one lane per row), and the cell's right-hand side.
+// k_ci_mat_sweep then runs both sweeps in one cluster launch with kCISlots threads per row, one
+// per CI variable: per hyperplane step a thread takes one row of each neighbour block (dot
+// products of length NC) and, once the row's threads have exchanged their right-hand sides
+// through shared memory, one row of the diagonal block's inverse.  The FP64 work of a cell is
+// spread over NC threads (and the four SM sub-partitions) instead of one lane.
+// Record of cell c (doubles): blocks [fwd i][fwd j][bwd i][bwd j], NC rows of NP (NC rounded up
+// to even), then the forward right-hand side (NP); per row j after the N cell records: the
+// periodic-i wrap blocks (forward, backward).
+// ---------------------------------------------------------------------------------------
+constexpr int kCISlots = 16;
+constexpr int kCIRows = 16;     // rows per CTA at most (kCISlots x kCIRows threads)
+
+template <class G>
+struct CIRec {
+  static constexpr int NC = Aux<G, 2>::NCI;
+  static constexpr int NP = (NC + 1) / 2 * 2;
+  static constexpr int BLK = NC * NP;
+  static constexpr int CELL = 4 * BLK + NP;
+  static constexpr int ROW = 2 * BLK;
+  static_assert(NC <= kCISlots, "one thread per CI variable");
+};
+
+// the block of neighbour nb across face Sf on side `side` (direction d for its radius)
+template <class G>
+__device__ __forceinline__ void ci_block_of(const DevGrid& g, int nb, int d, const double* Sf, int side,
+                                            double* out) {
+  constexpr int NC = CIRec<G>::NC, NP = CIRec<G>::NP;
+  const double l = g.lamCI[d * (size_t)g.N + nb];
+#pragma unroll 1
+  for (int k = 0; k < NC; ++k) {
+    double e[NC], ax[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) e[q] = q == k ? 1.0 : 0.0;
+    jvp_ci<G, 2>(g, nb, Sf, e, ax);
+    if (g.cisplit) {
+      double bx[NC];
+      absjac_ci<G, 2>(g, nb, Sf, e, bx);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) ax[q] += (side < 0 ? bx[q] : -bx[q]);
+    }
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+      const double lv = v == k ? l : 0.0;
+      out[v * NP + k] = side < 0 ? 0.5 * (ax[v] + lv) : -0.5 * (ax[v] - lv);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NC; ++v)
+#pragma unroll
+    for (int k = NC; k < NP; ++k) out[v * NP + k] = 0.0;
+}
+
+template <class G>
+__global__ void __launch_bounds__(64) k_ci_mat(DevGrid g) {
+  using M = CIRec<G>;
+  using A = Aux<G, 2>;
+  constexpr int NS = G::NS, NF = A::NF, NC = M::NC, NP = M::NP, BLK = M::BLK;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  const int ni = g.ni, nj = g.nj, i = c % ni, j = c / ni;
+  double* rec = g.CIM + (size_t)c * M::CELL;
+  // a face on the grid's boundary couples nothing: its block is zero
+  if (i == 0 || j == 0 || i == ni - 1 || j == nj - 1) {
+    for (int e = 0; e < 4 * BLK; ++e) rec[e] = 0.0;
+  }
+  if (i > 0) ci_block_of<G>(g, c - 1, 0, face_vec(g, 0, i, j, 0, -1), -1, rec);
+  if (j > 0) ci_block_of<G>(g, c - ni, 1, face_vec(g, 1, i, j, 0, -1), -1, rec + BLK);
+  if (i < ni - 1) ci_block_of<G>(g, c + 1, 0, face_vec(g, 0, i, j, 0, +1), +1, rec + 2 * BLK);
+  if (j < nj - 1) ci_block_of<G>(g, c + ni, 1, face_vec(g, 1, i, j, 0, +1), +1, rec + 3 * BLK);
+  // forward right-hand side in CI variables: -(sum_s R_s, R_m, R_E[, R_ev], R_2 .. R_ns)
+  double* rhs = rec + 4 * BLK;
+  double rr = 0.0;
+  for (int s = 0; s < NS; ++s) rr += g.R[s * N + c];
+  rhs[0] = -rr;
+  for (int v = 1; v < NF; ++v) rhs[v] = -g.R[(NS + v - 1) * N + c];
+  for (int s = 1; s < NS; ++s) rhs[NF + s - 1] = -g.R[s * N + c];
+  for (int v = NC; v < NP; ++v) rhs[v] = 0.0;
+  if (g.bc[0] == BC_PERIODIC) {
+    double* pr = g.CIM + N * M::CELL + (size_t)j * M::ROW;
+    // forward: (0, j) precedes (ni-1, j) across the cut, on its + side; backward: (ni-1, j)
+    // precedes (0, j), on its - side
+    if (i == ni - 1) ci_block_of<G>(g, ni * j, 0, face_vec(g, 0, i, j, 0, +1), +1, pr);
+    if (i == 0) ci_block_of<G>(g, ni - 1 + ni * j, 0, face_vec(g, 0, i, j, 0, -1), -1, pr + BLK);
+  }
+}
+
+// inputs of one thread's cell at step q (raw loads, one step ahead; the inverse's row is loaded
+// at the start of its own step, ahead of the cluster barrier)
+template <class G>
+struct CIStep {
+  double bi[CIRec<G>::NP], bj[CIRec<G>::NP], base;
+  int c, i;
+  bool act;
+};
+
+template <class G>
+__device__ __forceinline__ void ci_step_load(const DevGrid& g, int q, int j, bool on, bool fwd, int v,
+                                             CIStep<G>& m) {
+  using M = CIRec<G>;
+  constexpr int NP = M::NP, BLK = M::BLK;
+  const int ni = g.ni, H = ni + g.nj - 2;
+  const int i = (fwd ? q : H - q) - j;
+  m.act = on && q <= H && i >= 0 && i < ni;
+  m.i = i;
+  if (!m.act) return;
+  const int c = i + ni * j;
+  m.c = c;
+  const double* rec = g.CIM + (size_t)c * M::CELL;
+  const double2* ri = reinterpret_cast<const double2*>(rec + (fwd ? 0 : 2 * BLK) + v * NP);
+  const double2* rj = reinterpret_cast<const double2*>(rec + (fwd ? BLK : 3 * BLK) + v * NP);
+#pragma unroll
+  for (int k = 0; k < NP / 2; ++k) {
+    const double2 a = ri[k], b = rj[k];
+    m.bi[2 * k] = a.x;
+    m.bi[2 * k + 1] = a.y;
+    m.bj[2 * k] = b.x;
+    m.bj[2 * k + 1] = b.y;
+  }
+  m.base = fwd ? rec[4 * BLK + v] : g.dQcs[(size_t)v * g.N + c];
+}
+
+template <class G>
+__global__ void __launch_bounds__(kCISlots * kCIRows) k_ci_mat_sweep(DevGrid g, int R) {
+  using M = CIRec<G>;
+  constexpr int NC = M::NC, BLK = M::BLK, NP = M::NP;
+  __shared__ __align__(16) double xv[2][kCIRows][kCISlots];   // results of the last two steps
+  __shared__ __align__(16) double ac[kCIRows][kCISlots];      // a row's right-hand sides
+  __shared__ __align__(16) double xf[kCIRows][kCISlots];      // a row's first result of the pass
+  const size_t N = g.N;
+  const unsigned rank = cluster_ctarank();
+  const int t = threadIdx.x / kCISlots, v = threadIdx.x % kCISlots;
+  const int j = rank * R + t;
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const bool on = t < R && j < nj && v < NC;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    double* out = fwd ? g.dQcs : g.dQc;
+    const bool hasj = fwd ? j > 0 : j < nj - 1;
+    xf[t][v] = 0.0;
+    __syncwarp();
+    CIStep<G> cur, nxt;
+    ci_step_load<G>(g, 0, j, on, fwd, v, cur);
+    for (int q = 0; q <= H; ++q) {
+      ci_step_load<G>(g, q + 1, j, on, fwd, v, nxt);     // prefetch the next step
+      // the row's own previous cell (and the periodic wrap): no other row involved, coupled
+      // while the cluster barrier is pending
+      double acc = 0.0, dinv[NC];
+      if (cur.act) {
+        const double* Dv = g.DINV + (size_t)cur.c * NC * NC + v * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) dinv[k] = Dv[k];
+        const int i = cur.i;
+        if (fwd) acc = cur.base;
+        if (fwd ? i > 0 : i < ni - 1) {
+          const double* xp = xv[(q - 1) & 1][t];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc += cur.bi[k] * xp[k];
+        }
+        if (per && i == (fwd ? ni - 1 : 0)) {
+          const double* pw = g.CIM + N * M::CELL + (size_t)j * M::ROW + (fwd ? 0 : BLK) + v * NP;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc += pw[k] * xf[t][k];
+        }
+      }
+      if (q > 0) cluster_wait();
+      if (cur.act) {
+        if (hasj) {
+          const int par = (q - 1) & 1;
+          const double* src;
+          if (fwd) src = (t > 0) ? xv[par][t - 1] : dsmem(&xv[par][R - 1][0], rank - 1);
+          else src = (t < R - 1) ? xv[par][t + 1] : dsmem(&xv[par][0][0], rank + 1);
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc += cur.bj[k] * src[k];
+        }
+        ac[t][v] = acc;
+      }
+      __syncwarp();                    // a row's kCISlots threads share one warp
+      if (cur.act) {
+        double y = 0.0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) y += dinv[k] * ac[t][k];
+        const double x = fwd ? y : cur.base + y;
+        out[(size_t)v * N + cur.c] = x;
+        xv[q & 1][t][v] = x;
+        if (cur.i == (fwd ? 0 : ni - 1)) xf[t][v] = x;
+      }
+      __syncwarp();
+      cluster_arrive();
+      cur = nxt;
     }
     cluster_wait();
   }

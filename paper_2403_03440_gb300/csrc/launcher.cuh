@@ -61,6 +61,8 @@ struct Launcher {
   virtual int sweep_coupled_dir(const DevGrid& g, cudaStream_t st, bool fwd) = 0;
   // both coupled sweeps of a 2D grid in one cluster launch; 0 where it does not apply
   virtual int sweep_coupled_cluster(const DevGrid& g, cudaStream_t st) = 0;
+  // doubles of DevGrid::CIM, the 2D coupled neighbour blocks (0: not used)
+  virtual size_t ci_mat_doubles(const DevGrid& g) const = 0;
   virtual void correct(const DevGrid& g, cudaStream_t st, int mode, int clip, const double* dq) = 0;
   // chemistry surrogate coupling (raw samples; standardised inputs; decoded diagonal)
   virtual void surr_sample(const DevGrid& g, cudaStream_t st, float* X, float* T) = 0;
@@ -497,12 +499,57 @@ struct LauncherT : Launcher {
     k_ci_block<G, ND><<<blocks(g.N, 64), 64, 0, st>>>(g);
   }
 
+  size_t ci_mat_doubles(const DevGrid& g) const override {
+    return ND == 2 ? (size_t)g.N * CIRec<G>::CELL + (size_t)g.nj * CIRec<G>::ROW : 0;
+  }
+  // both coupled sweeps over assembled neighbour blocks (k_ci_mat, then k_ci_mat_sweep with
+  // kCISlots threads per row); 0 where the blocks are not allocated or no cluster fits
+  int ci_mat_probed_ = -1;
+  int sweep_coupled_mat(const DevGrid& g, cudaStream_t st) {
+    if constexpr (ND != 2) {
+      return 0;
+    } else {
+      if (!g.CIM || g.bc[2] == BC_PERIODIC) return 0;
+      if (ci_mat_probed_ < 0) {
+        ci_mat_probed_ = 0;
+        for (int C : {16, 8, 4, 2}) {
+          const int R = (g.nj + C - 1) / C;
+          if (R > kCIRows) continue;
+          if (cluster_fits(k_ci_mat_sweep<G>, C, (kCISlots * R + 31) / 32, 0)) {
+            ci_mat_probed_ = C;
+            break;
+          }
+        }
+      }
+      const int C = ci_mat_probed_;
+      if (C == 0) return 0;
+      const int R = (g.nj + C - 1) / C;
+      k_ci_mat<G><<<blocks(g.N, 64), 64, 0, st>>>(g);
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      cfg.gridDim = dim3(C);
+      cfg.blockDim = dim3((kCISlots * R + 31) / 32 * 32);
+      cfg.stream = st;
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (cudaLaunchKernelEx(&cfg, k_ci_mat_sweep<G>, g, R) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      return 2;
+    }
+  }
   int ci_probed_ = -1;
   int sweep_coupled_cluster(const DevGrid& g, cudaStream_t st) override {
     if constexpr (ND != 2) {
       return 0;
     } else {
       if (g.bc[2] == BC_PERIODIC) return 0;
+      if (const int n = sweep_coupled_mat(g, st)) return n;
       if (ci_probed_ < 0) {
         ci_probed_ = 0;
         for (int C : {16, 8, 4, 2}) {
