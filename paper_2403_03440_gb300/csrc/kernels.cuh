@@ -2451,7 +2451,8 @@ __global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
 }
 
 // ---------------------------------------------------------------------------------------
-// K6e: FP64 split sweeps of a 2D grid with the neighbour couplings assembled beforehand.
+// K6e: split sweeps of a 2D grid with the neighbour couplings assembled beforehand (FP64, or
+// FP32 for the mixed-precision operator).
 // The coupling of cell c with a neighbour nb across face S is the linear map
 // x_nb -> D_c^-1 (+-1/2)(A_nb(S) x_nb +- lambda_nb x_nb) (Sec. 2.2, 2.3.1-2.3.2): it depends
 // only on the state frozen for the iteration, not on the increments.  k_sweep_mat forms it for
@@ -2466,9 +2467,10 @@ __global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
 // Record of cell c (elements of the operator's type T: FP64, or FP32 for the mixed-precision
 // operator, formed in FP64 and rounded once): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF
 // rows of NP (NF rounded up to a whole 16-byte load, so that every row starts on 16 bytes),
-// then the species coefficients in the same order.  Per row j after the N cell records: the periodic-i wrap couplings
-// (forward: cell (ni-1, j) with (0, j); backward: (0, j) with (ni-1, j)), flow blocks then
-// species coefficients.
+// then the species coefficients in the same order.  Per row j after the N cell records: the
+// periodic-i wrap couplings (forward: cell (ni-1, j) with (0, j); backward: (0, j) with
+// (ni-1, j)), flow blocks then species coefficients.  k_split_mat (the cluster-barrier form)
+// is FP64 only.
 // ---------------------------------------------------------------------------------------
 constexpr int kMatSlots = 8;       // threads per row of a CTA
 constexpr int kMatSpecies = kMatSlots;
