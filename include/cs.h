@@ -139,9 +139,10 @@ cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double *dQ_out);
 /* Coupled (CI) operator: unified spectral radius, dense diagonal blocks with the source
  * Jacobian, LU-SGS.  dQ_out (host or device, [nci][ncell], nullable).  The first call
  * allocates library-owned work arrays: the LU factors, pivots and inverse of every cell's
- * diagonal block (2 nci^2 doubles + nci ints per cell) and, on 2D grids, the four neighbour
- * coupling blocks of the one-launch sweep (4 nci nP + nP doubles per cell, nP = nci rounded up
- * to even, plus 2 nci nP per row j; without them the sweep applies the products matrix-free).
+ * diagonal block (2 nci^2 doubles + nci ints per cell) and, on 2D grids of at most 256 rows
+ * in j, the four neighbour coupling blocks of the one-launch sweep (4 nci nP + nP doubles per
+ * cell, nP = nci rounded up to even, plus 2 nci nP per row j; without them the sweep applies
+ * the products matrix-free).
  * Errors: CS_ERR_STATE (no residual), CS_ERR_OOM (the factors could not be allocated). */
 cs_status cs_lusgs_coupled(cs_grid g, double cfl, double *dQ_out);
 

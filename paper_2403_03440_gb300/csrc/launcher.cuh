@@ -400,7 +400,8 @@ struct LauncherT : Launcher {
   // the operator's type (FP64, or FP32 for the mixed-precision operator).  Single grids only: a
   // batch keeps the one-warp direct kernel, whose CTAs need fewer registers and no records.
   size_t mat_doubles(const DevGrid& g) const override {
-    if (ND != 2) return 0;
+    // only where a cluster of at most 16 CTAs can hold the rows
+    if (ND != 2 || g.bc[2] == BC_PERIODIC || g.nj > 16 * kClusterRows) return 0;
     const size_t d = (size_t)g.N * MatRec<G, double>::CELL + (size_t)g.nj * MatRec<G, double>::ROW;
     const size_t f = ((size_t)g.N * MatRec<G, float>::CELL + (size_t)g.nj * MatRec<G, float>::ROW + 1) / 2;
     return d > f ? d : f;
@@ -500,7 +501,9 @@ struct LauncherT : Launcher {
   }
 
   size_t ci_mat_doubles(const DevGrid& g) const override {
-    return ND == 2 ? (size_t)g.N * CIRec<G>::CELL + (size_t)g.nj * CIRec<G>::ROW : 0;
+    // only where a cluster of at most 16 CTAs can hold the rows
+    if (ND != 2 || g.bc[2] == BC_PERIODIC || g.nj > 16 * kCIRows) return 0;
+    return (size_t)g.N * CIRec<G>::CELL + (size_t)g.nj * CIRec<G>::ROW;
   }
   // both coupled sweeps over assembled neighbour blocks (k_ci_mat, then k_ci_mat_sweep with
   // kCISlots threads per row); 0 where the blocks are not allocated or no cluster fits
