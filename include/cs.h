@@ -186,8 +186,8 @@ cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
  * CTAs exchange the rows at their boundaries point to point (st.async into the next CTA's
  * shared memory, one mbarrier per hyperplane; (ni + nj - 1) x (8 x element size + 8) bytes of
  * shared memory per CTA, at most 200 KiB; single grids only), 6 the FP64 couplings with one
- * cluster barrier per hyperplane (the FP32 operator falls back to 1); 0 runs one launch per
- * hyperplane.
+ * cluster barrier per hyperplane (the FP32 operator falls back to 4, else 2); 0 runs one launch
+ * per hyperplane.
  * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.
  * "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per component of the 2D cluster
  * sweeps (0, the default: the largest that fits; a C that does not fit the grid or the device

@@ -173,7 +173,7 @@ struct cs_grid_s {
   int stag = -1;
   int have_R = 0, have_bc = 0, iter = 0;
   int last_op = -1;           // 0 split, 1 coupled
-  bool mat_refused = false;   // the coupling records of the 2D FP64 sweep could not be allocated
+  bool mat_refused = false;   // the coupling records of the 2D split sweep could not be allocated
   char err[512] = {0};
   // per-phase CUDA-event timing of cs_step (enabled by cs_profile)
   bool prof = false;
@@ -835,8 +835,8 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     // 0 per hyperplane, 1 direct-load cluster kernel, 2 record cluster kernel, 3 default (by
     // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2),
     // 5 assembled couplings exchanged point to point between CTAs where the ring fits (else
-    // FP64: 6, FP32: 1), 6 the same FP64 couplings with a cluster barrier per hyperplane (the
-    // FP32 operator falls back to 1)
+    // FP64: 6 then 1, FP32: 4 then 2), 6 the same FP64 couplings with a cluster barrier per
+    // hyperplane (the FP32 operator falls back to 4 then 2)
     g->L->use_cluster = value != 0.0;
     g->L->cluster_kind = value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;
