@@ -36,8 +36,9 @@ struct Launcher {
   virtual int sweep_split_cluster(const DevGrid& g, cudaStream_t st, bool mixed = false) = 0;
   bool use_cluster = true;
   int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records,
-                           // 3: one CTA per component (FP32), 4: assembled couplings (FP64),
-                           // point to point where it fits, 5: the same with a cluster barrier
+                           // 3: one CTA per component (FP32), 4: assembled couplings exchanged
+                           // point to point where the ring fits (FP64 or FP32), 5: the FP64
+                           // assembled couplings with a cluster barrier
   int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
   int cluster_warps = 2;   // warps per CTA of the direct-load cluster kernel (batches: 1)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
@@ -50,7 +51,7 @@ struct Launcher {
   // inside a stream capture)
   virtual void prepare(const DevGrid& g, bool mixed) = 0;
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
-  // doubles of DevGrid::SMC, the coupling records of the FP64 2D sweep (0: not used)
+  // doubles of DevGrid::SMC, the coupling records of the 2D split sweep (0: not used)
   virtual size_t mat_doubles(const DevGrid& g) const = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) {
