@@ -119,6 +119,12 @@ cs_status cs_set_boundary(cs_grid g, const cs_freestream *fs, const cs_wall *wal
 /* Q (host or device, [nq][ncell]): set the conserved state.  Resets the iteration counter
  * and the temperature warm starts. */
 cs_status cs_set_state(cs_grid g, const double *Q);
+/* Q (host or device, [nq][ncell]): replace the conserved state and continue the run: unlike
+ * cs_set_state, the iteration counter (and with it the CFL ramp) and the temperature warm
+ * starts are kept.  For a caller that holds the state in its own memory between iterations of
+ * one run.  The copy is enqueued on the grid's stream (a host Q must stay valid until the next
+ * call that synchronises it).  Errors: CS_ERR_ARG (null), CS_ERR_CUDA. */
+cs_status cs_load_state(cs_grid g, const double *Q);
 /* Fill Q with the uniform freestream (after cs_set_boundary). */
 cs_status cs_init_freestream(cs_grid g);
 /* Q_out (host or device, [nq][ncell]). */
@@ -172,6 +178,21 @@ cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
  * nullable) receive the totals accumulated since the last call; the call then resets them
  * and enables (enable = 1) or disables timing. */
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);
+
+/* FP64 fused multiply-add throughput of the current device in GFLOP/s (a measurement aid, not
+ * part of the method): independent DFMA chains on every SM, timed with CUDA events on
+ * cuda_stream (NULL: legacy default stream), best of three launches after a warm-up (~0.1 s in
+ * all).  The FP64-bound kernels of the residual are compared with this rate.  Errors:
+ * CS_ERR_ARG (null), CS_ERR_CUDA. */
+cs_status cs_measure_fp64_rate(void *cuda_stream, double *gflops_out);
+
+/* Which kernel ran the last split sweep of g (a measurement aid, not part of the method):
+ * out[0] in the numbering of the "cluster_sweep" option below (0 one launch per hyperplane,
+ * 1 direct loads, 2 wavefront records, 4 one CTA per component, 5 assembled couplings exchanged
+ * point to point, 6 assembled couplings with a cluster barrier; -1 before the first sweep),
+ * out[1] its CTAs per cluster (0 for one launch per hyperplane).  Host only, no device work.
+ * Errors: CS_ERR_ARG (null). */
+cs_status cs_sweep_info(cs_grid g, int out[2]);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
  * split sweeps in one launch, choosing per precision: 5 where its records can be allocated and
@@ -243,8 +264,9 @@ cs_status cs_dual_advance(cs_grid g);
  * nspecies + ndim) and cell volumes V_dev (device, [ncell]) owned by the caller.  Its scratch is
  * a static device array of CS_NORMS_STATIC_MAX_BLOCKS x 2 doubles (256 KiB) that every GPU
  * loading the library keeps until exit; ncell above CS_NORMS_STATIC_MAX_CELLS is rejected with
- * CS_ERR_ARG.  It allocates nothing: the first call on a device looks up the array's device
- * address (make that first call before any stream capture).  All calls share the array, so
+ * CS_ERR_ARG.  It allocates nothing: every call looks up the array's address in the current
+ * context (cudaGetSymbolAddress); the first call in a context may load the library's device
+ * code, so make that first call before any stream capture.  All calls share the array, so
  * calls that overlap on the GPU race; the call synchronises cuda_stream (NULL: legacy default
  * stream) before returning.  Errors: CS_ERR_ARG (null pointer, size, nspecies, ndim),
  * CS_ERR_CUDA. */

@@ -17,7 +17,7 @@ _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libcs_gb300.so")
 SOURCES = ["launch_air11_2d.cu", "launch_air11_3d.cu", "launch_air5_2d.cu", "launch_air5_3d.cu",
-           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu", "mlp.cu",
+           "launch_perfect_2d.cu", "launch_perfect_3d.cu", "capi.cu", "noalloc.cu", "probe.cu", "mlp.cu",
            "species_box.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC"]
@@ -96,9 +96,9 @@ class cs_step_stats(C.Structure):
 
 
 EXPORTS = ["cs_grid_create", "cs_grid_destroy", "cs_grid_dims", "cs_set_boundary",
-           "cs_set_state", "cs_init_freestream", "cs_get_state", "cs_residual",
+           "cs_set_state", "cs_load_state", "cs_init_freestream", "cs_get_state", "cs_residual",
            "cs_lusgs_split", "cs_lusgs_coupled", "cs_correct", "cs_step", "cs_get_field",
-           "cs_gas_info", "cs_profile", "cs_set_option", "cs_set_dual", "cs_dual_advance",
+           "cs_gas_info", "cs_profile", "cs_sweep_info", "cs_measure_fp64_rate", "cs_set_option", "cs_set_dual", "cs_dual_advance",
            "cs_residual_norms_static",
            "cs_last_error", "cs_batch_create", "cs_batch_destroy", "cs_batch_tune",
            "cs_batch_step", "cs_batch_stream", "cs_batch_last_error", "cs_mlp_create",
@@ -125,6 +125,8 @@ def lib():
     L.cs_grid_dims.argtypes = [vp, ip]
     L.cs_set_boundary.argtypes = [vp, C.POINTER(cs_freestream), C.POINTER(cs_wall)]
     L.cs_set_state.argtypes = [vp, vp]
+    L.cs_load_state.argtypes = [vp, vp]
+    L.cs_measure_fp64_rate.argtypes = [vp, dp]
     L.cs_init_freestream.argtypes = [vp]
     L.cs_get_state.argtypes = [vp, vp]
     L.cs_residual.argtypes = [vp, vp, dp]
@@ -135,6 +137,7 @@ def lib():
     L.cs_get_field.argtypes = [vp, C.c_char_p, vp, ip]
     L.cs_gas_info.argtypes = [C.c_int, dp, dp, ip]
     L.cs_profile.argtypes = [vp, C.c_int, dp, C.POINTER(C.c_long)]
+    L.cs_sweep_info.argtypes = [vp, ip]
     L.cs_set_option.argtypes = [vp, C.c_char_p, C.c_double]
     L.cs_set_dual.argtypes = [vp, C.c_double, C.c_double]
     dp = C.POINTER(C.c_double)
@@ -203,6 +206,15 @@ def gas_info(mech):
     return dict(ns=ns, nr=int(dims[1]), ntemp=int(dims[2]), M=M[:ns].copy(), hf=hf[:ns].copy())
 
 
+def measure_fp64_rate(stream=None):
+    """FP64 FMA throughput of the current device, GFLOP/s (cs_measure_fp64_rate)."""
+    out = C.c_double()
+    st = lib().cs_measure_fp64_rate(C.c_void_p(stream) if stream else None, C.byref(out))
+    if st:
+        raise CSError(st, "cs_measure_fp64_rate")
+    return out.value
+
+
 class Grid:
     """A structured grid with its state on the current CUDA device (one C-ABI grid object)."""
 
@@ -262,6 +274,10 @@ class Grid:
 
     def set_state(self, Q):
         self._check(lib().cs_set_state(self._h, _ptr(Q)), "cs_set_state")
+
+    def load_state(self, Q):
+        """Replace the state, keeping the iteration counter and temperature warm starts."""
+        self._check(lib().cs_load_state(self._h, _ptr(Q)), "cs_load_state")
 
     def init_freestream(self):
         self._check(lib().cs_init_freestream(self._h), "cs_init_freestream")
@@ -340,6 +356,12 @@ class Grid:
         nl = (C.c_long * 8)()
         self._check(lib().cs_profile(self._h, int(enable), ms, nl), "cs_profile")
         return {p: (ms[k], nl[k]) for k, p in enumerate(self.PHASES)}
+
+    def sweep_info(self):
+        """(kernel, CTAs per cluster) of the last split sweep ("cluster_sweep" numbering)."""
+        out = (C.c_int * 2)()
+        self._check(lib().cs_sweep_info(self._h, out), "cs_sweep_info")
+        return out[0], out[1]
 
     def field(self, name, size=None):
         if size is None:

@@ -264,6 +264,13 @@ extern "C" cs_status cs_profile(cs_grid g, int enable, double* ms_out, long* lau
   return CS_OK;
 }
 
+extern "C" cs_status cs_sweep_info(cs_grid g, int out[2]) {
+  if (!g || !out) return CS_ERR_ARG;
+  out[0] = g->L->last_sweep;
+  out[1] = g->L->last_sweep_C;
+  return CS_OK;
+}
+
 extern "C" cs_status cs_gas_info(int mech, double* M, double* hf, int dims[3]) {
   static const double MN = CS_MN, MO = CS_MO, ME = CS_ME;
   static const double Mair[11] = {2 * MN, 2 * MO, MN + MO, MN, MO, MN + MO - ME, 2 * MN - ME,
@@ -510,6 +517,14 @@ extern "C" cs_status cs_set_state(cs_grid g, const double* Q) {
   return CS_OK;
 }
 
+extern "C" cs_status cs_load_state(cs_grid g, const double* Q) {
+  if (!g || !Q) return CS_ERR_ARG;
+  CUDA_TRY(g, cudaMemcpyAsync(g->g.Q, Q, (size_t)g->L->nq * g->g.N * sizeof(double),
+                              cudaMemcpyDefault, g->stream));
+  g->have_R = 0;
+  return CS_OK;
+}
+
 extern "C" cs_status cs_init_freestream(cs_grid g) {
   if (!g) return CS_ERR_ARG;
   if (!g->have_bc) return fail(g, CS_ERR_STATE, "cs_init_freestream before cs_set_boundary");
@@ -563,10 +578,11 @@ extern "C" cs_status cs_residual(cs_grid g, double* R_out, double norms_host[3])
 }
 
 // coupling records of the 2D split sweep over assembled couplings (K6e; FP64 or FP32 records in
-// the same buffer); without them (allocation refused) the sweep falls back to the other cluster
-// kernels
-static void ensure_mat(cs_grid g) {
+// the same buffer), allocated only when a sweep of this precision will read them; without them
+// (allocation refused) the sweep falls back to the other cluster kernels
+static void ensure_mat(cs_grid g, bool mixed) {
   if (g->g.SMC || g->mat_refused) return;
+  if (!g->L->mat_usable(g->g, mixed)) return;   // not sticky: another precision may use them
   const size_t n = g->L->mat_doubles(g->g);
   if (n == 0 || dalloc(g, &g->g.SMC, n) != cudaSuccess) {
     cudaGetLastError();
@@ -590,7 +606,7 @@ extern "C" cs_status cs_lusgs_split(cs_grid g, double cfl, int precision, double
   cs_status st = begin(g);
   if (st) return st;
   if ((st = set_cfl(g, cfl))) return st;
-  ensure_mat(g);
+  ensure_mat(g, precision == CS_MIXED);
   g->L->spectral(g->g, g->stream);
   g->L->sweep_split(g->g, g->stream, precision == CS_MIXED);
   if (dQ_out)
@@ -758,7 +774,7 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
   cs_status st = check_opts(o);
   if (st) return st;
   if (o->scheme == CS_SCHEME_COUPLED && (st = ensure_ci(g))) return fail(g, st, "allocation");
-  if (o->scheme == CS_SCHEME_SPLIT) ensure_mat(g);
+  if (o->scheme == CS_SCHEME_SPLIT) ensure_mat(g, o->precision == CS_MIXED);
   if ((st = begin(g))) return st;
   int done = 0;
   for (int it = 0; it < o->iters; ++it) {

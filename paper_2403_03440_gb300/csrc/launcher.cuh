@@ -42,6 +42,11 @@ struct Launcher {
   int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
   int cluster_warps = 2;   // warps per CTA of the direct-load cluster kernel (batches: 1)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
+  // kernel of the last split sweep, numbered as the "cluster_sweep" option (0 one launch per
+  // hyperplane, 1 direct loads, 2 wavefront records, 4 one CTA per component, 5 assembled
+  // couplings point to point, 6 assembled couplings with a cluster barrier; -1 none yet) and
+  // its CTAs per cluster
+  int last_sweep = -1, last_sweep_C = 0;
   // bit C of the result is set when the cluster sweep of `kind` (1 direct, 2 wavefront
   // records) can run with C CTAs per component on this grid and device
   virtual int cluster_sizes(const DevGrid& g, int kind, bool mixed) = 0;
@@ -53,6 +58,8 @@ struct Launcher {
   virtual int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed = false) = 0;
   // doubles of DevGrid::SMC, the coupling records of the 2D split sweep (0: not used)
   virtual size_t mat_doubles(const DevGrid& g) const = 0;
+  // does a split sweep of this precision use the records on this grid and device?
+  virtual bool mat_usable(const DevGrid& g, bool mixed) = 0;
   virtual void ci_block(const DevGrid& g, cudaStream_t st) = 0;
   void sweep_coupled(const DevGrid& g, cudaStream_t st) {
     if (use_cluster && sweep_coupled_cluster(g, st)) return;
@@ -182,16 +189,20 @@ struct LauncherT : Launcher {
   }
 
   // Can `kern` run as clusters of C CTAs (32 x warps threads each), one cluster per component
-  // (the flow block and `groups` species groups)?
+  // (the flow block and `groups` species groups), with dyn_smem bytes of dynamic shared memory?
+  // The opt-in limit is a property of the kernel, shared by every grid of the process, so it is
+  // set to attr_smem, the largest size any grid launches the kernel with (a probe of a smaller
+  // grid must not lower the limit a larger grid's launches rely on).
   template <class K>
-  bool cluster_fits(K kern, int C, int warps, int groups, size_t dyn_smem = 0) {
+  bool cluster_fits(K kern, int C, int warps, int groups, size_t dyn_smem = 0, size_t attr_smem = 0) {
     if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
+    if (attr_smem < dyn_smem) attr_smem = dyn_smem;
     // static plus dynamic shared memory above 48 KiB needs the opt-in
-    if (dyn_smem > 0 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem) != cudaSuccess) {
+    if (attr_smem > 0 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)attr_smem) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -338,6 +349,8 @@ struct LauncherT : Launcher {
     k_split_block<G><<<1 + species_clusters<G>(), threads, block_smem_bytes<G>(), st>>>(g);
     if (cudaGetLastError() != cudaSuccess) return 0;
     sweep_split_cluster_ok = true;
+    last_sweep = 4;
+    last_sweep_C = 1;
     return 2;
   }
 
@@ -364,6 +377,8 @@ struct LauncherT : Launcher {
       return 0;
     }
     sweep_split_cluster_ok = true;
+    last_sweep = 2;
+    last_sweep_C = C;
     return 2;
   }
   template <class T>
@@ -392,6 +407,8 @@ struct LauncherT : Launcher {
       return 0;
     }
     sweep_split_cluster_ok = true;
+    last_sweep = 1;
+    last_sweep_C = C;
     return 1;
   }
 
@@ -408,6 +425,15 @@ struct LauncherT : Launcher {
     return d > f ? d : f;
   }
   static constexpr size_t kP2PMaxSmem = 200 * 1024;
+  // will a split sweep of this precision read the coupling records?  (The records are
+  // allocated only then: for the FP32 operator they serve only k_split_p2p, whose ring may not
+  // fit the grid.)
+  bool mat_usable(const DevGrid& g, bool mixed) override {
+    const int kind = cluster_kind ? cluster_kind : 4;
+    if (ND != 2 || !use_cluster || cluster_warps == 1 || (kind != 4 && kind != 5)) return false;
+    if (mixed) return kind == 4 && mat_cluster_size<float>(g, true) > 0;
+    return (kind == 4 && mat_cluster_size<double>(g, true) > 0) || mat_cluster_size<double>(g, false) > 0;
+  }
   template <class T>
   bool mat_fits(const DevGrid& g, int C, bool p2p) {
     const int R = (g.nj + C - 1) / C;
@@ -415,7 +441,7 @@ struct LauncherT : Launcher {
     const int warps = (kMatSlots * R + 31) / 32;
     if (!p2p) return std::is_same<T, double>::value && cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
     const size_t smem = p2p_smem_bytes<T>(g.ni, g.nj);
-    return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G, T>, C, warps, mat_species_groups<G>(), smem);
+    return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G, T>, C, warps, mat_species_groups<G>(), smem, kP2PMaxSmem);
   }
   template <class T>
   int mat_cluster_size(const DevGrid& g, bool p2p) {
@@ -472,6 +498,8 @@ struct LauncherT : Launcher {
         return 0;
       }
       sweep_split_cluster_ok = true;
+      last_sweep = p2p ? 5 : 6;
+      last_sweep_C = C;
       return 2;
     }
   }
@@ -479,6 +507,8 @@ struct LauncherT : Launcher {
   int sweep_split_dir(const DevGrid& g, cudaStream_t st, bool fwd, bool mixed) override {
     const int H = g.ni + g.nj + (ND == 3 ? g.nk : 1) - 2;
     int launches = 0;
+    last_sweep = 0;
+    last_sweep_C = 0;
     for (int t = 0; t <= H; ++t) {
       const int h = fwd ? t : H - t;
       int off, cnt;

@@ -15,8 +15,6 @@
 // on the array and must be serialised by the caller.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "../../include/cs.h"
 
 namespace {
@@ -81,24 +79,16 @@ __global__ void __launch_bounds__(kThreads) k_norm_final(double* scratch, int nb
   }
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_ptr[kMaxDevices] = {nullptr};
-
-cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+// Device address of the scratch array in the current context.  The address belongs to the
+// context, not to the device ordinal (it changes after cudaDeviceReset or under another context
+// on the same device), so it is looked up on every call: cudaGetSymbolAddress allocates
+// nothing.  The first lookup in a context may load the module, which is why the first call
+// should come before any stream capture.
+cudaError_t scratch_for_current_context(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_norm_scratch);
-    if (e != cudaSuccess) return e;
-    g_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -111,7 +101,7 @@ extern "C" cs_status cs_residual_norms_static(const double* R_dev, const double*
   if (ncell < 1 || ncell > CS_NORMS_STATIC_MAX_CELLS) return CS_ERR_ARG;
   if (nspecies < 1 || (ndim != 2 && ndim != 3)) return CS_ERR_ARG;
   double* scratch = nullptr;
-  if (scratch_for_current_device(&scratch) != cudaSuccess) return CS_ERR_CUDA;
+  if (scratch_for_current_context(&scratch) != cudaSuccess) return CS_ERR_CUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int nb = (ncell + kThreads - 1) / kThreads;
   k_norm_partials<<<nb, kThreads, 0, st>>>(R_dev, V_dev, ncell, nspecies, nspecies + ndim, scratch);
