@@ -42,7 +42,7 @@ WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # peak, so the roofline of this path is the FP64 ALU, not HBM; the sweeps are latency-bound
 # (one dependent hyperplane step after another).
 FP64_FLOPS_PER_CELL = {
-    "primitive": 13818.0,
+    "primitive": 12302.0,      # mean of the 20 timed launches (profiles/k_primitive_fp64_counts_...)
     "gradient": 400.0,
     "flux": 2844.0,            # both directions
     "assemble": 130.0,
@@ -51,6 +51,10 @@ FP64_FLOPS_PER_CELL = {
     "sweep_bwd": 0.0,
     "correct": 109.0,
 }
+FLOPS_SOURCE = ("ncu FP64 thread instructions (2 DFMA + DMUL + DADD) per cell, mean over the 20 "
+                "launches of the timed iterations 6..25 (profiles/k_primitive_fp64_counts_timed_window_"
+                "384x256_air11.md); other phases: one launch of the 5th iteration "
+                "(profiles/kernels_half_cylinder_384x256_air11.md)")
 # the mixed operator's sweep phase: couplings formed in FP64 (k_sweep_mat, 753 FP64 flop) and
 # swept in FP32 (k_split_p2p, the FP64 form's 374 flop as FP32)
 FP64_FLOPS_PER_CELL_SWEEP_MIXED = 753.0
@@ -66,10 +70,17 @@ DRAM_BYTES_SWEEP_FP32 = None              # FP32 records: not captured with ncu
 # kernel k_ci_cluster, which re-reads nothing; the default kernels (k_ci_mat + k_ci_mat_sweep)
 # also write and read the assembled neighbour blocks and were not captured
 CI_SWEEP_ALGO_BYTES = 367.3e6
-# GB300 FP64 peak: the nominal 1.25 TFLOP/s of the platform (a DFMA throughput microbenchmark
-# measured 1.20 TFLOP/s on this machine).  FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz.
-FP64_PEAK_GFLOPS = 1250.0
+# FP64 peak: measured on the device at the start of every run (cs_measure_fp64_rate: DFMA
+# chains on every SM); the nominal 1.25 TFLOP/s of the platform only if that fails.  FP32: 152
+# SMs x 128 lanes x 2 flop x 2.07 GHz.
+FP64_NOMINAL_GFLOPS = 1250.0
 FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
+# Algorithmic HBM bytes per cell and iteration of the four-pass split design (every array
+# crosses HBM once per pass: words = 7 s + 3 g + 3 a + 4 n with s stored conserved values, g
+# geometry values, a auxiliary values and n split unknowns per cell).  2D, 11 species, 2T:
+# s 15, g 5, a 23, n 16 -> 253 words; 3D: s 16, g 10, a 26, n 17 -> 288 words.
+ALGO_BYTES_PER_CELL = {"c2": 8 * (7 * 15 + 3 * 5 + 3 * 23 + 4 * 16),
+                       "c3": 8 * (7 * 16 + 3 * 10 + 3 * 26 + 4 * 17)}
 
 
 def job_time_ms(local_ms, dist=None, device="cpu"):
@@ -182,6 +193,9 @@ SCHEME = (0, 1)   # (scheme, correction): CS-1 split by default; --scheme cs2 / 
 def step_kwargs(iters):
     return dict(scheme=SCHEME[0], correction=SCHEME[1], clip=1, cfl=CFL, cfl_start=CFL_START,
                 ramp_iters=RAMP, iters=iters, precision=PRECISION)
+
+
+ORACLE_BUILD = "gcc -O3 -ffp-contract=off, one thread"
 
 
 def oracle_rate(iters, seconds_cap=30.0):
@@ -467,6 +481,9 @@ def main():
     ap.add_argument("--scheme", default="cs1", choices=["cs1", "cs2", "ci", "ci_eig"])
     ap.add_argument("--batch-cases", type=int, default=64)
     ap.add_argument("--iters-per-graph", type=int, default=1)
+    ap.add_argument("--no-convergence", action="store_true",
+                    help="skip the C1 time-to-1e-8 runs of the default line")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch throughput of the default line")
     args = ap.parse_args()
     global PRECISION, WORKLOAD, C3, SCHEME
     SCHEME = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}[args.scheme]
@@ -499,6 +516,138 @@ def main():
         run_mlp(args, rank, world, local)
         return
 
+    run_iteration(args, rank, world, local)
+
+
+def make_grid(P):
+    nodes, fs = make_case(P)
+    g = P.Grid(nodes, case_bc(), MECH)
+    g.set_boundary(fs, Tw=T_WALL)
+    return g, fs
+
+
+def prepare_grid(P, args):
+    """A grid of the workload run from the freestream through the warm-up iterations."""
+    g, _ = make_grid(P)
+    if args.scheme == "ci_eig":
+        g.set_option("ci_splitting", 1)
+    g.init_freestream()
+    if args.dual_dt > 0:
+        # dual time stepping: one physical step begun from the freestream, theta = 1/2 (the
+        # pseudo-time iterations below are its inner iterations)
+        g.set_dual(args.dual_dt, 0.5)
+        g.dual_advance()
+    for _ in range(args.warmup):
+        g.step(**step_kwargs(1))
+    return g
+
+
+def c1_time_to_drop(tol=1e-8, with_network=True):
+    """Time to a `tol` drop of both residual monitors on C1 (half cylinder 48 x 32, 5-species
+    1T air, Mach 10, minmod, CFL 10 ramped from 1 over 100 iterations, from the freestream):
+    CS-1 with the FP64 operator, CS-1 with the FP32 operator, CS-1 with the FP32 operator and
+    the network's chemistry diagonal (trained first on states of the same case), and the
+    coupled (CI) operator in FP64.  Every run checks the monitors after its first iteration
+    and then every 100 iterations."""
+    import paper_2403_03440_gb300.surrogate as S
+    c = S.CASES["c1"]
+    keys = ("status", "iterations", "seconds", "device_seconds", "q_stag", "drop", "fallback_chunks")
+    out = {"case": "half-cylinder-48x32-air5-1T-mach10-minmod-cfl10", "cells": c["ni"] * c["nj"],
+           "tol": tol, "runs": {}}
+    legs = [("cs1_fp64", dict(precision=0, scheme=0)), ("cs1_fp32_operator", dict(precision=1, scheme=0)),
+            ("ci_fp64", dict(precision=0, scheme=1))]
+    for name, kw in legs:
+        try:
+            r = S.run_to(c, tol, 20000, 100, **kw)
+            out["runs"][name] = {k: r[k] for k in keys}
+        except Exception as e:          # report, do not lose the bench line
+            out["runs"][name] = {"status": f"error: {e}"}
+    if with_network:
+        try:
+            t0 = time.perf_counter()
+            X, T = S.collect(c, 3000, 10, 0)
+            norm = S.standardisation(X, T)
+            net, record, val = S.train(X, T, norm, epochs=20, max_batch=c["ni"] * c["nj"])
+            norm_used, _ = S.calibrate(net, norm, val)
+            train_s = time.perf_counter() - t0
+            r = S.run_to(c, tol, 20000, 100, net=net, norm=norm_used, precision=1)
+            out["runs"]["cs1_fp32_operator_network"] = {k: r[k] for k in keys}
+            out["network"] = {"samples": int(X.shape[0]), "epochs": 20, "collect_and_train_seconds": train_s,
+                              "final_loss": record[-1]}
+        except Exception as e:
+            out["runs"]["cs1_fp32_operator_network"] = {"status": f"error: {e}"}
+    base = out["runs"].get("cs1_fp64", {})
+    for r in out["runs"].values():
+        if "q_stag" in r and "q_stag" in base and base["q_stag"]:
+            r["q_rel_diff_vs_cs1_fp64"] = abs(r["q_stag"] - base["q_stag"]) / abs(base["q_stag"])
+            r["time_ratio_vs_cs1_fp64"] = r["seconds"] / base["seconds"]
+    return out
+
+
+def batch_throughput(P, precision=0, steps=6, warmup=3, ncases=64):
+    """Mcell-iter/s of the 64-case batch (64 x 48 to 512 x 384 half cylinders, Mach 6-20, CFL
+    5-200, 5 or 11 species; CS-1, tuned, one graph launch per iteration), device time."""
+    import torch
+    cases = inputs.batch_cases(ncases, seed=0)
+    grids = []
+    for c in cases:
+        nodes = inputs.cylinder_half(c["ni"], c["nj"], dr1=5e-5 * 48 / c["ni"])
+        fs = inputs.freestream(c["mech"], T=T_INF, p=P_INF, mach=c["mach"])
+        g = P.Grid(nodes, inputs.cylinder_half_bc(), c["mech"])
+        g.set_boundary(fs, Tw=T_WALL)
+        g.init_freestream()
+        grids.append(g)
+    cells = sum(g.ncell for g in grids)
+    batch = P.Batch(grids)
+    t0 = time.perf_counter()
+    batch.tune(precision=precision, trials=2)
+    tune_s = time.perf_counter() - t0
+    opts = [dict(scheme=0, correction=1, clip=1, cfl=c["cfl"], cfl_start=0.5, ramp_iters=500,
+                 precision=precision) for c in cases]
+    batch.step(opts, iters=warmup, iters_per_graph=1)
+    stream = torch.cuda.ExternalStream(batch.stream())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = batch.step(opts, iters=steps, iters_per_graph=1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    out = {"workload": f"batch-{len(cases)}-half-cylinders-64x48-to-512x384-mach6-20-air5-or-air11-CS1",
+           "cases": len(cases), "cells": cells, "iterations": steps, "ms_per_iteration": ms / steps,
+           "value": cells * steps / (ms / 1e3) / 1e6, "unit": "Mcell-iter/s", "tune_seconds": tune_s,
+           "cases_failed": sum(1 for st in stats if st["status_cell"] != -1),
+           "launch": "one CUDA graph per iteration of all cases (each case's sweeps one cluster launch)"}
+    del batch
+    return out
+
+
+def host_cpu():
+    """(model name, logical cores) of the host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+            for line in r.stdout.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return model or "unknown", os.cpu_count()
+
+
+def run_iteration(args, rank, world, local):
+    """The default workload: pseudo-time iterations of one grid (C2 unless --workload c3)."""
     import torch
     import paper_2403_03440_gb300 as P
     P.build()
@@ -508,20 +657,17 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    nodes, fs = make_case(P)
-    g = P.Grid(nodes, case_bc(), MECH)
-    g.set_boundary(fs, Tw=T_WALL)
-    if args.scheme == "ci_eig":
-        g.set_option("ci_splitting", 1)
-    g.init_freestream()
-    if args.dual_dt > 0:
-        # dual time stepping: one physical step begun from the freestream, theta = 1/2 (the
-        # pseudo-time iterations below are its inner iterations)
-        g.set_dual(args.dual_dt, 0.5)
-        g.dual_advance()
+    try:
+        fp64_peak, fp64_kind = P.measure_fp64_rate(), "measured DFMA throughput (cs_measure_fp64_rate)"
+    except P.CSError:
+        fp64_peak, fp64_kind = FP64_NOMINAL_GFLOPS, "nominal FP64 (1.25 TFLOP/s; the measurement failed)"
+
+    # Two grids run the same warm-up from the freestream: A times iterations W+1 .. W+K on the
+    # device, B the same iterations end to end with host buffers.  The runs are deterministic,
+    # so both legs time the same iterations from the same state (checked at the end).
+    g = prepare_grid(P, args)
+    ge = prepare_grid(P, args)
     N = g.ncell
-    for _ in range(args.warmup):
-        g.step(**step_kwargs(1))
     # L2 flush buffer (larger than the 126 MiB L2)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -544,18 +690,22 @@ def main():
     total_ms = job_time_ms(sum(step_ms), dist, "cuda")
     value = job_value(world, N, args.steps, total_ms)
 
-    # ---- end to end through the C ABI with host buffers ----
-    Qh = torch.empty((g.nq, N), dtype=torch.float64, pin_memory=True).numpy()
-    g.get_state(Qh)
+    # ---- end to end through the C ABI with host buffers: every iteration uploads the state
+    # from pinned host memory (cs_load_state: the run continues, warm starts and CFL ramp
+    # kept), iterates and downloads the new state ----
+    Qh = torch.empty((ge.nq, N), dtype=torch.float64, pin_memory=True).numpy()
+    ge.get_state(Qh)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        g.set_state(Qh)
-        s = g.step(**step_kwargs(1))
-        g.get_state(Qh)
+    for _ in range(args.steps):
+        ge.load_state(Qh)
+        ge.step(**step_kwargs(1))
+        ge.get_state(Qh)
     e2e_s = time.perf_counter() - t0
-    e2e = world * N * args.e2e_steps / e2e_s / 1e6
+    e2e = world * N * args.steps / e2e_s / 1e6
     nbytes = Qh.nbytes
+    Qa = g.get_state()
+    same = float(np.max(np.abs(Qa - Qh).max(axis=1) / np.maximum(np.abs(Qa).max(axis=1), 1e-300)))
 
     # ---- roofline of the dominant phase (live CUDA-event timing inside the timed region) ----
     dom = max(prof, key=lambda p: prof[p][0])
@@ -563,23 +713,32 @@ def main():
     launches = sum(v[1] for v in prof.values())
     fp32_sweep = PRECISION == 1 and dom.startswith("sweep")
     flops = (FP32_FLOPS_PER_CELL_SWEEP if fp32_sweep else FP64_FLOPS_PER_CELL[dom]) * N
-    peak = FP32_PEAK_GFLOPS if fp32_sweep else FP64_PEAK_GFLOPS
+    peak = FP32_PEAK_GFLOPS if fp32_sweep else fp64_peak
     achieved = flops / (dom_ms / 1e3) / 1e9
+    hbm, hbm_kind = measured_hbm_peak()
+    wl = "c3" if C3 else "c2"
+    algo_gbs = ALGO_BYTES_PER_CELL[wl] * N / (total_ms / args.steps / 1e3) / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
             "frac": achieved / peak,
             "traffic": DRAM_BYTES_SWEEP_FP32 if fp32_sweep else DRAM_BYTES_PER_LAUNCH.get(dom),
             "kernel_phase": dom,
             "peak_kind": ("FP32 from unit counts and clock (152 x 128 x 2 x 2.07 GHz)" if fp32_sweep
-                          else "nominal FP64 of the recipe (1.25 TFLOP/s)"),
+                          else fp64_kind),
+            "flops_per_cell": flops / N,
+            "flops_source": FLOPS_SOURCE,
             "note": ("the sweeps are bound by the latency of one dependent hyperplane step after "
-                     "another (2 x 638 per iteration), not by throughput" if dom.startswith("sweep")
-                     else "FP64-ALU bound (ncu: FP64 pipe 74-86 % busy, DRAM < 15 % of peak)"),
+                     "another, not by throughput" if dom.startswith("sweep")
+                     else "FP64-ALU bound (ncu: FP64 pipe busy, DRAM far below its peak)"),
+            "hbm": {"bytes_per_cell": ALGO_BYTES_PER_CELL[wl], "achieved": algo_gbs, "peak": hbm,
+                    "unit": "GB/s", "frac": algo_gbs / hbm, "peak_kind": hbm_kind,
+                    "scope": "whole iteration: algorithmic bytes of the four-pass design over the "
+                             "device time per iteration"},
             "phases_ms_per_step": {p: prof[p][0] / args.steps for p in prof},
             "phases_fp64_frac": {p: (FP64_FLOPS_PER_CELL[p] * N / (prof[p][0] / args.steps / 1e3) / 1e9
-                                     / FP64_PEAK_GFLOPS) if prof[p][0] > 0 else None for p in prof}}
+                                     / fp64_peak) if prof[p][0] > 0 else None for p in prof}}
     if PRECISION == 1 and prof["sweep_fwd"][0] > 0:
         roof["phases_fp64_frac"]["sweep_fwd"] = (FP64_FLOPS_PER_CELL_SWEEP_MIXED * N / (prof["sweep_fwd"][0] / args.steps / 1e3)
-                                                 / 1e9 / FP64_PEAK_GFLOPS)
+                                                 / 1e9 / fp64_peak)
     if SCHEME[0] == 1:
         # coupled operator: the sweep and block phases run other kernels (k_ci_mat,
         # k_ci_mat_sweep, k_ci_block), whose FP64 counts were not taken; the sweep is reported
@@ -587,16 +746,26 @@ def main():
         for p in ("spectral", "sweep_fwd", "sweep_bwd"):
             roof["phases_fp64_frac"][p] = None
         if dom == "sweep_fwd":
-            hbm, kind = measured_hbm_peak()
             gbs = CI_SWEEP_ALGO_BYTES / (dom_ms / 1e3) / 1e9
             roof.update({"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                         "traffic": None, "peak_kind": kind})
+                         "traffic": None, "peak_kind": hbm_kind})
+
+    extras = {}
+    if rank == 0 and not C3 and args.scheme == "cs1" and args.dual_dt == 0 and not args.no_convergence:
+        extras["time_to_1e8_c1"] = c1_time_to_drop()
+    if rank == 0 and not C3 and args.scheme == "cs1" and args.dual_dt == 0 and not args.no_batch:
+        try:
+            extras["batch"] = batch_throughput(P, precision=PRECISION)
+        except Exception as e:
+            extras["batch"] = {"status": f"error: {e}"}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         v, it, dt = oracle_rate(3, 30.0)
+        model, ncpu = host_cpu()
         cpu = {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
-               "sample": f"{it} oracle iterations of the full 384x256 grid from the freestream ({dt:.1f} s)"}
+               "sample": f"{it} oracle iterations of the full 384x256 grid from the freestream ({dt:.1f} s)",
+               "host_cpu": model, "host_logical_cores": ncpu, "build": ORACLE_BUILD}
     if rank == 0:
         line = {
             "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,
@@ -607,17 +776,21 @@ def main():
             "config": {"workload": WORKLOAD, "cells": N, "species": 11, "temperatures": 2,
                        "scheme": {"cs1": "CS-1 split LU-SGS", "cs2": "CS-2 split LU-SGS",
                                   "ci": "coupled (CI) LU-SGS",
-                                  "ci_eig": "coupled (CI) LU-SGS, eigenvalue splitting"}[args.scheme], "cfl": CFL,
+                                  "ci_eig": "coupled (CI) LU-SGS, eigenvalue splitting"}[args.scheme],
+                       "cfl": f"{CFL_START} ramped geometrically to {CFL} over {RAMP} iterations",
+                       "timed_iterations": f"{args.warmup + 1}..{args.warmup + args.steps} from the freestream",
                        "l2": "flushed before every timed iteration (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
             "clocks": clk.summary(),
             "e2e": {"value": e2e, "unit": "Mcell-iter/s", "h2d_bytes_per_step": nbytes,
-                    "d2h_bytes_per_step": nbytes + 24},
+                    "d2h_bytes_per_step": nbytes, "same_iterations_as_value": same <= 1e-12,
+                    "state_rel_diff_vs_value_leg": same},
             "gpu_launches": int(launches),
             "roofline": roof,
             "cpu_baseline": cpu,
             "last_stats": {k: (float(v) if isinstance(v, float) else v) for k, v in st.items()},
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -672,6 +672,7 @@ typedef struct {
     int nd, n[3], bc[6], limiter;
     double efix;
     int hcorr;                       /* H-correction of the entropy fix on/off */
+    int viscous;                     /* viscous and diffusive fluxes (and radii) on/off */
     double update_limit;             /* largest relative density change per update (0: off) */
     int ncell, nf[3];                /* faces per direction */
     int nq, nF, nsplit, nci;
@@ -1347,7 +1348,8 @@ static int residual(orc_grid *G)
                         int a = cidx(G, oa[0], oa[1], nd == 3 ? oa[2] : 0);
                         int b = cidx(G, o[0], o[1], nd == 3 ? o[2] : 0);
                         inviscid_interior(G, a, b, d, S, etaH, Fi);
-                        viscous_interior(G, a, b, S, Fv);
+                        if (G->viscous) viscous_interior(G, a, b, S, Fv);
+                        else for (int v = 0; v < nq; v++) Fv[v] = 0.0;
                     } else if (per) {
                         int oa[3] = {o[0], o[1], o[2]}, ob[3] = {o[0], o[1], o[2]};
                         oa[d] = n - 1;
@@ -1355,13 +1357,15 @@ static int residual(orc_grid *G)
                         int a = cidx(G, oa[0], oa[1], nd == 3 ? oa[2] : 0);
                         int b = cidx(G, ob[0], ob[1], nd == 3 ? ob[2] : 0);
                         inviscid_interior(G, a, b, d, S, etaH, Fi);
-                        viscous_interior(G, a, b, S, Fv);
+                        if (G->viscous) viscous_interior(G, a, b, S, Fv);
+                        else for (int v = 0; v < nq; v++) Fv[v] = 0.0;
                     } else {
                         int oc[3] = {o[0], o[1], o[2]}, s;
                         if (lo < 0) { oc[d] = 0; s = -1; } else { oc[d] = n - 1; s = +1; }
                         int c = cidx(G, oc[0], oc[1], nd == 3 ? oc[2] : 0);
                         inviscid_boundary(G, c, d, s, S, etaH, Fi);
-                        viscous_boundary(G, c, d, s, f, S, Fv);
+                        if (G->viscous) viscous_boundary(G, c, d, s, f, S, Fv);
+                        else for (int v = 0; v < nq; v++) Fv[v] = 0.0;
                     }
                     for (int v = 0; v < nq; v++) F[v] = Fi[v] + Fv[v];
                 }
@@ -1426,6 +1430,7 @@ static void spectral(orc_grid *G, double cfl)
             nuF = fmax(4.0 * w->mu / 3.0, w->kt / w->cv);
         }
         nuF /= w->rho;
+        if (!G->viscous) nuF = nuC = 0.0;
         nuCI = fmax(nuF, nuC);
         double sumdt = 0.0, sF = 0.0, sC = 0.0, sCI = 0.0, sCIv = 0.0;
         double Sbar[3][3] = {{0}};
@@ -1949,7 +1954,7 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
     if (gas_init(&G->gas, mech)) { free(G); return 1; }
     G->nd = nd; G->n[0] = ni; G->n[1] = nj; G->n[2] = (nd == 3) ? nk : 1;
     for (int k = 0; k < 6; k++) G->bc[k] = bc[k];
-    G->limiter = lim; G->efix = efix; G->hcorr = 1;
+    G->limiter = lim; G->efix = efix; G->hcorr = 1; G->viscous = 1;
     G->ncell = ni * nj * G->n[2];
     int ns = G->gas.ns;
     G->nq = ns + nd + 1 + (G->gas.ntemp == 2);
@@ -1995,6 +2000,10 @@ int orc_create(int nd, int ni, int nj, int nk, const int *bc, int mech, int lim,
 int orc_set_reacting(orc_grid *G, int reacting) { G->react = reacting != 0; return 0; }
 /* H-correction of the entropy fix on (1, the default) or off (0) */
 int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
+
+/* Inviscid flow (a test switch): off drops the viscous and diffusive fluxes from the residual
+ * and the viscous radii from the operator (mu = k = rho D = 0 in both). */
+int orc_set_viscous(orc_grid *G, int on) { G->viscous = on != 0; return 0; }
 /* update limit f (see correct_update); 0 switches it off */
 int orc_set_update_limit(orc_grid *G, double f) { if (!(f >= 0.0)) return 1; G->update_limit = f; return 0; }
 

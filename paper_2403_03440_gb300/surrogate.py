@@ -27,6 +27,10 @@ import inputs  # noqa: E402
 import paper_2403_03440_gb300 as P  # noqa: E402
 
 CASES = {
+    # 5-species 1T air, Mach 10, over the windward half of the cylinder (48 x 32), minmod,
+    # CFL 10 reached by a geometric ramp from 1 over 100 iterations
+    "c1": dict(ni=48, nj=32, mech=inputs.MECH_AIR5, mach=10.0, dr1=5e-5, limiter=1,
+               cfl=10.0, cfl_start=1.0, ramp=100),
     # 11-species 2T air, Mach 15, over the windward half of the cylinder
     "c1m": dict(ni=48, nj=32, mech=inputs.MECH_AIR11, mach=15.0, dr1=5e-5, limiter=0,
                 cfl=2.0, cfl_start=0.5, ramp=100),
@@ -44,9 +48,9 @@ def make_grid(c):
     return g
 
 
-def step_opts(c, precision=0):
-    return dict(scheme=0, correction=1, clip=1, cfl=c["cfl"], cfl_start=c["cfl_start"],
-                ramp_iters=c["ramp"], precision=precision)
+def step_opts(c, precision=0, scheme=0, correction=1):
+    return dict(scheme=scheme, correction=correction, clip=1, cfl=c["cfl"],
+                cfl_start=c["cfl_start"], ramp_iters=c["ramp"], precision=precision)
 
 
 def collect(c, iters, every, precision=0, dense=None, frac=1.0, seed=0):
@@ -145,8 +149,12 @@ def calibrate(net, norm, val, q=0.95):
     return out, shift
 
 
-def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=True):
-    """Run the case from the freestream until both residual monitors drop by `tol`.  With a
+def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=True, scheme=0,
+           correction=1):
+    """Run the case from the freestream until both residual monitors drop by `tol` (checked
+    after the first iteration and then every `chunk` iterations).  `seconds` is the time
+    between two device synchronisations around the whole run (CUDA events on the grid's
+    stream bracket the same interval: `device_seconds`).  With a
     network attached and `fallback`, a chunk of iterations that ends in a non-physical state
     is redone from its starting state with the exact chemistry diagonal (the exact chemistry
     stays in the residual, so the network can always be dropped), then the network resumes;
@@ -155,7 +163,7 @@ def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=
     g = make_grid(c)
     if net is not None:
         g.attach_surrogate(net, norm)
-    kw = step_opts(c, precision)
+    kw = step_opts(c, precision, scheme, correction)
     fallbacks = 0
 
     def advance(k):
@@ -175,8 +183,10 @@ def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=
             g.attach_surrogate(net, norm)
 
     g.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e0.record()
     status, done = "max_iters", 0
     try:
         first = advance(1)
@@ -192,10 +202,12 @@ def run_to(c, tol, max_iters, chunk, net=None, norm=None, precision=0, fallback=
         status = f"error: {e}"
         st = dict(q_stag=float("nan"), r_species=float("nan"), r_energy=float("nan"))
         r0 = (1.0, 1.0)
+    e1.record()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     prof = g.profile(False)
-    return dict(status=status, iterations=done, seconds=dt, q_stag=st["q_stag"],
+    return dict(status=status, iterations=done, seconds=dt, device_seconds=e0.elapsed_time(e1) / 1e3,
+                q_stag=st["q_stag"],
                 drop=max(st["r_species"] / r0[0], st["r_energy"] / r0[1]),
                 fallback_chunks=fallbacks,
                 primitive_ms_per_iter=prof["primitive"][0] / max(done, 1),
