@@ -782,7 +782,7 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
     int nf, nb;
     if ((st = enqueue_iteration(g, o, slot, false, &nf, &nb))) return st;
     if (g->prof) {
-      const long per[CS_NPHASE] = {1, 1, (long)g->g.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
+      const long per[CS_NPHASE] = {2, 1, (long)g->g.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
       for (int p = 0; p < CS_NPHASE; ++p) g->prof_launches[p] += per[p];
       g->ev_used = slot + 1;
     }

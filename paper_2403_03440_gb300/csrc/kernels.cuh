@@ -26,7 +26,7 @@ struct Aux {
                        CVVE = CVTR + 1, CV = CVVE + 1, MU = CV + 1, KT = MU + 1, KV = KT + 1,
                        RHOD = KV + 1, PREV = RHOD + 1, RELAX = PREV + 1, OMV = RELAX + 1,
                        PY = OMV + 1, Y = PY + 1, PRS = Y + NS, HS = PRS + NS, EVE = HS + NS,
-                       OM = EVE + NS, DOM = OM + NS, COUNT = DOM + NS;
+                       OM = EVE + NS, DOM = OM + NS, EMP = DOM + NS, COUNT = EMP + NS;
   static constexpr int NQ = NS + ND + 1 + (G::NTEMP == 2);
   static constexpr int NF = 1 + ND + 1 + (G::NTEMP == 2);
   static constexpr int NCI = NF + NS - 1;
@@ -137,10 +137,11 @@ template <class G>
 __device__ __forceinline__ void mix_e1(const double* Y, double T, double& e, double& cv) {
   e = 0.0;
   cv = 0.0;
+  const double iT = 1.0 / T;
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
-    double ev, cvv;
-    vib<G>(s, T, ev, cvv);
+    double ev, cvv, em;
+    vib_it<G>(s, iT, ev, cvv, em);
     e += Y[s] * (cvtr<G>(s) * T + ev + hf<G>(s));
     cv += Y[s] * (cvtr<G>(s) + cvv);
   }
@@ -150,16 +151,48 @@ template <class G>
 __device__ __forceinline__ void mix_pool(const double* Y, double Tv, double& e, double& cv) {
   e = 0.0;
   cv = 0.0;
+  const double iTv = 1.0 / Tv;
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
     if (G::sp(s).kind == ELECTRON) {
       e += Y[s] * 1.5 * Rs<G>(s) * Tv;
       cv += Y[s] * 1.5 * Rs<G>(s);
     } else {
-      double ev, cvv;
-      vib<G>(s, Tv, ev, cvv);
+      double ev, cvv, em;
+      vib_it<G>(s, iTv, ev, cvv, em);
       e += Y[s] * ev;
       cv += Y[s] * cvv;
+    }
+  }
+}
+
+// Mixture energy (1T: e(T), POOL: the vibrational-electronic pool e_v(Tv)) and its heat
+// capacity in FP32: the predictor of the temperature solves.
+template <class G, bool POOL>
+__device__ __forceinline__ void mix_f32(const float* Y, float T, float& e, float& cv) {
+  e = 0.0f;
+  cv = 0.0f;
+  const float iT = 1.0f / T;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    const SpeciesData& d = G::sp(s);
+    const float R = c_gas.Rsf[s];
+    float ev = 0.0f, cvv = 0.0f;
+    if (d.kind == ELECTRON && POOL) {
+      ev = 1.5f * R * T;
+      cvv = 1.5f * R;
+    } else if (d.kind == DIATOMIC && d.thv > 0.0) {
+      const float x = c_gas.thvf[s] * iT, em = __expf(-x), r = 1.0f / (1.0f - em);
+      ev = R * c_gas.thvf[s] * em * r;
+      cvv = R * x * x * em * r * r;
+    }
+    if (POOL) {
+      e += Y[s] * ev;
+      cv += Y[s] * cvv;
+    } else {
+      const float ct = d.kind == DIATOMIC ? 2.5f * R : 1.5f * R;
+      e += Y[s] * (ct * T + ev + c_gas.hff[s]);
+      cv += Y[s] * (ct + cvv);
     }
   }
 }
@@ -167,30 +200,71 @@ __device__ __forceinline__ void mix_pool(const double* Y, double Tv, double& e, 
 // Safeguarded Newton for a monotone energy: returns 0 on convergence, 1 otherwise.  The
 // energies at the bracket ends [kTmin, kTmax] are evaluated only when a Newton step leaves the
 // bracket (a state below / above them is clamped to the end, as in a plain bracketed solve).
+// An FP32 Newton predictor first brings the guess to ~1e-6 relative (where the warm start is
+// not already that close); the FP64 iteration then stops when a Newton step is at most 1e-8 T
+// (quadratic convergence puts the new iterate within ~1e-16 T, the accuracy the bracketed
+// solve's own test |dT| <= 1e-12 T gives one iteration later) or a bisection step is at most
+// 1e-12 T.  Fewer FP64 iterations, and fewer lanes of a warp idling while others iterate.
 template <class G, bool POOL>
 __device__ int solve_temperature(const double* Y, double target, double guess, double& Tout) {
   double lo = kTmin, hi = kTmax, e, cv;
+  // (the loop below counts the bracket-end evaluations as passes: 200 Newton / bisection
+  // steps plus at most two end checks)
   bool lo_checked = false, hi_checked = false;
   double T = (guess > lo && guess < hi) ? guess : 1000.0;
-  for (int it = 0; it < 200; ++it) {
-    if (POOL) mix_pool<G>(Y, T, e, cv); else mix_e1<G>(Y, T, e, cv);
-    const double f = e - target;
-    if (f > 0) hi = T; else lo = T;
-    double Tn = (cv > 0) ? T - f / cv : 0.5 * (lo + hi);
-    if (!(Tn > lo && Tn < hi)) {
-      if (Tn <= lo && lo == kTmin && !lo_checked) {
+  {
+    float Yf[G::NS];
+#pragma unroll
+    for (int s = 0; s < G::NS; ++s) Yf[s] = (float)Y[s];
+    const float tf = (float)target;
+    float Tf = (float)T;
+    bool ok = true;
+#pragma unroll 1
+    for (int it = 0; it < 12; ++it) {
+      float ef, cf;
+      mix_f32<G, POOL>(Yf, Tf, ef, cf);
+      const float dT = (tf - ef) / cf;
+      const float Tn = Tf + dT;
+      if (!(Tn > (float)kTmin && Tn < (float)kTmax)) { ok = false; break; }
+      Tf = Tn;
+      if (fabsf(dT) <= 3e-6f * Tf) break;
+    }
+    if (ok && fabs((double)Tf - T) > 3e-6 * T) T = (double)Tf;
+  }
+  // One energy evaluation per pass of the loop: at the Newton iterate, or (check = 1 / 2) at a
+  // bracket end the iterate has stepped past, evaluated once each.
+  int check = 0;
+#pragma unroll 1
+  for (int it = 0; it < 202; ++it) {
+    const double Te = check == 1 ? kTmin : (check == 2 ? kTmax : T);
+    if (POOL) mix_pool<G>(Y, Te, e, cv); else mix_e1<G>(Y, Te, e, cv);
+    double Tn;
+    bool newton;
+    if (check) {
+      if (check == 1) {
         lo_checked = true;
-        if (POOL) mix_pool<G>(Y, kTmin, e, cv); else mix_e1<G>(Y, kTmin, e, cv);
         if (e >= target) { Tout = kTmin; return 0; }
-      }
-      if (Tn >= hi && hi == kTmax && !hi_checked) {
+      } else {
         hi_checked = true;
-        if (POOL) mix_pool<G>(Y, kTmax, e, cv); else mix_e1<G>(Y, kTmax, e, cv);
         if (e <= target) { Tout = kTmax; return 1; }
       }
+      check = 0;
       Tn = 0.5 * (lo + hi);
+      newton = false;
+    } else {
+      const double f = e - target;
+      if (f > 0) hi = T; else lo = T;
+      Tn = (cv > 0) ? T - f / cv : 0.5 * (lo + hi);
+      newton = cv > 0;
+      if (!(Tn > lo && Tn < hi)) {
+        if (Tn <= lo && lo == kTmin && !lo_checked) { check = 1; continue; }
+        if (Tn >= hi && hi == kTmax && !hi_checked) { check = 2; continue; }
+        Tn = 0.5 * (lo + hi);
+        newton = false;
+      }
     }
-    if (fabs(Tn - T) <= 1e-12 * T) { Tout = Tn; return 0; }
+    const double step = fabs(Tn - T);
+    if (step <= 1e-12 * T || (newton && step <= 1e-8 * T)) { Tout = Tn; return 0; }
     T = Tn;
   }
   Tout = T;
@@ -202,11 +276,17 @@ template <class G, int ND>
 struct Prim {
   double rhos[G::NS], Y[G::NS], rho, u[ND], T, Tv, p, c, beta, rhoE, rhoev, ev, H, Gam;
   double prs[G::NS], prev, cvtr, cvve, cv, mu, kt, kv, rhoD, hs[G::NS], eve[G::NS];
+  double emP[G::NS];   // exp(-theta_v/T) at the vibrational temperature (Tv, or T in 1T)
 };
 
-// Conserved -> primitive.  Returns ST_OK, ST_NONPHYSICAL or ST_NEWTON.
-template <class G, int ND>
-__device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G, ND>& w) {
+// Conserved -> primitive.  Returns ST_OK, ST_NONPHYSICAL or ST_NEWTON.  With STORE the
+// per-species results (Y, prs, hs, eve, emP) are also written to the auxiliary array as they
+// are produced (Wc = &W[cell], stride N), so that they need not stay in registers until the
+// record is stored; the caller then stores the scalars (store_prim_scalars).
+template <class G, int ND, bool STORE = false>
+__device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G, ND>& w,
+                         double* Wc = nullptr, size_t N = 0) {
+  using A = Aux<G, ND>;
   constexpr int NS = G::NS;
   double rho = 0.0;
 #pragma unroll
@@ -219,7 +299,10 @@ __device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G,
   w.rho = rho;
   const double irho = 1.0 / rho;
 #pragma unroll
-  for (int s = 0; s < NS; ++s) w.Y[s] = w.rhos[s] * irho;
+  for (int s = 0; s < NS; ++s) {
+    w.Y[s] = w.rhos[s] * irho;
+    if (STORE) Wc[(A::Y + s) * N] = w.Y[s];
+  }
   double ke = 0.0;
 #pragma unroll
   for (int d = 0; d < ND; ++d) {
@@ -252,6 +335,7 @@ __device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G,
   }
   if (st) return ST_NEWTON;
   const double T = w.T, Tv = w.Tv;
+  const double iTp = 1.0 / (G::NTEMP == 2 ? Tv : T);
   double p = 0.0, Rh = 0.0, cvt = 0.0, cvve = 0.0, cv = 0.0, pe = 0.0;
   double evs[NS], cvvs[NS];
 #pragma unroll
@@ -263,11 +347,13 @@ __device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G,
       pe += w.rhos[s] * R;
       evs[s] = 1.5 * R * Tv;
       cvvs[s] = 1.5 * R;
+      w.emP[s] = 0.0;
     } else {
       p += w.rhos[s] * R * T;
       Rh += w.Y[s] * R;
-      vib<G>(s, G::NTEMP == 2 ? Tv : T, evs[s], cvvs[s]);
+      vib_it<G>(s, iTp, evs[s], cvvs[s], w.emP[s]);
     }
+    if (STORE) Wc[(A::EMP + s) * N] = w.emP[s];
     cvt += w.Y[s] * cvtr<G>(s);
     if (G::NTEMP == 2) cvve += w.Y[s] * cvvs[s];
     else cv += w.Y[s] * (cvtr<G>(s) + cvvs[s]);
@@ -301,20 +387,52 @@ __device__ int primitive(const double* q, double Tguess, double Tvguess, Prim<G,
       w.hs[s] = es + R * (elec ? Tv : T);
       w.eve[s] = elec ? 2.5 * R * Tv : evs[s];
     }
+    if (STORE) {
+      Wc[(A::PRS + s) * N] = w.prs[s];
+      Wc[(A::HS + s) * N] = w.hs[s];
+      Wc[(A::EVE + s) * N] = w.eve[s];
+    }
   }
   w.c = sqrt((1.0 + beta) * p * irho);
   w.H = (w.rhoE + p) * irho;
   w.Gam = rhoe / p;
   w.mu = kSuthMu * T * sqrt(T) / (T + kSuthT);
   if (G::NTEMP == 2) {
-    w.kt = w.mu * (cvt + Rh) / kPr;
-    w.kv = w.mu * cvve / kPr;
+    w.kt = w.mu * (cvt + Rh) * kInvPr;
+    w.kv = w.mu * cvve * kInvPr;
   } else {
-    w.kt = w.mu * (cv + Rh) / kPr;
+    w.kt = w.mu * (cv + Rh) * kInvPr;
     w.kv = 0.0;
   }
-  w.rhoD = w.mu / kSc;
+  w.rhoD = w.mu * kInvSc;
   return ST_OK;
+}
+
+// the scalar fields of the record (the per-species ones: primitive<G, ND, true>)
+template <class G, int ND>
+__device__ __forceinline__ void store_prim_scalars(const DevGrid& g, int c, const Prim<G, ND>& w) {
+  using A = Aux<G, ND>;
+  double* W = g.W;
+  const size_t N = g.N;
+  W[A::RHO * N + c] = w.rho;
+#pragma unroll
+  for (int d = 0; d < ND; ++d) W[(A::U + d) * N + c] = w.u[d];
+  W[A::T * N + c] = w.T;
+  W[A::TV * N + c] = w.Tv;
+  W[A::P * N + c] = w.p;
+  W[A::C * N + c] = w.c;
+  W[A::BETA * N + c] = w.beta;
+  W[A::GAM * N + c] = w.Gam;
+  W[A::EV * N + c] = w.ev;
+  W[A::H * N + c] = w.H;
+  W[A::CVTR * N + c] = w.cvtr;
+  W[A::CVVE * N + c] = w.cvve;
+  W[A::CV * N + c] = w.cv;
+  W[A::MU * N + c] = w.mu;
+  W[A::KT * N + c] = w.kt;
+  W[A::KV * N + c] = w.kv;
+  W[A::RHOD * N + c] = w.rhoD;
+  W[A::PREV * N + c] = w.prev;
 }
 
 template <class G, int ND>
@@ -347,6 +465,7 @@ __device__ __forceinline__ void store_prim(const DevGrid& g, int c, const Prim<G
     W[(A::PRS + s) * N + c] = w.prs[s];
     W[(A::HS + s) * N + c] = w.hs[s];
     W[(A::EVE + s) * N + c] = w.eve[s];
+    W[(A::EMP + s) * N + c] = w.emP[s];
   }
 }
 
@@ -358,21 +477,21 @@ __device__ __forceinline__ void store_prim(const DevGrid& g, int c, const Prim<G
 
 // g_s/(R_u T) and H_s/(R_u T) at the standard pressure, simplified form (translational,
 // rotational and vibrational enthalpy terms cancel between H/RT and S/R); em = exp(-theta_v/T)
-// is supplied by the caller, iT = 1/T.
+// and r = 1/(1 - em) are supplied by the caller, iT = 1/T.
 template <class G>
-__device__ __forceinline__ void gibbs(int s, double iT, double lnT, double em, double& gRT,
-                                      double& hRT) {
+__device__ __forceinline__ void gibbs(int s, double iT, double lnT, double em, double r,
+                                      double& gRT, double& hRT) {
   const SpeciesData& d = G::sp(s);
-  const double hr = d.h0 * (iT / kRu);
+  const double hr = d.h0 * iT * kInvRu;
   double g = hr - 2.5 * lnT + c_gas.gc0[s];
   double h = 2.5 + hr;
   if (d.kind == DIATOMIC) {
     g -= lnT;
     h += 1.0;
     if (d.thv > 0.0) {
-      const double x = d.thv * iT, om = 1.0 - em;
-      g += log(om);
-      h += x * em / om;
+      const double x = d.thv * iT;
+      g += log(1.0 - em);
+      h += x * em * r;
     }
   }
   gRT = g;
@@ -385,15 +504,24 @@ __device__ __forceinline__ void vib_exp(double iT, double* em) {
 #pragma unroll
   for (int s = 0; s < G::NS; ++s) {
     const SpeciesData& d = G::sp(s);
-    em[s] = (d.kind == DIATOMIC && d.thv > 0.0) ? exp(-d.thv * iT) : 0.0;
+    em[s] = (d.kind == DIATOMIC && d.thv > 0.0) ? exp_tab(-d.thv * iT) : 0.0;
   }
 }
-// harmonic-oscillator energy and heat capacity from em = exp(-theta/T)
+// 1/(1 - em) of every species
 template <class G>
-__device__ __forceinline__ void vib_em(int s, double iT, double em, double& e, double& cv) {
+__device__ __forceinline__ void vib_rcp(const double* em, double* r) {
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    const SpeciesData& d = G::sp(s);
+    r[s] = (d.kind == DIATOMIC && d.thv > 0.0) ? 1.0 / (1.0 - em[s]) : 1.0;
+  }
+}
+// harmonic-oscillator energy and heat capacity from em = exp(-theta/T) and r = 1/(1 - em)
+template <class G>
+__device__ __forceinline__ void vib_em(int s, double iT, double em, double r, double& e, double& cv) {
   const SpeciesData& d = G::sp(s);
   if (d.kind != DIATOMIC || d.thv <= 0.0) { e = 0.0; cv = 0.0; return; }
-  const double x = d.thv * iT, r = 1.0 / (1.0 - em), Rem = c_gas.Rs[s] * em * r;
+  const double x = d.thv * iT, Rem = c_gas.Rs[s] * em * r;
   e = Rem * d.thv;
   cv = Rem * x * x * r;
 }
@@ -411,16 +539,16 @@ struct ChemCtx {
   double X[NS], gT[NS], hT[NS], gV[NS], hV[NS];
   double omega[NS], jd[NS], wT[NS], wTv[NS];
   double J[FULL ? NS * NS : 1];
-  double lnT, lnTv, lnTa, iT, iTv, iTa, lnPT, lnPTv, T, Tv;
+  double lnT, lnTv, lnTa, iT, iTv, iTa, lnPT, lnPTv, T, Tv, Ta;
 };
 
 template <int K>
-__device__ __forceinline__ void pick_temp(double T, double Tv, double lnT, double lnTv,
+__device__ __forceinline__ void pick_temp(double T, double Tv, double Ta, double lnT, double lnTv,
                                           double lnTa, double iT, double iTv, double iTa,
                                           double& Tk, double& lnTk, double& iTk) {
   if (K == TK_T) { Tk = T; lnTk = lnT; iTk = iT; }
   else if (K == TK_V) { Tk = Tv; lnTk = lnTv; iTk = iTv; }
-  else { Tk = sqrt(T * Tv); lnTk = lnTa; iTk = iTa; }
+  else { Tk = Ta; lnTk = lnTa; iTk = iTa; }
 }
 
 struct RxTerms {
@@ -500,10 +628,10 @@ __device__ __forceinline__ void reaction(ChemCtx<G, FULL>& c) {
   if (x.nr > 1) { sg -= gB[x.r1]; sh -= hB[x.r1]; --dn; }
   const double lnKc = -sg + dn * (bv ? c.lnPTv : c.lnPT);
   double Tf, lnTf, iTf, Tb, lnTb, iTb;
-  pick_temp<x.tf>(c.T, c.Tv, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tf, lnTf, iTf);
-  pick_temp<x.tb>(c.T, c.Tv, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tb, lnTb, iTb);
-  const double kf = exp(d.lnA + d.n * lnTf - d.theta * iTf);
-  const double kb = exp(d.lnA + d.n * lnTb - d.theta * iTb - lnKc);
+  pick_temp<x.tf>(c.T, c.Tv, c.Ta, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tf, lnTf, iTf);
+  pick_temp<x.tb>(c.T, c.Tv, c.Ta, c.lnT, c.lnTv, c.lnTa, c.iT, c.iTv, c.iTa, Tb, lnTb, iTb);
+  const double kf = exp_tab(d.lnA + d.n * lnTf - d.theta * iTf);
+  const double kb = exp_tab(d.lnA + d.n * lnTb - d.theta * iTb - lnKc);
   double M = 1.0;
   if (x.third) {
     M = 0.0;
@@ -543,11 +671,13 @@ __device__ __forceinline__ void all_reactions(ChemCtx<G, FULL>& c, std::integer_
 // omega[s]; the fixed-T Jacobian diagonal jd[s] = d omega_s/d rho_s (or the full fixed-T
 // Jacobian J[s*NS+r] when FULL) and the temperature derivatives wT[s], wTv[s] (all zero when
 // JAC is false: the source alone).
-// emT/emTv: exp(-theta_v/T) and exp(-theta_v/Tv) of every species (vib_exp).
+// emT/emTv: exp(-theta_v/T) and exp(-theta_v/Tv) of every species (vib_exp), rT/rV their
+// 1/(1 - em) (vib_rcp).
 template <class G, bool FULL, bool JAC = true>
 __device__ __forceinline__ void chemistry(const double* rhos, double T, double Tv, const double* emT,
-                                          const double* emTv, double* omega, double* jd,
-                                          double* J, double* wT, double* wTv) {
+                                          const double* emTv, const double* rT, const double* rV,
+                                          double* omega, double* jd, double* J, double* wT,
+                                          double* wTv) {
   constexpr int NS = G::NS;
   ChemCtx<G, FULL> c;
 #pragma unroll
@@ -568,13 +698,14 @@ __device__ __forceinline__ void chemistry(const double* rhos, double T, double T
   c.iT = 1.0 / T;
   c.iTv = (G::NTEMP == 2) ? 1.0 / Tv : c.iT;
   c.lnTa = 0.5 * (c.lnT + c.lnTv);
-  c.iTa = (G::NTEMP == 2) ? 1.0 / sqrt(T * Tv) : c.iT;
-  c.lnPT = log(kPref / kRu) - c.lnT;
-  c.lnPTv = log(kPref / kRu) - c.lnTv;
+  c.Ta = (G::NTEMP == 2) ? sqrt(T * Tv) : T;
+  c.iTa = (G::NTEMP == 2) ? 1.0 / c.Ta : c.iT;
+  c.lnPT = c_gas.lnPRu - c.lnT;
+  c.lnPTv = c_gas.lnPRu - c.lnTv;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    gibbs<G>(s, c.iT, c.lnT, emT[s], c.gT[s], c.hT[s]);
-    if (G::NTEMP == 2) gibbs<G>(s, c.iTv, c.lnTv, emTv[s], c.gV[s], c.hV[s]);
+    gibbs<G>(s, c.iT, c.lnT, emT[s], rT[s], c.gT[s], c.hT[s]);
+    if (G::NTEMP == 2) gibbs<G>(s, c.iTv, c.lnTv, emTv[s], rV[s], c.gV[s], c.hV[s]);
     else { c.gV[s] = c.gT[s]; c.hV[s] = c.hT[s]; }
   }
   all_reactions<G, FULL, JAC>(c, std::make_integer_sequence<int, G::NR>{});
@@ -590,28 +721,43 @@ __device__ __forceinline__ void chemistry(const double* rhos, double T, double T
     for (int k = 0; k < NS * NS; ++k) J[k] = c.J[k];
 }
 
-// Derivatives of T and Tv with respect to rho_s at fixed other conserved variables.
+// Derivatives of T and Tv with respect to rho_s at fixed other conserved variables; irc =
+// 1/(rho c_v) (1T) or 1/(rho c_v,tr) (2T), ircv = 1/(rho c_v,ve) (0 without a pool).
 template <class G, int ND>
-__device__ __forceinline__ void dT_drho(const Prim<G, ND>& w, int s, double evs, double& dT,
-                                        double& dTv) {
+__device__ __forceinline__ void dT_drho_r(const Prim<G, ND>& w, int s, double evs, double irc,
+                                          double ircv, double& dT, double& dTv) {
   double ke = 0.0;
 #pragma unroll
   for (int d = 0; d < ND; ++d) ke += 0.5 * w.u[d] * w.u[d];
   if (G::NTEMP == 1) {
     const double es = cvtr<G>(s) * w.T + evs + hf<G>(s);
-    dT = (ke - es) / (w.rho * w.cv);
+    dT = (ke - es) * irc;
     dTv = dT;
   } else {
-    dT = (ke - hf<G>(s) - cvtr<G>(s) * w.T) / (w.rho * w.cvtr);
-    dTv = (w.cvve > 0.0) ? -evs / (w.rho * w.cvve) : 0.0;
+    dT = (ke - hf<G>(s) - cvtr<G>(s) * w.T) * irc;
+    dTv = -evs * ircv;
   }
 }
-
-// Millikan-White + Park vibrational relaxation and the vibrational source (2T).
-// emT/emTv: exp(-theta_v/T), exp(-theta_v/Tv) per species.
 template <class G, int ND>
-__device__ void vib_source(const Prim<G, ND>& w, const double* omega, const double* emT,
-                           const double* emTv, double& omv, double& relax) {
+__device__ __forceinline__ void dT_drho_recips(const Prim<G, ND>& w, double& irc, double& ircv) {
+  irc = 1.0 / (w.rho * (G::NTEMP == 1 ? w.cv : w.cvtr));
+  ircv = (G::NTEMP == 2 && w.cvve > 0.0) ? 1.0 / (w.rho * w.cvve) : 0.0;
+}
+template <class G, int ND>
+__device__ __forceinline__ void dT_drho(const Prim<G, ND>& w, int s, double evs, double& dT,
+                                        double& dTv) {
+  double irc, ircv;
+  dT_drho_recips<G, ND>(w, irc, ircv);
+  dT_drho_r<G, ND>(w, s, evs, irc, ircv, dT, dTv);
+}
+
+// Millikan-White + Park vibrational relaxation (2T): the Landau-Teller part of the vibrational
+// source (lt) and the relaxation diagonal (relax).  The chemistry-vibration coupling
+// sum_s omega_s e_p,s is added by vib_coupling once the species sources are known.
+// emT/emTv: exp(-theta_v/T), exp(-theta_v/Tv) per species; rT/rV: their 1/(1 - em).
+template <class G, int ND>
+__device__ void vib_relax(const Prim<G, ND>& w, const double* emT, const double* emTv,
+                          const double* rT, const double* rV, double& lt_out, double& relax) {
   constexpr int NS = G::NS;
   double X[NS], xs = 0.0, ph = 0.0;
 #pragma unroll
@@ -622,9 +768,11 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, const doub
     xs += X[s];
     ph += w.rhos[s] * Rs<G>(s) * w.T;
   }
-  const double patm = ph / kPref, nden = xs * kNa, T13 = rcbrt(w.T);
+  const double patm = ph * kInvPref, nden = xs * kNa, T13 = rcbrt(w.T);
   const double iT = 1.0 / w.T, iTv = 1.0 / w.Tv, sqT = sqrt(w.T);
   const double sv = 1e-21 * (50000.0 * iT) * (50000.0 * iT);
+  // Park's collision-limited time 1/(n sigma cbar): cbar = cbk_s sqrt(T)
+  const double ipark = 1.0 / (nden * sv * sqT);
   double lt = 0.0, rc = 0.0, rcT = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
@@ -636,30 +784,41 @@ __device__ void vib_source(const Prim<G, ND>& w, const double* omega, const doub
       for (int q = 0; q < NS; ++q) {
         if (G::sp(q).kind == ELECTRON) continue;
         num += X[q];
-        den += X[q] * exp(c_gas.mwAB[s][q] - c_gas.mwA[s][q] * T13);
+        den += X[q] * exp_tab(c_gas.mwAB[s][q] - c_gas.mwA[s][q] * T13);
       }
       den *= patm;
-      const double tau = num / den + 1.0 / (nden * sv * c_gas.cbk[s] * sqT);
+      const double tau = num / den + ipark * c_gas.icbk[s];
       const double itau = 1.0 / tau;
       double eT, cT, eV, cV;
-      vib_em<G>(s, iT, emT[s], eT, cT);
-      vib_em<G>(s, iTv, emTv[s], eV, cV);
+      vib_em<G>(s, iT, emT[s], rT[s], eT, cT);
+      vib_em<G>(s, iTv, emTv[s], rV[s], eV, cV);
       lt += w.rhos[s] * (eT - eV) * itau;
       rc += w.rhos[s] * cV * itau;
       rcT += w.rhos[s] * cT * itau;
     }
-    const double ep = (d.kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
-    lt += omega[s] * ep;
   }
-  omv = lt;
+  lt_out = lt;
   // -d(Landau-Teller)/d(rho e_v) at fixed rho_s, momentum and rho E: Tv rises with rho e_v
   // and T falls (the total energy being fixed); tau's temperature dependence is left out
   relax = ((w.cvve > 0.0) ? rc / (w.rho * w.cvve) : 0.0) +
           ((w.cvtr > 0.0) ? rcT / (w.rho * w.cvtr) : 0.0);
 }
+// Vibrational energy carried by species created or destroyed (2T): sum_s omega_s e_p,s with the
+// pool energy e_p of each species (electrons: 3/2 R_e Tv).
+template <class G, int ND>
+__device__ __forceinline__ double vib_coupling(const Prim<G, ND>& w, const double* omega) {
+  double lt = 0.0;
+#pragma unroll
+  for (int s = 0; s < G::NS; ++s) {
+    const double ep = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+    lt += omega[s] * ep;
+  }
+  return lt;
+}
 
 // ---------------------------------------------------------------------------------------
-// K1: primitives, transport, chemistry, vibrational source (per cell)
+// K1: primitives and transport (per cell): the temperature solves and everything that follows
+// from the state alone.
 // ---------------------------------------------------------------------------------------
 template <class G, int ND>
 __global__ void __launch_bounds__(128) k_primitive(DevGrid g) {
@@ -671,44 +830,93 @@ __global__ void __launch_bounds__(128) k_primitive(DevGrid g) {
 #pragma unroll
   for (int v = 0; v < A::NQ; ++v) q[v] = g.Q[v * N + c];
   Prim<G, ND> w;
-  const int st = primitive<G, ND>(q, g.W[A::T * N + c], g.W[A::TV * N + c], w);
+  const int st = primitive<G, ND, true>(q, g.W[A::T * N + c], g.W[A::TV * N + c], w, g.W + c, N);
   if (st != ST_OK) {
     set_status(g, st, c);
     return;
   }
-  store_prim<G, ND>(g, c, w);
-  double om[G::NS], jd[G::NS], wT[G::NS], wTv[G::NS];
+  store_prim_scalars<G, ND>(g, c, w);
+}
+
+// ---------------------------------------------------------------------------------------
+// K1b: chemistry, species Jacobian diagonal and vibrational source (per cell), from the state
+// and the primitives of K1 (a separate kernel: the chemistry's working set and the temperature
+// solves' iteration counts do not share one thread's registers and lanes).  A cell whose
+// primitive recovery failed has its status set; the iteration is then rejected as a whole.
+// ---------------------------------------------------------------------------------------
+#ifndef CS_CHEM_MIN_BLOCKS
+#define CS_CHEM_MIN_BLOCKS 2   // resident CTAs per SM the register allocation must allow
+#endif
+template <class G, int ND>
+__global__ void __launch_bounds__(128, CS_CHEM_MIN_BLOCKS) k_chem(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double om[NS], jd[NS], wT[NS], wTv[NS];
   double omv = 0.0, relax = 0.0;
   if (g.react && G::NR > 0) {
-    double emT[G::NS], emTv[G::NS];
+    const double* W = g.W;
+    Prim<G, ND> w;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      w.rhos[s] = g.Q[s * N + c];
+      w.eve[s] = W[(A::EVE + s) * N + c];
+    }
+    w.rho = W[A::RHO * N + c];
+#pragma unroll
+    for (int d = 0; d < ND; ++d) w.u[d] = W[(A::U + d) * N + c];
+    w.T = W[A::T * N + c];
+    w.Tv = W[A::TV * N + c];
+    w.cv = W[A::CV * N + c];
+    w.cvtr = W[A::CVTR * N + c];
+    w.cvve = W[A::CVVE * N + c];
+    // exp(-theta_v/T) at the vibrational temperature comes from the primitive recovery;
+    // with two temperatures the trans-rotational one needs its own
+    double emT[NS], emTv[NS], rT[NS], rV[NS];
     const double iT = 1.0 / w.T;
-    vib_exp<G>(iT, emT);
-    if (G::NTEMP == 2) vib_exp<G>(1.0 / w.Tv, emTv);
-    else for (int s = 0; s < G::NS; ++s) emTv[s] = emT[s];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) emTv[s] = W[(A::EMP + s) * N + c];
+    if (G::NTEMP == 2) vib_exp<G>(iT, emT);
+    else for (int s = 0; s < NS; ++s) emT[s] = emTv[s];
+    vib_rcp<G>(emT, rT);
+    if (G::NTEMP == 2) vib_rcp<G>(emTv, rV);
+    else for (int s = 0; s < NS; ++s) rV[s] = rT[s];
+    // the parts that need exp(-theta_v/T) and 1/(1 - em) come first, so that these arrays
+    // are dead once the chemistry has formed its Gibbs energies
+    double evT[NS];
+    if (G::NTEMP == 1) {
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        double cvv;
+        vib_em<G>(s, iT, emT[s], rT[s], evT[s], cvv);
+      }
+    }
+    if (G::NTEMP == 2) vib_relax<G, ND>(w, emT, emTv, rT, rV, omv, relax);
     if (g.nojac) {
       // the species Jacobian diagonal comes from the surrogate network: source only
-      chemistry<G, false, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
+      chemistry<G, false, false>(w.rhos, w.T, w.Tv, emT, emTv, rT, rV, om, jd, nullptr, wT, wTv);
     } else {
-      chemistry<G, false>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, nullptr, wT, wTv);
-    }
-    if (!g.nojac) {
+      chemistry<G, false>(w.rhos, w.T, w.Tv, emT, emTv, rT, rV, om, jd, nullptr, wT, wTv);
+      double irc, ircv;
+      dT_drho_recips<G, ND>(w, irc, ircv);
 #pragma unroll
-      for (int s = 0; s < G::NS; ++s) {
-        double ev = 0.0, cvv;
-        if (G::NTEMP == 1) vib_em<G>(s, iT, emT[s], ev, cvv);
-        else ev = (G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s];
+      for (int s = 0; s < NS; ++s) {
+        const double ev = G::NTEMP == 1 ? evT[s]
+                          : ((G::sp(s).kind == ELECTRON) ? 1.5 * Rs<G>(s) * w.Tv : w.eve[s]);
         double dT, dTv;
-        dT_drho<G, ND>(w, s, ev, dT, dTv);
+        dT_drho_r<G, ND>(w, s, ev, irc, ircv, dT, dTv);
         jd[s] += wT[s] * dT + wTv[s] * dTv;
       }
     }
-    if (G::NTEMP == 2) vib_source<G, ND>(w, om, emT, emTv, omv, relax);
+    if (G::NTEMP == 2) omv += vib_coupling<G, ND>(w, om);
   } else {
 #pragma unroll
-    for (int s = 0; s < G::NS; ++s) { om[s] = 0.0; jd[s] = 0.0; }
+    for (int s = 0; s < NS; ++s) { om[s] = 0.0; jd[s] = 0.0; }
   }
 #pragma unroll
-  for (int s = 0; s < G::NS; ++s) {
+  for (int s = 0; s < NS; ++s) {
     g.W[(A::OM + s) * N + c] = om[s];
     g.W[(A::DOM + s) * N + c] = jd[s];
   }
@@ -3177,11 +3385,13 @@ __global__ void __launch_bounds__(64) k_ci_block(DevGrid g) {
       set_status(g, ST_NONPHYSICAL, c);
       return;
     }
-    double om[NS], jd[NS], J[NS * NS], wT[NS], wTv[NS], emT[NS], emTv[NS];
+    double om[NS], jd[NS], J[NS * NS], wT[NS], wTv[NS], emT[NS], emTv[NS], rT[NS], rV[NS];
     vib_exp<G>(1.0 / w.T, emT);
     if (G::NTEMP == 2) vib_exp<G>(1.0 / w.Tv, emTv);
     else for (int s = 0; s < NS; ++s) emTv[s] = emT[s];
-    chemistry<G, true>(w.rhos, w.T, w.Tv, emT, emTv, om, jd, J, wT, wTv);
+    vib_rcp<G>(emT, rT);
+    vib_rcp<G>(emTv, rV);
+    chemistry<G, true>(w.rhos, w.T, w.Tv, emT, emTv, rT, rV, om, jd, J, wT, wTv);
     // temperature derivatives with respect to the full conserved variables
     double dT[NQ], dTv[NQ];
     double ke = 0.0;

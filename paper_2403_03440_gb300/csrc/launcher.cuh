@@ -134,6 +134,7 @@ struct LauncherT : Launcher {
       if (sp[s].kind == DIATOMIC) v += log(sp[s].sigma * sp[s].thr);
       gc.gc0[s] = v;
       gc.cbk[s] = sqrt(8.0 * kRu / (kPi * sp[s].M));
+      gc.icbk[s] = 1.0 / gc.cbk[s];
       for (int q = 0; q < G::NS; ++q) {
         if (sp[s].kind != DIATOMIC || sp[s].thv <= 0.0 || sp[q].kind == ELECTRON) continue;
         const double mu = sp[s].M * sp[q].M / (sp[s].M + sp[q].M);
@@ -144,6 +145,16 @@ struct LauncherT : Launcher {
         gc.mwAB[s][q] = A * B + 18.42;
       }
     }
+    gc.lnPRu = log(kPref / kRu);
+    for (int s = 0; s < G::NS; ++s) {
+      gc.Rsf[s] = (float)gc.Rs[s];
+      gc.hff[s] = (float)gc.hf[s];
+      gc.thvf[s] = (float)sp[s].thv;
+    }
+    double tab[64];
+    for (int j = 0; j < 64; ++j) tab[j] = exp2(j / 64.0);
+    e = cudaMemcpyToSymbol(g_exp2_64, tab, sizeof tab);
+    if (e != cudaSuccess) return e;
     return cudaMemcpyToSymbol(c_gas, &gc, sizeof gc);
   }
 
@@ -156,6 +167,7 @@ struct LauncherT : Launcher {
 
   void primitive(const DevGrid& g, cudaStream_t st) override {
     k_primitive<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+    k_chem<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
   }
   void gradient(const DevGrid& g, cudaStream_t st) override {
     k_gradient<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
