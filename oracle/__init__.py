@@ -44,6 +44,7 @@ def lib():
         L.orc_set_reacting.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_hcorr.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_viscous.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_transport.argtypes = [C.c_void_p, C.c_int]
         L.orc_set_update_limit.argtypes = [C.c_void_p, C.c_double]
         L.orc_set_dual.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.orc_set_ci_splitting.argtypes = [C.c_void_p, C.c_int]
@@ -247,6 +248,10 @@ class OracleGrid:
     def set_viscous(self, on):
         """Viscous and diffusive fluxes and radii on (default) or off (inviscid flow)."""
         lib().orc_set_viscous(self._h, int(bool(on)))
+
+    def set_transport(self, model):
+        """Transport model: 0 Sutherland / constant Pr, Sc; 1 Blottner-Eucken-Wilke-Blanc."""
+        self._check(lib().orc_set_transport(self._h, int(model)), "set_transport")
 
     def set_update_limit(self, f):
         self._check(lib().orc_set_update_limit(self._h, float(f)), "set_update_limit")

@@ -127,6 +127,7 @@ static const reaction_t RX_AIR[21] = {
 
 typedef struct {
     int mech, ns, nr, ntemp;        /* ntemp = 1 (one temperature) or 2 (T, Tv) */
+    int transport;                  /* 0: Sutherland, constant Pr and Sc; 1: species model */
     species_t sp[NSMAX];
     double M[NSMAX], Rs[NSMAX], hf[NSMAX];   /* kg/kmol, J/(kg K), J/kg */
     reaction_t rx[NRMAX];
@@ -270,12 +271,108 @@ typedef struct {
     double rhoE, rhoev, ev, H, Gam;            /* Gam = rho*e/p, rho*e = rhoE - rho|u|^2/2 */
     double prs[NSMAX], prev;                   /* dp/drho_s, dp/d(rho e_v) */
     double cvtr, cvve, cv;                     /* per unit mass */
-    double mu, kt, kv, rhoD;
+    double mu, kt, kv, rhoD;                   /* rhoD: the largest species rho D_s */
+    double rhoDs[NSMAX];                       /* effective diffusion rho D_s per species */
     double hs[NSMAX], eve[NSMAX];              /* species enthalpy and pool energy */
     double omega[NSMAX], omega_v, dom[NSMAX];  /* chemistry source and d omega_s/d rho_s */
     double relax;                              /* -d omega_v / d(rho e_v) */
     double tau[NSMAX];                         /* vibrational relaxation times */
 } prim_t;
+
+/* ---------------------------------------------------------------------------------------
+ * Species transport model (Sec. 2.1 defers viscosity, conductivity and the effective
+ * diffusion coefficient D_s of each species to its references).  Reading, in this order:
+ *  1. species viscosity from Blottner's curve fits mu_s = 0.1 exp((A ln T + B) ln T + C)
+ *     kg/(m s) (Blottner, Johnson & Ellis, Sandia report SC-RR-70-754, 1971); the four other
+ *     ions take the fit given for NO+; heavy species at T, electrons at Tv;
+ *  2. species conductivities from Eucken's relation: k_s = mu_s (5/2 c_v,t + c_v,r + c_v,v),
+ *     split in the two-temperature model into k_tr,s = mu_s (5/2 c_v,t + c_v,r) and
+ *     k_ve,s = mu_s c_v,v(Tv); electrons k_e = mu_e 5/2 c_v,t,e (all in the pool);
+ *  3. mixture values by Wilke's rule: phi_s = sum_r X_r (1 + sqrt(mu_s/mu_r)(M_r/M_s)^(1/4))^2
+ *     / sqrt(8 (1 + M_s/M_r)), mu = sum_s X_s mu_s / phi_s, likewise k_tr and k_ve;
+ *  4. binary diffusion coefficients of hard spheres in the first Chapman-Enskog
+ *     approximation, D_sr = 3/(8 n sigma_sr^2) sqrt(k T / (2 pi m_sr)), with each species'
+ *     diameter from its Blottner viscosity, pi sigma_s^2 = (5/16) sqrt(pi m_s k T) / mu_s,
+ *     sigma_sr = (sigma_s + sigma_r)/2, m_sr the reduced mass, n the number density, T the
+ *     heavy-particle temperature;
+ *  5. effective coefficient of each heavy species in the mixture by Blanc's law,
+ *     D_s = (1 - X_s) / sum_{r != s, heavy} X_r / D_sr (the self-diffusion coefficient D_ss
+ *     where the species is (nearly) alone); electrons carry no Fick flux of their own: their
+ *     flux follows the ions' (no net charge flux, see the viscous flux).
+ * ------------------------------------------------------------------------------------- */
+static const double BLOTTNER[11][3] = {
+    {0.0268142, 0.3177838, -11.3155513},   /* N2 */
+    {0.0449290, -0.0826158, -9.2019475},   /* O2 */
+    {0.0436378, -0.0335511, -9.5767430},   /* NO */
+    {0.0115572, 0.6031679, -12.4327495},   /* N */
+    {0.0203144, 0.4294404, -11.6031403},   /* O */
+    {0.3020141, -3.5039791, -3.7355157},   /* NO+ */
+    {0.3020141, -3.5039791, -3.7355157},   /* N2+ (fit of NO+) */
+    {0.3020141, -3.5039791, -3.7355157},   /* O2+ (fit of NO+) */
+    {0.3020141, -3.5039791, -3.7355157},   /* N+ (fit of NO+) */
+    {0.3020141, -3.5039791, -3.7355157},   /* O+ (fit of NO+) */
+    {0.0, 0.0, -12.5},                     /* e- */
+};
+
+static void species_transport(const gas_t *g, prim_t *w)
+{
+    int ns = g->ns;
+    double T = w->T, Tv = w->Tv;
+    double mus[NSMAX], ktr[NSMAX], kve[NSMAX], X[NSMAX], sig[NSMAX], m[NSMAX];
+    double xs = 0.0, n = 0.0;
+    for (int s = 0; s < ns; s++) {
+        double Ts = is_heavy(g, s) ? T : Tv;
+        double lnT = log(Ts);
+        mus[s] = 0.1 * exp((BLOTTNER[s][0] * lnT + BLOTTNER[s][1]) * lnT + BLOTTNER[s][2]);
+        double cvt = 1.5 * g->Rs[s], cvr = (g->sp[s].kind == KIND_DIATOMIC) ? g->Rs[s] : 0.0;
+        if (!is_heavy(g, s)) {
+            ktr[s] = 0.0;
+            kve[s] = mus[s] * 2.5 * cvt;
+        } else if (g->ntemp == 2) {
+            ktr[s] = mus[s] * (2.5 * cvt + cvr);
+            kve[s] = mus[s] * cv_vib(g, s, Tv);
+        } else {
+            ktr[s] = mus[s] * (2.5 * cvt + cvr + cv_vib(g, s, T));
+            kve[s] = 0.0;
+        }
+        X[s] = w->Y[s] / g->M[s];
+        xs += X[s];
+        m[s] = g->M[s] / NAV;
+        n += w->rhos[s] / m[s];
+        sig[s] = sqrt((5.0 / 16.0) * sqrt(PI * m[s] * KB * Ts) / mus[s] / PI);
+    }
+    for (int s = 0; s < ns; s++) X[s] /= xs;
+    double mu = 0.0, kt = 0.0, kv = 0.0;
+    for (int s = 0; s < ns; s++) {
+        double phi = 0.0;
+        for (int r = 0; r < ns; r++) {
+            double a = 1.0 + sqrt(mus[s] / mus[r]) * pow(g->M[r] / g->M[s], 0.25);
+            phi += X[r] * a * a / sqrt(8.0 * (1.0 + g->M[s] / g->M[r]));
+        }
+        mu += X[s] * mus[s] / phi;
+        kt += X[s] * ktr[s] / phi;
+        kv += X[s] * kve[s] / phi;
+    }
+    w->mu = mu;
+    w->kt = kt;
+    w->kv = (g->ntemp == 2) ? kv : 0.0;
+    w->rhoD = 0.0;
+    for (int s = 0; s < ns; s++) {
+        w->rhoDs[s] = 0.0;
+        if (!is_heavy(g, s)) continue;
+        double den = 0.0, Dss = 0.0;
+        for (int r = 0; r < ns; r++) {
+            if (!is_heavy(g, r)) continue;
+            double sr = 0.5 * (sig[s] + sig[r]), mr = m[s] * m[r] / (m[s] + m[r]);
+            double D = 3.0 / (8.0 * n * sr * sr) * sqrt(KB * T / (2.0 * PI * mr));
+            if (r == s) Dss = D;
+            else den += X[r] / D;
+        }
+        double D = (1.0 - X[s] > 1e-12 && den > 0.0) ? (1.0 - X[s]) / den : Dss;
+        w->rhoDs[s] = w->rho * D;
+        if (w->rhoDs[s] > w->rhoD) w->rhoD = w->rhoDs[s];
+    }
+}
 
 /* Conserved -> primitive (Sec. 2.1, e_t / e_v definitions and ideal-gas law).  Tguess /
  * Tvguess <= 0 means "no previous value".  Returns 0, or 2 for a non-physical state, or 3 for
@@ -367,6 +464,10 @@ static int prim_from_cons(const gas_t *g, int nd, const double *q, double Tguess
         w->eve[s] = (g->ntemp == 2) ? (is_heavy(g, s) ? e_pool(g, s, Tv)
                                                      : 2.5 * g->Rs[s] * Tv) : 0.0;
     }
+    if (g->transport == 1) {
+        species_transport(g, w);
+        return 0;
+    }
     /* transport (reading: Sutherland viscosity, constant Prandtl and Schmidt numbers) */
     w->mu = SUTH_MU0 * T * sqrt(T) / (T + SUTH_TS);
     if (g->ntemp == 2) {
@@ -377,6 +478,7 @@ static int prim_from_cons(const gas_t *g, int nd, const double *q, double Tguess
         w->kv = 0.0;
     }
     w->rhoD = w->mu / SCHMIDT;
+    for (int s = 0; s < ns; s++) w->rhoDs[s] = w->rhoD;
     return 0;
 }
 
@@ -1185,22 +1287,51 @@ static void compute_gradients(orc_grid *G)
 
 /* viscous flux through S given face gradients g[k][q], face velocity uf, transport
  * coefficients and face species enthalpies; wall = 1 suppresses species diffusion */
-static void viscous_flux(const orc_grid *G, const double *g, const double *uf, double mu,
-                         double kt, double kv, double rhoD, const double *hs, const double *eve,
-                         const double *S, int wall, double *F)
+/* Diffusive mass fluxes through S (Sec. 2.1 Fick's law with an effective coefficient per
+ * species): J_s = -rho D_s grad(Y_s).S.  With the species transport model the electrons' flux
+ * follows from no net charge flux, J_e = M_e sum_ions J_i / M_i, and a correction velocity makes
+ * the fluxes sum to zero, J_s -= Y_s sum_r J_r (Yf: face mass fractions; the mixture being
+ * neutral, the correction keeps the charge flux zero).  With the single-coefficient model the
+ * fluxes sum to zero by themselves. */
+static void diffusive_fluxes(const orc_grid *G, const double *g, const double *rhoDs,
+                             const double *Yf, const double *S, double *J)
 {
     int ns = G->gas.ns, nd = G->nd, two = (G->gas.ntemp == 2);
-    int iT = nd, iTv = nd + 1, iY = nd + 1 + two;
+    int iY = nd + 1 + two;
+    for (int s = 0; s < ns; s++) {
+        J[s] = 0.0;
+        for (int q = 0; q < nd; q++) J[s] -= rhoDs[s] * g[3 * (iY + s) + q] * S[q];
+    }
+    if (G->gas.transport != 1) return;
+    double sum = 0.0, je = 0.0;
+    int e = -1;
+    for (int s = 0; s < ns; s++) {
+        if (!is_heavy(&G->gas, s)) { e = s; continue; }
+        if (G->gas.sp[s].charge != 0) je += J[s] / G->gas.M[s];
+    }
+    if (e >= 0) J[e] = je * G->gas.M[e];
+    for (int s = 0; s < ns; s++) sum += J[s];
+    for (int s = 0; s < ns; s++) J[s] -= Yf[s] * sum;
+}
+
+static void viscous_flux(const orc_grid *G, const double *g, const double *uf, double mu,
+                         double kt, double kv, const double *rhoDs, const double *Yf,
+                         const double *hs, const double *eve, const double *S, int wall,
+                         double *F)
+{
+    int ns = G->gas.ns, nd = G->nd, two = (G->gas.ntemp == 2);
+    int iT = nd, iTv = nd + 1;
     double tau[3][3], div = 0.0;
     for (int i = 0; i < nd; i++) div += g[3 * i + i];
     for (int i = 0; i < nd; i++)
         for (int l = 0; l < nd; l++)
             tau[i][l] = mu * (g[3 * i + l] + g[3 * l + i]) - (i == l ? 2.0 / 3.0 * mu * div : 0.0);
     for (int v = 0; v < G->nq; v++) F[v] = 0.0;
-    double qdiff = 0.0, qvdiff = 0.0;
+    double qdiff = 0.0, qvdiff = 0.0, Js[NSMAX];
+    if (wall) for (int s = 0; s < ns; s++) Js[s] = 0.0;
+    else diffusive_fluxes(G, g, rhoDs, Yf, S, Js);
     for (int s = 0; s < ns; s++) {
-        double J = 0.0;
-        if (!wall) for (int q = 0; q < nd; q++) J -= rhoD * g[3 * (iY + s) + q] * S[q];
+        double J = Js[s];
         F[s] = J;
         qdiff += J * hs[s];
         if (two) qvdiff += J * eve[s];
@@ -1242,11 +1373,16 @@ static void viscous_interior(const orc_grid *G, int a, int b, const double *S, d
         for (int q = 0; q < nd; q++) g[3 * k + q] += corr * t[q];
     }
     const prim_t *A = &G->w[a], *B = &G->w[b];
-    double uf[3] = {0, 0, 0}, hs[NSMAX], eve[NSMAX];
+    double uf[3] = {0, 0, 0}, hs[NSMAX], eve[NSMAX], rD[NSMAX], Yf[NSMAX];
     for (int q = 0; q < nd; q++) uf[q] = 0.5 * (A->u[q] + B->u[q]);
-    for (int s = 0; s < ns; s++) { hs[s] = 0.5 * (A->hs[s] + B->hs[s]); eve[s] = 0.5 * (A->eve[s] + B->eve[s]); }
+    for (int s = 0; s < ns; s++) {
+        hs[s] = 0.5 * (A->hs[s] + B->hs[s]);
+        eve[s] = 0.5 * (A->eve[s] + B->eve[s]);
+        rD[s] = 0.5 * (A->rhoDs[s] + B->rhoDs[s]);
+        Yf[s] = 0.5 * (A->Y[s] + B->Y[s]);
+    }
     viscous_flux(G, g, uf, 0.5 * (A->mu + B->mu), 0.5 * (A->kt + B->kt), 0.5 * (A->kv + B->kv),
-                 0.5 * (A->rhoD + B->rhoD), hs, eve, S, 0, F);
+                 rD, Yf, hs, eve, S, 0, F);
 }
 
 /* viscous flux at a wall face of cell c (isothermal, no-slip, non-catalytic); other boundary
@@ -1276,7 +1412,7 @@ static void viscous_boundary(const orc_grid *G, int c, int d, int s, int f, cons
     }
     const prim_t *w = &G->w[c];
     double uf[3] = {0, 0, 0};
-    viscous_flux(G, g, uf, w->mu, w->kt, w->kv, w->rhoD, w->hs, w->eve, S, 1, F);
+    viscous_flux(G, g, uf, w->mu, w->kt, w->kv, w->rhoDs, w->Y, w->hs, w->eve, S, 1, F);
 }
 
 /* ---------------------------------------------------------------------------------------
@@ -2004,6 +2140,16 @@ int orc_set_hcorr(orc_grid *G, int on) { G->hcorr = on != 0; return 0; }
 /* Inviscid flow (a test switch): off drops the viscous and diffusive fluxes from the residual
  * and the viscous radii from the operator (mu = k = rho D = 0 in both). */
 int orc_set_viscous(orc_grid *G, int on) { G->viscous = on != 0; return 0; }
+
+/* Transport model: 0 Sutherland viscosity with constant Prandtl and Schmidt numbers (one
+ * diffusion coefficient), 1 the species model (Blottner, Eucken, Wilke, Blanc; air only). */
+int orc_set_transport(orc_grid *G, int model)
+{
+    if (model != 0 && model != 1) return 1;
+    if (model == 1 && G->gas.mech == 0) return 1;
+    G->gas.transport = model;
+    return 0;
+}
 /* update limit f (see correct_update); 0 switches it off */
 int orc_set_update_limit(orc_grid *G, double f) { if (!(f >= 0.0)) return 1; G->update_limit = f; return 0; }
 
@@ -2212,9 +2358,10 @@ int orc_field(const orc_grid *G, const char *name, double *out)
 #define CELLF(nm, expr) if (!strcmp(name, nm)) { for (int c = 0; c < N; c++) out[c] = G->w[c].expr; return N; }
     CELLF("T", T) CELLF("Tv", Tv) CELLF("p", p) CELLF("c", c) CELLF("beta", beta) CELLF("rho", rho)
     CELLF("mu", mu) CELLF("kt", kt) CELLF("kv", kv) CELLF("rhoD", rhoD) CELLF("omega_v", omega_v)
-    CELLF("relax", relax) CELLF("Gam", Gam) CELLF("H", H)
+    CELLF("relax", relax) CELLF("Gam", Gam) CELLF("H", H) CELLF("cv", cv) CELLF("cvtr", cvtr) CELLF("cvve", cvve)
 #undef CELLF
     if (!strcmp(name, "omega")) { for (int s = 0; s < ns; s++) for (int c = 0; c < N; c++) out[(size_t)s * N + c] = G->w[c].omega[s]; return N * ns; }
+    if (!strcmp(name, "rhoDs")) { for (int s = 0; s < ns; s++) for (int c = 0; c < N; c++) out[(size_t)s * N + c] = G->w[c].rhoDs[s]; return N * ns; }
     if (!strcmp(name, "dom")) { for (int s = 0; s < ns; s++) for (int c = 0; c < N; c++) out[(size_t)s * N + c] = G->w[c].dom[s]; return N * ns; }
     if (!strcmp(name, "prs")) { for (int s = 0; s < ns; s++) for (int c = 0; c < N; c++) out[(size_t)s * N + c] = G->w[c].prs[s]; return N * ns; }
     return -1;
