@@ -189,14 +189,16 @@ cs_status cs_measure_fp64_rate(void *cuda_stream, double *gflops_out);
 /* Which kernel ran the last split sweep of g (a measurement aid, not part of the method):
  * out[0] in the numbering of the "cluster_sweep" option below (0 one launch per hyperplane,
  * 1 direct loads, 2 wavefront records, 4 one CTA per component, 5 assembled couplings exchanged
- * point to point, 6 assembled couplings with a cluster barrier; -1 before the first sweep),
+ * point to point, 6 assembled couplings with a cluster barrier, 7 assembled couplings swept by
+ * systolic warps; -1 before the first sweep),
  * out[1] its CTAs per cluster (0 for one launch per hyperplane).  Host only, no device work.
  * Errors: CS_ERR_ARG (null). */
 cs_status cs_sweep_info(cs_grid g, int out[2]);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
- * split sweeps in one launch, choosing per precision: 5 where its records can be allocated and
- * its ring fits, else for the FP32 operator 4 where it applies, else 2, and for FP64 6, else 1.
+ * split sweeps in one launch, choosing per precision: 7 where its records can be allocated and
+ * its inboxes fit, else 5 where its ring fits, else for the FP32 operator 4 where it applies,
+ * else 2, and for FP64 6, else 1.
  * 1 is a thread-block-cluster kernel reading the cell arrays directly, 2 a cluster kernel over
  * hyperplane-ordered cell records, 4 the FP32 operator's sweeps with one CTA per component
  * holding every row (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall
@@ -207,8 +209,13 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * CTAs exchange the rows at their boundaries point to point (st.async into the next CTA's
  * shared memory, one mbarrier per hyperplane; (ni + nj - 1) x (8 x element size + 8) bytes of
  * shared memory per CTA, at most 200 KiB; single grids only), 6 the FP64 couplings with one
- * cluster barrier per hyperplane (the FP32 operator falls back to 4, else 2); 0 runs one launch
- * per hyperplane.
+ * cluster barrier per hyperplane (the FP32 operator falls back to 4, else 2), 7 the same
+ * couplings swept by systolic warps: the four rows of a warp exchange results by warp shuffles
+ * and each warp waits only for the row before its first (after its last, backward), written
+ * into the warp's own inbox by the neighbouring warp or CTA with st.async and one mbarrier per
+ * hyperplane, no CTA-wide barrier per step ((ni + nj - 1) x (8 x element size + 8) bytes of
+ * shared memory per warp, at most 200 KiB per CTA, else as 5); 0 runs one launch per
+ * hyperplane.
  * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.
  * "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per component of the 2D cluster
  * sweeps (0, the default: the largest that fits; a C that does not fit the grid or the device
@@ -233,8 +240,18 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * (V/dtau + sum 2 lambda_vis) I + sum_d |A(S_d)| - V dS/dQ and the neighbours couple with
  * -(A + |A| + 2 lambda_vis)/2 and (A - |A| - 2 lambda_vis)/2.  The split operator is not
  * affected.
- * Errors: CS_ERR_ARG for an unknown name, a negative / NaN update_limit or a ci_splitting
- * other than 0 or 1. */
+ * Method option: "transport" = 0 (default): Sutherland viscosity, conductivities from constant
+ * Prandtl number 0.72, one diffusion coefficient rho D = mu / 0.5 for every species; 1: the
+ * species model (air only; Sec. 2.1 defers transport data to its references and diffuses each
+ * species with its own effective coefficient D_s): Blottner viscosity fits (Blottner, Johnson
+ * & Ellis 1971; the ions take the fit of NO+), Eucken conductivities (two temperatures:
+ * trans-rotational and vibrational-electronic parts), Wilke's mixing rule, hard-sphere binary
+ * diffusion coefficients (first Chapman-Enskog approximation, diameters from the Blottner
+ * viscosities) combined by Blanc's law into D_s, electrons diffusing with the ions (no net
+ * charge flux) and a correction velocity so that the diffusive mass fluxes sum to zero; the
+ * species radius takes max_s D_s (Eq. (vislambda)).  One more kernel per iteration.
+ * Errors: CS_ERR_ARG for an unknown name, a negative / NaN update_limit, a ci_splitting other
+ * than 0 or 1, a transport other than 0 or 1 or the species model for a perfect gas. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Dual time stepping for unsteady flow (Sec. 2.3, the dual-time form of the implicit scheme).

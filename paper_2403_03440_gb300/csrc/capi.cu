@@ -782,7 +782,7 @@ extern "C" cs_status cs_step(cs_grid g, const cs_step_opts* o, cs_step_stats* st
     int nf, nb;
     if ((st = enqueue_iteration(g, o, slot, false, &nf, &nb))) return st;
     if (g->prof) {
-      const long per[CS_NPHASE] = {2, 1, (long)g->g.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
+      const long per[CS_NPHASE] = {2L + g->g.transport, 1, (long)g->g.nd, 2, o->scheme == CS_SCHEME_SPLIT ? 1 : 2, nf, nb, 1};
       for (int p = 0; p < CS_NPHASE; ++p) g->prof_launches[p] += per[p];
       g->ev_used = slot + 1;
     }
@@ -852,9 +852,10 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2),
     // 5 assembled couplings exchanged point to point between CTAs where the ring fits (else
     // FP64: 6 then 1, FP32: 4 then 2), 6 the same FP64 couplings with a cluster barrier per
-    // hyperplane (the FP32 operator falls back to 4 then 2)
+    // hyperplane (the FP32 operator falls back to 4 then 2), 7 the assembled couplings swept by
+    // systolic warps where their inboxes fit (else as 5)
     g->L->use_cluster = value != 0.0;
-    g->L->cluster_kind = value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
+    g->L->cluster_kind = value >= 7.0 ? 6 : value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;
   }
   if (!strcmp(name, "cluster_size")) {
@@ -879,6 +880,13 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
   if (!strcmp(name, "ci_splitting")) {
     if (value != 0.0 && value != 1.0) return fail(g, CS_ERR_ARG, "ci_splitting must be 0 or 1");
     g->g.cisplit = (int)value;
+    return CS_OK;
+  }
+  if (!strcmp(name, "transport")) {
+    if (value != 0.0 && value != 1.0) return fail(g, CS_ERR_ARG, "transport must be 0 or 1");
+    if (value == 1.0 && g->L->ns < 5) return fail(g, CS_ERR_ARG, "the species transport model needs an air mixture");
+    g->g.transport = (int)value;
+    g->have_R = 0;
     return CS_OK;
   }
   return fail(g, CS_ERR_ARG, "unknown option %s", name);

@@ -71,6 +71,20 @@ __constant__ SpeciesData c_species_perfect[1] = {
     {DIATOMIC, 28.9647, 0.0, 2.88, 2, 1, 0.0},
 };
 
+// Blottner's viscosity fits mu_s = 0.1 exp((A ln T + B) ln T + C) kg/(m s) (Blottner, Johnson
+// & Ellis, Sandia report SC-RR-70-754, 1971), species order of the air table; the four other
+// ions take the fit given for NO+.
+#define CS_BLOTTNER                                                                          \
+  {                                                                                          \
+    {0.0268142, 0.3177838, -11.3155513}, {0.0449290, -0.0826158, -9.2019475},                \
+        {0.0436378, -0.0335511, -9.5767430}, {0.0115572, 0.6031679, -12.4327495},            \
+        {0.0203144, 0.4294404, -11.6031403}, {0.3020141, -3.5039791, -3.7355157},            \
+        {0.3020141, -3.5039791, -3.7355157}, {0.3020141, -3.5039791, -3.7355157},            \
+        {0.3020141, -3.5039791, -3.7355157}, {0.3020141, -3.5039791, -3.7355157},            \
+        {0.0, 0.0, -12.5},                                                                   \
+  }
+static const double kBlottnerHost[11][3] = CS_BLOTTNER;
+
 // Park's air reactions, forward rate A T^n exp(-theta/T).  Species order:
 // N2 O2 NO N O NO+ N2+ O2+ N+ O+ e-.  ln A is filled on the host from A in cm^3/(mol s).
 #define CS_EFF_N2 {1, 1, 1, 30.0 / 7.0, 30.0 / 7.0, 1, 1, 1, 30.0 / 7.0, 30.0 / 7.0, 3.0e24 / 7.0e21}
@@ -94,6 +108,13 @@ struct GasConst {
   double icbk[11];  // 1 / cbk
   double lnPRu;     // ln(p0 / R_u)
   float Rsf[11], hff[11], thvf[11];   // FP32 copies for the temperature solves' predictor
+  // species transport model (option transport = 1): Blottner fit coefficients A, B, C;
+  // Wilke's (M_r/M_s)^(1/4) and 1/sqrt(8 (1 + M_s/M_r)); hard-sphere constants
+  // hsd[s] = (5/16) sqrt(pi m_s k) / pi (sigma_s^2 = hsd sqrt(T) / mu_s), dsr[s][r] =
+  // 3/8 sqrt(k / (2 pi m_sr)) (D_sr = dsr sqrt(T) / (n sigma_sr^2)), ipm[s] = N_A / M_s
+  double blA[11], blB[11], blC[11];
+  double wm[11][11], wd[11][11];
+  double hsd[11], dsr[11][11], ipm[11];
 };
 __constant__ GasConst c_gas;
 

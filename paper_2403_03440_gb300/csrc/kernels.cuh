@@ -26,7 +26,8 @@ struct Aux {
                        CVVE = CVTR + 1, CV = CVVE + 1, MU = CV + 1, KT = MU + 1, KV = KT + 1,
                        RHOD = KV + 1, PREV = RHOD + 1, RELAX = PREV + 1, OMV = RELAX + 1,
                        PY = OMV + 1, Y = PY + 1, PRS = Y + NS, HS = PRS + NS, EVE = HS + NS,
-                       OM = EVE + NS, DOM = OM + NS, EMP = DOM + NS, COUNT = EMP + NS;
+                       OM = EVE + NS, DOM = OM + NS, EMP = DOM + NS, RHODS = EMP + NS,
+                       COUNT = RHODS + NS;
   static constexpr int NQ = NS + ND + 1 + (G::NTEMP == 2);
   static constexpr int NF = 1 + ND + 1 + (G::NTEMP == 2);
   static constexpr int NCI = NF + NS - 1;
@@ -39,6 +40,7 @@ struct DevGrid {
   int bc[6];
   int limiter, react, hcorr, nojac;
   int cisplit;            // coupled operator: 0 spectral splitting, 1 eigenvalue splitting
+  int transport;          // 0 Sutherland, constant Pr and Sc; 1 species model (k_transport)
   double efix, Tw, ulim;
   int nf[3];
   const double* S[3];
@@ -925,6 +927,109 @@ __global__ void __launch_bounds__(128, CS_CHEM_MIN_BLOCKS) k_chem(DevGrid g) {
 }
 
 // ---------------------------------------------------------------------------------------
+// K1c (option transport = 1): species transport model replacing the Sutherland / constant
+// Pr, Sc values of K1 (Sec. 2.1 defers the transport data to its references).  Blottner
+// viscosity fits (heavy species at T, electrons at Tv), Eucken conductivities (2T: k_tr,s =
+// mu_s (5/2 c_v,t + c_v,r), k_ve,s = mu_s c_v,v(Tv), electrons 5/2 mu_e c_v,t in the pool),
+// Wilke's mixing rule; hard-sphere binary diffusion coefficients in the first Chapman-Enskog
+// approximation with each species' diameter from its viscosity; Blanc's law for the effective
+// coefficient of each heavy species (self-diffusion where a species is (nearly) alone); the
+// electrons' flux follows the ions' in the face flux.  RHOD holds the largest rho D_s.
+// ---------------------------------------------------------------------------------------
+template <class G, int ND>
+__global__ void __launch_bounds__(128) k_transport(DevGrid g) {
+  using A = Aux<G, ND>;
+  constexpr int NS = G::NS;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.N) return;
+  const size_t N = g.N;
+  double* W = g.W;
+  const double T = W[A::T * N + c], Tv = W[A::TV * N + c], rho = W[A::RHO * N + c];
+  const double lnT = log(T), lnTv = G::NTEMP == 2 ? log(Tv) : lnT;
+  const double iTp = 1.0 / (G::NTEMP == 2 ? Tv : T);
+  const double sqT = sqrt(T), sqTv = G::NTEMP == 2 ? sqrt(Tv) : sqT;
+  double X[NS], mus[NS], ktr[NS], kve[NS], sig[NS];
+  double xs = 0.0, n = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const SpeciesData& d = G::sp(s);
+    const bool elec = d.kind == ELECTRON;
+    const double l = elec ? lnTv : lnT;
+    mus[s] = 0.1 * exp((c_gas.blA[s] * l + c_gas.blB[s]) * l + c_gas.blC[s]);
+    const double R = Rs<G>(s), cvt = 1.5 * R, cvr = d.kind == DIATOMIC ? R : 0.0;
+    double cvv = 0.0;
+    if (d.kind == DIATOMIC && d.thv > 0.0) {
+      const double em = W[(A::EMP + s) * N + c], x = d.thv * iTp, r = 1.0 / (1.0 - em);
+      cvv = R * x * x * em * r * r;
+    }
+    if (elec) {
+      ktr[s] = 0.0;
+      kve[s] = mus[s] * 2.5 * cvt;
+    } else if (G::NTEMP == 2) {
+      ktr[s] = mus[s] * (2.5 * cvt + cvr);
+      kve[s] = mus[s] * cvv;
+    } else {
+      ktr[s] = mus[s] * (2.5 * cvt + cvr + cvv);
+      kve[s] = 0.0;
+    }
+    const double Y = W[(A::Y + s) * N + c];
+    X[s] = Y * c_gas.invM[s];
+    xs += X[s];
+    n += rho * Y * c_gas.ipm[s];
+    sig[s] = sqrt(c_gas.hsd[s] * (elec ? sqTv : sqT) / mus[s]);
+  }
+  const double ixs = 1.0 / xs;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) X[s] *= ixs;
+  // Wilke: phi_s = sum_r X_r (1 + sqrt(mu_s / mu_r) (M_r/M_s)^(1/4))^2 / sqrt(8 (1 + M_s/M_r))
+  double sq[NS], isq[NS];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    sq[s] = sqrt(mus[s]);
+    isq[s] = 1.0 / sq[s];
+  }
+  double mu = 0.0, kt = 0.0, kv = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double phi = 0.0;
+#pragma unroll
+    for (int r = 0; r < NS; ++r) {
+      const double a = 1.0 + sq[s] * isq[r] * c_gas.wm[s][r];
+      phi += X[r] * a * a * c_gas.wd[s][r];
+    }
+    const double w = X[s] / phi;
+    mu += w * mus[s];
+    kt += w * ktr[s];
+    kv += w * kve[s];
+  }
+  W[A::MU * N + c] = mu;
+  W[A::KT * N + c] = kt;
+  W[A::KV * N + c] = G::NTEMP == 2 ? kv : 0.0;
+  // Blanc: D_s = (1 - X_s) / sum_{r != s, heavy} X_r / D_sr, D_sr = dsr sqrt(T) / (n sigma_sr^2)
+  const double sTn = sqT / n;   // D_sr = dsr sTn / sigma_sr^2
+  double rDmax = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    double rD = 0.0;
+    if (G::sp(s).kind != ELECTRON) {
+      double den = 0.0, Dss = 0.0;
+#pragma unroll
+      for (int r = 0; r < NS; ++r) {
+        if (G::sp(r).kind == ELECTRON) continue;
+        const double sr = 0.5 * (sig[s] + sig[r]);
+        if (r == s) Dss = c_gas.dsr[s][r] * sTn / (sr * sr);
+        else den += X[r] * sr * sr / (c_gas.dsr[s][r] * sTn);
+      }
+      const double D = (1.0 - X[s] > 1e-12 && den > 0.0) ? (1.0 - X[s]) / den : Dss;
+      rD = rho * D;
+    }
+    W[(A::RHODS + s) * N + c] = rD;
+    rDmax = rD > rDmax ? rD : rDmax;
+  }
+  W[A::RHOD * N + c] = rDmax;
+}
+
+// ---------------------------------------------------------------------------------------
 // Boundary ghost values (reading: far-field in/out by the freestream's normal velocity; wall
 // no-slip mirror for limiter slopes; outflow/axis copy).
 // ---------------------------------------------------------------------------------------
@@ -1154,27 +1259,50 @@ __global__ void __launch_bounds__(128) k_gradient(DevGrid g) {
 
 // Viscous / diffusive flux through S from face gradients (Sec. 2.1 tau, q, q_v and Fick
 // diffusion; the energy flux includes -k_v grad Tv).
+// rDs (nullable): per-species rho D_s of the species transport model, with Yf the face mass
+// fractions: the electrons' flux then follows from no net charge flux, J_e = M_e sum_ions J_i /
+// M_i, and a correction velocity makes the fluxes sum to zero, J_s -= Y_s sum_r J_r.  Without
+// rDs one coefficient rhoD serves every species (the fluxes then sum to zero by themselves).
 template <class G, int ND>
 __device__ void viscous(const double (*gf)[ND], const double* uf, double mu, double kt, double kv,
-                        double rhoD, const double* hs, const double* eve, const double* S,
-                        bool wall, double* F) {
+                        double rhoD, const double* rDs, const double* Yf, const double* hs,
+                        const double* eve, const double* S, bool wall, double* F) {
   constexpr int NS = G::NS, NQ = Aux<G, ND>::NQ;
   constexpr bool TWO = G::NTEMP == 2;
   constexpr int iT = ND, iTv = ND + 1, iY = ND + 1 + (TWO ? 1 : 0);
   double div = 0.0;
 #pragma unroll
   for (int a = 0; a < ND; ++a) div += gf[a][a];
-  double qd = 0.0, qvd = 0.0;
+  double Js[NS];
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
     double J = 0.0;
     if (!wall) {
+      const double r = rDs ? rDs[s] : rhoD;
 #pragma unroll
-      for (int q = 0; q < ND; ++q) J -= rhoD * gf[iY + s][q] * S[q];
+      for (int q = 0; q < ND; ++q) J -= r * gf[iY + s][q] * S[q];
     }
-    F[s] = J;
-    qd += J * hs[s];
-    if (TWO) qvd += J * eve[s];
+    Js[s] = J;
+  }
+  if (rDs && !wall) {
+    double je = 0.0, sum = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s)
+      if (s >= 5 && s < 10) je += Js[s] * c_gas.invM[s];   // the ions NO+ .. O+ of the air table
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      if (G::sp(s).kind == ELECTRON) Js[s] = je * G::sp(s).M;
+      sum += Js[s];
+    }
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Js[s] -= Yf[s] * sum;
+  }
+  double qd = 0.0, qvd = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    F[s] = Js[s];
+    qd += Js[s] * hs[s];
+    if (TWO) qvd += Js[s] * eve[s];
   }
   double work = 0.0;
 #pragma unroll
@@ -1340,7 +1468,17 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
     const double kt = 0.5 * (g.W[A::KT * N + a] + g.W[A::KT * N + b]);
     const double kv = 0.5 * (g.W[A::KV * N + a] + g.W[A::KV * N + b]);
     const double rd = 0.5 * (g.W[A::RHOD * N + a] + g.W[A::RHOD * N + b]);
-    viscous<G, ND>(gf, uf, mu, kt, kv, rd, hs, eve, S, false, Fv);
+    if (g.transport) {
+      double rDs[NS], Yf[NS];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        rDs[s] = 0.5 * (g.W[(A::RHODS + s) * N + a] + g.W[(A::RHODS + s) * N + b]);
+        Yf[s] = 0.5 * (g.W[(A::Y + s) * N + a] + g.W[(A::Y + s) * N + b]);
+      }
+      viscous<G, ND>(gf, uf, mu, kt, kv, rd, rDs, Yf, hs, eve, S, false, Fv);
+    } else {
+      viscous<G, ND>(gf, uf, mu, kt, kv, rd, nullptr, nullptr, hs, eve, S, false, Fv);
+    }
   } else {
     // ---- boundary face ----
     const int s = (pos == 0) ? -1 : +1;
@@ -1389,7 +1527,7 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
         eve[sp] = g.W[(A::EVE + sp) * N + c];
       }
       viscous<G, ND>(gf, uf, g.W[A::MU * N + c], g.W[A::KT * N + c], g.W[A::KV * N + c],
-                     g.W[A::RHOD * N + c], hs, eve, S, true, Fv);
+                     g.W[A::RHOD * N + c], nullptr, nullptr, hs, eve, S, true, Fv);
     } else if (bcode == BC_FARFIELD || bcode == BC_OUTFLOW) {
       double wi[NR], wg[NR];
       recon_load<G, ND>(g.W, N, c, wi);
@@ -3094,7 +3232,9 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
           if (!boundary_in) {
             src = xs[(q - 1) & 1][fwd ? t - 1 : t + 1];
           } else {
-            if (!p2p_wait(smem_u32(mbar + q), (uint32_t)pass) && !timed_out) {
+            // after a wait has run out the results are invalid anyway: no further waits, so
+            // that a failed exchange costs one wait bound, not one per step
+            if (!timed_out && !p2p_wait(smem_u32(mbar + q), (uint32_t)pass)) {
               timed_out = true;
               set_status(g, ST_TIMEOUT, cur.c);
             }
@@ -3127,6 +3267,187 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
           for (int k = 0; k < NF; ++k) xf[k] = xp[k];
           sf = sp;
         }
+      }
+      mat_step_load<G, T>(g, q + 4, j, on, fwd, flow, v, s, cur);
+    };
+    MatStep<G, T> m0, m1, m2, m3;
+    mat_step_load<G, T>(g, 0, j, on, fwd, flow, v, s, m0);
+    mat_step_load<G, T>(g, 1, j, on, fwd, flow, v, s, m1);
+    mat_step_load<G, T>(g, 2, j, on, fwd, flow, v, s, m2);
+    mat_step_load<G, T>(g, 3, j, on, fwd, flow, v, s, m3);
+    for (int q = 0; q <= H; q += 4) {
+      step(q, m0);
+      if (q + 1 <= H) step(q + 1, m1);
+      if (q + 2 <= H) step(q + 2, m2);
+      if (q + 3 <= H) step(q + 3, m3);
+    }
+    __syncthreads();
+  }
+  // no CTA leaves while a neighbour may still write into its shared memory
+  cluster_arrive();
+  cluster_wait();
+}
+
+// Systolic form of the assembled-coupling sweep (both passes in one cluster launch): the four
+// rows of a warp exchange their results with warp shuffles, and each warp waits only for the
+// row before its first row (forward; after its last row backward), which a neighbouring warp of
+// the same CTA, or the neighbouring CTA, writes into the warp's inbox with st.async, one
+// mbarrier per hyperplane step.  No CTA-wide barrier per step: each warp advances as soon as
+// its own inputs are there (the hyperplane order is kept: a row's cell of step q needs the row
+// before it at step q - 1).  Dynamic shared memory: per warp an inbox [H + 1][kMatSlots] of T,
+// then the warps' [H + 1] mbarriers.  Waits are bounded (ST_TIMEOUT).
+template <class T>
+__host__ __device__ inline size_t sys_smem_bytes(int ni, int nj, int warps) {
+  return (size_t)warps * (ni + nj - 1) * (kMatSlots * sizeof(T) + sizeof(unsigned long long));
+}
+constexpr int kSysRows = 32 / kMatSlots;   // rows of one warp
+
+template <class G, class T>
+__global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_sys(DevGrid g, int R) {
+  using M = MatRec<G, T>;
+  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
+  extern __shared__ __align__(16) unsigned char sys_dyn[];
+  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
+  const int W = (R + kSysRows - 1) / kSysRows;                 // warps per CTA
+  T* inbox = reinterpret_cast<T*>(sys_dyn);                    // [W][H + 1][kMatSlots]
+  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(inbox + (size_t)W * (H + 1) * kMatSlots);
+  const size_t N = g.N;
+  const int comp = blockIdx.x / (int)cluster_nctarank();      // 0: flow block, else a species group
+  const unsigned rank = cluster_ctarank();
+  const unsigned nrank = cluster_nctarank();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int tl = lane / kMatSlots, v = lane % kMatSlots;      // row within the warp, slot
+  const int t = warp * kSysRows + tl;                          // row within the CTA
+  const int j = rank * R + t;
+  const bool per = g.bc[0] == BC_PERIODIC;
+  const bool flow = comp == 0;
+  const int s = (comp - 1) * kMatSpecies + v;
+  const bool on = t < R && j < nj && (flow ? v < NF : s < G::NS);
+  const int nsend = flow ? NF : (G::NS - (comp - 1) * kMatSpecies < kMatSpecies ? G::NS - (comp - 1) * kMatSpecies : kMatSpecies);
+  // the warp's first and last rows within the CTA
+  const int tw0 = warp * kSysRows, tw1 = (tw0 + kSysRows - 1 < R - 1) ? tw0 + kSysRows - 1 : R - 1;
+  for (int q = threadIdx.x; q < W * (H + 1); q += blockDim.x)
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + q)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  __syncthreads();
+  bool timed_out = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fwd = pass == 0;
+    // each warp arms its inbox for this pass: the row that receives (first row forward, last
+    // row backward) gets its neighbouring row's result of step q - 1 in slot q
+    {
+      const int tc = fwd ? tw0 : tw1;
+      const int jc = (int)rank * R + tc;
+      const bool row_ok = tc < R && jc < nj && (fwd ? jc > 0 : jc + 1 < nj);
+      for (int q = lane; q <= H; q += 32) {
+        const int ic = (fwd ? q : H - q) - jc;
+        const uint32_t bytes = (row_ok && ic >= 0 && ic < ni) ? nsend * (uint32_t)sizeof(T) : 0u;
+        unsigned long long st;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
+                     : "=l"(st) : "r"(smem_u32(mbar + (size_t)warp * (H + 1) + q)), "r"(bytes) : "memory");
+      }
+    }
+    cluster_arrive();
+    cluster_wait();
+    T xp[NF], xu[NF], xf[NF], pw[NP];   // flow: own and neighbouring row's previous results
+    T sp = 0, su = 0, sf = 0, pc = 0;
+#pragma unroll
+    for (int k = 0; k < NF; ++k) xp[k] = xu[k] = xf[k] = T(0);
+#pragma unroll
+    for (int k = 0; k < NP; ++k) pw[k] = T(0);
+    if (on && per) {
+      const T* pr = reinterpret_cast<const T*>(g.SMC) + N * M::CELL + (size_t)j * M::ROW;
+      if (flow) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) pw[k] = pr[(fwd ? 0 : BLK) + v * NP + k];
+      } else {
+        pc = pr[2 * BLK + (fwd ? 0 : 1)];
+      }
+    }
+    double* out = fwd ? g.dQs : g.dQ;
+    const size_t orow = (size_t)(flow ? v : NF + s) * N;
+    const bool hasj = fwd ? j > 0 : j < nj - 1;
+    const bool sends = fwd ? j + 1 < nj : j > 0;
+    // receiving row of this warp (its neighbour lives in another warp or CTA) and sending row
+    const bool recv = t == (fwd ? tw0 : tw1);
+    const bool send = t == (fwd ? tw1 : tw0);
+    // where the sending row's results go: the next warp's inbox, or the neighbouring CTA's
+    int dwarp;
+    unsigned dpeer;
+    if (fwd) {
+      dwarp = t == R - 1 ? 0 : warp + 1;
+      dpeer = t == R - 1 ? rank + 1 : rank;
+    } else {
+      dwarp = t == 0 ? W - 1 : warp - 1;
+      dpeer = t == 0 ? rank - 1 : rank;
+    }
+    const bool dvalid = dpeer < nrank;
+    const int nb_lane = (fwd ? tl - 1 : tl + 1) * kMatSlots;     // neighbouring row in the warp
+    const int own_lane = tl * kMatSlots;
+    auto step = [&](int q, MatStep<G, T>& cur) {
+      T acc = 0;
+      if (cur.act) {
+        acc = fwd ? cur.d * cur.base : cur.base;
+        const bool hasi = fwd ? cur.i > 0 : cur.i < ni - 1;
+        const bool wrap = per && cur.i == (fwd ? ni - 1 : 0);
+        if (flow) {
+          if (hasi) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += cur.bi[k] * xp[k];
+          }
+          if (wrap) {
+#pragma unroll
+            for (int k = 0; k < NF; ++k) acc += pw[k] * xf[k];
+          }
+        } else {
+          if (hasi) acc += (cur.d * cur.bi[0]) * sp;
+          if (wrap) acc += cur.d * pc * sf;
+        }
+        if (hasj) {
+          if (recv) {
+            const uint32_t bar = smem_u32(mbar + (size_t)warp * (H + 1) + q);
+            if (!timed_out && !p2p_wait(bar, (uint32_t)pass)) {   // (one wait bound at most)
+              timed_out = true;
+              set_status(g, ST_TIMEOUT, cur.c);
+            }
+            const T* src = inbox + ((size_t)warp * (H + 1) + q) * kMatSlots;
+            if (flow) {
+#pragma unroll
+              for (int k = 0; k < NF; ++k) acc += cur.bj[k] * src[k];
+            } else {
+              acc += (cur.d * cur.bj[0]) * src[v];
+            }
+          } else {
+            if (flow) {
+#pragma unroll
+              for (int k = 0; k < NF; ++k) acc += cur.bj[k] * xu[k];
+            } else {
+              acc += (cur.d * cur.bj[0]) * su;
+            }
+          }
+        }
+        if (send && sends && dvalid) {
+          const uint32_t dst = cluster_map(smem_u32(inbox + ((size_t)dwarp * (H + 1) + q + 1) * kMatSlots + v), dpeer);
+          st_async(dst, acc, cluster_map(smem_u32(mbar + (size_t)dwarp * (H + 1) + q + 1), dpeer));
+        }
+        out[orow + cur.c] = (double)acc;
+      }
+      // the row's own results and the neighbouring row's, for the next step (every lane takes
+      // part in the shuffles; inactive lanes carry zeros)
+      if (flow) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) {
+          xp[k] = __shfl_sync(0xffffffffu, acc, own_lane + k);
+          xu[k] = __shfl_sync(0xffffffffu, acc, (nb_lane + k) & 31);
+        }
+      } else {
+        sp = acc;
+        su = __shfl_sync(0xffffffffu, acc, (nb_lane + v) & 31);
+      }
+      if (cur.act && cur.i == (fwd ? 0 : ni - 1)) {
+#pragma unroll
+        for (int k = 0; k < NF; ++k) xf[k] = xp[k];
+        sf = sp;
       }
       mat_step_load<G, T>(g, q + 4, j, on, fwd, flow, v, s, cur);
     };
