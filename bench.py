@@ -196,6 +196,26 @@ def step_kwargs(iters):
 
 
 ORACLE_BUILD = "gcc -O3 -ffp-contract=off, one thread"
+ORACLE_BUILD_OMP = ("gcc -O3 -ffp-contract=off -fopenmp: per-cell and per-face loops (primitives, "
+                    "chemistry, gradients, fluxes, radii) on all host cores, sweeps serial")
+
+
+def oracle_rate_all_cores(iters, seconds_cap=30.0):
+    """The oracle's OpenMP build on every host core, timed in a child process (the serial and
+    the OpenMP oracle libraries cannot share one process): (Mcell-iter/s, iterations,
+    seconds, threads) or None."""
+    env = dict(os.environ)
+    env.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-leg", "omp", "--cpu-leg-iters", str(iters),
+           "--cpu-leg-seconds", str(seconds_cap)]
+    if C3:
+        cmd += ["--workload", "c3"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return d["value"], d["iters"], d["seconds"], int(env["OMP_NUM_THREADS"])
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError, KeyError):
+        return None
 
 
 def oracle_rate(iters, seconds_cap=30.0):
@@ -484,6 +504,9 @@ def main():
     ap.add_argument("--no-convergence", action="store_true",
                     help="skip the C1 time-to-1e-8 runs of the default line")
     ap.add_argument("--no-batch", action="store_true", help="skip the batch throughput of the default line")
+    ap.add_argument("--cpu-leg", choices=["omp"], default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-leg-iters", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-leg-seconds", type=float, default=30.0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     global PRECISION, WORKLOAD, C3, SCHEME
     SCHEME = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}[args.scheme]
@@ -501,6 +524,13 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.cpu_leg == "omp":
+        # child process of oracle_rate_all_cores: the OpenMP oracle only, no GPU
+        import oracle
+        oracle.use_openmp()
+        v, it, dt = oracle_rate(args.cpu_leg_iters, args.cpu_leg_seconds)
+        print(json.dumps({"value": v, "iters": it, "seconds": dt}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args, rank)
         return
@@ -766,6 +796,11 @@ def run_iteration(args, rank, world, local):
         cpu = {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
                "sample": f"{it} oracle iterations of the full 384x256 grid from the freestream ({dt:.1f} s)",
                "host_cpu": model, "host_logical_cores": ncpu, "build": ORACLE_BUILD}
+        allc = oracle_rate_all_cores(3, 30.0)
+        if allc is not None:
+            cpu["all_cores"] = {"value": allc[0], "unit": "Mcell-iter/s", "cores": allc[3],
+                                "sample": f"{allc[1]} oracle iterations of the same grid ({allc[2]:.1f} s)",
+                                "build": ORACLE_BUILD_OMP}
     if rank == 0:
         line = {
             "metric": "Mcell-iter/s", "value": value, "unit": "Mcell-iter/s", "n_gpus": world,

@@ -196,9 +196,8 @@ cs_status cs_measure_fp64_rate(void *cuda_stream, double *gflops_out);
 cs_status cs_sweep_info(cs_grid g, int out[2]);
 
 /* Implementation options (not part of the method): "cluster_sweep" = 3 (default) runs the 2D
- * split sweeps in one launch, choosing per precision: 7 where its records can be allocated and
- * its inboxes fit, else 5 where its ring fits, else for the FP32 operator 4 where it applies,
- * else 2, and for FP64 6, else 1.
+ * split sweeps in one launch, choosing per precision: 5 where its records can be allocated and
+ * its ring fits, else for the FP32 operator 4 where it applies, else 2, and for FP64 6, else 1.
  * 1 is a thread-block-cluster kernel reading the cell arrays directly, 2 a cluster kernel over
  * hyperplane-ordered cell records, 4 the FP32 operator's sweeps with one CTA per component
  * holding every row (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall

@@ -14,23 +14,41 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cs_oracle.c")
 _OUT = os.path.join(_HERE, "_build", "libcs_oracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "libcs_oracle_omp.so")
 _lib = None
+_openmp = False
+
+
+def use_openmp():
+    """Load the OpenMP build (all host cores; used only to time the oracle) instead of the
+    serial one.  Must be called before the first oracle call of the process."""
+    global _openmp
+    if _lib is not None:
+        raise RuntimeError("the oracle library is already loaded")
+    _openmp = True
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
 
 
-def build(force=False):
+def build(force=False, openmp=None):
     """Compile the oracle with gcc (FP64, -O3, no contraction into FMA, no host-specific
-    instruction set: the same results on every host)."""
-    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
-        return _OUT
-    tmp = _OUT + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O3", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    instruction set: the same results on every host); openmp=True builds the variant whose
+    independent per-cell and per-face loops run on all host cores (timing only)."""
+    if openmp is None:
+        openmp = _openmp
+    out = _OUT_OMP if openmp else _OUT
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    tmp = out + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O3", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared"]
+    if openmp:
+        cmd.append("-fopenmp")
+    cmd += ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _OUT)
-    return _OUT
+    os.replace(tmp, out)
+    return out
 
 
 def lib():

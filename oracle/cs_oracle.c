@@ -1259,6 +1259,7 @@ static void grad_boundary_value(const orc_grid *G, int c, int d, int s, double *
 static void compute_gradients(orc_grid *G)
 {
     int ng = ngrad(G), nd = G->nd;
+#pragma omp parallel for schedule(static)
     for (int c = 0; c < G->ncell; c++) {
         int o[3];
         cell_coords(G, c, o);
@@ -1419,20 +1420,32 @@ static void viscous_boundary(const orc_grid *G, int c, int d, int s, int f, cons
  * Residual R(Q) (Sec. 2.2, Eq. (iterate)): R = sum over faces of (F_inv + F_vis).S_out
  * minus V * S.  dQ/dt V = -R.
  * ------------------------------------------------------------------------------------- */
+/* Every cell is independent; the first failing cell (lowest index) is reported.  (The
+ * OpenMP build of the oracle, used only to time it on all host cores, runs this loop, the
+ * gradients, the face fluxes and the spectral radii in parallel; results do not change.) */
 static int compute_primitives(orc_grid *G)
 {
-    int nst = G->nq;
-    for (int c = 0; c < G->ncell; c++) {
+    int nst = G->nq, N = G->ncell, bad = N, badst = 0;
+#pragma omp parallel for schedule(static) reduction(min : bad)
+    for (int c = 0; c < N; c++) {
         double q[NQMAX];
-        for (int v = 0; v < nst; v++) q[v] = G->Q[(size_t)v * G->ncell + c];
+        for (int v = 0; v < nst; v++) q[v] = G->Q[(size_t)v * N + c];
         double Tg = G->w[c].T, Tvg = G->w[c].Tv;
         int st = prim_from_cons(&G->gas, G->nd, q, Tg, Tvg, &G->w[c]);
         if (st) {
-            G->status_cell = c;
-            snprintf(G->err, sizeof(G->err), "primitive recovery failed (code %d) at cell %d", st, c);
-            return st == 3 ? 5 : 4;
+            if (c < bad) bad = c;
+            continue;
         }
         if (G->react) cell_sources(&G->gas, G->nd, &G->w[c]);
+    }
+    if (bad < N) {
+        double q[NQMAX];
+        prim_t w;
+        for (int v = 0; v < nst; v++) q[v] = G->Q[(size_t)v * N + bad];
+        badst = prim_from_cons(&G->gas, G->nd, q, G->w[bad].T, G->w[bad].Tv, &w);
+        G->status_cell = bad;
+        snprintf(G->err, sizeof(G->err), "primitive recovery failed (code %d) at cell %d", badst, bad);
+        return badst == 3 ? 5 : 4;
     }
     return 0;
 }
@@ -1468,6 +1481,7 @@ static int residual(orc_grid *G)
     /* face fluxes, each face once */
     for (int d = 0; d < nd; d++) {
         int li = G->n[0] + (d == 0), lj = G->n[1] + (d == 1), lk = (nd == 3) ? G->n[2] + (d == 2) : 1;
+#pragma omp parallel for collapse(2) schedule(static)
         for (int k = 0; k < lk; k++)
             for (int j = 0; j < lj; j++)
                 for (int i = 0; i < li; i++) {
@@ -1554,6 +1568,7 @@ static void absjac_ci(const orc_grid *G, const prim_t *w, const double *S, const
 static void spectral(orc_grid *G, double cfl)
 {
     int nd = G->nd, ns = G->gas.ns;
+#pragma omp parallel for schedule(static)
     for (int c = 0; c < G->ncell; c++) {
         int o[3];
         cell_coords(G, c, o);

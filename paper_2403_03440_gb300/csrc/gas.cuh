@@ -121,6 +121,33 @@ __constant__ GasConst c_gas;
 // 2^(j/64), j = 0..63, for exp_tab (filled on the host with exp2; read through the L1 cache)
 __device__ double g_exp2_64[64];
 
+// ln(1 + j/256) and 1/(1 + j/256), j = 0..255, for log_tab (filled on the host)
+__device__ double g_lnF_256[256];
+__device__ double g_invF_256[256];
+
+// Natural logarithm by Tang's table-driven method (P. T. P. Tang, ACM Trans. Math. Softw.
+// 16(4), 1990), with 256 table entries: x = 2^k y, y in [1, 2), F = 1 + j/256 the leading eight
+// bits of y's mantissa, so that ln x = k ln2 + ln F + ln(1 + u) with u = (y - F)/F, 0 <= u <
+// 1/256 (y - F is exact); ln(1 + u) from its Taylor series to degree 6 (truncation below 2e-18).
+// Absolute error a few units of 1e-17 for the arguments of this library (temperatures, 1 -
+// exp(-theta/T)); non-normal or non-finite arguments take CUDA's log.
+__device__ __forceinline__ double log_tab(double x) {
+  if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) return log(x);
+  const long long b = __double_as_longlong(x);
+  const int k = (int)((b >> 52) & 0x7ff) - 1023;
+  const int j = (int)((b >> 44) & 0xff);
+  const double y = __longlong_as_double((b & 0xFFFFFFFFFFFFFLL) | 0x3FF0000000000000LL);
+  const double F = __longlong_as_double(0x3FF0000000000000LL | ((long long)j << 44));
+  const double u = (y - F) * __ldg(&g_invF_256[j]);
+  double p = fma(u, -1.0 / 6.0, 0.2);
+  p = fma(u, p, -0.25);
+  p = fma(u, p, 1.0 / 3.0);
+  p = fma(u, p, -0.5);
+  p = fma(u, p, 1.0);
+  p *= u;
+  return fma((double)k, 0.6931471805599453, __ldg(&g_lnF_256[j]) + p);
+}
+
 // Exponential by Tang's table-driven method (P. T. P. Tang, ACM Trans. Math. Softw. 15(2),
 // 1989), with 64 table entries: x = (64 m + j) ln2/64 + r, |r| <= ln2/128, so that
 // exp(x) = 2^m 2^(j/64) exp(r) with exp(r) - 1 from its Taylor series to degree 5 (truncation

@@ -492,7 +492,7 @@ __device__ __forceinline__ void gibbs(int s, double iT, double lnT, double em, d
     h += 1.0;
     if (d.thv > 0.0) {
       const double x = d.thv * iT;
-      g += log(1.0 - em);
+      g += log_tab(1.0 - em);
       h += x * em * r;
     }
   }
@@ -695,8 +695,8 @@ __device__ __forceinline__ void chemistry(const double* rhos, double T, double T
     for (int k = 0; k < NS * NS; ++k) c.J[k] = 0.0;
   c.T = T;
   c.Tv = Tv;
-  c.lnT = log(T);
-  c.lnTv = (G::NTEMP == 2) ? log(Tv) : c.lnT;
+  c.lnT = log_tab(T);
+  c.lnTv = (G::NTEMP == 2) ? log_tab(Tv) : c.lnT;
   c.iT = 1.0 / T;
   c.iTv = (G::NTEMP == 2) ? 1.0 / Tv : c.iT;
   c.lnTa = 0.5 * (c.lnT + c.lnTv);
@@ -945,7 +945,7 @@ __global__ void __launch_bounds__(128) k_transport(DevGrid g) {
   const size_t N = g.N;
   double* W = g.W;
   const double T = W[A::T * N + c], Tv = W[A::TV * N + c], rho = W[A::RHO * N + c];
-  const double lnT = log(T), lnTv = G::NTEMP == 2 ? log(Tv) : lnT;
+  const double lnT = log_tab(T), lnTv = G::NTEMP == 2 ? log_tab(Tv) : lnT;
   const double iTp = 1.0 / (G::NTEMP == 2 ? Tv : T);
   const double sqT = sqrt(T), sqTv = G::NTEMP == 2 ? sqrt(Tv) : sqT;
   double X[NS], mus[NS], ktr[NS], kve[NS], sig[NS];
@@ -955,7 +955,7 @@ __global__ void __launch_bounds__(128) k_transport(DevGrid g) {
     const SpeciesData& d = G::sp(s);
     const bool elec = d.kind == ELECTRON;
     const double l = elec ? lnTv : lnT;
-    mus[s] = 0.1 * exp((c_gas.blA[s] * l + c_gas.blB[s]) * l + c_gas.blC[s]);
+    mus[s] = 0.1 * exp_tab((c_gas.blA[s] * l + c_gas.blB[s]) * l + c_gas.blC[s]);
     const double R = Rs<G>(s), cvt = 1.5 * R, cvr = d.kind == DIATOMIC ? R : 0.0;
     double cvv = 0.0;
     if (d.kind == DIATOMIC && d.thv > 0.0) {
@@ -3119,10 +3119,105 @@ __device__ __forceinline__ bool p2p_wait(uint32_t bar, uint32_t parity) {
   return false;
 }
 
-// dynamic shared memory of k_split_p2p: the ring [H + 1][kMatSlots] of T, then H + 1 mbarriers
+// Inputs of one thread for one hyperplane step of k_split_p2p, staged in shared memory by
+// cp.async kP2PStageD steps ahead (one slot per thread and step, a ring of kP2PStageD + 1
+// slots): the coupling rows bi, bj (NP elements of T each; species: the two coefficients), then
+// the raw FP64 diagonal inverse d and base (right-hand side forward, forward result backward).
+constexpr int kP2PStageD = 6;
+template <class T, int NP>
+struct P2PSlot {
+  static constexpr int BYTES = 2 * NP * (int)sizeof(T) + 2 * (int)sizeof(double);
+  static_assert(BYTES % 16 == 0, "slots start on 16 bytes");
+};
+// dynamic shared memory of k_split_p2p: the ring [H + 1][kMatSlots] of T, H + 1 mbarriers, then
+// (from a 16-byte boundary) the staging ring [kP2PStageD + 1][threads] of slots
 template <class T>
-__host__ __device__ inline size_t p2p_smem_bytes(int ni, int nj) {
-  return (size_t)(ni + nj - 1) * (kMatSlots * sizeof(T) + sizeof(unsigned long long));
+__host__ __device__ inline size_t p2p_ring_bytes(int ni, int nj) {
+  return ((size_t)(ni + nj - 1) * (kMatSlots * sizeof(T) + sizeof(unsigned long long)) + 15) / 16 * 16;
+}
+template <class T, int NP>
+__host__ __device__ inline size_t p2p_smem_bytes(int ni, int nj, int threads) {
+  return p2p_ring_bytes<T>(ni, nj) + (size_t)(kP2PStageD + 1) * threads * P2PSlot<T, NP>::BYTES;
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Issue the copies of step q's inputs of this thread into its slot (nothing for a step whose
+// cell does not exist; the caller commits one group per step).
+template <class G, class T>
+__device__ __forceinline__ void p2p_stage_issue(const DevGrid& g, int q, int j, bool on, bool fwd,
+                                                bool flow, int v, int s, unsigned char* slot) {
+  using M = MatRec<G, T>;
+  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
+  const int ni = g.ni, H = ni + g.nj - 2;
+  const int i = (fwd ? q : H - q) - j;
+  if (!(on && q <= H && i >= 0 && i < ni)) return;
+  const size_t N = g.N;
+  const int c = i + ni * j;
+  const T* rec = reinterpret_cast<const T*>(g.SMC) + (size_t)c * M::CELL;
+  T* bi = reinterpret_cast<T*>(slot);
+  T* bj = bi + NP;
+  double* db = reinterpret_cast<double*>(bj + NP);
+  if (flow) {
+    const T* ri = rec + (fwd ? 0 : 2 * BLK) + v * NP;
+    const T* rj = rec + (fwd ? BLK : 3 * BLK) + v * NP;
+#pragma unroll
+    for (int k = 0; k < NP * (int)sizeof(T) / 16; ++k) {
+      cp_async16(reinterpret_cast<char*>(bi) + 16 * k, reinterpret_cast<const char*>(ri) + 16 * k);
+      cp_async16(reinterpret_cast<char*>(bj) + 16 * k, reinterpret_cast<const char*>(rj) + 16 * k);
+    }
+    cp_async8(db, g.invD + ((G::NTEMP == 2 && v == NF - 1) ? N : 0) + c);
+    cp_async8(db + 1, fwd ? g.rhsF + v * N + c : g.dQs + v * N + c);
+  } else {
+    const T* co = rec + 4 * BLK + (fwd ? 0 : 2);
+    if (sizeof(T) == 8) {
+      cp_async16(bi, co);            // the two coefficients, one 16-byte piece
+    } else {
+      cp_async4(bi, co);
+      cp_async4(bj, co + 1);
+    }
+    cp_async8(db, g.invD + (2 + s) * N + c);
+    cp_async8(db + 1, fwd ? g.R + (size_t)s * N + c : g.dQs + (size_t)(NF + s) * N + c);
+  }
+}
+// Step q's inputs from this thread's slot (valid once the slot's copies have completed)
+template <class G, class T>
+__device__ __forceinline__ void p2p_stage_read(const DevGrid& g, int q, int j, bool on, bool fwd,
+                                               bool flow, const unsigned char* slot,
+                                               MatStep<G, T>& m) {
+  using M = MatRec<G, T>;
+  constexpr int NP = M::NP;
+  const int ni = g.ni, H = ni + g.nj - 2;
+  const int i = (fwd ? q : H - q) - j;
+  m.act = on && q <= H && i >= 0 && i < ni;
+  m.i = i;
+  if (!m.act) return;
+  m.c = i + ni * j;
+  const T* bi = reinterpret_cast<const T*>(slot);
+  const T* bj = bi + NP;
+  const double* db = reinterpret_cast<const double*>(bj + NP);
+  if (flow) {
+#pragma unroll
+    for (int k = 0; k < NP; ++k) { m.bi[k] = bi[k]; m.bj[k] = bj[k]; }
+    m.d = (T)db[0];
+    m.base = (T)db[1];
+  } else {
+    if (sizeof(T) == 8) {
+      m.bi[0] = bi[0];
+      m.bj[0] = bi[1];
+    } else {
+      m.bi[0] = bi[0];
+      m.bj[0] = bj[0];
+    }
+    m.d = (T)db[0];
+    m.base = (T)(fwd ? -db[1] : db[1]);
+  }
 }
 // one element into another CTA's shared memory, completing bytes on that CTA's mbarrier
 __device__ __forceinline__ void st_async(uint32_t dst, double v, uint32_t bar) {
@@ -3143,6 +3238,9 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
   const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
   T* ring = reinterpret_cast<T*>(p2p_dyn);
   unsigned long long* mbar = reinterpret_cast<unsigned long long*>(ring + (size_t)(H + 1) * kMatSlots);
+  constexpr int SB = P2PSlot<T, NP>::BYTES, S = kP2PStageD + 1;
+  unsigned char* stage = p2p_dyn + p2p_ring_bytes<T>(ni, nj);
+  auto slot_of = [&](int q) { return stage + ((size_t)(q % S) * blockDim.x + threadIdx.x) * SB; };
   const size_t N = g.N;
   const int comp = blockIdx.x / (int)cluster_nctarank();   // 0: flow block, else a species group
   const unsigned rank = cluster_ctarank();
@@ -3174,6 +3272,7 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
                      : "=l"(st) : "r"(smem_u32(mbar + q)), "r"(bytes) : "memory");
       }
     }
+    if (!fwd) __threadfence();   // forward results are read back through cp.async (L2)
     cluster_arrive();
     cluster_wait();
     T xp[NF], xf[NF], pw[NP];   // flow: the row's previous and first results, wrap block row
@@ -3199,9 +3298,13 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
     const unsigned peer = fwd ? rank + 1 : rank - 1;
     const bool hasj = fwd ? j > 0 : j < nj - 1;
     const bool sends = fwd ? j + 1 < nj : j > 0;
-    // the inputs of step q are loaded four steps ahead, into the buffer of step q mod 4 right
-    // after step q - 4 has used it: the loads have three steps to arrive
-    auto step = [&](int q, MatStep<G, T>& cur) {
+    // the inputs of step q were copied kP2PStageD steps ahead into this thread's slot q mod S
+    auto step = [&](int q) {
+      cp_async_wait<kP2PStageD - 1>();    // this thread's copies of step q have landed
+      MatStep<G, T> cur;
+      p2p_stage_read<G, T>(g, q, j, on, fwd, flow, slot_of(q), cur);
+      p2p_stage_issue<G, T>(g, q + kP2PStageD, j, on, fwd, flow, v, s, slot_of(q + kP2PStageD));
+      cp_async_commit();                   // one group per step, possibly empty
       // the row's own earlier cells (and the periodic wrap) need no other row: coupled before
       // this step's synchronisation
       T acc = 0;
@@ -3268,19 +3371,15 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
           sf = sp;
         }
       }
-      mat_step_load<G, T>(g, q + 4, j, on, fwd, flow, v, s, cur);
     };
-    MatStep<G, T> m0, m1, m2, m3;
-    mat_step_load<G, T>(g, 0, j, on, fwd, flow, v, s, m0);
-    mat_step_load<G, T>(g, 1, j, on, fwd, flow, v, s, m1);
-    mat_step_load<G, T>(g, 2, j, on, fwd, flow, v, s, m2);
-    mat_step_load<G, T>(g, 3, j, on, fwd, flow, v, s, m3);
-    for (int q = 0; q <= H; q += 4) {
-      step(q, m0);
-      if (q + 1 <= H) step(q + 1, m1);
-      if (q + 2 <= H) step(q + 2, m2);
-      if (q + 3 <= H) step(q + 3, m3);
+#pragma unroll 1
+    for (int q = 0; q < kP2PStageD; ++q) {
+      p2p_stage_issue<G, T>(g, q, j, on, fwd, flow, v, s, slot_of(q));
+      cp_async_commit();
     }
+#pragma unroll 1
+    for (int q = 0; q <= H; ++q) step(q);
+    cp_async_wait<0>();
     __syncthreads();
   }
   // no CTA leaves while a neighbour may still write into its shared memory

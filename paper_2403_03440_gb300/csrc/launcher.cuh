@@ -170,6 +170,13 @@ struct LauncherT : Launcher {
     for (int j = 0; j < 64; ++j) tab[j] = exp2(j / 64.0);
     e = cudaMemcpyToSymbol(g_exp2_64, tab, sizeof tab);
     if (e != cudaSuccess) return e;
+    double lnF[256], invF[256];
+    for (int j = 0; j < 256; ++j) {
+      lnF[j] = log1p(j / 256.0);
+      invF[j] = 1.0 / (1.0 + j / 256.0);
+    }
+    if ((e = cudaMemcpyToSymbol(g_lnF_256, lnF, sizeof lnF)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyToSymbol(g_invF_256, invF, sizeof invF)) != cudaSuccess) return e;
     return cudaMemcpyToSymbol(c_gas, &gc, sizeof gc);
   }
 
@@ -285,7 +292,7 @@ struct LauncherT : Launcher {
     // measured on GB300: the assembled couplings exchanged point to point (both precisions),
     // then in FP32 the one-CTA-per-component kernel (where nj fits) and the wavefront-record
     // kernel, in FP64 the assembled couplings with a cluster barrier and the direct-load kernel
-    const int kind = cluster_kind ? cluster_kind : 6;
+    const int kind = cluster_kind ? cluster_kind : 4;
     if (kind >= 4) {
       // 6: systolic warps, then point to point, then (FP64) the cluster barrier; 4: point to
       // point, then the barrier; 5: the barrier
@@ -341,7 +348,7 @@ struct LauncherT : Launcher {
   }
 
   void prepare(const DevGrid& g, bool mixed) override {
-    const int kind = cluster_kind ? cluster_kind : 6;
+    const int kind = cluster_kind ? cluster_kind : 4;
     if (kind >= 4 && g.SMC) {
       if (mixed) {
         if (kind != 5) mat_cluster_size<float>(g, true);
@@ -462,7 +469,7 @@ struct LauncherT : Launcher {
   // allocated only then: for the FP32 operator they serve only k_split_p2p, whose ring may not
   // fit the grid.)
   bool mat_usable(const DevGrid& g, bool mixed) override {
-    const int kind = cluster_kind ? cluster_kind : 6;
+    const int kind = cluster_kind ? cluster_kind : 4;
     if (ND != 2 || !use_cluster || cluster_warps == 1 || kind < 4) return false;
     if (mixed) return kind != 5 && (mat_cluster_size<float>(g, true) > 0 || (kind == 6 && mat_cluster_size<float>(g, true, true) > 0));
     return (kind != 5 && mat_cluster_size<double>(g, true) > 0) ||
@@ -478,7 +485,7 @@ struct LauncherT : Launcher {
       return smem <= kP2PMaxSmem && cluster_fits(k_split_sys<G, T>, C, warps, mat_species_groups<G>(), smem, kP2PMaxSmem);
     }
     if (!p2p) return std::is_same<T, double>::value && cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
-    const size_t smem = p2p_smem_bytes<T>(g.ni, g.nj);
+    const size_t smem = p2p_smem_bytes<T, MatRec<G, T>::NP>(g.ni, g.nj, 32 * warps);
     return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G, T>, C, warps, mat_species_groups<G>(), smem, kP2PMaxSmem);
   }
   template <class T>
@@ -525,7 +532,7 @@ struct LauncherT : Launcher {
       cfg.gridDim = dim3(C * (1 + mat_species_groups<G>()));
       cfg.blockDim = dim3((kMatSlots * R + 31) / 32 * 32);
       cfg.dynamicSmemBytes = sys ? sys_smem_bytes<T>(g.ni, g.nj, (kMatSlots * R + 31) / 32)
-                                 : (p2p ? p2p_smem_bytes<T>(g.ni, g.nj) : 0);
+                                 : (p2p ? p2p_smem_bytes<T, MatRec<G, T>::NP>(g.ni, g.nj, (kMatSlots * R + 31) / 32 * 32) : 0);
       cfg.stream = st;
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = C;

@@ -64,7 +64,7 @@ def test_gradients_match_oracle(n):
     blocks = mlp.unpack(np.arange(mlp.NPARAM))
     for name, idx in blocks.items():
         idx = idx.ravel()
-        assert rel_l2(g[idx], go[idx]) < 3e-2, name
+        assert rel_l2(g[idx], go[idx]) < 1e-2, name      # measured: <= 4e-5
 
 
 def test_training_follows_oracle_and_reduces_loss():

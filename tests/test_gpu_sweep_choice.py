@@ -5,8 +5,8 @@ memory on grids with ni + nj - 1 > 682 (FP64).  The opt-in limit is a property o
 shared by every grid, so a smaller grid probing the kernel after a larger one must not lower
 it: the larger grid would then fail to launch the kernel and fall back to another sweep.
 These tests alternate iterations of two grids of different sizes and check, through
-cs_sweep_info, that both keep the chosen kernel (5: point to point between CTAs; 7: systolic
-warps, the default, whose per-warp inboxes also exceed 48 KiB here), and that the large grid's
+cs_sweep_info, that both keep the chosen kernel (5: point to point between CTAs, the default;
+7: systolic warps, whose per-warp inboxes also exceed 48 KiB here), and that the large grid's
 increments are those of the same grid stepped alone."""
 import numpy as np
 import pytest
