@@ -42,7 +42,7 @@ WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # peak, so the roofline of this path is the FP64 ALU, not HBM; the sweeps are latency-bound
 # (one dependent hyperplane step after another).
 FP64_FLOPS_PER_CELL = {
-    "primitive": 12302.0,      # mean of the 20 timed launches (profiles/k_primitive_fp64_counts_...)
+    "primitive": 7795.0,       # k_primitive 2784 + k_chem 5011, means over the 20 timed iterations
     "gradient": 400.0,
     "flux": 2844.0,            # both directions
     "assemble": 130.0,
@@ -51,17 +51,18 @@ FP64_FLOPS_PER_CELL = {
     "sweep_bwd": 0.0,
     "correct": 109.0,
 }
-FLOPS_SOURCE = ("ncu FP64 thread instructions (2 DFMA + DMUL + DADD) per cell, mean over the 20 "
-                "launches of the timed iterations 6..25 (profiles/k_primitive_fp64_counts_timed_window_"
-                "384x256_air11.md); other phases: one launch of the 5th iteration "
-                "(profiles/kernels_half_cylinder_384x256_air11.md)")
+FLOPS_SOURCE = ("ncu FP64 thread instructions (2 DFMA + DMUL + DADD) per cell; primitive phase "
+                "(k_primitive + k_chem): means over the launches of the timed iterations 6..25 "
+                "(profiles/primitive_chem_fp64_counts_timed_window_384x256_air11.md); other phases: one "
+                "launch of the 5th iteration (profiles/kernels_half_cylinder_384x256_air11.md)")
 # the mixed operator's sweep phase: couplings formed in FP64 (k_sweep_mat, 753 FP64 flop) and
 # swept in FP32 (k_split_p2p, the FP64 form's 374 flop as FP32)
 FP64_FLOPS_PER_CELL_SWEEP_MIXED = 753.0
 FP32_FLOPS_PER_CELL_SWEEP = 374.0
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
-    "primitive": 34.0e6, "flux": 69.1e6 + 70.0e6, "sweep_fwd": 195.7e6 + 143.6e6, "gradient": 17.4e6,
+    "primitive": None,         # the split k_primitive / k_chem kernels: DRAM not captured
+    "flux": 69.1e6 + 70.0e6, "sweep_fwd": None, "gradient": 17.4e6,
     "spectral": 54.1e6, "assemble": 33.9e6, "correct": 24.4e6,
 }
 DRAM_BYTES_SWEEP_FP32 = None              # FP32 records: not captured with ncu
@@ -751,7 +752,7 @@ def run_iteration(args, rank, world, local):
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
             "frac": achieved / peak,
             "traffic": DRAM_BYTES_SWEEP_FP32 if fp32_sweep else DRAM_BYTES_PER_LAUNCH.get(dom),
-            "kernel_phase": dom,
+            "kernel_phase": dom + (" (k_primitive + k_chem)" if dom == "primitive" else ""),
             "peak_kind": ("FP32 from unit counts and clock (152 x 128 x 2 x 2.07 GHz)" if fp32_sweep
                           else fp64_kind),
             "flops_per_cell": flops / N,

@@ -3123,7 +3123,10 @@ __device__ __forceinline__ bool p2p_wait(uint32_t bar, uint32_t parity) {
 // cp.async kP2PStageD steps ahead (one slot per thread and step, a ring of kP2PStageD + 1
 // slots): the coupling rows bi, bj (NP elements of T each; species: the two coefficients), then
 // the raw FP64 diagonal inverse d and base (right-hand side forward, forward result backward).
-constexpr int kP2PStageD = 6;
+#ifndef CS_P2P_STAGE
+#define CS_P2P_STAGE 6
+#endif
+constexpr int kP2PStageD = CS_P2P_STAGE;
 template <class T, int NP>
 struct P2PSlot {
   static constexpr int BYTES = 2 * NP * (int)sizeof(T) + 2 * (int)sizeof(double);
