@@ -249,8 +249,15 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * viscosities) combined by Blanc's law into D_s, electrons diffusing with the ions (no net
  * charge flux) and a correction velocity so that the diffusive mass fluxes sum to zero; the
  * species radius takes max_s D_s (Eq. (vislambda)).  One more kernel per iteration.
- * Errors: CS_ERR_ARG for an unknown name, a negative / NaN update_limit, a ci_splitting other
- * than 0 or 1, a transport other than 0 or 1 or the species model for a perfect gas. */
+ * Method option: "dtau_source" = 0 (default): V/dtau = sum_d (lambda_inv,d + lambda_vis,d) / CFL,
+ * the source entering only through the diagonals (V max(0, -d omega_s/d rho_s) on the species,
+ * the relaxation rate on the flow block's vibrational row); 1: the local time step of Sec. 2.2
+ * with its source radius, V/dtau = (sum_d (lambda_inv,d + lambda_vis,d) + V lambda_S) / CFL,
+ * lambda_S read as the largest magnitude on the source Jacobian's diagonal (max over species
+ * of |d omega_s / d rho_s| and, 2T, the vibrational relaxation rate).  Both schemes; no effect
+ * on a non-reacting grid.  The converged solution does not change.
+ * Errors: CS_ERR_ARG for an unknown name, a negative / NaN update_limit, a ci_splitting,
+ * transport or dtau_source other than 0 or 1, or the species model for a perfect gas. */
 cs_status cs_set_option(cs_grid g, const char *name, double value);
 
 /* Dual time stepping for unsteady flow (Sec. 2.3, the dual-time form of the implicit scheme).

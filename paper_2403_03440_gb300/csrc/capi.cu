@@ -882,6 +882,11 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     g->g.cisplit = (int)value;
     return CS_OK;
   }
+  if (!strcmp(name, "dtau_source")) {
+    if (value != 0.0 && value != 1.0) return fail(g, CS_ERR_ARG, "dtau_source must be 0 or 1");
+    g->g.dtau_src = (int)value;
+    return CS_OK;
+  }
   if (!strcmp(name, "transport")) {
     if (value != 0.0 && value != 1.0) return fail(g, CS_ERR_ARG, "transport must be 0 or 1");
     if (value == 1.0 && g->L->ns < 5) return fail(g, CS_ERR_ARG, "the species transport model needs an air mixture");

@@ -188,7 +188,7 @@ struct LauncherT : Launcher {
   }
 
   void primitive(const DevGrid& g, cudaStream_t st) override {
-    k_primitive<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+    k_primitive<G, ND><<<blocks(g.N, CS_PRIM_THREADS), CS_PRIM_THREADS, 0, st>>>(g);
     if (g.transport) k_transport<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
     k_chem<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
   }
