@@ -66,6 +66,7 @@ def lib():
         L.orc_set_update_limit.argtypes = [C.c_void_p, C.c_double]
         L.orc_set_dual.argtypes = [C.c_void_p, C.c_double, C.c_double]
         L.orc_set_ci_splitting.argtypes = [C.c_void_p, C.c_int]
+        L.orc_set_dtau_source.argtypes = [C.c_void_p, C.c_int]
         L.orc_dual_advance.argtypes = [C.c_void_p]
         L.orc_set_boundary.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double,
                                        _dp, _dp, C.c_double]
@@ -277,6 +278,10 @@ class OracleGrid:
     def set_ci_splitting(self, mode):
         """Flux-Jacobian splitting of the coupled operator: 0 spectral, 1 eigenvalue."""
         self._check(lib().orc_set_ci_splitting(self._h, int(mode)), "set_ci_splitting")
+
+    def set_dtau_source(self, on):
+        """Source radius lambda_S in the local time step's denominator (Sec. 2.2): 0 / 1."""
+        self._check(lib().orc_set_dtau_source(self._h, int(on)), "set_dtau_source")
 
     def set_dual(self, dt, theta=0.0):
         """Dual time stepping with physical step dt (0: steady) and coefficient theta."""

@@ -791,6 +791,7 @@ typedef struct {
     double *lamF, *lamC, *lamCI;     /* hat-lambda per cell and direction [cell*3] */
     double *lamCIv;                  /* 2 lambda_vis of the coupled operator [cell*3] */
     int ci_split;                    /* coupled operator: 0 spectral splitting, 1 eigenvalue */
+    int dtau_src;                    /* 1: lambda_S in the local time step (Sec. 2.2 Delta tau) */
     double *DF, *DFev, *Ds;          /* diagonals */
     double *DLU; int *piv;           /* CI diagonal blocks, LU factors */
     double norms[2], qstag;
@@ -1561,7 +1562,11 @@ static int residual(orc_grid *G)
  *   coupled:    nu_eff = max of all of the above.
  * S_d = mean of the two face vectors of the cell in direction d; hat-lambda = lambda_inv +
  * 2 lambda_vis; V/dtau = sum_d (lambda_inv,d + lambda_vis,d) / CFL (flow radius, both
- * schemes); the source's radius lambda_S enters through the diagonal, not through dtau.
+ * schemes); by default the source's radius lambda_S enters through the diagonals only.  With
+ * dtau_src the local time step is the one Sec. 2.2 prints, its denominator carrying lambda_S
+ * too: V/dtau = (sum_d (lambda_inv,d + lambda_vis,d) + V lambda_S) / CFL, lambda_S read as the
+ * largest magnitude on the diagonal of the source Jacobian A_S = dS/dQ (|d omega_s/d rho_s| of
+ * every species and, 2T, the vibrational relaxation rate).
  * ------------------------------------------------------------------------------------- */
 static void absjac_ci(const orc_grid *G, const prim_t *w, const double *S, const double *dc, double *out);
 
@@ -1606,6 +1611,11 @@ static void spectral(orc_grid *G, double cfl)
             sF += G->lamF[3 * c + d];
             sC += G->lamC[3 * c + d];
             sCI += G->lamCI[3 * c + d];
+        }
+        if (G->dtau_src && G->react) {
+            double lS = G->gas.ntemp == 2 ? w->relax : 0.0;
+            for (int s = 0; s < ns; s++) lS = fmax(lS, fabs(w->dom[s]));
+            sumdt += G->V[c] * lS;
         }
         double Vdt = sumdt / cfl;                  /* V / dtau */
         double da, db;
@@ -2174,6 +2184,15 @@ int orc_set_ci_splitting(orc_grid *G, int mode)
 {
     if (mode != 0 && mode != 1) return 1;
     G->ci_split = mode;
+    return 0;
+}
+
+/* Local time step of Sec. 2.2 with (1) or without (0, default) the source term's radius
+ * lambda_S in its denominator. */
+int orc_set_dtau_source(orc_grid *G, int on)
+{
+    if (on != 0 && on != 1) return 1;
+    G->dtau_src = on;
     return 0;
 }
 

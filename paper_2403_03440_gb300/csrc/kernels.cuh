@@ -259,6 +259,15 @@ __device__ int solve_temperature(const double* Y, double target, double guess, d
       if (f > 0) hi = T; else lo = T;
       Tn = (cv > 0) ? T - f / cv : 0.5 * (lo + hi);
       newton = cv > 0;
+      // A Newton step of at most 1e-8 T has converged even where it lands on, or by rounding
+      // just past, the bracket end that T itself has just become: at the exact root (f == 0,
+      // e.g. the warm start of an unchanged cell) T becomes the lower end and Tn == T, which
+      // the open-bracket test below would send into a bisection towards kTmax and a dozen
+      // more passes back.
+      if (newton && fabs(Tn - T) <= 1e-8 * T) {
+        Tout = fmin(fmax(Tn, kTmin), kTmax);
+        return 0;
+      }
       if (!(Tn > lo && Tn < hi)) {
         if (Tn <= lo && lo == kTmin && !lo_checked) { check = 1; continue; }
         if (Tn >= hi && hi == kTmax && !hi_checked) { check = 2; continue; }

@@ -126,6 +126,32 @@ def test_split_operator_parity(name):
     assert rel(dg[ref.nF:], dr[ref.nF:], ns=ref.ns) < TOL
 
 
+@pytest.mark.parametrize("name", ["c1_ogrid_air5", "half_cyl_air11", "sphere_cone_air11"])
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_operator_parity_with_source_radius_in_dtau(name, scheme):
+    """Option dtau_source (Sec. 2.2's local time step with lambda_S in its denominator) acts on
+    both sides alike and changes the diagonals of both operators."""
+    ref, gpu, _ = make_pair(name, seed=2)
+    ref.residual()
+    gpu.residual(want_R=False)
+    cfl = 6.0
+    base = gpu.lusgs_split(cfl) if scheme == 0 else gpu.lusgs_coupled(cfl)
+    DF0 = gpu.field("DF")
+    ref.set_dtau_source(1)
+    gpu.set_option("dtau_source", 1)
+    dr = ref.lusgs_split(cfl) if scheme == 0 else ref.lusgs_coupled(cfl)
+    dg = gpu.lusgs_split(cfl) if scheme == 0 else gpu.lusgs_coupled(cfl)
+    assert rel(gpu.field("DF"), ref.field("DF")) < TOL
+    assert rel(gpu.field("Ds").reshape(ref.ns, -1), ref.field("Ds").reshape(ref.ns, -1)) < TOL
+    assert np.all(gpu.field("DF") >= DF0) and np.any(gpu.field("DF") > DF0 * (1 + 1e-6))
+    # (coupled: the tolerance of test_coupled_operator_parity, set by the blocks' condition)
+    tol = TOL if scheme == 0 else (1e-8 if ref.ns < 11 else 1e-6)
+    nF = ref.nF
+    assert rel(dg[:nF], dr[:nF]) < tol
+    assert rel(dg[nF:], dr[nF:], ns=(ref.ns if scheme == 0 else ref.nci - nF)) < tol
+    assert rel(dg, base) > 1e-8
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_coupled_operator_parity(name):
     ref, gpu, _ = make_pair(name, seed=3)

@@ -276,3 +276,44 @@ def test_stagnation_heat_flux_is_the_residual_wall_conduction(mech, T1, Tv1):
     np.testing.assert_allclose(R[ns + 2, c], norms[2] * area, rtol=1e-12)
     # the cells above the wall row carry no energy residual
     assert np.max(np.abs(R[ns + 2, ni:])) <= 1e-9 * abs(R[ns + 2, c])
+
+
+@pytest.mark.parametrize("mech,kw", [(inputs.MECH_AIR5, dict(T=9000.0, p=40000.0)),
+                                     (inputs.MECH_AIR11, dict(T=9000.0, Tv=6000.0, p=8000.0))])
+def test_source_radius_in_the_local_time_step(mech, kw):
+    """Sec. 2.2's local time step with the source radius (option dtau_source): V/dtau grows by
+    V lambda_S / CFL in every cell, on every diagonal alike, with lambda_S the largest magnitude
+    on the diagonal of the conserved-variable source Jacobian -- taken here from the single-state
+    Jacobian (itself pinned by central differences in test_oracle_chem) and, 2T, the
+    relaxation rate (pinned as -d omega_v / d(rho e_v) there) -- and nothing changes without
+    chemistry."""
+    nd = 2
+    nodes = inputs.cylinder_ogrid(6, 5)
+    cfl = 7.0
+    out = {}
+    for react in (True, False):
+        for on in (0, 1):
+            g = oracle.OracleGrid(nodes, inputs.cylinder_bc(), mech, limiter=0)
+            g.set_boundary(inputs.freestream(mech, mach=8.0), Tw=500.0)
+            g.set_reacting(react)
+            g.set_dtau_source(on)
+            Q = _state(mech, nd, (g.nj, g.ni), seed=11, **kw)
+            g.set_state(Q)
+            g.residual()
+            g.build_diagonals(cfl)
+            out[react, on] = (g.field("DF"), g.field("DFev"), g.field("Ds").reshape(-1, g.ncell), g.field("V"), Q)
+    for k in range(3):
+        assert np.array_equal(out[False, 0][k], out[False, 1][k])
+    DF0, DFev0, Ds0, V, Q = out[True, 0]
+    DF1, DFev1, Ds1, _, _ = out[True, 1]
+    ns = Ds0.shape[0]
+    two_t = oracle.gas_info(mech)["ntemp"] == 2
+    for c in range(len(V)):
+        _, J = oracle.state_source_jac(mech, nd, Q[:, c])
+        lam = np.max(np.abs(np.diag(J[:, :ns])))
+        if two_t:
+            lam = max(lam, oracle.state_vib(mech, nd, Q[:, c])["relax"])
+        want = V[c] * lam / cfl
+        assert want > 1e-4 * DF0[c]        # the states are chemically active
+        for a, b in ((DF1[c], DF0[c]), (DFev1[c], DFev0[c])) + tuple((Ds1[s, c], Ds0[s, c]) for s in range(ns)):
+            assert abs((a - b) - want) <= 1e-9 * a, (c, a - b, want)
