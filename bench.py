@@ -599,7 +599,7 @@ def c1_time_to_drop(tol=1e-8, with_network=True):
             X, T = S.collect(c, 3000, 10, 0)
             norm = S.standardisation(X, T)
             net, record, val = S.train(X, T, norm, epochs=20, max_batch=c["ni"] * c["nj"])
-            norm_used, _ = S.calibrate(net, norm, val)
+            norm_used, _ = S.calibrate(net, norm, val, q=c["calib_q"])
             train_s = time.perf_counter() - t0
             r = S.run_to(c, tol, 20000, 100, net=net, norm=norm_used, precision=1)
             out["runs"]["cs1_fp32_operator_network"] = {k: r[k] for k in keys}

@@ -34,7 +34,7 @@ SCHEMES = {"cs1": (0, 1), "cs2": (0, 2), "ci": (1, 1), "ci_eig": (1, 1)}
 
 
 def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, precision, clip=1,
-        update_limit=0.0):
+        update_limit=0.0, dtau_source=0):
     c = CASES[case]
     if "nk" in c:
         nodes, bc = inputs.sphere_cone(c["ni"], c["nj"], c["nk"]), inputs.sphere_cone_bc()
@@ -48,6 +48,8 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
     g.init_freestream()
     if update_limit > 0:
         g.set_option("update_limit", update_limit)
+    if dtau_source:
+        g.set_option("dtau_source", 1)
     if scheme == "ci_eig":
         g.set_option("ci_splitting", 1)
     sch, corr = SCHEMES[scheme]
@@ -76,7 +78,7 @@ def run(case, scheme, cfl, cfl_start, ramp, tol, max_iters, chunk, limiter, prec
     dt = time.perf_counter() - t0
     best = min(max(h[1], h[2]) for h in hist)
     return dict(case=case, scheme=scheme, precision="mixed" if precision else "fp64", cfl=cfl,
-                cfl_start=cfl_start, ramp=ramp, update_limit=update_limit,
+                cfl_start=cfl_start, ramp=ramp, update_limit=update_limit, dtau_source=dtau_source,
                 limiter=limiter, tol=tol, status=status, iterations=done, seconds=dt,
                 ms_per_iter=1e3 * dt / max(done - 1, 1), min_drop=best,
                 q_stag_final=hist[-1][3], cells=c["ni"] * c["nj"] * c.get("nk", 1),
@@ -96,10 +98,13 @@ def main():
     ap.add_argument("--limiter", type=int, default=1)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--update-limit", type=float, default=0.0)
+    ap.add_argument("--dtau-source", type=int, default=0, choices=[0, 1],
+                    help="1: the source radius in the local time step (Sec. 2.2)")
     a = ap.parse_args()
     P.build()
     out = run(a.case, a.scheme, a.cfl, a.cfl_start, a.ramp, a.tol, a.max_iters, a.chunk,
-              a.limiter, 1 if a.precision == "mixed" else 0, update_limit=a.update_limit)
+              a.limiter, 1 if a.precision == "mixed" else 0, update_limit=a.update_limit,
+              dtau_source=a.dtau_source)
     print(json.dumps(out))
 
 
