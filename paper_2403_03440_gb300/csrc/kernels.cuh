@@ -3230,24 +3230,31 @@ __device__ __forceinline__ void p2p_stage_read(const DevGrid& g, int q, int j, b
   m.i = i;
   if (!m.act) return;
   m.c = i + ni * j;
+  // 16-byte shared-memory loads: the slot and its three parts start on 16 bytes
+  using V = typename Vec16<T>::type;
+  constexpr int VEC = M::VEC;
   const T* bi = reinterpret_cast<const T*>(slot);
   const T* bj = bi + NP;
-  const double* db = reinterpret_cast<const double*>(bj + NP);
+  const double2 db = *reinterpret_cast<const double2*>(bj + NP);
   if (flow) {
 #pragma unroll
-    for (int k = 0; k < NP; ++k) { m.bi[k] = bi[k]; m.bj[k] = bj[k]; }
-    m.d = (T)db[0];
-    m.base = (T)db[1];
+    for (int k = 0; k < NP / VEC; ++k) {
+      Vec16<T>::unpack(reinterpret_cast<const V*>(bi)[k], m.bi + VEC * k);
+      Vec16<T>::unpack(reinterpret_cast<const V*>(bj)[k], m.bj + VEC * k);
+    }
+    m.d = (T)db.x;
+    m.base = (T)db.y;
   } else {
     if (sizeof(T) == 8) {
-      m.bi[0] = bi[0];
-      m.bj[0] = bi[1];
+      const double2 co = *reinterpret_cast<const double2*>(bi);
+      m.bi[0] = (T)co.x;
+      m.bj[0] = (T)co.y;
     } else {
       m.bi[0] = bi[0];
       m.bj[0] = bj[0];
     }
-    m.d = (T)db[0];
-    m.base = (T)(fwd ? -db[1] : db[1]);
+    m.d = (T)db.x;
+    m.base = (T)(fwd ? -db.y : db.y);
   }
 }
 // one element into another CTA's shared memory, completing bytes on that CTA's mbarrier
