@@ -42,7 +42,7 @@ WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # peak, so the roofline of this path is the FP64 ALU, not HBM; the sweeps are latency-bound
 # (one dependent hyperplane step after another).
 FP64_FLOPS_PER_CELL = {
-    "primitive": 7795.0,       # k_primitive 2784 + k_chem 5011, means over the 20 timed iterations
+    "primitive": 6089.0,       # k_primitive 1078 + k_chem 5011, means over the 20 timed iterations
     "gradient": 400.0,
     "flux": 2844.0,            # both directions
     "assemble": 130.0,

@@ -3230,31 +3230,24 @@ __device__ __forceinline__ void p2p_stage_read(const DevGrid& g, int q, int j, b
   m.i = i;
   if (!m.act) return;
   m.c = i + ni * j;
-  // 16-byte shared-memory loads: the slot and its three parts start on 16 bytes
-  using V = typename Vec16<T>::type;
-  constexpr int VEC = M::VEC;
   const T* bi = reinterpret_cast<const T*>(slot);
   const T* bj = bi + NP;
-  const double2 db = *reinterpret_cast<const double2*>(bj + NP);
+  const double* db = reinterpret_cast<const double*>(bj + NP);
   if (flow) {
 #pragma unroll
-    for (int k = 0; k < NP / VEC; ++k) {
-      Vec16<T>::unpack(reinterpret_cast<const V*>(bi)[k], m.bi + VEC * k);
-      Vec16<T>::unpack(reinterpret_cast<const V*>(bj)[k], m.bj + VEC * k);
-    }
-    m.d = (T)db.x;
-    m.base = (T)db.y;
+    for (int k = 0; k < NP; ++k) { m.bi[k] = bi[k]; m.bj[k] = bj[k]; }
+    m.d = (T)db[0];
+    m.base = (T)db[1];
   } else {
     if (sizeof(T) == 8) {
-      const double2 co = *reinterpret_cast<const double2*>(bi);
-      m.bi[0] = (T)co.x;
-      m.bj[0] = (T)co.y;
+      m.bi[0] = bi[0];
+      m.bj[0] = bi[1];
     } else {
       m.bi[0] = bi[0];
       m.bj[0] = bj[0];
     }
-    m.d = (T)db.x;
-    m.base = (T)(fwd ? -db.y : db.y);
+    m.d = (T)db[0];
+    m.base = (T)(fwd ? -db[1] : db[1]);
   }
 }
 // one element into another CTA's shared memory, completing bytes on that CTA's mbarrier
@@ -4394,13 +4387,15 @@ __device__ __forceinline__ void surr_raw_features(const DevGrid& g, int c, float
   using A = Aux<G, ND>;
   const size_t N = g.N;
   // logarithms throughout: the rates are Arrhenius in T and mass-action in the densities, and
-  // trace species span many decades (1e-10 floors the mass fractions)
-  f[0] = (float)log10(g.W[A::RHO * N + c]);
-  f[1] = (float)log10(g.W[A::T * N + c]);
-  f[2] = (float)log10(g.W[A::TV * N + c]);
+  // trace species span many decades (1e-10 floors the mass fractions).  The network's inputs
+  // are FP32, so the logarithms are taken in FP32 (an FP64 logarithm per input cost more than
+  // the network itself)
+  f[0] = log10f((float)g.W[A::RHO * N + c]);
+  f[1] = log10f((float)g.W[A::T * N + c]);
+  f[2] = log10f((float)g.W[A::TV * N + c]);
 #pragma unroll
   for (int s = 0; s < kSurrNS; ++s)
-    f[3 + s] = s < G::NS ? (float)log10(fmax(g.W[(A::Y + s) * N + c], 0.0) + 1e-10) : -10.f;
+    f[3 + s] = s < G::NS ? log10f(fmaxf((float)g.W[(A::Y + s) * N + c], 0.f) + 1e-10f) : -10.f;
 }
 
 // raw features [N][14] and raw targets [N][22] of every cell (from the auxiliary fields of the
@@ -4453,10 +4448,11 @@ __global__ void __launch_bounds__(128) k_surr_decode(DevGrid g, const float* Y, 
     // de-standardised stiffness asinh(max(0, -d omega / d rho)), held to the span of the
     // training targets (mean +- 8 standard deviations, and >= 0); a non-finite output maps to
     // the upper bound, which only adds to the operator's diagonal
-    const double y = (double)Y[(size_t)c * kSurrOut + o] * st[o] + mt[o];
-    const double hi = mt[o] + 8.0 * st[o];
-    const double t = y == y ? fmin(fmax(y, fmax(0.0, mt[o] - 8.0 * st[o])), hi) : hi;
-    g.W[(A::DOM + s) * N + c] = -sinh(t);
+    // (FP32 arithmetic: the network's output carries FP32 / bf16 precision)
+    const float y = Y[(size_t)c * kSurrOut + o] * (float)st[o] + (float)mt[o];
+    const float hi = (float)(mt[o] + 8.0 * st[o]);
+    const float t = y == y ? fminf(fmaxf(y, fmaxf(0.f, (float)(mt[o] - 8.0 * st[o]))), hi) : hi;
+    g.W[(A::DOM + s) * N + c] = -(double)sinhf(t);
   }
 }
 

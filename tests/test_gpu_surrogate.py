@@ -52,7 +52,8 @@ def test_samples_match_oracle_fields():
     want_x = np.concatenate([np.log10(rho)[:, None], np.log10(ref.field("T")[:N, None]),
                              np.log10(ref.field("Tv")[:N, None]),
                              np.log10(np.maximum(Y.T, 0.0) + 1e-10)], axis=1)
-    assert np.max(np.abs(X - want_x) / np.maximum(np.abs(want_x), 1e-3)) < 1e-5
+    # (the features are the network's FP32 inputs, computed in FP32: a few FP32 ulps at |x| <= 10)
+    assert np.max(np.abs(X - want_x)) < 4e-6
     om = ref.field("omega").reshape(11, -1)[:, :N].T
     dom = ref.field("dom").reshape(11, -1)[:, :N].T
     want_t = np.concatenate([np.arcsinh(om), np.arcsinh(np.maximum(0.0, -dom))], axis=1)
