@@ -206,8 +206,10 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * FP32 for the FP32 operator) of 4 nF nP + 4 elements per cell and 2 nF nP + 4 per row j, nP =
  * nF rounded up to a whole 16-byte load; then a cluster kernel with 8 threads per row whose
  * CTAs exchange the rows at their boundaries point to point (st.async into the next CTA's
- * shared memory, one mbarrier per hyperplane; (ni + nj - 1) x (8 x element size + 8) bytes of
- * shared memory per CTA, at most 200 KiB; single grids only), 6 the FP64 couplings with one
+ * shared memory, one mbarrier per hyperplane) and each thread copies its step inputs six steps
+ * ahead with cp.async into a ring in shared memory ((ni + nj - 1) x (8 x element size + 8)
+ * bytes plus 7 x threads x (2 nP x element size + 16) bytes per CTA, at most 200 KiB; single
+ * grids only), 6 the FP64 couplings with one
  * cluster barrier per hyperplane (the FP32 operator falls back to 4, else 2), 7 the same
  * couplings swept by systolic warps: the four rows of a warp exchange results by warp shuffles
  * and each warp waits only for the row before its first (after its last, backward), written
