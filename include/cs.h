@@ -172,9 +172,12 @@ cs_status cs_get_field(cs_grid g, const char *name, double *out, int *count_out)
 cs_status cs_gas_info(int mech, double *M, double *hf, int dims[3]);
 
 /* Per-phase device timing of cs_step with CUDA events on the grid's stream (not part of the
- * method; a measurement aid).  Phases: 0 primitives + chemistry, 1 gradients, 2 face fluxes,
- * 3 residual assembly + norms, 4 spectral radii / diagonals (+ coupled blocks), 5 forward
- * sweep, 6 backward sweep, 7 correction + update.  ms_out[8] and launches_out[8] (host,
+ * method; a measurement aid).  Phases: 0 primitives (the temperature solves; with the
+ * chemistry where the second stream below could not be made), 1 gradients, 2 face fluxes, up
+ * to the end of the chemistry, which cs_step runs on a second library-owned stream beside
+ * phases 1 and 2 (forked from and joined back into the grid's stream), 3 residual assembly +
+ * norms, 4 spectral radii / diagonals (+ coupled blocks), 5 forward sweep, 6 backward sweep, 7
+ * correction + update.  ms_out[8] and launches_out[8] (host,
  * nullable) receive the totals accumulated since the last call; the call then resets them
  * and enables (enable = 1) or disables timing. */
 cs_status cs_profile(cs_grid g, int enable, double *ms_out, long *launches_out);

@@ -175,6 +175,10 @@ struct cs_grid_s {
   int last_op = -1;           // 0 split, 1 coupled
   bool mat_refused = false;   // the coupling records of the 2D split sweep could not be allocated
   char err[512] = {0};
+  // second stream of the iteration: the chemistry beside the gradient and fluxes (created on
+  // first use; the fork and join events order it within the grid's stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // per-phase CUDA-event timing of cs_step (enabled by cs_profile)
   bool prof = false;
   cudaEvent_t ev[8][CS_NPHASE + 1];
@@ -291,6 +295,8 @@ extern "C" cs_status cs_gas_info(int mech, double* M, double* hf, int dims[3]) {
   dims[2] = nt;
   return CS_OK;
 }
+
+static void make_side(cs_grid g);
 
 extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* nodes_host,
                                     void* cuda_stream, cs_grid* out) {
@@ -435,6 +441,7 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
   k_geom_cells<<<Launcher::blocks(N, 128), 128, 0, g->stream>>>(ga);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(g->stream) != cudaSuccess)
     return CS_ERR_CUDA;
+  make_side(g);
   *out = G.release();
   return CS_OK;
 }
@@ -442,6 +449,12 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
 extern "C" cs_status cs_grid_destroy(cs_grid g) {
   if (!g) return CS_ERR_ARG;
   cudaStreamSynchronize(g->stream);
+  if (g->side) {
+    cudaStreamSynchronize(g->side);
+    cudaStreamDestroy(g->side);
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
   for (void* p : g->allocs) cudaFree(p);
   if (g->g.DLU) cudaFree(g->g.DLU);
   if (g->g.DINV) cudaFree(g->g.DINV);
@@ -705,6 +718,30 @@ static cs_status check_opts(const cs_step_opts* o) {
   return CS_OK;
 }
 
+// The chemistry of an iteration (k_chem: source, Jacobian diagonal, relaxation) reads only the
+// state and the primitives and is read first by the assembly, so it runs on a second stream
+// beside the gradient and flux kernels (which fill the SMs its last wave of CTAs leaves idle).
+// Returns false (the caller then runs it in order) if the stream or events cannot be made.
+static void make_side(cs_grid g) {   // at grid creation (not during a stream capture)
+  if (cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (g->side) cudaStreamDestroy(g->side);
+    if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+    g->side = nullptr;
+    g->ev_fork = g->ev_join = nullptr;
+  }
+}
+static bool fork_chem(cs_grid g) {
+  if (!g->side) return false;
+  if (cudaEventRecord(g->ev_fork, g->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(g->side, g->ev_fork, 0) != cudaSuccess)
+    return false;
+  g->L->chem(g->g, g->side);
+  return cudaEventRecord(g->ev_join, g->side) == cudaSuccess;
+}
+
 // Enqueue one pseudo-time iteration on g->stream (no host synchronisation).  device_cfl: the
 // CFL comes from k_cfl and the device iteration counter and no profiling events are recorded
 // (stream capture); otherwise the CFL of iteration g->iter is copied from pinned memory slot
@@ -726,11 +763,15 @@ static cs_status enqueue_iteration(cs_grid g, const cs_step_opts* o, int slot, b
   const bool rec = !device_cfl;
   const DevGrid& d = g->g;
   if (rec) prof_record(g, slot, 0);
-  g->L->primitive(d, g->stream);
+  g->L->primitive_state(d, g->stream);
+  const bool side = fork_chem(g);
+  if (!side) g->L->chem(d, g->stream);
   if (rec) prof_record(g, slot, 1);
   g->L->gradient(d, g->stream);
   if (rec) prof_record(g, slot, 2);
   g->L->flux(d, g->stream);
+  // join: the assembly reads the chemistry (the flux phase ends when both are done)
+  if (side) CUDA_TRY(g, cudaStreamWaitEvent(g->stream, g->ev_join, 0));
   if (rec) prof_record(g, slot, 3);
   g->L->assemble(d, g->stream, g->stag, g->norms);
   if (rec) prof_record(g, slot, 4);

@@ -21,7 +21,14 @@ struct Launcher {
     flux(g, st);
     assemble(g, st, stag, out);
   }
-  virtual void primitive(const DevGrid& g, cudaStream_t st) = 0;
+  // primitive() = primitive_state() (temperature solves, primitives, transport) + chem()
+  // (chemistry, its Jacobian diagonal, vibrational relaxation)
+  void primitive(const DevGrid& g, cudaStream_t st) {
+    primitive_state(g, st);
+    chem(g, st);
+  }
+  virtual void primitive_state(const DevGrid& g, cudaStream_t st) = 0;
+  virtual void chem(const DevGrid& g, cudaStream_t st) = 0;
   virtual void gradient(const DevGrid& g, cudaStream_t st) = 0;
   virtual void flux(const DevGrid& g, cudaStream_t st) = 0;
   virtual void assemble(const DevGrid& g, cudaStream_t st, int stag, double* out) = 0;
@@ -187,9 +194,11 @@ struct LauncherT : Launcher {
     k_fill<G, ND><<<blocks(g.N, 256), 256, 0, st>>>(g, fsQ);
   }
 
-  void primitive(const DevGrid& g, cudaStream_t st) override {
+  void primitive_state(const DevGrid& g, cudaStream_t st) override {
     k_primitive<G, ND><<<blocks(g.N, CS_PRIM_THREADS), CS_PRIM_THREADS, 0, st>>>(g);
     if (g.transport) k_transport<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
+  }
+  void chem(const DevGrid& g, cudaStream_t st) override {
     k_chem<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
   }
   void gradient(const DevGrid& g, cudaStream_t st) override {
