@@ -33,7 +33,10 @@ import inputs  # noqa: E402
 NI, NJ = 384, 256
 MECH = inputs.MECH_AIR11
 MACH, T_INF, P_INF, T_WALL = 15.0, 300.0, 500.0, 500.0
-CFL, CFL_START, RAMP = 2.0, 0.5, 100
+# CFL 20 reached by a geometric ramp from 0.5 over 2000 iterations, with the source radius in the
+# local time step (option dtau_source, Sec. 2.2): the setting in which C2 reaches a 1e-8 drop
+CFL, CFL_START, RAMP = 20.0, 0.5, 2000
+DTAU_SOURCE = 1
 WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 # Floating-point operations per cell and iteration of each phase (2 x FMA + MUL + ADD thread
 # instructions counted by ncu on this workload, one launch from the 5th iteration, divided by
@@ -230,6 +233,7 @@ def oracle_rate(iters, seconds_cap=30.0):
     nodes, fs = make_case(None)
     g = oracle.OracleGrid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
+    g.set_dtau_source(DTAU_SOURCE)
     g.set_state(g.freestream_state())
     done, t0 = 0, time.perf_counter()
     kw = step_kwargs(1)
@@ -253,6 +257,7 @@ def run_reference(args, rank):
     nodes, fs = make_case(None)
     g = oracle.OracleGrid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
+    g.set_dtau_source(DTAU_SOURCE)
     g.set_state(g.freestream_state())
     kw = step_kwargs(1)
     kw.pop("precision")
@@ -268,7 +273,9 @@ def run_reference(args, rank):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cells": case_cells(), "cfl": CFL},
+        "config": {"workload": WORKLOAD, "cells": case_cells(),
+                   "cfl": f"{CFL_START} ramped geometrically to {CFL} over {RAMP} iterations",
+                   "dtau_source": DTAU_SOURCE},
         "cpu_baseline": {"value": v, "unit": "Mcell-iter/s", "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} iterations of the full grid from the freestream"},
         "e2e": {"value": v, "unit": "Mcell-iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -557,6 +564,7 @@ def make_grid(P):
     nodes, fs = make_case(P)
     g = P.Grid(nodes, case_bc(), MECH)
     g.set_boundary(fs, Tw=T_WALL)
+    g.set_option("dtau_source", DTAU_SOURCE)
     return g, fs
 
 
@@ -615,6 +623,26 @@ def c1_time_to_drop(tol=1e-8, with_network=True):
         if "q_stag" in r and "q_stag" in base and base["q_stag"]:
             r["q_rel_diff_vs_cs1_fp64"] = abs(r["q_stag"] - base["q_stag"]) / abs(base["q_stag"])
             r["time_ratio_vs_cs1_fp64"] = r["seconds"] / base["seconds"]
+    return out
+
+
+def c2_time_to_drop(tol=1e-8):
+    """Time to a `tol` drop of both residual monitors on C2 itself (the 384 x 256 grid of the
+    throughput line; first order, update limit 0.2, CFL ramped from 0.5 to 20 over 2000
+    iterations with the source radius in the local time step): CS-1 with the FP64 operator and
+    with the FP32 operator, monitors checked every 500 iterations, device time between two
+    synchronisations around each run."""
+    from paper_2403_03440_gb300 import convergence as CV
+    out = {"case": "half-cylinder-384x256-air11-2T-mach15-first-order-cfl20-dtau-source",
+           "cells": 98304, "tol": tol, "runs": {}}
+    for name, prec in (("cs1_fp64", 0), ("cs1_fp32_operator", 1)):
+        try:
+            r = CV.run("c2", "cs1", CFL, CFL_START, RAMP, tol, 40000, 500, 0, prec,
+                       update_limit=0.2, dtau_source=1)
+            out["runs"][name] = {k: r[k] for k in ("status", "iterations", "seconds", "ms_per_iter",
+                                                   "q_stag_final", "min_drop")}
+        except Exception as e:          # report, do not lose the bench line
+            out["runs"][name] = {"status": f"error: {e}"}
     return out
 
 
@@ -787,6 +815,7 @@ def run_iteration(args, rank, world, local):
     extras = {}
     if rank == 0 and not C3 and args.scheme == "cs1" and args.dual_dt == 0 and not args.no_convergence:
         extras["time_to_1e8_c1"] = c1_time_to_drop()
+        extras["time_to_1e8_c2"] = c2_time_to_drop()
     if rank == 0 and not C3 and args.scheme == "cs1" and args.dual_dt == 0 and not args.no_batch:
         try:
             extras["batch"] = batch_throughput(P, precision=PRECISION)
@@ -817,6 +846,7 @@ def run_iteration(args, rank, world, local):
                                   "ci": "coupled (CI) LU-SGS",
                                   "ci_eig": "coupled (CI) LU-SGS, eigenvalue splitting"}[args.scheme],
                        "cfl": f"{CFL_START} ramped geometrically to {CFL} over {RAMP} iterations",
+                       "dtau_source": DTAU_SOURCE,
                        "timed_iterations": f"{args.warmup + 1}..{args.warmup + args.steps} from the freestream",
                        "l2": "flushed before every timed iteration (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
