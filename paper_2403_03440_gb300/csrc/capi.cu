@@ -354,8 +354,9 @@ extern "C" cs_status cs_grid_create(const cs_grid_desc* desc, const double* node
     d.S[k] = S;
     d.fc[k] = fc;
     ALLOC(d.F[k], (size_t)L->nq * d.nf[k]);
+    ALLOC(d.eta[k], (size_t)d.nf[k]);
   }
-  for (int k = nd; k < 3; ++k) { d.S[k] = nullptr; d.fc[k] = nullptr; d.F[k] = nullptr; }
+  for (int k = nd; k < 3; ++k) { d.S[k] = nullptr; d.fc[k] = nullptr; d.F[k] = nullptr; d.eta[k] = nullptr; }
   double *V, *xc;
   ALLOC(V, N);
   ALLOC(xc, 3 * N);

@@ -53,6 +53,7 @@ struct DevGrid {
   double* fsW;            // freestream aux record [aux]
   double* grad;           // [ng*3][N]
   double* F[3];           // [nq][nf]
+  double* eta[3];         // [nf] H-correction eta of every face (k_eta)
   double* R;              // [nq][N]
   double* lamF;           // [3][N]
   double* lamC;
@@ -1365,11 +1366,35 @@ __device__ __forceinline__ double eta_cells(const DevGrid& g, int a, int b, cons
   return 0.5 * (fabs(dun) + fabs(g.W[A::C * N + b] - g.W[A::C * N + a]));
 }
 
-// H width of the direction-D face with cells a (minus side) and b (plus side), either of which
-// is -1 on a non-periodic boundary; S is the face's own vector.
+// eta of every direction-D face, once per residual (k_eta): the face's two cells (interior, or
+// across a periodic seam), 0 on a non-periodic boundary.  eta_cells is symmetric in its two
+// cells (the jumps enter through their magnitudes), so a face's eta is the same whichever of
+// its cells asks for it.
 template <class G, int ND, int D>
-__device__ __forceinline__ double eta_h(const DevGrid& g, int a, int b, const double* S) {
-  double eta = (a >= 0 && b >= 0) ? eta_cells<G, ND>(g, a, b, S) : 0.0;
+__global__ void __launch_bounds__(256) k_eta(DevGrid g) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= g.nf[D]) return;
+  const int fi = g.ni + (D == 0), fj = g.nj + (D == 1);
+  const int i = f % fi, j = (f / fi) % fj, k = f / (fi * fj);
+  const int n = extent(g, D), pos = coord(D, i, j, k);
+  int p[3] = {i, j, k};
+  int a = -1, b = -1;
+  if (pos > 0 && pos < n) {
+    p[D] = pos - 1; a = cell_of(g, p[0], p[1], p[2]);
+    p[D] = pos;     b = cell_of(g, p[0], p[1], p[2]);
+  } else if (g.bc[2 * D] == BC_PERIODIC) {
+    p[D] = n - 1; a = cell_of(g, p[0], p[1], p[2]);
+    p[D] = 0;     b = cell_of(g, p[0], p[1], p[2]);
+  }
+  g.eta[D][f] = a >= 0 ? eta_cells<G, ND>(g, a, b, g.S[D] + 3 * (size_t)f) : 0.0;
+}
+
+// H width of the direction-D face f with cells a (minus side) and b (plus side), either of
+// which is -1 on a non-periodic boundary: the largest eta over the face itself and the faces
+// of the other directions that bound its cells (from k_eta)
+template <class G, int ND, int D>
+__device__ __forceinline__ double eta_h(const DevGrid& g, int a, int b, int f) {
+  double eta = g.eta[D][f];
 #pragma unroll
   for (int m = 0; m < 2; ++m) {
     const int c = m ? b : a;
@@ -1379,13 +1404,10 @@ __device__ __forceinline__ double eta_h(const DevGrid& g, int a, int b, const do
 #pragma unroll
     for (int e = 0; e < ND; ++e) {
       if (e == D) continue;
-#pragma unroll
-      for (int s = -1; s <= 1; s += 2) {
-        bool lw;
-        const int nb = neighbour(g, ci, cj, ck, e, s, lw);
-        if (nb < 0) continue;
-        eta = fmax(eta, eta_cells<G, ND>(g, c, nb, face_vec(g, e, ci, cj, ck, s)));
-      }
+      int q[3] = {ci, cj, ck};
+      eta = fmax(eta, g.eta[e][face_of(g, e, q[0], q[1], q[2])]);
+      q[e]++;
+      eta = fmax(eta, g.eta[e][face_of(g, e, q[0], q[1], q[2])]);
     }
   }
   return eta;
@@ -1443,7 +1465,7 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
         vr[v] -= 0.5 * limiter(g.limiter, dc, dp);
       }
     }
-    const double etaH = g.hcorr ? eta_h<G, ND, D>(g, a, b, S) : 0.0;
+    const double etaH = g.hcorr ? eta_h<G, ND, D>(g, a, b, f) : 0.0;
     if (!recon_ok<G, ND>(vl) || !recon_ok<G, ND>(vr)) {
       roe<G, ND>(wa, wb, S, g.efix, etaH, Fi);
     } else {
@@ -1551,7 +1573,7 @@ __global__ void __launch_bounds__(128) k_flux(DevGrid g) {
       double wi[NR], wg[NR];
       recon_load<G, ND>(g.W, N, c, wi);
       recon_ghost<G, ND>(g, c, p[0], p[1], p[2], D, s, wg);
-      const double etaH = g.hcorr ? eta_h<G, ND, D>(g, s > 0 ? c : -1, s > 0 ? -1 : c, S) : 0.0;
+      const double etaH = g.hcorr ? eta_h<G, ND, D>(g, s > 0 ? c : -1, s > 0 ? -1 : c, f) : 0.0;
       if (s > 0) roe<G, ND>(wi, wg, S, g.efix, etaH, Fi);
       else roe<G, ND>(wg, wi, S, g.efix, etaH, Fi);
     }

@@ -205,6 +205,11 @@ struct LauncherT : Launcher {
     k_gradient<G, ND><<<blocks(g.N, 128), 128, 0, st>>>(g);
   }
   void flux(const DevGrid& g, cudaStream_t st) override {
+    if (g.hcorr) {
+      k_eta<G, ND, 0><<<blocks(g.nf[0], 256), 256, 0, st>>>(g);
+      k_eta<G, ND, 1><<<blocks(g.nf[1], 256), 256, 0, st>>>(g);
+      if (ND == 3) k_eta<G, ND, (ND == 3 ? 2 : 1)><<<blocks(g.nf[2], 256), 256, 0, st>>>(g);
+    }
     k_flux<G, ND, 0><<<blocks(g.nf[0], 128), 128, 0, st>>>(g);
     k_flux<G, ND, 1><<<blocks(g.nf[1], 128), 128, 0, st>>>(g);
     if (ND == 3) k_flux<G, ND, (ND == 3 ? 2 : 1)><<<blocks(g.nf[2], 128), 128, 0, st>>>(g);

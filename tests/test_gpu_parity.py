@@ -302,6 +302,30 @@ def test_multi_iteration_parity(scheme, corr):
         assert abs(sg[k] - sr[k]) <= 1e-8 * abs(sr[k]), k
 
 
+def test_multi_iteration_parity_with_source_radius_in_dtau():
+    """20 iterations from the freestream with the local time step of Sec. 2.2 carrying the
+    source radius (option dtau_source) on the 11-species two-temperature half cylinder."""
+    nodes_fn, bc, mech, _ = CASES["half_cyl_air11"]
+    nodes = nodes_fn()
+    fs = inputs.freestream(mech, T=300.0, p=500.0, mach=15.0)
+    ref = oracle.OracleGrid(nodes, bc, mech, limiter=0)
+    ref.set_boundary(fs, Tw=500.0)
+    ref.set_dtau_source(1)
+    gpu = P.Grid(nodes, bc, mech, limiter=0)
+    gpu.set_boundary(fs, Tw=500.0)
+    gpu.set_option("dtau_source", 1)
+    Q0 = ref.freestream_state()
+    ref.set_state(Q0)
+    gpu.set_state(Q0)
+    kw = dict(scheme=0, correction=1, clip=1, cfl=20.0, cfl_start=0.5, ramp_iters=10, iters=20)
+    sr = ref.step(**kw)
+    sg = gpu.step(**kw)
+    assert sr["iters_done"] == sg["iters_done"] == 20
+    assert rel(gpu.get_state(), ref.get_state(), ns=ref.ns) < 1e-9
+    for k in ("r_species", "r_energy", "q_stag"):
+        assert abs(sg[k] - sr[k]) <= 1e-8 * abs(sr[k]), k
+
+
 def test_full_size_c2_parity():
     """The 384 x 256 11-species two-temperature cylinder (the benchmark's grid and launch
     configuration): full residual, split increments and CS-1 update against the oracle on a
