@@ -662,7 +662,7 @@ def batch_throughput(P, precision=0, steps=6, warmup=3, ncases=64):
     cells = sum(g.ncell for g in grids)
     batch = P.Batch(grids)
     t0 = time.perf_counter()
-    batch.tune(precision=precision, trials=2)
+    choice = batch.tune(precision=precision, trials=2)
     tune_s = time.perf_counter() - t0
     opts = [dict(scheme=0, correction=1, clip=1, cfl=c["cfl"], cfl_start=0.5, ramp_iters=500,
                  precision=precision) for c in cases]
@@ -678,6 +678,7 @@ def batch_throughput(P, precision=0, steps=6, warmup=3, ncases=64):
     out = {"workload": f"batch-{len(cases)}-half-cylinders-64x48-to-512x384-mach6-20-air5-or-air11-CS1",
            "cases": len(cases), "cells": cells, "iterations": steps, "ms_per_iteration": ms / steps,
            "value": cells * steps / (ms / 1e3) / 1e6, "unit": "Mcell-iter/s", "tune_seconds": tune_s,
+           "sweep_kernels_chosen": {str(kd): sum(1 for kk, _ in choice if kk == kd) for kd in sorted({kk for kk, _ in choice})},
            "cases_failed": sum(1 for st in stats if st["status_cell"] != -1),
            "launch": "one CUDA graph per iteration of all cases (each case's sweeps one cluster launch)"}
     del batch
