@@ -192,8 +192,7 @@ cs_status cs_measure_fp64_rate(void *cuda_stream, double *gflops_out);
 /* Which kernel ran the last split sweep of g (a measurement aid, not part of the method):
  * out[0] in the numbering of the "cluster_sweep" option below (0 one launch per hyperplane,
  * 1 direct loads, 2 wavefront records, 4 one CTA per component, 5 assembled couplings exchanged
- * point to point, 6 assembled couplings with a cluster barrier, 7 assembled couplings swept by
- * systolic warps; -1 before the first sweep),
+ * point to point, 6 assembled couplings with a cluster barrier; -1 before the first sweep),
  * out[1] its CTAs per cluster (0 for one launch per hyperplane).  Host only, no device work.
  * Errors: CS_ERR_ARG (null). */
 cs_status cs_sweep_info(cs_grid g, int out[2]);
@@ -212,14 +211,9 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * shared memory, one mbarrier per hyperplane) and each thread copies its step inputs six steps
  * ahead with cp.async into a ring in shared memory ((ni + nj - 1) x (8 x element size + 8)
  * bytes plus 7 x threads x (2 nP x element size + 16) bytes per CTA, at most 200 KiB; single
- * grids only), 6 the FP64 couplings with one
- * cluster barrier per hyperplane (the FP32 operator falls back to 4, else 2), 7 the same
- * couplings swept by systolic warps: the four rows of a warp exchange results by warp shuffles
- * and each warp waits only for the row before its first (after its last, backward), written
- * into the warp's own inbox by the neighbouring warp or CTA with st.async and one mbarrier per
- * hyperplane, no CTA-wide barrier per step ((ni + nj - 1) x (8 x element size + 8) bytes of
- * shared memory per warp, at most 200 KiB per CTA, else as 5); 0 runs one launch per
- * hyperplane.
+ * grids only), 6 the FP64 couplings with one cluster barrier per hyperplane (the FP32 operator
+ * falls back to 4, else 2); 7 (a retired form that swept the couplings with systolic warps)
+ * runs as 5; 0 runs one launch per hyperplane.
  * All give the same arithmetic up to rounding.  cs_batch_tune reports 4 as kind 3 with C = 1.
  * "cluster_size" = C in {1, 2, 4, 8, 16} fixes the CTAs per component of the 2D cluster
  * sweeps (0, the default: the largest that fits; a C that does not fit the grid or the device

@@ -894,10 +894,10 @@ extern "C" cs_status cs_set_option(cs_grid g, const char* name, double value) {
     // precision), 4 one CTA per component (FP32 operator only; the others fall back to 2),
     // 5 assembled couplings exchanged point to point between CTAs where the ring fits (else
     // FP64: 6 then 1, FP32: 4 then 2), 6 the same FP64 couplings with a cluster barrier per
-    // hyperplane (the FP32 operator falls back to 4 then 2), 7 the assembled couplings swept by
-    // systolic warps where their inboxes fit (else as 5)
+    // hyperplane (the FP32 operator falls back to 4 then 2); 7 (a retired systolic-warp form)
+    // runs as 5
     g->L->use_cluster = value != 0.0;
-    g->L->cluster_kind = value >= 7.0 ? 6 : value >= 6.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
+    g->L->cluster_kind = value >= 6.0 && value < 7.0 ? 5 : value >= 5.0 ? 4 : value >= 4.0 ? 3 : (value >= 3.0 ? 0 : (value >= 2.0 ? 2 : 1));
     return CS_OK;
   }
   if (!strcmp(name, "cluster_size")) {

@@ -3440,187 +3440,6 @@ __global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_p2p(DevGrid 
   cluster_wait();
 }
 
-// Systolic form of the assembled-coupling sweep (both passes in one cluster launch): the four
-// rows of a warp exchange their results with warp shuffles, and each warp waits only for the
-// row before its first row (forward; after its last row backward), which a neighbouring warp of
-// the same CTA, or the neighbouring CTA, writes into the warp's inbox with st.async, one
-// mbarrier per hyperplane step.  No CTA-wide barrier per step: each warp advances as soon as
-// its own inputs are there (the hyperplane order is kept: a row's cell of step q needs the row
-// before it at step q - 1).  Dynamic shared memory: per warp an inbox [H + 1][kMatSlots] of T,
-// then the warps' [H + 1] mbarriers.  Waits are bounded (ST_TIMEOUT).
-template <class T>
-__host__ __device__ inline size_t sys_smem_bytes(int ni, int nj, int warps) {
-  return (size_t)warps * (ni + nj - 1) * (kMatSlots * sizeof(T) + sizeof(unsigned long long));
-}
-constexpr int kSysRows = 32 / kMatSlots;   // rows of one warp
-
-template <class G, class T>
-__global__ void __launch_bounds__(kMatSlots * kClusterRows) k_split_sys(DevGrid g, int R) {
-  using M = MatRec<G, T>;
-  constexpr int NF = M::NF, NP = M::NP, BLK = M::BLK;
-  extern __shared__ __align__(16) unsigned char sys_dyn[];
-  const int ni = g.ni, nj = g.nj, H = ni + nj - 2;
-  const int W = (R + kSysRows - 1) / kSysRows;                 // warps per CTA
-  T* inbox = reinterpret_cast<T*>(sys_dyn);                    // [W][H + 1][kMatSlots]
-  unsigned long long* mbar = reinterpret_cast<unsigned long long*>(inbox + (size_t)W * (H + 1) * kMatSlots);
-  const size_t N = g.N;
-  const int comp = blockIdx.x / (int)cluster_nctarank();      // 0: flow block, else a species group
-  const unsigned rank = cluster_ctarank();
-  const unsigned nrank = cluster_nctarank();
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int tl = lane / kMatSlots, v = lane % kMatSlots;      // row within the warp, slot
-  const int t = warp * kSysRows + tl;                          // row within the CTA
-  const int j = rank * R + t;
-  const bool per = g.bc[0] == BC_PERIODIC;
-  const bool flow = comp == 0;
-  const int s = (comp - 1) * kMatSpecies + v;
-  const bool on = t < R && j < nj && (flow ? v < NF : s < G::NS);
-  const int nsend = flow ? NF : (G::NS - (comp - 1) * kMatSpecies < kMatSpecies ? G::NS - (comp - 1) * kMatSpecies : kMatSpecies);
-  // the warp's first and last rows within the CTA
-  const int tw0 = warp * kSysRows, tw1 = (tw0 + kSysRows - 1 < R - 1) ? tw0 + kSysRows - 1 : R - 1;
-  for (int q = threadIdx.x; q < W * (H + 1); q += blockDim.x)
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + q)) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  __syncthreads();
-  bool timed_out = false;
-  for (int pass = 0; pass < 2; ++pass) {
-    const bool fwd = pass == 0;
-    // each warp arms its inbox for this pass: the row that receives (first row forward, last
-    // row backward) gets its neighbouring row's result of step q - 1 in slot q
-    {
-      const int tc = fwd ? tw0 : tw1;
-      const int jc = (int)rank * R + tc;
-      const bool row_ok = tc < R && jc < nj && (fwd ? jc > 0 : jc + 1 < nj);
-      for (int q = lane; q <= H; q += 32) {
-        const int ic = (fwd ? q : H - q) - jc;
-        const uint32_t bytes = (row_ok && ic >= 0 && ic < ni) ? nsend * (uint32_t)sizeof(T) : 0u;
-        unsigned long long st;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;\n"
-                     : "=l"(st) : "r"(smem_u32(mbar + (size_t)warp * (H + 1) + q)), "r"(bytes) : "memory");
-      }
-    }
-    cluster_arrive();
-    cluster_wait();
-    T xp[NF], xu[NF], xf[NF], pw[NP];   // flow: own and neighbouring row's previous results
-    T sp = 0, su = 0, sf = 0, pc = 0;
-#pragma unroll
-    for (int k = 0; k < NF; ++k) xp[k] = xu[k] = xf[k] = T(0);
-#pragma unroll
-    for (int k = 0; k < NP; ++k) pw[k] = T(0);
-    if (on && per) {
-      const T* pr = reinterpret_cast<const T*>(g.SMC) + N * M::CELL + (size_t)j * M::ROW;
-      if (flow) {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) pw[k] = pr[(fwd ? 0 : BLK) + v * NP + k];
-      } else {
-        pc = pr[2 * BLK + (fwd ? 0 : 1)];
-      }
-    }
-    double* out = fwd ? g.dQs : g.dQ;
-    const size_t orow = (size_t)(flow ? v : NF + s) * N;
-    const bool hasj = fwd ? j > 0 : j < nj - 1;
-    const bool sends = fwd ? j + 1 < nj : j > 0;
-    // receiving row of this warp (its neighbour lives in another warp or CTA) and sending row
-    const bool recv = t == (fwd ? tw0 : tw1);
-    const bool send = t == (fwd ? tw1 : tw0);
-    // where the sending row's results go: the next warp's inbox, or the neighbouring CTA's
-    int dwarp;
-    unsigned dpeer;
-    if (fwd) {
-      dwarp = t == R - 1 ? 0 : warp + 1;
-      dpeer = t == R - 1 ? rank + 1 : rank;
-    } else {
-      dwarp = t == 0 ? W - 1 : warp - 1;
-      dpeer = t == 0 ? rank - 1 : rank;
-    }
-    const bool dvalid = dpeer < nrank;
-    const int nb_lane = (fwd ? tl - 1 : tl + 1) * kMatSlots;     // neighbouring row in the warp
-    const int own_lane = tl * kMatSlots;
-    auto step = [&](int q, MatStep<G, T>& cur) {
-      T acc = 0;
-      if (cur.act) {
-        acc = fwd ? cur.d * cur.base : cur.base;
-        const bool hasi = fwd ? cur.i > 0 : cur.i < ni - 1;
-        const bool wrap = per && cur.i == (fwd ? ni - 1 : 0);
-        if (flow) {
-          if (hasi) {
-#pragma unroll
-            for (int k = 0; k < NF; ++k) acc += cur.bi[k] * xp[k];
-          }
-          if (wrap) {
-#pragma unroll
-            for (int k = 0; k < NF; ++k) acc += pw[k] * xf[k];
-          }
-        } else {
-          if (hasi) acc += (cur.d * cur.bi[0]) * sp;
-          if (wrap) acc += cur.d * pc * sf;
-        }
-        if (hasj) {
-          if (recv) {
-            const uint32_t bar = smem_u32(mbar + (size_t)warp * (H + 1) + q);
-            if (!timed_out && !p2p_wait(bar, (uint32_t)pass)) {   // (one wait bound at most)
-              timed_out = true;
-              set_status(g, ST_TIMEOUT, cur.c);
-            }
-            const T* src = inbox + ((size_t)warp * (H + 1) + q) * kMatSlots;
-            if (flow) {
-#pragma unroll
-              for (int k = 0; k < NF; ++k) acc += cur.bj[k] * src[k];
-            } else {
-              acc += (cur.d * cur.bj[0]) * src[v];
-            }
-          } else {
-            if (flow) {
-#pragma unroll
-              for (int k = 0; k < NF; ++k) acc += cur.bj[k] * xu[k];
-            } else {
-              acc += (cur.d * cur.bj[0]) * su;
-            }
-          }
-        }
-        if (send && sends && dvalid) {
-          const uint32_t dst = cluster_map(smem_u32(inbox + ((size_t)dwarp * (H + 1) + q + 1) * kMatSlots + v), dpeer);
-          st_async(dst, acc, cluster_map(smem_u32(mbar + (size_t)dwarp * (H + 1) + q + 1), dpeer));
-        }
-        out[orow + cur.c] = (double)acc;
-      }
-      // the row's own results and the neighbouring row's, for the next step (every lane takes
-      // part in the shuffles; inactive lanes carry zeros)
-      if (flow) {
-#pragma unroll
-        for (int k = 0; k < NF; ++k) {
-          xp[k] = __shfl_sync(0xffffffffu, acc, own_lane + k);
-          xu[k] = __shfl_sync(0xffffffffu, acc, (nb_lane + k) & 31);
-        }
-      } else {
-        sp = acc;
-        su = __shfl_sync(0xffffffffu, acc, (nb_lane + v) & 31);
-      }
-      if (cur.act && cur.i == (fwd ? 0 : ni - 1)) {
-#pragma unroll
-        for (int k = 0; k < NF; ++k) xf[k] = xp[k];
-        sf = sp;
-      }
-      mat_step_load<G, T>(g, q + 4, j, on, fwd, flow, v, s, cur);
-    };
-    MatStep<G, T> m0, m1, m2, m3;
-    mat_step_load<G, T>(g, 0, j, on, fwd, flow, v, s, m0);
-    mat_step_load<G, T>(g, 1, j, on, fwd, flow, v, s, m1);
-    mat_step_load<G, T>(g, 2, j, on, fwd, flow, v, s, m2);
-    mat_step_load<G, T>(g, 3, j, on, fwd, flow, v, s, m3);
-    for (int q = 0; q <= H; q += 4) {
-      step(q, m0);
-      if (q + 1 <= H) step(q + 1, m1);
-      if (q + 2 <= H) step(q + 2, m2);
-      if (q + 3 <= H) step(q + 3, m3);
-    }
-    __syncthreads();
-  }
-  // no CTA leaves while a neighbour may still write into its shared memory
-  cluster_arrive();
-  cluster_wait();
-}
-
 // ---------------------------------------------------------------------------------------
 // K7: consistency corrections and update (Sec. 2.3.3; CS-1 weight W_s = Y_s, negative
 // densities clipped to 0 and counted).

@@ -45,15 +45,14 @@ struct Launcher {
   int cluster_kind = 0;    // 0: by precision, 1: direct-load cluster kernel, 2: wavefront records,
                            // 3: one CTA per component (FP32), 4: assembled couplings exchanged
                            // point to point where the ring fits (FP64 or FP32), 5: the FP64
-                           // assembled couplings with a cluster barrier, 6: the assembled
-                           // couplings swept by systolic warps where their inboxes fit
+                           // assembled couplings with a cluster barrier
   int force_C = 0;         // CTAs per cluster chosen by the batch tuner (0: largest that fits)
   int cluster_warps = 2;   // warps per CTA of the direct-load cluster kernel (batches: 1)
   bool sweep_split_cluster_ok = false;   // set by the last sweep_split_cluster call
   // kernel of the last split sweep, numbered as the "cluster_sweep" option (0 one launch per
   // hyperplane, 1 direct loads, 2 wavefront records, 4 one CTA per component, 5 assembled
-  // couplings point to point, 6 assembled couplings with a cluster barrier, 7 assembled
-  // couplings by systolic warps; -1 none yet) and its CTAs per cluster
+  // couplings point to point, 6 assembled couplings with a cluster barrier; -1 none yet) and
+  // its CTAs per cluster
   int last_sweep = -1, last_sweep_C = 0;
   // bit C of the result is set when the cluster sweep of `kind` (1 direct, 2 wavefront
   // records) can run with C CTAs per component on this grid and device
@@ -308,10 +307,9 @@ struct LauncherT : Launcher {
     // kernel, in FP64 the assembled couplings with a cluster barrier and the direct-load kernel
     const int kind = cluster_kind ? cluster_kind : 4;
     if (kind >= 4) {
-      // 6: systolic warps, then point to point, then (FP64) the cluster barrier; 4: point to
-      // point, then the barrier; 5: the barrier
-      const int n = mixed ? (kind != 5 ? sweep_mat<float>(g, st, true, kind == 6) : 0)
-                          : sweep_mat<double>(g, st, kind != 5, kind == 6);
+      // 4: point to point, then (FP64) the cluster barrier; 5: the barrier
+      const int n = mixed ? (kind != 5 ? sweep_mat<float>(g, st, true) : 0)
+                          : sweep_mat<double>(g, st, kind != 5);
       if (n) return n;
     }
     const int alt = kind >= 4 ? (mixed ? 3 : 1) : kind;
@@ -366,11 +364,9 @@ struct LauncherT : Launcher {
     if (kind >= 4 && g.SMC) {
       if (mixed) {
         if (kind != 5) mat_cluster_size<float>(g, true);
-        if (kind == 6) mat_cluster_size<float>(g, true, true);
       } else {
         mat_cluster_size<double>(g, false);
         if (kind != 5) mat_cluster_size<double>(g, true);
-        if (kind == 6) mat_cluster_size<double>(g, true, true);
       }
     }
     const int alt = kind >= 4 ? (mixed ? 3 : 1) : kind;
@@ -485,59 +481,51 @@ struct LauncherT : Launcher {
   bool mat_usable(const DevGrid& g, bool mixed) override {
     const int kind = cluster_kind ? cluster_kind : 4;
     if (ND != 2 || !use_cluster || cluster_warps == 1 || kind < 4) return false;
-    if (mixed) return kind != 5 && (mat_cluster_size<float>(g, true) > 0 || (kind == 6 && mat_cluster_size<float>(g, true, true) > 0));
-    return (kind != 5 && mat_cluster_size<double>(g, true) > 0) ||
-           (kind == 6 && mat_cluster_size<double>(g, true, true) > 0) || mat_cluster_size<double>(g, false) > 0;
+    if (mixed) return kind != 5 && mat_cluster_size<float>(g, true) > 0;
+    return (kind != 5 && mat_cluster_size<double>(g, true) > 0) || mat_cluster_size<double>(g, false) > 0;
   }
   template <class T>
-  bool mat_fits(const DevGrid& g, int C, bool p2p, bool sys = false) {
+  bool mat_fits(const DevGrid& g, int C, bool p2p) {
     const int R = (g.nj + C - 1) / C;
     if (R > kClusterRows) return false;
     const int warps = (kMatSlots * R + 31) / 32;
-    if (sys) {
-      const size_t smem = sys_smem_bytes<T>(g.ni, g.nj, warps);
-      return smem <= kP2PMaxSmem && cluster_fits(k_split_sys<G, T>, C, warps, mat_species_groups<G>(), smem, kP2PMaxSmem);
-    }
     if (!p2p) return std::is_same<T, double>::value && cluster_fits(k_split_mat<G>, C, warps, mat_species_groups<G>());
     const size_t smem = p2p_smem_bytes<T, MatRec<G, T>::NP>(g.ni, g.nj, 32 * warps);
     return smem <= kP2PMaxSmem && cluster_fits(k_split_p2p<G, T>, C, warps, mat_species_groups<G>(), smem, kP2PMaxSmem);
   }
   template <class T>
-  int mat_cluster_size(const DevGrid& g, bool p2p, bool sys = false) {
+  int mat_cluster_size(const DevGrid& g, bool p2p) {
     if (ND != 2 || g.bc[2] == BC_PERIODIC) return 0;
-    const int m = sys ? (4 + (std::is_same<T, float>::value ? 1 : 0))
-                      : (p2p ? 1 : 0) + (std::is_same<T, float>::value ? 2 : 0);
+    const int m = (p2p ? 1 : 0) + (std::is_same<T, float>::value ? 2 : 0);
     if (force_C > 0) {
       if (mat_forced_C_[m] != force_C) {
         mat_forced_C_[m] = force_C;
-        mat_forced_ok_[m] = mat_fits<T>(g, force_C, p2p, sys);
+        mat_forced_ok_[m] = mat_fits<T>(g, force_C, p2p);
       }
       return mat_forced_ok_[m] ? force_C : 0;
     }
     if (mat_probed_[m] >= 0) return mat_probed_[m];
     mat_probed_[m] = 0;
     for (int C : {16, 8, 4, 2}) {
-      if (mat_fits<T>(g, C, p2p, sys)) {
+      if (mat_fits<T>(g, C, p2p)) {
         mat_probed_[m] = C;
         break;
       }
     }
     return mat_probed_[m];
   }
-  int mat_probed_[6] = {-1, -1, -1, -1, -1, -1}, mat_forced_C_[6] = {0, 0, 0, 0, 0, 0};
-  bool mat_forced_ok_[6] = {false, false, false, false, false, false};
+  int mat_probed_[4] = {-1, -1, -1, -1}, mat_forced_C_[4] = {0, 0, 0, 0};
+  bool mat_forced_ok_[4] = {false, false, false, false};
   template <class T>
-  int sweep_mat(const DevGrid& g, cudaStream_t st, bool allow_p2p, bool allow_sys = false) {
+  int sweep_mat(const DevGrid& g, cudaStream_t st, bool allow_p2p) {
     sweep_split_cluster_ok = false;
     if constexpr (ND != 2) {
       return 0;
     } else {
       if (cluster_warps == 1 || !g.SMC) return 0;
-      int C = allow_sys ? mat_cluster_size<T>(g, true, true) : 0;
-      const bool sys = C > 0;
-      if (!sys && allow_p2p) C = mat_cluster_size<T>(g, true);
-      const bool p2p = !sys && C > 0;
-      if (!sys && !p2p) C = std::is_same<T, double>::value ? mat_cluster_size<T>(g, false) : 0;
+      int C = allow_p2p ? mat_cluster_size<T>(g, true) : 0;
+      const bool p2p = C > 0;
+      if (!p2p) C = std::is_same<T, double>::value ? mat_cluster_size<T>(g, false) : 0;
       if (C == 0) return 0;
       const int R = (g.nj + C - 1) / C;
       k_sweep_mat<G, T><<<blocks(g.N, 128), 128, 0, st>>>(g);
@@ -545,8 +533,7 @@ struct LauncherT : Launcher {
       cudaLaunchAttribute at[1];
       cfg.gridDim = dim3(C * (1 + mat_species_groups<G>()));
       cfg.blockDim = dim3((kMatSlots * R + 31) / 32 * 32);
-      cfg.dynamicSmemBytes = sys ? sys_smem_bytes<T>(g.ni, g.nj, (kMatSlots * R + 31) / 32)
-                                 : (p2p ? p2p_smem_bytes<T, MatRec<G, T>::NP>(g.ni, g.nj, (kMatSlots * R + 31) / 32 * 32) : 0);
+      cfg.dynamicSmemBytes = p2p ? p2p_smem_bytes<T, MatRec<G, T>::NP>(g.ni, g.nj, (kMatSlots * R + 31) / 32 * 32) : 0;
       cfg.stream = st;
       at[0].id = cudaLaunchAttributeClusterDimension;
       at[0].val.clusterDim.x = C;
@@ -554,15 +541,14 @@ struct LauncherT : Launcher {
       at[0].val.clusterDim.z = 1;
       cfg.attrs = at;
       cfg.numAttrs = 1;
-      const cudaError_t e = sys ? cudaLaunchKernelEx(&cfg, k_split_sys<G, T>, g, R)
-                          : p2p ? cudaLaunchKernelEx(&cfg, k_split_p2p<G, T>, g, R)
+      const cudaError_t e = p2p ? cudaLaunchKernelEx(&cfg, k_split_p2p<G, T>, g, R)
                                 : cudaLaunchKernelEx(&cfg, k_split_mat<G>, g, R);
       if (e != cudaSuccess) {
         cudaGetLastError();
         return 0;
       }
       sweep_split_cluster_ok = true;
-      last_sweep = sys ? 7 : (p2p ? 5 : 6);
+      last_sweep = p2p ? 5 : 6;
       last_sweep_C = C;
       return 2;
     }
