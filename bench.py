@@ -47,9 +47,9 @@ WORKLOAD = "half-cylinder-384x256-air11-2T-mach15-CS1-fp64"
 FP64_FLOPS_PER_CELL = {
     "primitive": 1078.0,       # k_primitive, mean over the 20 timed iterations
     "gradient": 400.0,
-    # both directions (2844) + k_chem (5011), which runs on a second stream beside the gradient
-    # and fluxes; the flux phase ends when both are done
-    "flux": 7855.0,
+    # k_eta (55 per direction) + k_flux (1148 per direction) + k_chem (5011), which runs on a
+    # second stream beside the gradient and fluxes; the flux phase ends when both are done
+    "flux": 7417.0,
     "assemble": 130.0,
     "spectral": 361.0,
     "sweep_fwd": 1128.0,       # couplings (k_sweep_mat, 753) + both sweeps (k_split_p2p, 374)
@@ -60,7 +60,8 @@ FLOPS_SOURCE = ("ncu FP64 thread instructions (2 DFMA + DMUL + DADD) per cell; k
                 "k_chem (the latter counted in the flux phase, beside which it runs on a second "
                 "stream): means over the launches of the timed iterations 6..25 "
                 "(profiles/primitive_chem_fp64_counts_timed_window_384x256_air11.md); other phases: one "
-                "launch of the 5th iteration (profiles/kernels_half_cylinder_384x256_air11.md)")
+                "launch of the 5th iteration (profiles/kernels_half_cylinder_384x256_air11.md; k_flux and k_eta: "
+                "profiles/launches_half_cylinder_384x256_air11_fp64.md)")
 # the mixed operator's sweep phase: couplings formed in FP64 (k_sweep_mat, 753 FP64 flop) and
 # swept in FP32 (k_split_p2p, the FP64 form's 374 flop as FP32)
 FP64_FLOPS_PER_CELL_SWEEP_MIXED = 753.0
