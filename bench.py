@@ -62,10 +62,10 @@ FLOPS_SOURCE = ("ncu FP64 thread instructions (2 DFMA + DMUL + DADD) per cell; k
                 "(profiles/primitive_chem_fp64_counts_timed_window_384x256_air11.md); other phases: one "
                 "launch of the 5th iteration (profiles/kernels_half_cylinder_384x256_air11.md; k_flux and k_eta: "
                 "profiles/launches_half_cylinder_384x256_air11_fp64.md)")
-# the mixed operator's sweep phase: couplings formed in FP64 (k_sweep_mat, 753 FP64 flop) and
-# swept in FP32 (k_split_p2p, the FP64 form's 374 flop as FP32)
-FP64_FLOPS_PER_CELL_SWEEP_MIXED = 753.0
-FP32_FLOPS_PER_CELL_SWEEP = 374.0
+# the mixed operator's sweep phase: couplings formed (k_sweep_mat, 753 flop) and swept
+# (k_split_p2p, 374 flop) in FP32, the FP64 forms' counts
+FP64_FLOPS_PER_CELL_SWEEP_MIXED = 0.0
+FP32_FLOPS_PER_CELL_SWEEP = 1127.0
 # DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 DRAM_BYTES_PER_LAUNCH = {
     "primitive": None,         # the split k_primitive / k_chem kernels: DRAM not captured

@@ -204,8 +204,8 @@ cs_status cs_sweep_info(cs_grid g, int out[2]);
  * hyperplane-ordered cell records, 4 the FP32 operator's sweeps with one CTA per component
  * holding every row (nj <= 384; __syncthreads between hyperplanes; FP64 and larger grids fall
  * back to 2), 5 the sweeps over neighbour couplings assembled beforehand: D^-1 times the split
- * Jacobian blocks, formed in FP64 by one parallel launch into library-owned records (FP64, or
- * FP32 for the FP32 operator) of 4 nF nP + 4 elements per cell and 2 nF nP + 4 per row j, nP =
+ * Jacobian blocks, formed by one parallel launch into library-owned records (FP64, or FP32,
+ * formed in FP32, for the FP32 operator) of 4 nF nP + 4 elements per cell and 2 nF nP + 4 per row j, nP =
  * nF rounded up to a whole 16-byte load; then a cluster kernel with 8 threads per row whose
  * CTAs exchange the rows at their boundaries point to point (st.async into the next CTA's
  * shared memory, one mbarrier per hyperplane) and each thread copies its step inputs six steps

@@ -2860,8 +2860,8 @@ __global__ void __launch_bounds__(32 * W) k_split_cluster(DevGrid g, int R) {
 // cluster barrier, on one or two sub-partitions) the bound of K6b; here each row of a CTA has
 // kMatSlots threads, one per flow component (or species of the CTA's group), and a CTA's rows
 // cover all four sub-partitions.
-// Record of cell c (elements of the operator's type T: FP64, or FP32 for the mixed-precision
-// operator, formed in FP64 and rounded once): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF
+// Record of cell c (elements of the operator's type T, in which they are also formed: FP64, or
+// FP32 for the mixed-precision operator): flow blocks [fwd i][fwd j][bwd i][bwd j], each NF
 // rows of NP (NF rounded up to a whole 16-byte load, so that every row starts on 16 bytes),
 // then the species coefficients in the same order.  Per row j after the N cell records: the
 // periodic-i wrap couplings (forward: cell (ni-1, j) with (0, j); backward: (0, j) with
@@ -2901,20 +2901,23 @@ template <class G, class T>
 __device__ __forceinline__ void mat_block(const DevGrid& g, int nb, const double* S, double lam,
                                           int side, double dF, double dEv, T* out) {
   constexpr int NF = MatRec<G, T>::NF, NP = MatRec<G, T>::NP;
-  CellState<G, 2, double> w;
-  load_state<G, 2, double>(g, nb, w);
-  const double Sf[2] = {S[0], S[1]};
+  // formed in the operator's own type: FP64, or FP32 for the FP32 operator (whose sweep reads
+  // the couplings as FP32 anyway)
+  CellState<G, 2, T> w;
+  load_state<G, 2, T>(g, nb, w);
+  const T Sf[2] = {(T)S[0], (T)S[1]};
+  const T lamT = (T)lam, dFT = (T)dF, dEvT = (T)dEv;
 #pragma unroll
   for (int k = 0; k < NF; ++k) {
-    double e[NF], a[NF];
+    T e[NF], a[NF];
 #pragma unroll
-    for (int q = 0; q < NF; ++q) e[q] = q == k ? 1.0 : 0.0;
-    jvp_flow<G, 2, double>(w, Sf, e, a);
+    for (int q = 0; q < NF; ++q) e[q] = q == k ? T(1) : T(0);
+    jvp_flow<G, 2, T>(w, Sf, e, a);
 #pragma unroll
     for (int v = 0; v < NF; ++v) {
-      const double l = v == k ? lam : 0.0;
-      const double m = side < 0 ? 0.5 * (a[v] + l) : -0.5 * (a[v] - l);
-      out[v * NP + k] = (T)(((G::NTEMP == 2 && v == NF - 1) ? dEv : dF) * m);
+      const T l = v == k ? lamT : T(0);
+      const T m = side < 0 ? T(0.5) * (a[v] + l) : T(-0.5) * (a[v] - l);
+      out[v * NP + k] = ((G::NTEMP == 2 && v == NF - 1) ? dEvT : dFT) * m;
     }
   }
 #pragma unroll
